@@ -1,0 +1,194 @@
+/*
+ * rexi.h -- C ABI of librexi, a GB300 (sm_103a) implementation of one REXII
+ * time step  out = r(dt A) f  ~  e^{dt A} f  for the linear rotating
+ * shallow-water (LRSW) operator A on a doubly periodic staggered (C) grid.
+ *
+ * Method: Caliari, Einkemmer, Moriggl, Ostermann, "An accurate and
+ * time-parallel rational exponential integrator for hyperbolic and oscillatory
+ * PDEs" (arXiv 2008.11607).  r is the REXII rational approximation of
+ * Section 2.1 (eq. modifiedRexi) with the L = 24 conjugate-symmetric
+ * coefficients of Appendix A (Table tab:coef_al); the matrix form is
+ * eq. REXI_Modified_matrix, reduced for real data by
+ * eq. modifiedRexiMatrixReducedSum; the pole count follows
+ * eq. matrixAccuracyBound with the tolerance constant of Appendix B.
+ *
+ * Operator (Section 4, with depth H, gravity g, Coriolis f):
+ *   eta_t = -H(x,y) (u_x + v_y),  u_t = -g eta_x + f v,  v_t = -g eta_y - f u,
+ * second-order centred differences on the C grid: eta_{i,j} at cell centres
+ * ((i+1/2)dx, (j+1/2)dy), u_{i,j} at ((i+1)dx, (j+1/2)dy), v_{i,j} at
+ * ((i+1/2)dx, (j+1)dy); Coriolis by the four-point average (v to u) and its
+ * transpose (u to v).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - State layout: 3 fields (eta, u, v), each ny rows of nx complex128 values
+ *   (interleaved re, im doubles), x fastest:  element (field, j, i) at
+ *   ((field * ny + j) * nx + i).  Device pointers unless stated otherwise;
+ *   they must be 16-byte aligned.
+ * - Memory ownership: the caller owns every buffer passed in.  The library
+ *   never frees caller memory.  A plan owns only small tables (twiddles);
+ *   rexi_plan_create allocates them and rexi_plan_destroy frees them.
+ *   rexi_step allocates nothing: its scratch is the caller's workspace.
+ * - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *   default stream).  Calls are asynchronous on that stream; inputs must stay
+ *   valid and unmodified until the stream reaches the call.
+ * - Errors: every call returns a rexi_status; nothing aborts, traps or waits
+ *   without bound.  Invalid arguments give REXI_EINVAL and launch nothing.
+ * - Precision: coefficients (host) and all accumulation over poles are FP64.
+ */
+#ifndef REXI_H
+#define REXI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rexi_plan_s* rexi_plan_t; /* opaque, library-owned */
+
+typedef enum {
+  REXI_OK = 0,
+  REXI_EINVAL = -1,      /* bad argument, size, alignment or unsupported combination */
+  REXI_ENOMEM = -2,      /* a plan table could not be allocated, or the workspace is too small */
+  REXI_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed */
+  REXI_ENOCONV = -4,     /* Krylov iteration cap reached before the residual target */
+  REXI_ETIMEOUT = -5,    /* a bounded device-side wait gave up */
+  REXI_EUNSUPPORTED = -6 /* the requested form is not available for this plan */
+} rexi_status;
+
+/* Arithmetic form of the pole loop (plan creation). */
+enum {
+  REXI_FORM_FP64 = 0,  /* fused: all solves of a wavenumber in FP64 registers */
+  REXI_FORM_MIXED = 1, /* fused: solves in FP32 pairs (double-float), FP64 endpoints */
+  REXI_FORM_PLAIN = 2  /* paper-style: per-term solve pairs materialised, then a
+                          separate reduction pass (Section 4.1, GPU algorithm) */
+};
+
+/* Per-call diagnostics; filled after an internal stream synchronisation only
+   when the pointer passed to rexi_step is non-NULL. */
+typedef struct {
+  int32_t M;          /* Gaussian-sum half width from the pole-count rule */
+  int32_t N;          /* M + L, L = 24 */
+  int32_t n_terms;    /* REXII terms evaluated: N + 1 (real input) or 2N + 1 */
+  int32_t n_poles;    /* single-shift poles J: 2(N + 1) or 2(2N + 1) */
+  double tau_rho;     /* dt * rho(A) */
+  double rho;         /* spectral radius used */
+  int32_t krylov_iters;        /* Krylov path: largest iteration count over terms */
+  int32_t krylov_unconverged;  /* Krylov path: terms that hit the iteration cap */
+  double krylov_max_rel_res;   /* Krylov path: largest final relative residual */
+} rexi_step_info;
+
+/* ------------------------------------------------------------------------ */
+/* Coefficients (host, FP64).                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Pole count M for a given tau*rho, parameter h and tolerance.
+ * M = ceil(tau_rho / h) + ceil(c(tol) - 1),  c(tol) = 2 sqrt(-ln(sqrt(4 pi) tol))
+ * (eq. matrixAccuracyBound; Appendix B: c ~ 12 and m0 = c - 1 ~ 11 at
+ * tol = 1e-16, so this is the paper's M = ceil(rho/h) + 11 there).
+ * EINVAL unless tau_rho >= 0, 0 < h < pi and 1e-16 <= tol <= 0.1. */
+rexi_status rexi_pole_count(double tau_rho, double h, double tol, int32_t* M_out);
+
+/* REXII term coefficients of eq. modifiedRexi (Section 2.1, Step 3):
+ *   c1_n = h sum_{k=L1(n)}^{L2(n)} Re(a_k) b_{n-k},  c2_n = h sum Im(a_k) b_{n-k},
+ *   b_m = e^{-imh} e^{h^2} (eq. bm), L1 = max(-L, n-M), L2 = min(L, n+M),
+ * for n = -N..N (N = M + 24), written as interleaved (re, im) doubles:
+ * c1_re_im[2*(n+N)], c1_re_im[2*(n+N)+1].  Pass NULL arrays to query the
+ * count (*n_terms = 2N+1); otherwise cap >= 2N+1 is required (EINVAL).
+ * Also returns mu (Table tab:coef_al) so that alpha_n = h(mu + i n). */
+rexi_status rexi_rexii_terms(int32_t M, double h, double* mu_out, int32_t* n_terms,
+                             double* c1_re_im, double* c2_re_im, int32_t cap);
+
+/* Single-shift partial-fraction form of the same rational function:
+ *   r(z) = sum_j beta_j / (z - z_j),  z = dt * (eigenvalue of A),
+ * obtained from each term (C1 - C2 z)/((alpha_{-n} - z)(alpha_n + z)) of
+ * eq. REXI_Modified_matrix (C1 = c1 h mu + c2 h n, C2 = i c2) by partial
+ * fractions.  real_input = 1 gives the reduced set n = 0..N with
+ * Gamma_0 = 1, Gamma_n = 2 folded into beta (the result is then Re of the
+ * sum, eq. modifiedRexiMatrixReducedSum): J = 2(N+1); real_input = 0 gives
+ * n = -N..N: J = 2(2N+1).  Arrays are interleaved (re, im), host memory;
+ * NULL arrays query *n_poles; otherwise cap >= J (EINVAL). */
+rexi_status rexi_coeffs(double tau_rho, double tol, double h, int32_t real_input, int32_t* M_out,
+                        int32_t* n_poles, double* poles_re_im, double* weights_re_im, int32_t cap);
+
+/* ------------------------------------------------------------------------ */
+/* Plans.                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Create a plan for an nx x ny grid on [0, Lx) x [0, Ly).
+ * depth_dev == NULL: constant depth H_const, Fourier (FFT) path.
+ * depth_dev != NULL: variable depth, ny*nx FP64 values at eta points
+ *   (device memory, must stay valid for the plan's lifetime): Krylov path.
+ * form: REXI_FORM_FP64 / REXI_FORM_MIXED / REXI_FORM_PLAIN.
+ * h: REXII parameter (0 < h < pi; the paper's best range is 0.3..0.6).
+ * Sizes: 2 <= nx, ny <= 4096, every prime factor of nx and ny <= 127
+ * (constant-depth path; the variable-depth path accepts 3 <= nx, ny <= 16384).
+ * g > 0, H_const > 0 (and depth values > 0), Lx, Ly > 0.
+ * Allocates device tables (cudaMalloc) on the current device. */
+rexi_status rexi_plan_create(rexi_plan_t* plan, int32_t nx, int32_t ny, double Lx, double Ly,
+                             double g, double f, double H_const, const double* depth_dev,
+                             int32_t form, double h);
+
+void rexi_plan_destroy(rexi_plan_t plan);
+
+/* Spectral radius of A used for the pole count: the exact maximum over the
+ * discrete wavenumbers for constant depth, and the bound
+ * sqrt(g Hmax (4/dx^2 + 4/dy^2)) + |f| for variable depth (Hmax taken from
+ * depth_dev at plan creation). */
+rexi_status rexi_spectral_radius(rexi_plan_t plan, double* rho_out);
+
+/* Krylov path settings (ignored by the FFT path): relative residual target
+ * per term, iteration cap per term, number of terms solved together. */
+rexi_status rexi_plan_set_krylov(rexi_plan_t plan, double rtol, int32_t max_iters, int32_t term_batch);
+
+/* Bytes of device workspace rexi_step needs for this plan, dt and tol. */
+rexi_status rexi_workspace_size(rexi_plan_t plan, double dt, double tol, int32_t real_input,
+                                size_t* bytes);
+
+/* ------------------------------------------------------------------------ */
+/* The time step.                                                           */
+/* ------------------------------------------------------------------------ */
+
+/* out = r(dt A) in, r the REXII approximation with M from the pole-count rule
+ * for dt * rho(A) and tol (eq. modifiedRexiMatrixReducedSum for real input,
+ * eq. REXI_Modified_matrix otherwise).
+ * real_input = 1: the imaginary parts of `in` are ignored and `out` is real
+ *   (imaginary parts written as 0).  real_input = 0: complex state.
+ * term_begin/term_end: evaluate only the REXII terms n with |n| in
+ *   [term_begin, term_end) (0 <= term_begin <= term_end <= N + 1), so that
+ *   several devices can each take a slice of the terms and sum their outputs
+ *   (the step is linear in the terms); pass 0, -1 for all terms.
+ * `in` and `out` may be the same buffer on the FFT path; on the Krylov path
+ * they must not overlap (EINVAL).  workspace_dev: >= rexi_workspace_size
+ * bytes, 256-byte aligned.  info: NULL, or filled after a stream sync. */
+rexi_status rexi_step(rexi_plan_t plan, const void* in_dev, void* out_dev, double dt, double tol,
+                      int32_t real_input, int32_t term_begin, int32_t term_end, void* workspace_dev,
+                      size_t workspace_bytes, void* stream, rexi_step_info* info);
+
+/* Adjoint of rexi_step with respect to the Euclidean inner product of the
+ * state vector (sum of conj(a) b over all 3 nx ny entries):
+ *   grad_in = r(dt A)^H grad_out,
+ * i.e. the gradient of a real loss with respect to the (complex) input state
+ * given its gradient with respect to the output.  Same layouts and rules as
+ * rexi_step. */
+rexi_status rexi_step_adjoint(rexi_plan_t plan, const void* grad_out_dev, void* grad_in_dev,
+                              double dt, double tol, int32_t real_input, void* workspace_dev,
+                              size_t workspace_bytes, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* rexi_status_string(rexi_status status);
+
+/* Library version string (static). */
+const char* rexi_version(void);
+
+/* Text of the last error recorded by a failing call on this host thread
+ * (static per-thread buffer; empty when the last call succeeded). */
+const char* rexi_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REXI_H */

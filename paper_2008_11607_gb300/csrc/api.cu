@@ -1,0 +1,575 @@
+// C ABI of librexi (declared in include/rexi.h): argument checking, plans,
+// workspace layout and the step driver for the Fourier path.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+#include "krylov.h"
+
+using namespace rexi;
+
+namespace {
+
+thread_local char g_err[512];
+
+rexi_status fail(rexi_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+rexi_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(REXI_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(expr, where)                   \
+  do {                                          \
+    cudaError_t _e = (expr);                    \
+    if (_e != cudaSuccess) return cuda_fail(_e, where); \
+  } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct rexi_plan_s {
+  int nx = 0, ny = 0;
+  double Lx = 1, Ly = 1, g = 1, f = 1, H = 1, h = 0.5;
+  const double* depth = nullptr;
+  int form = REXI_FORM_FP64;
+  double rho = 0.0;
+  double Hmax = 0.0, Hmean = 0.0;
+  // Fourier path tables (device)
+  FftPlan1D fx, fy;
+  double2* tw_x = nullptr;
+  double2* tw_y = nullptr;
+  double2* half_x = nullptr;
+  double2* half_y = nullptr;
+  // coefficient staging (pinned host) guarded by an event
+  void* staging = nullptr;
+  size_t staging_bytes = 0;
+  cudaEvent_t staging_done = nullptr;
+  bool staging_pending = false;
+  // Krylov path
+  KrylovSettings kry;
+};
+
+extern "C" {
+
+const char* rexi_status_string(rexi_status s) {
+  switch (s) {
+    case REXI_OK: return "REXI_OK";
+    case REXI_EINVAL: return "REXI_EINVAL";
+    case REXI_ENOMEM: return "REXI_ENOMEM";
+    case REXI_ECUDA: return "REXI_ECUDA";
+    case REXI_ENOCONV: return "REXI_ENOCONV";
+    case REXI_ETIMEOUT: return "REXI_ETIMEOUT";
+    case REXI_EUNSUPPORTED: return "REXI_EUNSUPPORTED";
+  }
+  return "REXI_UNKNOWN";
+}
+
+const char* rexi_version(void) { return "librexi 0.1 (sm_103a)"; }
+
+const char* rexi_last_error_message(void) { return g_err; }
+
+rexi_status rexi_pole_count(double tau_rho, double h, double tol, int32_t* M_out) {
+  g_err[0] = 0;
+  if (!M_out) return fail(REXI_EINVAL, "M_out is NULL");
+  const int M = pole_count(tau_rho, h, tol);
+  if (M < 0) return fail(REXI_EINVAL, "bad tau_rho/h/tol (%g, %g, %g)", tau_rho, h, tol);
+  *M_out = M;
+  return REXI_OK;
+}
+
+rexi_status rexi_rexii_terms(int32_t M, double h, double* mu_out, int32_t* n_terms, double* c1,
+                             double* c2, int32_t cap) {
+  g_err[0] = 0;
+  if (M < 0 || M > 50000000 || !valid_h(h) || !n_terms) return fail(REXI_EINVAL, "bad M/h");
+  const int N = M + kL;
+  *n_terms = 2 * N + 1;
+  if (mu_out) *mu_out = table_mu();
+  if (!c1 && !c2) return REXI_OK;
+  if (!c1 || !c2 || cap < 2 * N + 1) return fail(REXI_EINVAL, "arrays NULL or cap < 2N+1");
+  TermSet ts;
+  rexii_terms(M, h, &ts);
+  for (int i = 0; i < 2 * N + 1; ++i) {
+    c1[2 * i] = ts.c1re[i];
+    c1[2 * i + 1] = ts.c1im[i];
+    c2[2 * i] = ts.c2re[i];
+    c2[2 * i + 1] = ts.c2im[i];
+  }
+  return REXI_OK;
+}
+
+rexi_status rexi_coeffs(double tau_rho, double tol, double h, int32_t real_input, int32_t* M_out,
+                        int32_t* n_poles, double* poles, double* weights, int32_t cap) {
+  g_err[0] = 0;
+  if (!M_out || !n_poles) return fail(REXI_EINVAL, "M_out/n_poles NULL");
+  const int M = pole_count(tau_rho, h, tol);
+  if (M < 0) return fail(REXI_EINVAL, "bad tau_rho/h/tol");
+  const int N = M + kL;
+  const int J = real_input ? 2 * (N + 1) : 2 * (2 * N + 1);
+  *M_out = M;
+  *n_poles = J;
+  if (!poles && !weights) return REXI_OK;
+  if (!poles || !weights || cap < J) return fail(REXI_EINVAL, "arrays NULL or cap < J");
+  TermSet ts;
+  rexii_terms(M, h, &ts);
+  const double hmu = h * ts.mu;
+  int j = 0;
+  for (int n = real_input ? 0 : -N; n <= N; ++n) {
+    const double gam = (real_input && n > 0) ? 2.0 : 1.0;
+    const int i = n + N;
+    // C1 = c1 h mu + c2 h n, C2 = i c2, alpha_{+-n} = h (mu +- i n)
+    const double C1r = ts.c1re[i] * hmu + ts.c2re[i] * h * n;
+    const double C1i = ts.c1im[i] * hmu + ts.c2im[i] * h * n;
+    const double C2r = -ts.c2im[i], C2i = ts.c2re[i];
+    const double apr = hmu, api = h * n;    // alpha_n
+    const double amr = hmu, ami = -h * n;   // alpha_{-n}
+    const double inv2 = 1.0 / (2.0 * hmu);  // 1 / (alpha_n + alpha_{-n})
+    // P = (C1 - C2 alpha_{-n}) / (2 h mu),  Q = (C1 + C2 alpha_n) / (2 h mu)
+    const double Pr = (C1r - (C2r * amr - C2i * ami)) * inv2;
+    const double Pi = (C1i - (C2r * ami + C2i * amr)) * inv2;
+    const double Qr = (C1r + (C2r * apr - C2i * api)) * inv2;
+    const double Qi = (C1i + (C2r * api + C2i * apr)) * inv2;
+    // pole alpha_{-n}, weight -Gamma P;  pole -alpha_n, weight Gamma Q
+    poles[2 * j] = amr;
+    poles[2 * j + 1] = ami;
+    weights[2 * j] = -gam * Pr;
+    weights[2 * j + 1] = -gam * Pi;
+    ++j;
+    poles[2 * j] = -apr;
+    poles[2 * j + 1] = -api;
+    weights[2 * j] = gam * Qr;
+    weights[2 * j + 1] = gam * Qi;
+    ++j;
+  }
+  return REXI_OK;
+}
+
+void rexi_plan_destroy(rexi_plan_t p) {
+  if (!p) return;
+  if (p->staging_done) {
+    cudaEventSynchronize(p->staging_done);
+    cudaEventDestroy(p->staging_done);
+  }
+  cudaFree(p->tw_x);
+  cudaFree(p->tw_y);
+  cudaFree(p->half_x);
+  cudaFree(p->half_y);
+  if (p->staging) cudaFreeHost(p->staging);
+  krylov_destroy(&p->kry);
+  delete p;
+}
+
+static bool upload_table(const std::vector<double2>& host, double2** dev, rexi_status* st) {
+  if (cudaMalloc(dev, host.size() * sizeof(double2)) != cudaSuccess) {
+    *st = fail(REXI_ENOMEM, "cudaMalloc of a plan table failed");
+    return false;
+  }
+  if (cudaMemcpy(*dev, host.data(), host.size() * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess) {
+    *st = fail(REXI_ECUDA, "upload of a plan table failed");
+    return false;
+  }
+  return true;
+}
+
+rexi_status rexi_plan_create(rexi_plan_t* out, int32_t nx, int32_t ny, double Lx, double Ly, double g,
+                             double f, double H, const double* depth, int32_t form, double h) {
+  g_err[0] = 0;
+  if (!out) return fail(REXI_EINVAL, "plan pointer NULL");
+  *out = nullptr;
+  if (!(Lx > 0 && Ly > 0 && g > 0 && isfinite(f) && isfinite(Lx) && isfinite(Ly) && isfinite(g)))
+    return fail(REXI_EINVAL, "bad Lx/Ly/g/f");
+  if (!valid_h(h)) return fail(REXI_EINVAL, "h must lie in (0, pi)");
+  if (form != REXI_FORM_FP64 && form != REXI_FORM_MIXED && form != REXI_FORM_PLAIN)
+    return fail(REXI_EINVAL, "unknown form %d", form);
+  rexi_plan_s* p = new rexi_plan_s();
+  p->nx = nx; p->ny = ny; p->Lx = Lx; p->Ly = Ly; p->g = g; p->f = f; p->H = H; p->h = h;
+  p->depth = depth; p->form = form;
+  rexi_status st = REXI_OK;
+  const double dx = Lx / nx, dy = Ly / ny;
+  if (!depth) {
+    if (!(H > 0 && isfinite(H))) { delete p; return fail(REXI_EINVAL, "H_const must be > 0"); }
+    if (!fft_factor(nx, &p->fx) || !fft_factor(ny, &p->fy)) {
+      delete p;
+      return fail(REXI_EINVAL, "grid %dx%d: need 2..4096 with prime factors <= %d", nx, ny, kMaxRadix);
+    }
+    // twiddles w[t] = exp(-2 pi i t / n) and half angles (cos(pi k/n), sin(pi k/n))
+    auto make = [](int n, std::vector<double2>& tw, std::vector<double2>& half) {
+      tw.resize(n);
+      half.resize(n);
+      for (int t = 0; t < n; ++t) {
+        const double a = 2.0 * M_PI * (double)t / (double)n;
+        tw[t] = make_double2(cos(a), -sin(a));
+        const double b = M_PI * (double)t / (double)n;
+        half[t] = make_double2(cos(b), sin(b));
+      }
+    };
+    std::vector<double2> twx, hx, twy, hy;
+    make(nx, twx, hx);
+    make(ny, twy, hy);
+    if (!upload_table(twx, &p->tw_x, &st) || !upload_table(twy, &p->tw_y, &st) ||
+        !upload_table(hx, &p->half_x, &st) || !upload_table(hy, &p->half_y, &st)) {
+      rexi_plan_destroy(p);
+      return st;
+    }
+    p->fx.tw = p->tw_x;
+    p->fy.tw = p->tw_y;
+    // rho(A): largest omega over the discrete wavenumbers (exact for constant depth)
+    std::vector<double> sx2(nx), cx2(nx);
+    for (int k = 0; k < nx; ++k) { sx2[k] = hx[k].y * hx[k].y; cx2[k] = hx[k].x * hx[k].x; }
+    double best = 0.0;
+    for (int ky = 0; ky < ny; ++ky) {
+      const double sy2 = hy[ky].y * hy[ky].y, cy2 = hy[ky].x * hy[ky].x;
+      const double wy = 4.0 * sy2 / (dy * dy);
+      for (int kx = 0; kx < nx; ++kx) {
+        const double w2 = g * H * (4.0 * sx2[kx] / (dx * dx) + wy) + f * f * cx2[kx] * cy2;
+        best = std::max(best, w2);
+      }
+    }
+    p->rho = sqrt(best);
+    p->Hmax = H;
+    p->Hmean = H;
+  } else {
+    if (nx < 3 || ny < 3 || nx > 16384 || ny > 16384) {
+      delete p;
+      return fail(REXI_EINVAL, "variable-depth grid %dx%d outside 3..16384", nx, ny);
+    }
+    if (form == REXI_FORM_PLAIN) { delete p; return fail(REXI_EUNSUPPORTED, "plain form is Fourier-path only"); }
+    std::vector<double> Hh((size_t)nx * ny);
+    if (cudaMemcpy(Hh.data(), depth, Hh.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      delete p;
+      return fail(REXI_EINVAL, "depth_dev is not readable device memory");
+    }
+    double hmax = 0.0, hsum = 0.0, hmin = 1e300;
+    for (double v : Hh) { hmax = std::max(hmax, v); hmin = std::min(hmin, v); hsum += v; }
+    if (!(hmin > 0.0) || !isfinite(hmax)) { delete p; return fail(REXI_EINVAL, "depth must be > 0 and finite"); }
+    p->Hmax = hmax;
+    p->Hmean = hsum / (double)Hh.size();
+    p->rho = sqrt(g * hmax * (4.0 / (dx * dx) + 4.0 / (dy * dy))) + fabs(f);
+    st = krylov_init(&p->kry, nx, ny, Lx, Ly, g, f, depth, p->Hmean);
+    if (st != REXI_OK) { rexi_plan_destroy(p); return st; }
+  }
+  if (cudaEventCreateWithFlags(&p->staging_done, cudaEventDisableTiming) != cudaSuccess) {
+    rexi_plan_destroy(p);
+    return fail(REXI_ECUDA, "event creation failed");
+  }
+  *out = p;
+  return REXI_OK;
+}
+
+rexi_status rexi_spectral_radius(rexi_plan_t p, double* rho) {
+  g_err[0] = 0;
+  if (!p || !rho) return fail(REXI_EINVAL, "NULL argument");
+  *rho = p->rho;
+  return REXI_OK;
+}
+
+rexi_status rexi_plan_set_krylov(rexi_plan_t p, double rtol, int32_t max_iters, int32_t term_batch) {
+  g_err[0] = 0;
+  if (!p || !(rtol > 0.0 && rtol < 1.0) || max_iters < 1 || term_batch < 1)
+    return fail(REXI_EINVAL, "bad Krylov settings");
+  p->kry.rtol = rtol;
+  p->kry.max_iters = max_iters;
+  p->kry.term_batch = term_batch;
+  return REXI_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Workspace layout (Fourier path), every region 256-byte aligned:
+//   [table][spectrum 3 nx ny double2][plain form: accumulator + chunk of terms]
+namespace {
+
+struct FourierLayout {
+  int M, N, nterms_scalar, nterms_plain;
+  size_t table_off, table_bytes, spec_off, acc_off, chunk_off, chunk_terms, total;
+};
+
+constexpr size_t kPlainChunkBudget = size_t(8) << 30;  // bytes of materialised terms per chunk
+
+FourierLayout fourier_layout(const rexi_plan_s* p, int M, int real_input) {
+  FourierLayout L{};
+  L.M = M;
+  L.N = M + kL;
+  L.nterms_scalar = 2 * L.N + 1;
+  L.nterms_plain = real_input ? L.N + 1 : 2 * L.N + 1;
+  const size_t nk3 = 3 * (size_t)p->nx * p->ny;
+  size_t tb = 0;
+  if (p->form == REXI_FORM_PLAIN) tb = (size_t)L.nterms_plain * 4 * sizeof(double2);
+  else tb = (size_t)L.nterms_scalar * 48;
+  L.table_off = 0;
+  L.table_bytes = tb;
+  L.spec_off = align_up(tb, 256);
+  size_t end = L.spec_off + align_up(nk3 * sizeof(double2), 256);
+  L.acc_off = end;
+  L.chunk_off = end;
+  L.chunk_terms = 0;
+  if (p->form == REXI_FORM_PLAIN) {
+    L.acc_off = end;
+    end += align_up(nk3 * sizeof(double2), 256);
+    L.chunk_off = end;
+    size_t per = nk3 * sizeof(double2);
+    size_t ct = std::max<size_t>(1, kPlainChunkBudget / per);
+    ct = std::min<size_t>(ct, (size_t)L.nterms_plain);
+    ct = std::min<size_t>(ct, 65535);
+    L.chunk_terms = ct;
+    end += align_up(ct * per, 256);
+  }
+  L.total = end;
+  return L;
+}
+
+rexi_status check_step_args(rexi_plan_s* p, const void* in, void* out, double dt, double tol,
+                            void* ws, int* M) {
+  if (!p) return fail(REXI_EINVAL, "plan NULL");
+  if (!in || !out || !ws) return fail(REXI_EINVAL, "NULL buffer");
+  if (((uintptr_t)in | (uintptr_t)out) & 15) return fail(REXI_EINVAL, "state buffers must be 16-byte aligned");
+  if ((uintptr_t)ws & 255) return fail(REXI_EINVAL, "workspace must be 256-byte aligned");
+  if (!(dt >= 0.0) || !isfinite(dt)) return fail(REXI_EINVAL, "dt must be finite and >= 0");
+  *M = pole_count(dt * p->rho, p->h, tol);
+  if (*M < 0) return fail(REXI_EINVAL, "pole count rule rejected dt*rho=%g h=%g tol=%g", dt * p->rho, p->h, tol);
+  return REXI_OK;
+}
+
+rexi_status stage_upload(rexi_plan_s* p, const void* src, size_t bytes, void* dst, cudaStream_t s) {
+  if (p->staging_pending) {
+    CUDA_TRY(cudaEventSynchronize(p->staging_done), "staging wait");
+    p->staging_pending = false;
+  }
+  if (bytes > p->staging_bytes) {
+    if (p->staging) cudaFreeHost(p->staging);
+    p->staging = nullptr;
+    p->staging_bytes = 0;
+    size_t nb = std::max<size_t>(bytes, 1 << 16);
+    if (cudaHostAlloc(&p->staging, nb, cudaHostAllocDefault) != cudaSuccess)
+      return fail(REXI_ENOMEM, "pinned staging allocation failed");
+    p->staging_bytes = nb;
+  }
+  memcpy(p->staging, src, bytes);
+  CUDA_TRY(cudaMemcpyAsync(dst, p->staging, bytes, cudaMemcpyHostToDevice, s), "table upload");
+  CUDA_TRY(cudaEventRecord(p->staging_done, s), "staging event");
+  p->staging_pending = true;
+  return REXI_OK;
+}
+
+SymbolParams symbol_params(const rexi_plan_s* p) {
+  SymbolParams sp;
+  sp.nx = p->nx;
+  sp.ny = p->ny;
+  sp.inv_dx = p->nx / p->Lx;
+  sp.inv_dy = p->ny / p->Ly;
+  sp.g = p->g;
+  sp.f = p->f;
+  sp.H = p->H;
+  sp.half_x = p->half_x;
+  sp.half_y = p->half_y;
+  return sp;
+}
+
+bool term_selected(int n, int tb, int te) {
+  const int a = n < 0 ? -n : n;
+  return a >= tb && a < te;
+}
+
+rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, int M, int real_input,
+                         int tb, int te, void* ws, size_t ws_bytes, cudaStream_t s, bool adjoint) {
+  const FourierLayout L = fourier_layout(p, M, real_input);
+  if (ws_bytes < L.total) return fail(REXI_ENOMEM, "workspace %zu < %zu bytes", ws_bytes, L.total);
+  char* base = static_cast<char*>(ws);
+  double2* spec = reinterpret_cast<double2*>(base + L.spec_off);
+  const int N = L.N;
+  if (te < 0 || te > N + 1) te = N + 1;
+  if (tb < 0 || tb > te) return fail(REXI_EINVAL, "bad term range [%d, %d)", tb, te);
+  TermSet ts;
+  rexii_terms(M, p->h, &ts);
+  const double h = p->h, hmu = h * ts.mu, q = hmu * hmu;
+  const double tau = dt;
+  const SymbolParams sp = symbol_params(p);
+  const size_t nk = (size_t)p->nx * p->ny;
+  rexi_status st;
+
+  // forward transform (imaginary parts dropped for real input)
+  CUDA_TRY(fft2d(static_cast<const double2*>(in), spec, 3, p->fx, p->fy, -1, 1.0, real_input, 0, s),
+           "forward FFT");
+
+  if (p->form == REXI_FORM_FP64 || p->form == REXI_FORM_MIXED) {
+    // scalar terms n = -N..N restricted to |n| in [tb, te)
+    std::vector<int> sel;
+    for (int n = -N; n <= N; ++n)
+      if (term_selected(n, tb, te)) sel.push_back(n);
+    double R0r = 0.0, R0i = 0.0;
+    for (int n : sel) {
+      const int i = n + N;
+      const double hn = h * n, d = q + hn * hn;
+      R0r += (ts.c1re[i] * hmu + ts.c2re[i] * hn) / d;
+      R0i += (ts.c1im[i] * hmu + ts.c2im[i] * hn) / d;
+    }
+    FusedScalars fs;
+    fs.tau = tau;
+    fs.q = q;
+    fs.R0re = R0r;
+    fs.R0im = R0i;
+    fs.nterms = (int)sel.size();
+    fs.adjoint = adjoint ? 1 : 0;
+    if (p->form == REXI_FORM_FP64) {
+      std::vector<double> tab(6 * std::max<size_t>(sel.size(), 1), 0.0);
+      for (size_t t = 0; t < sel.size(); ++t) {
+        const int n = sel[t], i = n + N;
+        double* e = &tab[6 * t];
+        e[0] = h * n;
+        e[1] = ts.c1re[i] * hmu;
+        e[2] = ts.c1im[i] * hmu;
+        e[3] = ts.c2re[i];
+        e[4] = ts.c2im[i];
+        e[5] = 0.0;
+      }
+      if ((st = stage_upload(p, tab.data(), tab.size() * sizeof(double), base + L.table_off, s)) != REXI_OK) return st;
+      CUDA_TRY(pole_fused_fp64(spec, sp, reinterpret_cast<const double*>(base + L.table_off), fs, s),
+                 "pole_fused_fp64");
+    } else {
+      // grid G = 2^-g so that |x| + h N < 2^24 G: x <= tau rho
+      const double span = dt * p->rho + h * N + 4.0;
+      if (span > 4.0e6) return fail(REXI_EINVAL, "mixed form needs dt*rho + h*N < 4e6 (got %g)", span);
+      int gexp = 0;
+      while (ldexp(1.0, 23 - gexp) > span && gexp < 60) ++gexp;  // largest g with span < 2^(23-g)
+      const double G = ldexp(1.0, -(gexp - 1));
+      std::vector<float> tab(12 * std::max<size_t>(sel.size(), 1), 0.0f);
+      auto split = [](double v, float& hi, float& lo) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+      };
+      for (size_t t = 0; t < sel.size(); ++t) {
+        const int n = sel[t], i = n + N;
+        float* e = &tab[12 * t];
+        const double hn = h * n;
+        const double hn_g = rint(hn / G) * G;
+        float Arh, Arl, Aih, Ail, Brh, Brl, Bih, Bil;
+        split(ts.c1re[i] * hmu, Arh, Arl);
+        split(ts.c1im[i] * hmu, Aih, Ail);
+        split(ts.c2re[i], Brh, Brl);
+        split(ts.c2im[i], Bih, Bil);
+        e[0] = (float)hn_g; e[1] = Arh; e[2] = Aih; e[3] = Brh;
+        e[4] = Bih; e[5] = Arl; e[6] = Ail; e[7] = Brl;
+        e[8] = Bil; e[9] = (float)(hn - hn_g); e[10] = 0.f; e[11] = 0.f;
+      }
+      if ((st = stage_upload(p, tab.data(), tab.size() * sizeof(float), base + L.table_off, s)) != REXI_OK) return st;
+      CUDA_TRY(pole_fused_mixed(spec, sp, reinterpret_cast<const float*>(base + L.table_off), fs, G, s),
+               "pole_fused_mixed");
+    }
+  } else {
+    // plain form: terms n = 0..N (real) or -N..N (complex), |n| in [tb, te)
+    std::vector<double2> tab;
+    for (int n = real_input ? 0 : -N; n <= N; ++n) {
+      if (!term_selected(n, tb, te)) continue;
+      const int i = n + N;
+      const double gam = (real_input && n > 0) ? 2.0 : 1.0;
+      const double C1r = ts.c1re[i] * hmu + ts.c2re[i] * h * n;
+      const double C1i = ts.c1im[i] * hmu + ts.c2im[i] * h * n;
+      const double C2r = -ts.c2im[i], C2i = ts.c2re[i];
+      const double amr = hmu, ami = -h * n;
+      // K = C1 - C2 alpha_{-n}
+      const double Kr = C1r - (C2r * amr - C2i * ami);
+      const double Ki = C1i - (C2r * ami + C2i * amr);
+      tab.push_back(make_double2(hmu, h * n));
+      tab.push_back(make_double2(amr, ami));
+      tab.push_back(make_double2(gam * C2r, gam * C2i));
+      tab.push_back(make_double2(gam * Kr, gam * Ki));
+    }
+    const int nt = (int)(tab.size() / 4);
+    double2* acc = reinterpret_cast<double2*>(base + L.acc_off);
+    double2* chunk = reinterpret_cast<double2*>(base + L.chunk_off);
+    if (nt == 0) {
+      CUDA_TRY(cudaMemsetAsync(acc, 0, 3 * nk * sizeof(double2), s), "zero accumulator");
+    } else {
+      if ((st = stage_upload(p, tab.data(), tab.size() * sizeof(double2), base + L.table_off, s)) != REXI_OK) return st;
+      const double2* dtab = reinterpret_cast<const double2*>(base + L.table_off);
+      for (int t0 = 0; t0 < nt; t0 += (int)L.chunk_terms) {
+        PlainScalars ps;
+        ps.tau = tau;
+        ps.nterms = std::min<int>((int)L.chunk_terms, nt - t0);
+        ps.adjoint = adjoint ? 1 : 0;
+        CUDA_TRY(pole_plain_terms(spec, chunk, sp, dtab + 4 * t0, ps, s), "pole_plain_terms");
+        CUDA_TRY(pole_plain_reduce(chunk, acc, (long long)(3 * nk), ps.nterms, t0 == 0 ? 1 : 0, s),
+                 "pole_plain_reduce");
+      }
+    }
+    spec = acc;
+  }
+  // inverse transform, 1/(nx ny), real part for real input
+  CUDA_TRY(fft2d(spec, static_cast<double2*>(out), 3, p->fx, p->fy, +1, 1.0 / (double)nk, 0, real_input, s),
+           "inverse FFT");
+  return REXI_OK;
+}
+
+void fill_info(const rexi_plan_s* p, int M, int real_input, double dt, rexi_step_info* info) {
+  if (!info) return;
+  memset(info, 0, sizeof(*info));
+  info->M = M;
+  info->N = M + kL;
+  info->n_terms = real_input ? info->N + 1 : 2 * info->N + 1;
+  info->n_poles = real_input ? 2 * (info->N + 1) : 2 * (2 * info->N + 1);
+  info->tau_rho = dt * p->rho;
+  info->rho = p->rho;
+}
+
+}  // namespace
+
+extern "C" {
+
+rexi_status rexi_workspace_size(rexi_plan_t p, double dt, double tol, int32_t real_input, size_t* bytes) {
+  g_err[0] = 0;
+  if (!p || !bytes) return fail(REXI_EINVAL, "NULL argument");
+  if (!(dt >= 0.0) || !isfinite(dt)) return fail(REXI_EINVAL, "dt must be finite and >= 0");
+  const int M = pole_count(dt * p->rho, p->h, tol);
+  if (M < 0) return fail(REXI_EINVAL, "pole count rule rejected the arguments");
+  if (p->depth) {
+    *bytes = krylov_workspace_bytes(&p->kry, M, real_input, p->form);
+  } else {
+    *bytes = fourier_layout(p, M, real_input).total;
+  }
+  return REXI_OK;
+}
+
+rexi_status rexi_step(rexi_plan_t p, const void* in, void* out, double dt, double tol, int32_t real_input,
+                      int32_t term_begin, int32_t term_end, void* ws, size_t ws_bytes, void* stream,
+                      rexi_step_info* info) {
+  g_err[0] = 0;
+  int M = 0;
+  rexi_status st = check_step_args(p, in, out, dt, tol, ws, &M);
+  if (st != REXI_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->depth) {
+    st = krylov_step(&p->kry, p->form, p->h, M, in, out, dt, real_input, term_begin, term_end, ws, ws_bytes,
+                     s, info, false);
+    if (info) { info->M = M; info->N = M + kL; info->tau_rho = dt * p->rho; info->rho = p->rho; }
+    return st;
+  }
+  st = fourier_step(p, in, out, dt, M, real_input, term_begin, term_end, ws, ws_bytes, s, false);
+  if (st == REXI_OK) fill_info(p, M, real_input, dt, info);
+  return st;
+}
+
+rexi_status rexi_step_adjoint(rexi_plan_t p, const void* gout, void* gin, double dt, double tol,
+                              int32_t real_input, void* ws, size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  int M = 0;
+  rexi_status st = check_step_args(p, gout, gin, dt, tol, ws, &M);
+  if (st != REXI_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->depth)
+    return krylov_step(&p->kry, p->form, p->h, M, gout, gin, dt, real_input, 0, -1, ws, ws_bytes, s, nullptr,
+                       true);
+  return fourier_step(p, gout, gin, dt, M, real_input, 0, -1, ws, ws_bytes, s, true);
+}
+
+}  // extern "C"

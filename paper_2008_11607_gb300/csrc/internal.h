@@ -1,0 +1,72 @@
+// Internal declarations shared by the librexi translation units.
+// Nothing here is part of the public ABI (see include/rexi.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "rexi.h"
+
+namespace rexi {
+
+constexpr int kL = 24;             // conjugate pairs of the rational Gaussian fit (Appendix A)
+constexpr int kMaxStages = 40;     // FFT stages (radix >= 2, n <= 8192)
+constexpr int kMaxRadix = 127;     // largest prime factor accepted for FFT lengths
+
+// ---- host coefficient generation (coeffs.cpp) ----------------------------
+struct TermSet {
+  int M = 0, N = 0;
+  double h = 0.0, mu = 0.0;
+  std::vector<double> c1re, c1im, c2re, c2im;  // n = -N..N at index n + N
+};
+int pole_count(double tau_rho, double h, double tol);  // -1 on bad arguments
+bool valid_h(double h);
+bool valid_tol(double tol);
+double table_mu();
+void table_a(double re[kL + 1], double im[kL + 1]);
+void rexii_terms(int M, double h, TermSet* ts);
+
+// ---- FFT (fft.cu) ---------------------------------------------------------
+struct FftPlan1D {
+  int n = 0;
+  int nstages = 0;
+  int radix[kMaxStages] = {0};
+  const double2* tw = nullptr;  // device table w[t] = exp(-2 pi i t / n), t < n
+};
+bool fft_factor(int n, FftPlan1D* p);  // fills n, nstages, radix; false if unsupported
+// Forward (sign -1) or inverse (sign +1, scaled by `scale`) 2-D transform of
+// `nfields` fields of ny x nx complex128, from `in` to `out` (may alias).
+// zero_imag_in: treat the input as real; real_out: write Re, imaginary 0.
+cudaError_t fft2d(const double2* in, double2* out, int nfields, const FftPlan1D& px,
+                  const FftPlan1D& py, int sign, double scale, int zero_imag_in, int real_out,
+                  cudaStream_t s);
+
+// ---- Fourier-path pole kernels (pole_fft.cu) ------------------------------
+struct SymbolParams {
+  int nx, ny;
+  double inv_dx, inv_dy, g, f, H;
+  const double2* half_x;  // (cos(pi k/nx), sin(pi k/nx)), k < nx
+  const double2* half_y;
+};
+struct FusedScalars {
+  double tau, q, R0re, R0im;  // q = (h mu)^2, R0 = r(0) over the selected terms
+  int nterms;                 // scalar terms in the table
+  int adjoint;                // apply r(tau B)^H instead of r(tau B)
+};
+cudaError_t pole_fused_fp64(double2* spec, const SymbolParams& sp, const double* table,
+                            const FusedScalars& fs, cudaStream_t s);
+cudaError_t pole_fused_mixed(double2* spec, const SymbolParams& sp, const float* table,
+                             const FusedScalars& fs, double grid, cudaStream_t s);
+struct PlainScalars {
+  double tau;
+  int nterms;   // terms in this chunk
+  int adjoint;
+};
+cudaError_t pole_plain_terms(const double2* spec, double2* chunk, const SymbolParams& sp,
+                             const double2* table, const PlainScalars& ps, cudaStream_t s);
+cudaError_t pole_plain_reduce(const double2* chunk, double2* acc, long long nk3, int nterms,
+                              int first, cudaStream_t s);
+
+}  // namespace rexi

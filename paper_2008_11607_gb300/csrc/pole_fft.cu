@@ -1,0 +1,392 @@
+// Fourier-path pole kernels: every REXII term for every wavenumber.
+//
+// For constant depth each Fourier mode k evolves under the 3x3 symbol B(k)
+// of the C-grid operator, whose eigenvalues are 0 and +-i omega(k) (its
+// characteristic polynomial is z^3 + omega^2 z).  A shifted solve
+// (alpha I + tau B)^{-1} therefore reduces to scalar work on those
+// eigenvalues, and the sum over all REXII terms of eq. modifiedRexi,
+//   R+ = REXII(i x) = sum_n (c1_n h mu + c2_n (x + h n)) / ((h mu)^2 + (x + h n)^2),
+// x = tau omega(k), is accumulated in registers for one wavenumber pair
+// (k, -k) per thread (omega(-k) = omega(k)).  The conjugate symmetry of the
+// coefficients (remark before eq. modifiedRexiMatrixReducedSum) gives
+// REXII(-ix) = conj(R+), and with Bt = B / omega
+//   r(tau B) = R0 I + Im(R+) Bt + (R0 - Re R+) Bt^2,   R0 = REXII(0),
+// which is exact on all three eigenvalues (Bt^3 = -Bt).  No per-term field is
+// materialised.
+//
+// Forms:
+//  * pole_fused_fp64  -- FP64 registers; 1/d by the rcp.approx seed plus one
+//    Newton-Raphson step in FP64 (relative error ~2^-44 per term).
+//  * pole_fused_mixed -- the same sum in double-float arithmetic (pairs of
+//    FP32 values with Dekker/Knuth error-free transformations: TwoSum,
+//    TwoProduct by FMA), FP64 only for the per-wavenumber setup and the
+//    final combine.  FP32 runs ~58x faster than FP64 on this GPU.
+//  * pole_plain_terms / pole_plain_reduce -- the paper's GPU structure
+//    (Section 4.1): per REXII term n the two shifted 3x3 solves
+//    g1 = (alpha_n I + tau B)^{-1} f, g2 = (alpha_{-n} I - tau B)^{-1} g1,
+//    g3 = Gamma_n (C2 g1 + (C1 - C2 alpha_{-n}) g2) written to HBM for a chunk
+//    of terms, then a separate reduction pass over the chunk.
+#include "internal.h"
+
+namespace rexi {
+
+// ---------------------------------------------------------------------------
+// Symbol of the C-grid operator at wavenumber k (half-angle form, no
+// cancellation for small k).  With c = cos(theta/2), s = sin(theta/2):
+//   forward difference  (e^{i theta} - 1)/dx  = (2 s / dx)(-s + i c)
+//   backward difference (1 - e^{-i theta})/dx = (2 s / dx)( s + i c)
+//   P = (1 + e^{i theta_x})(1 + e^{-i theta_y}) / 4 = cx cy (cx + i sx)(cy - i sy)
+//   omega^2 = g H (4 sx^2/dx^2 + 4 sy^2/dy^2) + f^2 cx^2 cy^2
+struct Symbol {
+  double2 dxf, dyf, dxb, dyb, P;
+  double omega;
+};
+
+__device__ __forceinline__ Symbol symbol_at(const SymbolParams& sp, int kx, int ky) {
+  const double2 hx = sp.half_x[kx];
+  const double2 hy = sp.half_y[ky];
+  const double cx = hx.x, sx = hx.y, cy = hy.x, sy = hy.y;
+  Symbol S;
+  const double ax = 2.0 * sx * sp.inv_dx, ay = 2.0 * sy * sp.inv_dy;
+  S.dxf = make_double2(-ax * sx, ax * cx);
+  S.dxb = make_double2(ax * sx, ax * cx);
+  S.dyf = make_double2(-ay * sy, ay * cy);
+  S.dyb = make_double2(ay * sy, ay * cy);
+  const double cc = cx * cy;
+  S.P = make_double2(cc * (cx * cy + sx * sy), cc * (sx * cy - cx * sy));
+  const double w2 = sp.g * sp.H * (ax * ax + ay * ay) + sp.f * sp.f * cc * cc;
+  S.omega = sqrt(w2);
+  return S;
+}
+
+__device__ __forceinline__ double2 cm(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 ca(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cs(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cr(double a, double2 b) { return make_double2(a * b.x, a * b.y); }
+
+// y = B f (conj_sym: use conj(B), the symbol at -k; adjoint: use B^H).
+__device__ __forceinline__ void apply_B(const Symbol& S, const SymbolParams& sp, bool conj_sym,
+                                        bool adjoint, const double2 f[3], double2 y[3]) {
+  double2 dxf = S.dxf, dyf = S.dyf, dxb = S.dxb, dyb = S.dyb, P = S.P;
+  if (conj_sym) {
+    dxf = cj(dxf); dyf = cj(dyf); dxb = cj(dxb); dyb = cj(dyb); P = cj(P);
+  }
+  if (!adjoint) {
+    // [[0, -H dxb, -H dyb], [-g dxf, 0, f P], [-g dyf, -f conj(P), 0]]
+    y[0] = cr(-sp.H, ca(cm(dxb, f[1]), cm(dyb, f[2])));
+    y[1] = cs(cr(sp.f, cm(P, f[2])), cr(sp.g, cm(dxf, f[0])));
+    y[2] = cs(cr(-sp.g, cm(dyf, f[0])), cr(sp.f, cm(cj(P), f[1])));
+  } else {
+    // B^H = [[0, -g conj(dxf), -g conj(dyf)], [-H conj(dxb), 0, -f P], [-H conj(dyb), f conj(P), 0]]
+    y[0] = cr(-sp.g, ca(cm(cj(dxf), f[1]), cm(cj(dyf), f[2])));
+    y[1] = cs(cr(-sp.H, cm(cj(dxb), f[0])), cr(sp.f, cm(P, f[2])));
+    y[2] = ca(cr(-sp.H, cm(cj(dyb), f[0])), cr(sp.f, cm(cj(P), f[1])));
+  }
+}
+
+// out = R0 f + Im(R+) Bt f + (R0 - Re R+) Bt^2 f, Bt = B / omega, in place on
+// the three fields of wavenumber index `idx` (field stride fs).
+__device__ __forceinline__ void combine(double2* spec, size_t idx, size_t fs, const Symbol& S,
+                                        const SymbolParams& sp, bool conj_sym, bool adjoint,
+                                        double2 R0, double2 Rp) {
+  double2 f[3], y1[3], y2[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) f[c] = spec[idx + c * fs];
+  double2 c0 = adjoint ? cj(R0) : R0;
+  double2 out[3];
+  if (S.omega > 0.0) {
+    const double inv = 1.0 / S.omega;
+    apply_B(S, sp, conj_sym, adjoint, f, y1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y1[c] = cr(inv, y1[c]);
+    apply_B(S, sp, conj_sym, adjoint, y1, y2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y2[c] = cr(inv, y2[c]);
+    const double a1 = Rp.y;
+    double2 a2 = make_double2(R0.x - Rp.x, R0.y);
+    if (adjoint) a2 = cj(a2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c] = ca(ca(cm(c0, f[c]), cr(a1, y1[c])), cm(a2, y2[c]));
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c] = cm(c0, f[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) spec[idx + c * fs] = out[c];
+}
+
+// Map thread -> wavenumber pair.  Pairs (k, -k) with ky in [0, ny/2]; in the
+// self-conjugate rows (ky = 0, and ky = ny/2 for even ny) only kx <= nx/2.
+__device__ __forceinline__ bool pair_of(int p, int nx, int ny, int& kx, int& ky, int& kx2, int& ky2) {
+  ky = p / nx;
+  kx = p - ky * nx;
+  if (ky > ny / 2) return false;
+  const bool selfrow = (ky == 0) || (2 * ky == ny);
+  if (selfrow && kx > nx / 2) return false;
+  kx2 = kx == 0 ? 0 : nx - kx;
+  ky2 = ky == 0 ? 0 : ny - ky;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 fused pole loop.
+// Table (per scalar term, 6 doubles): h n, A_re, A_im, B_re, B_im, 0 with
+// A = c1_n h mu, B = c2_n.
+
+__device__ __forceinline__ double rcp_seed(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  return r;
+}
+
+constexpr int kChunk = 256;  // terms staged in shared memory at a time
+
+__global__ void __launch_bounds__(128) pole_fused_fp64_kernel(double2* spec, SymbolParams sp,
+                                                              const double* __restrict__ table,
+                                                              FusedScalars fs, int npairs) {
+  __shared__ double2 st[kChunk * 3];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  int kx = 0, ky = 0, kx2 = 0, ky2 = 0;
+  const bool active = p < npairs && pair_of(p, sp.nx, sp.ny, kx, ky, kx2, ky2);
+  Symbol S = symbol_at(sp, active ? kx : 0, active ? ky : 0);
+  const double x = fs.tau * S.omega;
+  double accr = 0.0, acci = 0.0;
+  const double q = fs.q;
+  const double2* tb = reinterpret_cast<const double2*>(table);
+  for (int t0 = 0; t0 < fs.nterms; t0 += kChunk) {
+    const int cnt = min(kChunk, fs.nterms - t0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt * 3; i += blockDim.x) st[i] = tb[(size_t)t0 * 3 + i];
+    __syncthreads();
+#pragma unroll 4
+    for (int t = 0; t < cnt; ++t) {
+      const double2 e0 = st[3 * t], e1 = st[3 * t + 1], e2 = st[3 * t + 2];
+      // e0 = (h n, A_re), e1 = (A_im, B_re), e2 = (B_im, 0)
+      const double y = x + e0.x;
+      const double d = fma(y, y, q);
+      const double r0 = rcp_seed(d);
+      const double r = fma(r0, fma(-d, r0, 1.0), r0);  // one Newton-Raphson step
+      accr = fma(fma(e1.y, y, e0.y), r, accr);
+      acci = fma(fma(e2.x, y, e1.x), r, acci);
+    }
+  }
+  if (!active) return;
+  const double2 R0 = make_double2(fs.R0re, fs.R0im);
+  const double2 Rp = make_double2(accr, acci);
+  const size_t fstride = (size_t)sp.nx * sp.ny;
+  const bool adj = fs.adjoint != 0;
+  combine(spec, (size_t)ky * sp.nx + kx, fstride, S, sp, false, adj, R0, Rp);
+  if (kx2 != kx || ky2 != ky)
+    combine(spec, (size_t)ky2 * sp.nx + kx2, fstride, S, sp, true, adj, R0, Rp);
+}
+
+static int pairs_count(int nx, int ny) { return nx * (ny / 2 + 1); }
+
+cudaError_t pole_fused_fp64(double2* spec, const SymbolParams& sp, const double* table,
+                            const FusedScalars& fs, cudaStream_t s) {
+  const int np = pairs_count(sp.nx, sp.ny);
+  const int tpb = 128;
+  pole_fused_fp64_kernel<<<(np + tpb - 1) / tpb, tpb, 0, s>>>(spec, sp, table, fs, np);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Double-float fused pole loop.
+// A value v is carried as an unevaluated sum hi + lo of two FP32 numbers.
+// Error-free transformations (Knuth TwoSum, Dekker TwoProduct via FMA); the
+// _rn intrinsics keep the compiler from contracting or reassociating them.
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {  // |a| >= |b| or a == 0
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ float rcp_approx_f32(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Table (per scalar term, 12 floats):
+//  [hn_hi, Ar_hi, Ai_hi, Br_hi], [Bi_hi, Ar_lo, Ai_lo, Br_lo], [Bi_lo, hn_lo, 0, 0]
+// hn_hi is h n rounded to the grid G = fs-supplied power of two, so that
+// X_hi + hn_hi is exact in FP32 (both multiples of G, magnitude < 2^24 G).
+__global__ void __launch_bounds__(128) pole_fused_mixed_kernel(double2* spec, SymbolParams sp,
+                                                               const float4* __restrict__ table,
+                                                               FusedScalars fs, double grid,
+                                                               float q_hi, float q_lo, int npairs) {
+  __shared__ float4 st[kChunk * 3];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  int kx = 0, ky = 0, kx2 = 0, ky2 = 0;
+  const bool active = p < npairs && pair_of(p, sp.nx, sp.ny, kx, ky, kx2, ky2);
+  Symbol S = symbol_at(sp, active ? kx : 0, active ? ky : 0);
+  const double x = fs.tau * S.omega;
+  const double xg = rint(x / grid) * grid;
+  const float X_hi = (float)xg;
+  const float X_lo = (float)(x - xg);
+  float ar_h = 0.f, ar_l = 0.f, ai_h = 0.f, ai_l = 0.f;
+  for (int t0 = 0; t0 < fs.nterms; t0 += kChunk) {
+    const int cnt = min(kChunk, fs.nterms - t0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt * 3; i += blockDim.x) st[i] = table[(size_t)t0 * 3 + i];
+    __syncthreads();
+#pragma unroll 2
+    for (int t = 0; t < cnt; ++t) {
+      const float4 e0 = st[3 * t], e1 = st[3 * t + 1], e2 = st[3 * t + 2];
+      // y = x + h n: exact high part, then renormalise
+      float y_h, y_l;
+      fast_two_sum(__fadd_rn(X_hi, e0.x), __fadd_rn(X_lo, e2.y), y_h, y_l);
+      // d = q + y^2
+      const float p_h = __fmul_rn(y_h, y_h);
+      const float p_l = __fmaf_rn(y_h, y_h, -p_h);
+      float d_h, d_e;
+      two_sum(q_hi, p_h, d_h, d_e);
+      const float d_l = __fadd_rn(__fadd_rn(d_e, p_l), __fmaf_rn(2.0f * y_h, y_l, q_lo));
+      // r = 1/d: FP32 seed, one Newton-Raphson correction carried in the low part
+      const float r0 = rcp_approx_f32(d_h);
+      float tcorr = __fmaf_rn(-d_h, r0, 1.0f);
+      tcorr = __fmaf_rn(-d_l, r0, tcorr);
+      const float r_l = __fmul_rn(r0, tcorr);
+      // N = A + B y (real and imaginary parts), then T = N r, acc += T
+      {
+        const float t_h = __fmul_rn(e0.w, y_h);
+        const float t_l = __fmaf_rn(e0.w, y_h, -t_h);
+        const float cross = __fmaf_rn(e0.w, y_l, __fmul_rn(e1.w, y_h));
+        float n_h, n_e;
+        two_sum(e0.y, t_h, n_h, n_e);
+        const float n_l = __fadd_rn(__fadd_rn(n_e, t_l), __fadd_rn(cross, e1.y));
+        const float T_h = __fmul_rn(n_h, r0);
+        const float T_l = __fadd_rn(__fmaf_rn(n_h, r0, -T_h), __fmaf_rn(n_h, r_l, __fmul_rn(n_l, r0)));
+        float s, e;
+        two_sum(ar_h, T_h, s, e);
+        ar_h = s;
+        ar_l = __fadd_rn(ar_l, __fadd_rn(e, T_l));
+      }
+      {
+        const float t_h = __fmul_rn(e1.x, y_h);
+        const float t_l = __fmaf_rn(e1.x, y_h, -t_h);
+        const float cross = __fmaf_rn(e1.x, y_l, __fmul_rn(e2.x, y_h));
+        float n_h, n_e;
+        two_sum(e0.z, t_h, n_h, n_e);
+        const float n_l = __fadd_rn(__fadd_rn(n_e, t_l), __fadd_rn(cross, e1.z));
+        const float T_h = __fmul_rn(n_h, r0);
+        const float T_l = __fadd_rn(__fmaf_rn(n_h, r0, -T_h), __fmaf_rn(n_h, r_l, __fmul_rn(n_l, r0)));
+        float s, e;
+        two_sum(ai_h, T_h, s, e);
+        ai_h = s;
+        ai_l = __fadd_rn(ai_l, __fadd_rn(e, T_l));
+      }
+    }
+  }
+  if (!active) return;
+  const double2 R0 = make_double2(fs.R0re, fs.R0im);
+  const double2 Rp = make_double2((double)ar_h + (double)ar_l, (double)ai_h + (double)ai_l);
+  const size_t fstride = (size_t)sp.nx * sp.ny;
+  const bool adj = fs.adjoint != 0;
+  combine(spec, (size_t)ky * sp.nx + kx, fstride, S, sp, false, adj, R0, Rp);
+  if (kx2 != kx || ky2 != ky)
+    combine(spec, (size_t)ky2 * sp.nx + kx2, fstride, S, sp, true, adj, R0, Rp);
+}
+
+cudaError_t pole_fused_mixed(double2* spec, const SymbolParams& sp, const float* table,
+                             const FusedScalars& fs, double grid, cudaStream_t s) {
+  const int np = pairs_count(sp.nx, sp.ny);
+  const int tpb = 128;
+  const float q_hi = (float)fs.q;
+  const float q_lo = (float)(fs.q - (double)q_hi);
+  pole_fused_mixed_kernel<<<(np + tpb - 1) / tpb, tpb, 0, s>>>(
+      spec, sp, reinterpret_cast<const float4*>(table), fs, grid, q_hi, q_lo, np);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Plain form (paper-style): materialise g3 per (term, k), then reduce.
+// Table per term (4 double2): alpha_n, alpha_{-n}, Gamma C2, Gamma (C1 - C2 alpha_{-n}).
+// (alpha I + s tau B)^{-1} v = v/alpha - s tau B v / D + tau^2 B^2 v / (alpha D),
+// D = alpha^2 + tau^2 omega^2, s = +1 or -1, because B^3 = -omega^2 B.
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double den = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+
+__device__ __forceinline__ void shifted_solve(const Symbol& S, const SymbolParams& sp, bool adjoint,
+                                              double2 alpha, double sgn, double tau, const double2 v[3],
+                                              double2 out[3]) {
+  double2 b1[3], b2[3];
+  apply_B(S, sp, false, adjoint, v, b1);
+  apply_B(S, sp, false, adjoint, b1, b2);
+  const double tw2 = tau * tau * S.omega * S.omega;
+  const double2 D = make_double2(alpha.x * alpha.x - alpha.y * alpha.y + tw2, 2.0 * alpha.x * alpha.y);
+  const double2 one = make_double2(1.0, 0.0);
+  const double2 ia = cdiv(one, alpha);
+  const double2 iD = cdiv(one, D);
+  const double2 k1 = cr(-sgn * tau, iD);
+  const double2 k2 = cr(tau * tau, cm(ia, iD));
+#pragma unroll
+  for (int c = 0; c < 3; ++c) out[c] = ca(ca(cm(ia, v[c]), cm(k1, b1[c])), cm(k2, b2[c]));
+}
+
+__global__ void __launch_bounds__(256) pole_plain_terms_kernel(const double2* __restrict__ spec,
+                                                               double2* __restrict__ chunk,
+                                                               SymbolParams sp,
+                                                               const double2* __restrict__ table,
+                                                               PlainScalars ps) {
+  const size_t nk = (size_t)sp.nx * sp.ny;
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y;
+  if (k >= nk || t >= ps.nterms) return;
+  const int ky = (int)(k / sp.nx), kx = (int)(k - (size_t)ky * sp.nx);
+  Symbol S = symbol_at(sp, kx, ky);
+  const bool adj = ps.adjoint != 0;
+  double2 alpha_n = table[4 * t], alpha_mn = table[4 * t + 1];
+  double2 gC2 = table[4 * t + 2], gK = table[4 * t + 3];
+  if (adj) {  // (r(tau B))^H: conjugated shifts and coefficients with B^H
+    alpha_n = cj(alpha_n); alpha_mn = cj(alpha_mn); gC2 = cj(gC2); gK = cj(gK);
+  }
+  double2 f[3], g1[3], g2[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) f[c] = spec[k + c * nk];
+  shifted_solve(S, sp, adj, alpha_n, +1.0, ps.tau, f, g1);
+  shifted_solve(S, sp, adj, alpha_mn, -1.0, ps.tau, g1, g2);
+  double2* out = chunk + (size_t)t * 3 * nk;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) out[k + c * nk] = ca(cm(gC2, g1[c]), cm(gK, g2[c]));
+}
+
+__global__ void __launch_bounds__(256) pole_plain_reduce_kernel(const double2* __restrict__ chunk,
+                                                                double2* __restrict__ acc,
+                                                                long long nk3, int nterms, int first) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nk3) return;
+  double2 s = first ? make_double2(0.0, 0.0) : acc[i];
+  for (int t = 0; t < nterms; ++t) {
+    const double2 v = chunk[(size_t)t * nk3 + i];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  acc[i] = s;
+}
+
+cudaError_t pole_plain_terms(const double2* spec, double2* chunk, const SymbolParams& sp,
+                             const double2* table, const PlainScalars& ps, cudaStream_t s) {
+  const size_t nk = (size_t)sp.nx * sp.ny;
+  dim3 grid((unsigned)((nk + 255) / 256), ps.nterms);
+  pole_plain_terms_kernel<<<grid, 256, 0, s>>>(spec, chunk, sp, table, ps);
+  return cudaGetLastError();
+}
+
+cudaError_t pole_plain_reduce(const double2* chunk, double2* acc, long long nk3, int nterms, int first,
+                              cudaStream_t s) {
+  pole_plain_reduce_kernel<<<(unsigned)((nk3 + 255) / 256), 256, 0, s>>>(chunk, acc, nk3, nterms, first);
+  return cudaGetLastError();
+}
+
+}  // namespace rexi

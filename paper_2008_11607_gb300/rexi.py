@@ -1,0 +1,225 @@
+"""Thin ctypes binding of librexi (include/rexi.h), same entry-point names.
+
+Only argument marshalling happens here: every step of the computation runs in
+the CUDA library.  PyTorch supplies device memory (the state, the output and
+the workspace) and the CUDA stream.  If the library is missing, ``load()``
+raises; there is no fallback.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librexi.so")
+
+REXI_OK = 0
+REXI_EINVAL = -1
+REXI_ENOMEM = -2
+REXI_ECUDA = -3
+REXI_ENOCONV = -4
+REXI_ETIMEOUT = -5
+REXI_EUNSUPPORTED = -6
+
+REXI_FORM_FP64 = 0
+REXI_FORM_MIXED = 1
+REXI_FORM_PLAIN = 2
+FORMS = {"fp64": REXI_FORM_FP64, "mixed": REXI_FORM_MIXED, "plain": REXI_FORM_PLAIN}
+
+
+class rexi_step_info(ctypes.Structure):
+    _fields_ = [
+        ("M", ctypes.c_int32),
+        ("N", ctypes.c_int32),
+        ("n_terms", ctypes.c_int32),
+        ("n_poles", ctypes.c_int32),
+        ("tau_rho", ctypes.c_double),
+        ("rho", ctypes.c_double),
+        ("krylov_iters", ctypes.c_int32),
+        ("krylov_unconverged", ctypes.c_int32),
+        ("krylov_max_rel_res", ctypes.c_double),
+    ]
+
+
+_c_int = ctypes.c_int32
+_c_dbl = ctypes.c_double
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+
+SIGNATURES = {
+    "rexi_pole_count": (_c_int, [_c_dbl, _c_dbl, _c_dbl, _ip]),
+    "rexi_rexii_terms": (_c_int, [_c_int, _c_dbl, _dp, _ip, _dp, _dp, _c_int]),
+    "rexi_coeffs": (_c_int, [_c_dbl, _c_dbl, _c_dbl, _c_int, _ip, _ip, _dp, _dp, _c_int]),
+    "rexi_plan_create": (_c_int, [ctypes.POINTER(_vp), _c_int, _c_int, _c_dbl, _c_dbl, _c_dbl, _c_dbl,
+                                  _c_dbl, _vp, _c_int, _c_dbl]),
+    "rexi_plan_destroy": (None, [_vp]),
+    "rexi_spectral_radius": (_c_int, [_vp, _dp]),
+    "rexi_plan_set_krylov": (_c_int, [_vp, _c_dbl, _c_int, _c_int]),
+    "rexi_workspace_size": (_c_int, [_vp, _c_dbl, _c_dbl, _c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "rexi_step": (_c_int, [_vp, _vp, _vp, _c_dbl, _c_dbl, _c_int, _c_int, _c_int, _vp, ctypes.c_size_t, _vp,
+                           ctypes.POINTER(rexi_step_info)]),
+    "rexi_step_adjoint": (_c_int, [_vp, _vp, _vp, _c_dbl, _c_dbl, _c_int, _vp, ctypes.c_size_t, _vp]),
+    "rexi_status_string": (ctypes.c_char_p, [_c_int]),
+    "rexi_version": (ctypes.c_char_p, []),
+    "rexi_last_error_message": (ctypes.c_char_p, []),
+}
+
+_LIB = None
+
+
+def load(path=LIB_PATH):
+    """Load librexi.so and declare the C signatures.  Raises if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError("librexi.so not found at %s: build it with __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+class RexiError(RuntimeError):
+    def __init__(self, status, where):
+        lib = load()
+        msg = lib.rexi_last_error_message().decode()
+        super().__init__("%s: %s (%s)" % (where, lib.rexi_status_string(status).decode(), msg))
+        self.status = status
+
+
+def _check(status, where):
+    if status != REXI_OK:
+        raise RexiError(status, where)
+
+
+# ---- host coefficient entry points -----------------------------------------
+
+def rexi_pole_count(tau_rho, h=0.5, tol=1e-10):
+    M = ctypes.c_int32()
+    _check(load().rexi_pole_count(tau_rho, h, tol, ctypes.byref(M)), "rexi_pole_count")
+    return M.value
+
+
+def rexi_rexii_terms(M, h=0.5):
+    """Returns (mu, c1, c2) with c1, c2 complex lists for n = -N..N."""
+    import numpy as np
+
+    lib = load()
+    mu = ctypes.c_double()
+    nt = ctypes.c_int32()
+    _check(lib.rexi_rexii_terms(M, h, ctypes.byref(mu), ctypes.byref(nt), None, None, 0), "rexi_rexii_terms")
+    c1 = np.zeros(2 * nt.value)
+    c2 = np.zeros(2 * nt.value)
+    _check(lib.rexi_rexii_terms(M, h, ctypes.byref(mu), ctypes.byref(nt),
+                                c1.ctypes.data_as(_dp), c2.ctypes.data_as(_dp), nt.value), "rexi_rexii_terms")
+    return mu.value, c1[0::2] + 1j * c1[1::2], c2[0::2] + 1j * c2[1::2]
+
+
+def rexi_coeffs(tau_rho, tol=1e-10, h=0.5, real_input=True):
+    """Returns (M, poles, weights) of the single-shift partial-fraction form."""
+    import numpy as np
+
+    lib = load()
+    M = ctypes.c_int32()
+    J = ctypes.c_int32()
+    _check(lib.rexi_coeffs(tau_rho, tol, h, int(real_input), ctypes.byref(M), ctypes.byref(J), None, None, 0),
+           "rexi_coeffs")
+    p = np.zeros(2 * J.value)
+    w = np.zeros(2 * J.value)
+    _check(lib.rexi_coeffs(tau_rho, tol, h, int(real_input), ctypes.byref(M), ctypes.byref(J),
+                           p.ctypes.data_as(_dp), w.ctypes.data_as(_dp), J.value), "rexi_coeffs")
+    return M.value, p[0::2] + 1j * p[1::2], w[0::2] + 1j * w[1::2]
+
+
+# ---- plans and the step -----------------------------------------------------
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """Owns one rexi_plan_t.  ``depth`` (torch float64 CUDA tensor, (ny, nx))
+    selects the variable-depth path; it must stay alive as long as the plan."""
+
+    def __init__(self, nx, ny, Lx=1.0, Ly=1.0, g=1.0, f=1.0, H=1.0, depth=None, form="fp64", h=0.5):
+        lib = load()
+        self._lib = lib
+        self.nx, self.ny, self.h = int(nx), int(ny), float(h)
+        self.form = form
+        self._depth = depth
+        handle = ctypes.c_void_p()
+        dptr = _ptr(depth) if depth is not None else None
+        _check(lib.rexi_plan_create(ctypes.byref(handle), self.nx, self.ny, Lx, Ly, g, f, H, dptr,
+                                    FORMS[form] if isinstance(form, str) else int(form), self.h),
+               "rexi_plan_create")
+        self._h = handle
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.rexi_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def rho(self):
+        r = ctypes.c_double()
+        _check(self._lib.rexi_spectral_radius(self._h, ctypes.byref(r)), "rexi_spectral_radius")
+        return r.value
+
+    def set_krylov(self, rtol=1e-10, max_iters=20000, term_batch=64):
+        _check(self._lib.rexi_plan_set_krylov(self._h, rtol, max_iters, term_batch), "rexi_plan_set_krylov")
+
+    def workspace_size(self, dt, tol=1e-10, real_input=True):
+        b = ctypes.c_size_t()
+        _check(self._lib.rexi_workspace_size(self._h, dt, tol, int(real_input), ctypes.byref(b)),
+               "rexi_workspace_size")
+        return b.value
+
+    def workspace(self, dt, tol=1e-10, real_input=True, device=None):
+        import torch
+
+        n = self.workspace_size(dt, tol, real_input)
+        return torch.empty(max(n, 256), dtype=torch.uint8, device=device or "cuda")
+
+    def step(self, state, dt, tol=1e-10, real_input=True, out=None, workspace=None, stream=None,
+             terms=(0, -1), want_info=False):
+        """out = r(dt A) state; ``state`` complex128 CUDA tensor (3, ny, nx)."""
+        import torch
+
+        if out is None:
+            out = torch.empty_like(state)
+        if workspace is None:
+            workspace = self.workspace(dt, tol, real_input, device=state.device)
+        info = rexi_step_info() if want_info else None
+        st = self._lib.rexi_step(self._h, _ptr(state), _ptr(out), dt, tol, int(real_input), int(terms[0]),
+                                 int(terms[1]), _ptr(workspace), workspace.numel(), _stream_handle(stream),
+                                 ctypes.byref(info) if info is not None else None)
+        _check(st, "rexi_step")
+        return (out, info) if want_info else out
+
+    def step_adjoint(self, grad_out, dt, tol=1e-10, real_input=True, out=None, workspace=None, stream=None):
+        import torch
+
+        if out is None:
+            out = torch.empty_like(grad_out)
+        if workspace is None:
+            workspace = self.workspace(dt, tol, real_input, device=grad_out.device)
+        st = self._lib.rexi_step_adjoint(self._h, _ptr(grad_out), _ptr(out), dt, tol, int(real_input),
+                                         _ptr(workspace), workspace.numel(), _stream_handle(stream))
+        _check(st, "rexi_step_adjoint")
+        return out

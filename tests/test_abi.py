@@ -1,0 +1,107 @@
+"""The C-ABI library builds, loads without a GPU and exports every entry point
+declared in include/*.h; host-only coefficient entry points agree with the
+oracle (no device compute is called here)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import coeffs as C
+from paper_2008_11607_gb300 import build as B
+from paper_2008_11607_gb300 import rexi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return rexi.load()
+
+
+def declared_functions():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(rexi_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("rexi_coeffs", "rexi_step", "rexi_step_adjoint", "rexi_plan_create", "rexi_workspace_size"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_header():
+    assert set(declared_functions()) <= set(rexi.SIGNATURES)
+
+
+def test_status_strings(lib):
+    assert lib.rexi_status_string(0) == b"REXI_OK"
+    assert lib.rexi_status_string(-1) == b"REXI_EINVAL"
+    assert b"sm_103a" in lib.rexi_version()
+
+
+@pytest.mark.parametrize("tr,h,tol", [(50.0, 0.5, 1e-10), (1000.0, 0.5, 1e-10), (568.69, 1.0, 1e-16),
+                                      (0.0, 0.5, 1e-10), (400.0, 0.3, 1e-12)])
+def test_pole_count_matches_oracle(lib, tr, h, tol):
+    assert rexi.rexi_pole_count(tr, h, tol) == C.pole_count_M(tr, h, tol)
+
+
+def test_pole_count_rejects_bad_arguments(lib):
+    M = ctypes.c_int32()
+    assert lib.rexi_pole_count(10.0, 0.5, 1e-17, ctypes.byref(M)) == rexi.REXI_EINVAL
+    assert lib.rexi_pole_count(10.0, 3.2, 1e-10, ctypes.byref(M)) == rexi.REXI_EINVAL
+    assert lib.rexi_pole_count(-1.0, 0.5, 1e-10, ctypes.byref(M)) == rexi.REXI_EINVAL
+    assert lib.rexi_pole_count(10.0, 0.5, 1e-10, None) == rexi.REXI_EINVAL
+
+
+@pytest.mark.parametrize("M,h", [(0, 0.5), (30, 0.5), (109, 0.5), (60, 0.3)])
+def test_rexii_terms_match_oracle(lib, M, h):
+    mu, c1, c2 = rexi.rexi_rexii_terms(M, h)
+    ns, o1, o2 = C.c_coeffs(h, M)
+    omu, _ = C.table_a()
+    assert mu == omu
+    scale = max(np.abs(o1).max(), np.abs(o2).max())
+    assert np.max(np.abs(c1 - o1)) < 1e-14 * scale
+    assert np.max(np.abs(c2 - o2)) < 1e-14 * scale
+
+
+@pytest.mark.parametrize("real_input", [True, False])
+def test_single_shift_coeffs_match_oracle(lib, real_input):
+    M, p, w = rexi.rexi_coeffs(50.0, 1e-10, 0.5, real_input)
+    op, ow = C.single_shift_poles(0.5, M, real_input)
+    assert M == 109 and len(p) == len(op)
+    assert np.max(np.abs(p - op)) < 1e-14 * np.abs(op).max()
+    assert np.max(np.abs(w - ow)) < 1e-12 * np.abs(ow).max()
+
+
+def test_coeffs_query_and_cap(lib):
+    M = ctypes.c_int32()
+    J = ctypes.c_int32()
+    assert lib.rexi_coeffs(1000.0, 1e-10, 0.5, 1, ctypes.byref(M), ctypes.byref(J), None, None, 0) == 0
+    assert (M.value, J.value) == (2009, 4068)
+    buf = (ctypes.c_double * 8)()
+    assert lib.rexi_coeffs(1000.0, 1e-10, 0.5, 1, ctypes.byref(M), ctypes.byref(J), buf, buf, 4) == rexi.REXI_EINVAL
+
+
+def test_plan_rejects_bad_grids_without_gpu(lib):
+    h = ctypes.c_void_p()
+    # argument checks happen before any device call
+    assert lib.rexi_plan_create(ctypes.byref(h), 64, 64, 1.0, 1.0, 1.0, 1.0, 1.0, None, 7, 0.5) == rexi.REXI_EINVAL
+    assert lib.rexi_plan_create(ctypes.byref(h), 64, 64, 1.0, 1.0, 1.0, 1.0, 1.0, None, 0, 4.0) == rexi.REXI_EINVAL
+    assert lib.rexi_plan_create(ctypes.byref(h), 64, 64, -1.0, 1.0, 1.0, 1.0, 1.0, None, 0, 0.5) == rexi.REXI_EINVAL
+    assert lib.rexi_plan_create(ctypes.byref(h), 64, 64, 1.0, 1.0, 1.0, 1.0, -2.0, None, 0, 0.5) == rexi.REXI_EINVAL
+    assert lib.rexi_plan_create(ctypes.byref(h), 2 * 131, 64, 1.0, 1.0, 1.0, 1.0, 1.0, None, 0, 0.5) == rexi.REXI_EINVAL
+    assert lib.rexi_plan_create(ctypes.byref(h), 8192, 64, 1.0, 1.0, 1.0, 1.0, 1.0, None, 0, 0.5) == rexi.REXI_EINVAL

@@ -1,0 +1,204 @@
+"""Parity of the constant-depth (Fourier) path against the FP64 oracle.
+
+Each case runs the CUDA library through the C ABI (ctypes binding) and the
+oracle's sparse-LU solve chain on the same seeded input.  Tolerances (relative
+l2 over the concatenated fields): 1e-10 for the FP64 forms, 1e-8 for the
+mixed (double-float) form.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import coeffs as C
+from oracle import exact as E
+from oracle import operator as O
+from oracle import rexi as R
+from paper_2008_11607_gb300 import inputs
+from tests.gpu_util import TOL, oracle_step, rel_l2, to_dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+FORMS = ["fp64", "mixed", "plain"]
+
+
+def run(torch, state, dt, form, real_input=True, tol=1e-10, terms=(0, -1), **phys):
+    from paper_2008_11607_gb300 import rexi
+
+    _, ny, nx = state.shape
+    plan = rexi.Plan(nx, ny, form=form, **phys)
+    x = to_dev(torch, state)
+    out, info = plan.step(x, dt, tol=tol, real_input=real_input, terms=terms, want_info=True)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), info, plan
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("case", ["16x16_real", "24x20_complex", "17x9_real", "12x10_phys"])
+def test_small_grids_against_sparse_oracle(form, case):
+    torch = torch_cuda()
+    phys = {}
+    if case == "16x16_real":
+        nx, ny, real, st = 16, 16, True, inputs.kminus3_field(16, 16, seed=0)
+    elif case == "24x20_complex":
+        nx, ny, real, st = 24, 20, False, inputs.complex_random_state(24, 20, seed=1)
+    elif case == "17x9_real":
+        nx, ny, real, st = 17, 9, True, inputs.gaussian_bump(17, 9, width=0.15)
+    else:
+        nx, ny, real, st = 12, 10, False, inputs.complex_random_state(12, 10, seed=2)
+        phys = dict(Lx=1.3, Ly=0.7, g=2.0, f=0.6, H=0.8)
+    from paper_2008_11607_gb300 import rexi
+
+    rho = rexi.Plan(nx, ny, form=form, **phys).rho
+    dt = 30.0 / rho
+    out, info, _ = run(torch, st, dt, form, real_input=real, **phys)
+    assert info.M == C.pole_count_M(30.0, 0.5, 1e-10)
+    ref = oracle_step(st, dt, info.M, real_input=real, **phys)
+    err = rel_l2(out, ref)
+    assert err < TOL[form], err
+    if real:
+        assert np.all(out.imag == 0)
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_config1_gaussian_64(form):
+    """64x64, H = g = f = 1, Gaussian bump, tau rho = 50, tol 1e-10 (M = 109):
+    against the full sparse oracle and the closed-form exponential."""
+    torch = torch_cuda()
+    st = inputs.gaussian_bump(64, 64)
+    rho = 2 * math.sqrt(2) * 64
+    dt = 50.0 / rho
+    out, info, plan = run(torch, st, dt, form)
+    assert abs(plan.rho - rho) < 1e-9 and info.M == 109 and info.n_poles == 268
+    ref = oracle_step(st, dt, 109)
+    assert rel_l2(out, ref) < TOL[form]
+    ex = E.exp_closed_form(st, dt).real
+    assert rel_l2(out, ex) < 1e-9
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_adjoint_dot_product(form):
+    """<y, R x> = <R^H y, x> for the complex-input step."""
+    torch = torch_cuda()
+    from paper_2008_11607_gb300 import rexi
+
+    nx, ny = 20, 18
+    x = inputs.complex_random_state(nx, ny, seed=3)
+    y = inputs.complex_random_state(nx, ny, seed=4)
+    plan = rexi.Plan(nx, ny, form=form, f=0.7)
+    dt = 25.0 / plan.rho
+    Rx = plan.step(to_dev(torch, x), dt, real_input=False).cpu().numpy()
+    RHy = plan.step_adjoint(to_dev(torch, y), dt, real_input=False).cpu().numpy()
+    lhs = np.vdot(y, Rx)
+    rhs = np.vdot(RHy, x)
+    assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+    # and against the oracle's adjoint (conjugate transpose via the sparse chain on A^T)
+    A = O.cgrid_operator(nx, ny, f=0.7)
+    M = C.pole_count_M(25.0, 0.5, 1e-10)
+    ref = np.conj(R.rexii_apply_sparse(A.T.tocsr(), np.conj(y).ravel(), dt, 0.5, M, real_input=False))
+    assert rel_l2(RHy.ravel(), ref) < TOL[form]
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_term_slices_sum_to_full(form):
+    torch = torch_cuda()
+    st = inputs.kminus3_field(32, 32, seed=5)
+    from paper_2008_11607_gb300 import rexi
+
+    plan = rexi.Plan(32, 32, form=form)
+    dt = 40.0 / plan.rho
+    x = to_dev(torch, st)
+    full, info = plan.step(x, dt, want_info=True)
+    N = info.N
+    cuts = [0, 3, N // 2, N + 1]
+    parts = sum(plan.step(x, dt, terms=(a, b)) for a, b in zip(cuts[:-1], cuts[1:]))
+    assert rel_l2(parts.cpu().numpy(), full.cpu().numpy()) < 1e-12
+    ref = oracle_step(st, dt, info.M, terms=set(range(3, N // 2)))
+    mid = plan.step(x, dt, terms=(3, N // 2)).cpu().numpy()
+    assert rel_l2(mid, ref) < TOL[form]
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_edge_cases(form):
+    torch = torch_cuda()
+    from paper_2008_11607_gb300 import rexi
+
+    # dt = 0: r(0) = 1 to the scalar accuracy
+    st = inputs.complex_random_state(8, 8, seed=6)
+    plan = rexi.Plan(8, 8, form=form)
+    out = plan.step(to_dev(torch, st), 0.0, real_input=False).cpu().numpy()
+    assert rel_l2(out, st) < 1e-10
+    # f = 0: omega(0) = 0 at k = 0 (B = 0 there)
+    st = inputs.kminus3_field(10, 6, seed=7)
+    st[0] += 0.25
+    plan = rexi.Plan(10, 6, f=0.0, form=form)
+    dt = 12.0 / plan.rho
+    out = plan.step(to_dev(torch, st), dt).cpu().numpy()
+    ref = oracle_step(st, dt, C.pole_count_M(12.0, 0.5, 1e-10), f=0.0)
+    assert rel_l2(out, ref) < TOL[form]
+    # smallest grids
+    for nx, ny in ((2, 2), (3, 2), (2, 5)):
+        st = inputs.complex_random_state(nx, ny, seed=nx * 10 + ny)
+        plan = rexi.Plan(nx, ny, form=form)
+        dt = 5.0 / plan.rho
+        out = plan.step(to_dev(torch, st), dt, real_input=False).cpu().numpy()
+        ref = oracle_step(st, dt, C.pole_count_M(5.0, 0.5, 1e-10), real_input=False)
+        assert rel_l2(out, ref) < TOL[form], (nx, ny)
+
+
+def test_in_place_and_errors():
+    torch = torch_cuda()
+    from paper_2008_11607_gb300 import rexi
+
+    st = inputs.kminus3_field(16, 16, seed=8)
+    plan = rexi.Plan(16, 16)
+    dt = 10.0 / plan.rho
+    x = to_dev(torch, st)
+    ref = plan.step(x, dt).clone()
+    y = x.clone()
+    plan.step(y, dt, out=y)  # in place
+    assert torch.equal(y, ref)
+    ws = plan.workspace(dt)
+    with pytest.raises(rexi.RexiError) as e:
+        plan.step(x, dt, workspace=ws[: ws.numel() // 2])
+    assert e.value.status == rexi.REXI_ENOMEM
+    with pytest.raises(rexi.RexiError) as e:
+        plan.step(x, dt, tol=1e-20)
+    assert e.value.status == rexi.REXI_EINVAL
+    bad = torch.empty(x.numel() * 2 + 1, dtype=torch.float64, device="cuda")[1:]
+    with pytest.raises(rexi.RexiError) as e:
+        plan.step(bad, dt)
+    assert e.value.status == rexi.REXI_EINVAL
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_config2_full_size_sampled(form):
+    """2048x2048, |k|^-3 field (seed 0), tau rho = 1000, tol 1e-10 (M = 2009,
+    J = 4068), in the launch configuration the benchmark times.  Checked on
+    sampled wavenumbers against the oracle's per-mode solve chain, and through
+    properties that hold at any size: the output is real, the energy is
+    conserved, the mean height is multiplied by REXII(0)."""
+    torch = torch_cuda()
+    from paper_2008_11607_gb300 import rexi
+
+    D = 2048
+    st = inputs.kminus3_field(D, D, seed=0)
+    plan = rexi.Plan(D, D, form=form)
+    dt = 1000.0 / plan.rho
+    assert abs(plan.rho - 2 * math.sqrt(2) * D) < 1e-8
+    out, info = plan.step(to_dev(torch, st), dt, want_info=True)
+    out = out.cpu().numpy()
+    assert (info.M, info.N, info.n_poles) == (2009, 2033, 4068)
+    assert np.all(out.imag == 0)
+    e_in = np.sum(np.abs(st) ** 2)
+    e_out = np.sum(np.abs(out) ** 2)
+    assert abs(e_out - e_in) / e_in < 1e-9
+    fin = np.fft.fft2(st, axes=(1, 2))
+    fout = np.fft.fft2(out, axes=(1, 2))
+    rng = np.random.default_rng(11)
+    ks = [(0, 0), (1, 0), (0, 1), (D // 2, D // 2), (D - 1, 3)] + [tuple(rng.integers(0, D, 2)) for _ in range(7)]
+    for kx, ky in ks:
+        B = O.symbol(kx, ky, D, D)
+        ref = R.rexii_apply_dense_mode(B, fin[:, ky, kx], dt, 0.5, info.M, real_input=False)
+        scale = max(np.linalg.norm(fin[:, ky, kx]), 1e-300)
+        err = np.linalg.norm(fout[:, ky, kx] - ref) / scale
+        assert err < TOL[form], (kx, ky, err)
