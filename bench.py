@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark of one REXII time step on the constant-depth (Fourier) path.
+
+Workload (one "step" = one whole REXII step over one batch of input):
+2048 x 2048 staggered grid, H = g = f = 1 on the unit square, eta from the
+seeded |k|^-3 recipe (seeds 0..9 cycled, u = v = 0, real input stored as
+complex128), dt with dt * rho(A) = 1000, pole-count tolerance 1e-10
+(M = 2009, N = 2033, J = 2(N + 1) = 4068 single-shift poles).
+
+Metric: grid points x poles solved per second = nx * ny * J / (time per step),
+summed over ranks.  Device time comes from CUDA events on the launching stream
+around exactly --steps steps after --warmup untimed steps (barrier and
+synchronise on both sides, max over ranks).  Each input state is 201 MB, larger
+than the 129 MB L2, and ten of them are cycled.
+
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload instead (rank 0 only).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+D = 2048
+TAU_RHO = 1000.0
+TOL = 1e-10
+H_PARAM = 0.5
+N_SEEDS = 10
+METRIC = "grid-points×poles solved/sec and HBM GB/s vs roofline at stated error vs FP64 oracle"
+UNIT = "grid-points*poles/s"
+
+# Per-term work of the fused pole loops, counted from the kernel source
+# (csrc/pole_fft.cu).  mixed: 72 FP32 arithmetic instructions per term, 12 of
+# them FFMA -> 84 flops; fp64: 7 DFMA + 1 DADD -> 15 flops.  One MUFU
+# reciprocal seed per term in both.
+FLOPS_PER_TERM = {"mixed": 84, "fp64": 15}
+FP32_INSTR_PER_TERM = 72
+FP64_INSTR_PER_TERM = 8
+# Peaks for ALU-bound kernels, derived from unit counts and the maximum clock:
+# 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz; FP64 from the nominal
+# 1.25 TFLOP/s of this GPU.
+SMS = 152
+SM_MAX_GHZ = 2.07
+PEAK_FP32_TFLOPS = SMS * 128 * 2 * SM_MAX_GHZ / 1e3
+PEAK_FP64_TFLOPS = 1.25
+# DRAM traffic of the pole kernel per launch from an ncu capture of this
+# workload's kernel (profiles/pole_fused_mixed_2048.md); None until captured.
+NCU_POLE_TRAFFIC_BYTES = {"mixed": None, "fp64": None}
+
+
+def workload_config(form):
+    M = 2009
+    N = M + 24
+    return {
+        "workload": "LRSW constant-depth Fourier path, %dx%d C-grid, |k|^-3 eta seeds 0-%d, tau*rho=%g, "
+                    "tol=%g, h=%g, real input, form=%s" % (D, D, N_SEEDS - 1, TAU_RHO, TOL, H_PARAM, form),
+        "grid": [D, D],
+        "tau_rho": TAU_RHO,
+        "tol": TOL,
+        "h": H_PARAM,
+        "M": M,
+        "J": 2 * (N + 1),
+        "form": form,
+        "l2": "inputs larger than L2 (201 MB state per step, %d states cycled)" % N_SEEDS,
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            cmd = ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except OSError:
+            pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU, replicas: no data-path collective)
+
+def dist_setup():
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (cpu_baseline leg and the reference arm): per-mode FP64 solve
+# chain of the oracle on sampled wavenumbers of the same input
+
+def oracle_sample(n_modes, seed=0, fout=None):
+    """Runs the oracle's per-mode REXII chain on `n_modes` wavenumbers of the
+    2048^2 seed-`seed` input.  Returns (seconds, max relative error of `fout`
+    at those modes or None)."""
+    import numpy as np
+
+    from oracle import coeffs as C
+    from oracle import operator as O
+    from oracle import rexi as R
+    from paper_2008_11607_gb300 import inputs
+
+    st = inputs.kminus3_field(D, D, seed=seed)
+    fin = np.fft.fft2(st[0])  # u = v = 0
+    rho = 2.0 * math.sqrt(2.0) * D
+    dt = TAU_RHO / rho
+    M = C.pole_count_M(TAU_RHO, H_PARAM, TOL)
+    rng = np.random.default_rng(1234)
+    ks = [(int(a), int(b)) for a, b in rng.integers(0, D, size=(n_modes, 2))]
+    worst = 0.0
+    t0 = time.perf_counter()
+    tw = C.matrix_term_weights(H_PARAM, M, real_input=False)  # once per step, as on the GPU
+    refs = []
+    for kx, ky in ks:
+        B = O.symbol(kx, ky, D, D)
+        fh = np.array([fin[ky, kx], 0.0, 0.0], dtype=np.complex128)
+        refs.append(R.rexii_apply_dense_mode(B, fh, dt, H_PARAM, M, real_input=False, term_weights=tw))
+    secs = time.perf_counter() - t0
+    if fout is not None:
+        for (kx, ky), ref in zip(ks, refs):
+            got = fout[:, ky, kx]
+            worst = max(worst, float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)))
+        return secs, worst
+    return secs, None
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    J = 2 * (2009 + 24 + 1)
+    modes = 1
+    for _ in range(args.warmup):
+        oracle_sample(modes)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_sample(modes)
+    secs = (time.perf_counter() - t0) / args.steps
+    value = modes * J / secs
+    cfg = workload_config("oracle")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d wavenumbers of the 2048^2 step per timed step, each through the "
+                                   "oracle's per-mode FP64 solve chain over all 2N+1 terms" % modes},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+
+def time_form(torch, rexi, form, states, steps, warmup, world, profile=True):
+    plan = rexi.Plan(D, D, form=form, h=H_PARAM)
+    dt = TAU_RHO / plan.rho
+    ws = plan.workspace(dt, TOL)
+    out = torch.empty_like(states[0])
+    for i in range(warmup):
+        plan.step(states[i % len(states)], dt, tol=TOL, out=out, workspace=ws)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    plan.set_profiling(profile)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(steps):
+        plan.step(states[i % len(states)], dt, tol=TOL, out=out, workspace=ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1) / steps
+    prof = plan.read_profile() if profile else None
+    return plan, dt, ms, prof, out
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup()
+    from paper_2008_11607_gb300 import build as B
+
+    B.build()
+    from paper_2008_11607_gb300 import inputs, rexi
+
+    rexi.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    seeds = [rank * N_SEEDS + s for s in range(N_SEEDS)]
+    host_states = [torch.from_numpy(inputs.kminus3_field(D, D, seed=s)) for s in seeds]
+    states = [h.to(dev) for h in host_states]
+    J = 2 * (2009 + 24 + 1)
+    units = D * D * J
+
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = None
+    sampler = ClockSampler(gpu_id)
+
+    # headline form, with clocks sampled during the timed region
+    sampler.start()
+    plan, dt, ms, prof, out = time_form(torch, rexi, args.form, states, args.steps, args.warmup, world)
+    clocks = sampler.stop()
+    ms_max = max_over_ranks(world, ms)
+    value = world * units / (ms_max / 1e3)
+    ms_phase, ncalls, nlaunch = prof
+    pole_ms = ms_phase[1] / max(ncalls, 1)
+    pairs = D * (D // 2 + 1)
+    nterms = 2 * (2009 + 24) + 1
+    flops = pairs * nterms * FLOPS_PER_TERM.get(args.form, 0)
+    achieved = flops / (pole_ms / 1e3) / 1e12
+    peak = PEAK_FP32_TFLOPS if args.form == "mixed" else PEAK_FP64_TFLOPS
+    roofline = {
+        "kernel": "pole_fused_%s_kernel" % args.form,
+        "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+        "traffic": NCU_POLE_TRAFFIC_BYTES.get(args.form),
+        "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if args.form == "mixed"
+                        else "nominal FP64 1.25 TFLOP/s (profiling recipe)"),
+        "pole_ms_per_launch": pole_ms,
+        "terms_per_launch": pairs * nterms,
+    }
+    if args.form == "mixed":
+        roofline["fp32_issue_frac"] = (pairs * nterms * FP32_INSTR_PER_TERM / (pole_ms / 1e3)) / (
+            SMS * 128 * SM_MAX_GHZ * 1e9)
+    phases = {"forward_fft_ms": ms_phase[0] / max(ncalls, 1), "pole_ms": pole_ms,
+              "inverse_fft_ms": ms_phase[2] / max(ncalls, 1), "table_upload_ms": ms_phase[3] / max(ncalls, 1)}
+    # HBM roofline of the FFT passes (2 passes each way, each reads + writes 3 fields)
+    fft_bytes = 2 * 2 * 3 * D * D * 16
+    fwd_gbs = fft_bytes / (phases["forward_fft_ms"] / 1e3) / 1e9
+    mp = {}
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = mp.get("hbm_gbs", 6800.0)
+    roofline_fft = {"kernel": "fft_rows_kernel + fft_cols_kernel (forward)", "bound": "hbm",
+                    "achieved": fwd_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": fwd_gbs / hbm_peak,
+                    "traffic": None,
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in mp else "fallback 6.8 TB/s"}
+
+    # end-to-end through the host-buffer C-ABI call (pinned host memory)
+    e2e = None
+    if not args.skip_e2e:
+        pinned = [h.pin_memory() for h in host_states]
+        out_host = torch.empty_like(pinned[0]).pin_memory()
+        wsh = plan.workspace_host(dt, TOL)
+        for i in range(min(2, args.warmup)):
+            plan.step_host(pinned[i], out_host, dt, tol=TOL, workspace=wsh)
+        k_e2e = max(3, min(args.steps, 20))
+        barrier(world)
+        t0 = time.perf_counter()
+        for i in range(k_e2e):
+            plan.step_host(pinned[i % N_SEEDS], out_host, dt, tol=TOL, workspace=wsh)
+        secs = (time.perf_counter() - t0) / k_e2e
+        secs = max_over_ranks(world, secs)
+        nbytes = 3 * D * D * 16
+        e2e = {"value": world * units / secs, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "ms_per_step": secs * 1e3, "steps": k_e2e}
+        del wsh
+
+    # other forms on the same GPU and workload (fewer steps)
+    forms = {}
+    if not args.skip_forms:
+        for form, k in (("fp64", 3), ("plain", 1)):
+            if form == args.form:
+                continue
+            _, _, fms, fprof, _ = time_form(torch, rexi, form, states, k, 1, world)
+            fms = max_over_ranks(world, fms)
+            forms[form] = {"value": world * units / (fms / 1e3), "ms_per_step": fms, "steps": k,
+                           "pole_ms": fprof[0][1] / max(fprof[1], 1)}
+
+    # CPU oracle on a bounded sample (rank 0, N = 1 only), also the accuracy check
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        import numpy as np
+
+        plan0, dt0, _, _, o0 = time_form(torch, rexi, args.form, states[:1], 1, 0, 1, profile=False)
+        fout = np.fft.fft2(o0.cpu().numpy(), axes=(1, 2))
+        secs, err = oracle_sample(args.cpu_modes, seed=seeds[0], fout=fout)
+        cpu = {"value": args.cpu_modes * J / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d random wavenumbers of the seed-0 2048^2 step through the oracle's per-mode FP64 "
+                         "solve chain (all 2N+1 terms, 2 dense 3x3 solves each), %.1f s" % (args.cpu_modes, secs),
+               "max_rel_err_vs_oracle": err}
+
+    if rank == 0:
+        cfg = workload_config(args.form)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32x2+f64" if args.form == "mixed" else "f64", "data": "synthetic",
+            "config": cfg, "clocks": clocks, "e2e": e2e, "gpu_launches": nlaunch, "roofline": roofline,
+            "roofline_fft": roofline_fft, "phases_ms": phases, "forms": forms, "cpu_baseline": cpu,
+            "accuracy": {"tolerance": 1e-8 if args.form == "mixed" else 1e-10,
+                         "max_rel_err_vs_oracle_sampled": cpu["max_rel_err_vs_oracle"] if cpu else None},
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="mixed", choices=["mixed", "fp64", "plain"])
+    ap.add_argument("--cpu-modes", type=int, default=20)
+    ap.add_argument("--skip-forms", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)  # timing rule: at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

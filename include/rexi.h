@@ -177,6 +177,31 @@ rexi_status rexi_step_adjoint(rexi_plan_t plan, const void* grad_out_dev, void* 
                               double dt, double tol, int32_t real_input, void* workspace_dev,
                               size_t workspace_bytes, void* stream);
 
+/* out = r(dt A) in with HOST buffers: copies `in_host` to the device
+ * workspace, runs rexi_step there and copies the result back into
+ * `out_host`, all on `stream`, then synchronises the stream so that
+ * `out_host` is ready on return.  Pinned host memory gives asynchronous,
+ * full-bandwidth copies; pageable memory works but is staged by the driver.
+ * The workspace must hold rexi_workspace_size() plus two states
+ * (2 * 3 * nx * ny * 16 bytes): see rexi_workspace_size_host. */
+rexi_status rexi_step_host(rexi_plan_t plan, const void* in_host, void* out_host, double dt, double tol,
+                           int32_t real_input, void* workspace_dev, size_t workspace_bytes, void* stream,
+                           rexi_step_info* info);
+
+/* Workspace bytes for rexi_step_host. */
+rexi_status rexi_workspace_size_host(rexi_plan_t plan, double dt, double tol, int32_t real_input,
+                                     size_t* bytes);
+
+/* Device-side phase timing of rexi_step calls: with profiling enabled, each
+ * call records CUDA events on its own stream around its phases.
+ * rexi_plan_read_profile waits for the recorded events, returns the summed
+ * milliseconds per phase since the last read (ms[0] forward transform or
+ * Krylov set-up, ms[1] the pole loop over all terms, ms[2] inverse
+ * transform or final accumulation, ms[3] table upload), the number of
+ * profiled calls and of kernels launched by them, then resets the sums. */
+rexi_status rexi_plan_set_profiling(rexi_plan_t plan, int32_t enable);
+rexi_status rexi_plan_read_profile(rexi_plan_t plan, double* ms4, int32_t* n_calls, int64_t* n_launches);
+
 /* Human-readable name of a status code (static string). */
 const char* rexi_status_string(rexi_status status);
 

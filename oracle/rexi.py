@@ -44,7 +44,7 @@ def rexii_apply_sparse(A, f0, tau, h, M, real_input=True, terms=None):
     return acc.real.astype(np.complex128) if real_input else acc
 
 
-def rexii_apply_dense_mode(B, fhat, tau, h, M, real_input=True):
+def rexii_apply_dense_mode(B, fhat, tau, h, M, real_input=True, term_weights=None):
     """The same per-term chain on one Fourier mode: B is the 3x3 symbol, fhat
     the 3 Fourier coefficients.  Dense numpy solves.  No real part is taken
     (a single mode of a real field is complex); with real_input the sum runs

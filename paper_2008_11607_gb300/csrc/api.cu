@@ -58,7 +58,28 @@ struct rexi_plan_s {
   bool staging_pending = false;
   // Krylov path
   KrylovSettings kry;
+  // profiling: per call 5 events (start, after upload, after forward, after poles, end)
+  bool prof_on = false;
+  std::vector<std::vector<cudaEvent_t>> prof_pool;
+  size_t prof_used = 0;
+  int64_t launches = 0;
+  int64_t prof_launch_base = 0;
 };
+
+namespace {
+void prof_mark(rexi_plan_s* p, int i, cudaStream_t s) {
+  if (!p->prof_on) return;
+  if (i == 0) {
+    if (p->prof_used == p->prof_pool.size()) {
+      std::vector<cudaEvent_t> set(5, nullptr);
+      for (auto& e : set) cudaEventCreate(&e);
+      p->prof_pool.push_back(set);
+    }
+    ++p->prof_used;
+  }
+  cudaEventRecord(p->prof_pool[p->prof_used - 1][i], s);
+}
+}  // namespace
 
 extern "C" {
 
@@ -166,6 +187,8 @@ void rexi_plan_destroy(rexi_plan_t p) {
   cudaFree(p->half_y);
   if (p->staging) cudaFreeHost(p->staging);
   krylov_destroy(&p->kry);
+  for (auto& set : p->prof_pool)
+    for (auto e : set) cudaEventDestroy(e);
   delete p;
 }
 
@@ -398,9 +421,16 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
   const size_t nk = (size_t)p->nx * p->ny;
   rexi_status st;
 
-  // forward transform (imaginary parts dropped for real input)
-  CUDA_TRY(fft2d(static_cast<const double2*>(in), spec, 3, p->fx, p->fy, -1, 1.0, real_input, 0, s),
-           "forward FFT");
+  prof_mark(p, 0, s);
+  const double2* in2 = static_cast<const double2*>(in);
+  auto forward = [&]() -> rexi_status {
+    prof_mark(p, 1, s);
+    // forward transform (imaginary parts dropped for real input)
+    CUDA_TRY(fft2d(in2, spec, 3, p->fx, p->fy, -1, 1.0, real_input, 0, s), "forward FFT");
+    p->launches += 2;
+    prof_mark(p, 2, s);
+    return REXI_OK;
+  };
 
   if (p->form == REXI_FORM_FP64 || p->form == REXI_FORM_MIXED) {
     // scalar terms n = -N..N restricted to |n| in [tb, te)
@@ -434,8 +464,10 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
         e[5] = 0.0;
       }
       if ((st = stage_upload(p, tab.data(), tab.size() * sizeof(double), base + L.table_off, s)) != REXI_OK) return st;
+      if ((st = forward()) != REXI_OK) return st;
       CUDA_TRY(pole_fused_fp64(spec, sp, reinterpret_cast<const double*>(base + L.table_off), fs, s),
-                 "pole_fused_fp64");
+               "pole_fused_fp64");
+      p->launches += 1;
     } else {
       // grid G = 2^-g so that |x| + h N < 2^24 G: x <= tau rho
       const double span = dt * p->rho + h * N + 4.0;
@@ -463,8 +495,10 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
         e[8] = Bil; e[9] = (float)(hn - hn_g); e[10] = 0.f; e[11] = 0.f;
       }
       if ((st = stage_upload(p, tab.data(), tab.size() * sizeof(float), base + L.table_off, s)) != REXI_OK) return st;
+      if ((st = forward()) != REXI_OK) return st;
       CUDA_TRY(pole_fused_mixed(spec, sp, reinterpret_cast<const float*>(base + L.table_off), fs, G, s),
                "pole_fused_mixed");
+      p->launches += 1;
     }
   } else {
     // plain form: terms n = 0..N (real) or -N..N (complex), |n| in [tb, te)
@@ -489,9 +523,11 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
     double2* acc = reinterpret_cast<double2*>(base + L.acc_off);
     double2* chunk = reinterpret_cast<double2*>(base + L.chunk_off);
     if (nt == 0) {
+      if ((st = forward()) != REXI_OK) return st;
       CUDA_TRY(cudaMemsetAsync(acc, 0, 3 * nk * sizeof(double2), s), "zero accumulator");
     } else {
       if ((st = stage_upload(p, tab.data(), tab.size() * sizeof(double2), base + L.table_off, s)) != REXI_OK) return st;
+      if ((st = forward()) != REXI_OK) return st;
       const double2* dtab = reinterpret_cast<const double2*>(base + L.table_off);
       for (int t0 = 0; t0 < nt; t0 += (int)L.chunk_terms) {
         PlainScalars ps;
@@ -501,13 +537,17 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
         CUDA_TRY(pole_plain_terms(spec, chunk, sp, dtab + 4 * t0, ps, s), "pole_plain_terms");
         CUDA_TRY(pole_plain_reduce(chunk, acc, (long long)(3 * nk), ps.nterms, t0 == 0 ? 1 : 0, s),
                  "pole_plain_reduce");
+        p->launches += 2;
       }
     }
     spec = acc;
   }
+  prof_mark(p, 3, s);
   // inverse transform, 1/(nx ny), real part for real input
   CUDA_TRY(fft2d(spec, static_cast<double2*>(out), 3, p->fx, p->fy, +1, 1.0 / (double)nk, 0, real_input, s),
            "inverse FFT");
+  p->launches += 2;
+  prof_mark(p, 4, s);
   return REXI_OK;
 }
 
@@ -570,6 +610,68 @@ rexi_status rexi_step_adjoint(rexi_plan_t p, const void* gout, void* gin, double
     return krylov_step(&p->kry, p->form, p->h, M, gout, gin, dt, real_input, 0, -1, ws, ws_bytes, s, nullptr,
                        true);
   return fourier_step(p, gout, gin, dt, M, real_input, 0, -1, ws, ws_bytes, s, true);
+}
+
+}  // extern "C"
+
+extern "C" {
+
+rexi_status rexi_workspace_size_host(rexi_plan_t p, double dt, double tol, int32_t real_input, size_t* bytes) {
+  size_t b = 0;
+  rexi_status st = rexi_workspace_size(p, dt, tol, real_input, &b);
+  if (st != REXI_OK) return st;
+  const size_t state = align_up(3 * (size_t)p->nx * p->ny * sizeof(double2), 256);
+  *bytes = 2 * state + b;
+  return REXI_OK;
+}
+
+rexi_status rexi_step_host(rexi_plan_t p, const void* in_host, void* out_host, double dt, double tol,
+                           int32_t real_input, void* ws, size_t ws_bytes, void* stream, rexi_step_info* info) {
+  g_err[0] = 0;
+  if (!p || !in_host || !out_host || !ws) return fail(REXI_EINVAL, "NULL argument");
+  if ((uintptr_t)ws & 255) return fail(REXI_EINVAL, "workspace must be 256-byte aligned");
+  const size_t bytes = 3 * (size_t)p->nx * p->ny * sizeof(double2);
+  const size_t state = align_up(bytes, 256);
+  if (ws_bytes < 2 * state) return fail(REXI_ENOMEM, "workspace too small for the host-buffer step");
+  char* base = static_cast<char*>(ws);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CUDA_TRY(cudaMemcpyAsync(base, in_host, bytes, cudaMemcpyHostToDevice, s), "host-to-device copy");
+  rexi_status st = rexi_step(p, base, base + state, dt, tol, real_input, 0, -1, base + 2 * state,
+                             ws_bytes - 2 * state, stream, info);
+  if (st != REXI_OK) return st;
+  CUDA_TRY(cudaMemcpyAsync(out_host, base + state, bytes, cudaMemcpyDeviceToHost, s), "device-to-host copy");
+  CUDA_TRY(cudaStreamSynchronize(s), "stream synchronise");
+  return REXI_OK;
+}
+
+rexi_status rexi_plan_set_profiling(rexi_plan_t p, int32_t enable) {
+  g_err[0] = 0;
+  if (!p) return fail(REXI_EINVAL, "plan NULL");
+  p->prof_on = enable != 0;
+  p->prof_used = 0;
+  p->prof_launch_base = p->launches;
+  return REXI_OK;
+}
+
+rexi_status rexi_plan_read_profile(rexi_plan_t p, double* ms4, int32_t* n_calls, int64_t* n_launches) {
+  g_err[0] = 0;
+  if (!p || !ms4) return fail(REXI_EINVAL, "NULL argument");
+  for (int i = 0; i < 4; ++i) ms4[i] = 0.0;
+  for (size_t k = 0; k < p->prof_used; ++k) {
+    auto& e = p->prof_pool[k];
+    CUDA_TRY(cudaEventSynchronize(e[4]), "profile event");
+    float t;
+    const int map[4][2] = {{1, 2}, {2, 3}, {3, 4}, {0, 1}};
+    for (int ph = 0; ph < 4; ++ph) {
+      CUDA_TRY(cudaEventElapsedTime(&t, e[map[ph][0]], e[map[ph][1]]), "profile elapsed");
+      ms4[ph] += t;
+    }
+  }
+  if (n_calls) *n_calls = (int32_t)p->prof_used;
+  if (n_launches) *n_launches = p->launches - p->prof_launch_base;
+  p->prof_used = 0;
+  p->prof_launch_base = p->launches;
+  return REXI_OK;
 }
 
 }  // extern "C"

@@ -58,6 +58,11 @@ SIGNATURES = {
     "rexi_step": (_c_int, [_vp, _vp, _vp, _c_dbl, _c_dbl, _c_int, _c_int, _c_int, _vp, ctypes.c_size_t, _vp,
                            ctypes.POINTER(rexi_step_info)]),
     "rexi_step_adjoint": (_c_int, [_vp, _vp, _vp, _c_dbl, _c_dbl, _c_int, _vp, ctypes.c_size_t, _vp]),
+    "rexi_step_host": (_c_int, [_vp, _vp, _vp, _c_dbl, _c_dbl, _c_int, _vp, ctypes.c_size_t, _vp,
+                                ctypes.POINTER(rexi_step_info)]),
+    "rexi_workspace_size_host": (_c_int, [_vp, _c_dbl, _c_dbl, _c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "rexi_plan_set_profiling": (_c_int, [_vp, _c_int]),
+    "rexi_plan_read_profile": (_c_int, [_vp, _dp, _ip, ctypes.POINTER(ctypes.c_int64)]),
     "rexi_status_string": (ctypes.c_char_p, [_c_int]),
     "rexi_version": (ctypes.c_char_p, []),
     "rexi_last_error_message": (ctypes.c_char_p, []),
@@ -211,6 +216,36 @@ class Plan:
                                  ctypes.byref(info) if info is not None else None)
         _check(st, "rexi_step")
         return (out, info) if want_info else out
+
+    def workspace_host(self, dt, tol=1e-10, real_input=True, device=None):
+        import torch
+
+        b = ctypes.c_size_t()
+        _check(self._lib.rexi_workspace_size_host(self._h, dt, tol, int(real_input), ctypes.byref(b)),
+               "rexi_workspace_size_host")
+        return torch.empty(max(b.value, 256), dtype=torch.uint8, device=device or "cuda")
+
+    def step_host(self, state_host, out_host, dt, tol=1e-10, real_input=True, workspace=None, stream=None):
+        """Host-buffer step: ``state_host``/``out_host`` are CPU tensors (pinned for full speed)."""
+        if workspace is None:
+            workspace = self.workspace_host(dt, tol, real_input)
+        st = self._lib.rexi_step_host(self._h, ctypes.c_void_p(state_host.data_ptr()),
+                                      ctypes.c_void_p(out_host.data_ptr()), dt, tol, int(real_input),
+                                      _ptr(workspace), workspace.numel(), _stream_handle(stream), None)
+        _check(st, "rexi_step_host")
+        return out_host
+
+    def set_profiling(self, enable=True):
+        _check(self._lib.rexi_plan_set_profiling(self._h, int(enable)), "rexi_plan_set_profiling")
+
+    def read_profile(self):
+        """Returns (ms per phase [fwd, poles, inv, upload], calls, kernel launches) since the last read."""
+        ms = (ctypes.c_double * 4)()
+        n = ctypes.c_int32()
+        L = ctypes.c_int64()
+        _check(self._lib.rexi_plan_read_profile(self._h, ms, ctypes.byref(n), ctypes.byref(L)),
+               "rexi_plan_read_profile")
+        return list(ms), n.value, L.value
 
     def step_adjoint(self, grad_out, dt, tol=1e-10, real_input=True, out=None, workspace=None, stream=None):
         import torch
