@@ -194,11 +194,18 @@ def test_config2_full_size_sampled(form):
     assert abs(e_out - e_in) / e_in < 1e-9
     fin = np.fft.fft2(st, axes=(1, 2))
     fout = np.fft.fft2(out, axes=(1, 2))
+    # per-mode errors are measured against max(|f(k)|, rms over modes): the
+    # transform's own rounding is ~1e-16 of the rms amplitude, which would
+    # swamp a strict per-mode relative error on modes that are ~0 (the |k|^-3
+    # field has no mean, so k = 0 holds only rounding noise)
+    rms = math.sqrt(np.sum(np.abs(fin) ** 2) / (D * D))
     rng = np.random.default_rng(11)
-    ks = [(0, 0), (1, 0), (0, 1), (D // 2, D // 2), (D - 1, 3)] + [tuple(rng.integers(0, D, 2)) for _ in range(7)]
+    ks = [(0, 0), (1, 0), (0, 1), (2, 1), (D // 2, D // 2), (D - 1, 3)]
+    ks += [tuple(int(v) for v in rng.integers(0, D, 2)) for _ in range(6)]
+    tw = C.matrix_term_weights(0.5, info.M, real_input=False)
     for kx, ky in ks:
         B = O.symbol(kx, ky, D, D)
-        ref = R.rexii_apply_dense_mode(B, fin[:, ky, kx], dt, 0.5, info.M, real_input=False)
-        scale = max(np.linalg.norm(fin[:, ky, kx]), 1e-300)
+        ref = R.rexii_apply_dense_mode(B, fin[:, ky, kx], dt, 0.5, info.M, real_input=False, term_weights=tw)
+        scale = max(np.linalg.norm(fin[:, ky, kx]), rms)
         err = np.linalg.norm(fout[:, ky, kx] - ref) / scale
         assert err < TOL[form], (kx, ky, err)
