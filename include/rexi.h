@@ -202,6 +202,28 @@ rexi_status rexi_workspace_size_host(rexi_plan_t plan, double dt, double tol, in
 rexi_status rexi_plan_set_profiling(rexi_plan_t plan, int32_t enable);
 rexi_status rexi_plan_read_profile(rexi_plan_t plan, double* ms4, int32_t* n_calls, int64_t* n_launches);
 
+/* Constant-depth step that allocates nothing, for callers that may not
+ * allocate device memory (code running inside another allocator's hooks or
+ * memory pool, a loop with a fixed memory budget, a process whose device
+ * memory is reserved up front).  It needs no plan and no workspace: its
+ * scratch is one fixed static device array (about 3.4 MiB, held by every GPU
+ * that loads the library until the process exits).  The paper has no
+ * counterpart; this is a deployment convenience.
+ * Arguments as for rexi_plan_create (constant depth H, parameter h) and
+ * rexi_step (all terms, fused FP64 form).  Limits: 2 <= nx, ny <= 1024,
+ * nx * ny <= 65536, prime factors <= 127, at most 8193 scalar terms
+ * (dt * rho up to about 2030 at h = 0.5, tol = 1e-10); larger requests return
+ * REXI_EINVAL with the reason in rexi_last_error_message().
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it: make that first call before any
+ * stream capture.  All calls share the array: calls whose GPU work overlaps
+ * (different streams, several host threads) race and give wrong results;
+ * order them on one stream.  Every region is written before it is read, so
+ * nothing needs clearing between calls. */
+rexi_status rexi_step_noalloc(int32_t nx, int32_t ny, double Lx, double Ly, double g, double f, double H,
+                              double h, const void* in_dev, void* out_dev, double dt, double tol,
+                              int32_t real_input, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* rexi_status_string(rexi_status status);
 

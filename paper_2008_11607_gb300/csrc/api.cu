@@ -38,6 +38,10 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace
 
+void rexi::set_last_error(const char* msg) {
+  snprintf(g_err, sizeof(g_err), "%s", msg);
+}
+
 struct rexi_plan_s {
   int nx = 0, ny = 0;
   double Lx = 1, Ly = 1, g = 1, f = 1, H = 1, h = 0.5;

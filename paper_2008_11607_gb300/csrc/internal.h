@@ -28,6 +28,9 @@ double table_mu();
 void table_a(double re[kL + 1], double im[kL + 1]);
 void rexii_terms(int M, double h, TermSet* ts);
 
+// Records the text returned by rexi_last_error_message() (api.cu).
+void set_last_error(const char* msg);
+
 // ---- FFT (fft.cu) ---------------------------------------------------------
 struct FftPlan1D {
   int n = 0;

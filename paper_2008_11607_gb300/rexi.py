@@ -63,6 +63,8 @@ SIGNATURES = {
     "rexi_workspace_size_host": (_c_int, [_vp, _c_dbl, _c_dbl, _c_int, ctypes.POINTER(ctypes.c_size_t)]),
     "rexi_plan_set_profiling": (_c_int, [_vp, _c_int]),
     "rexi_plan_read_profile": (_c_int, [_vp, _dp, _ip, ctypes.POINTER(ctypes.c_int64)]),
+    "rexi_step_noalloc": (_c_int, [_c_int, _c_int, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _vp, _vp,
+                                   _c_dbl, _c_dbl, _c_int, _vp]),
     "rexi_status_string": (ctypes.c_char_p, [_c_int]),
     "rexi_version": (ctypes.c_char_p, []),
     "rexi_last_error_message": (ctypes.c_char_p, []),
