@@ -53,8 +53,9 @@ SM_MAX_GHZ = 2.07
 PEAK_FP32_TFLOPS = SMS * 128 * 2 * SM_MAX_GHZ / 1e3
 PEAK_FP64_TFLOPS = 1.25
 # DRAM traffic of the pole kernel per launch from an ncu capture of this
-# workload's kernel (profiles/pole_fused_mixed_2048.md); None until captured.
-NCU_POLE_TRAFFIC_BYTES = {"mixed": None, "fp64": None}
+# kernel on the 2048^2 grid (profiles/pole_fused_mixed_2048_tau50.md: same grid and
+# bytes, fewer terms; traffic does not depend on the term count); None if not captured.
+NCU_POLE_TRAFFIC_BYTES = {"mixed": 342193152, "fp64": None}  # 201.50 MB read + 140.69 MB write
 
 
 def set_workload(grid, tau_rho):
