@@ -32,10 +32,10 @@ def error_bound(M, rtol, H, g=1.0, real_input=True, h=0.5):
     return float(np.sum(gam[sel] * per[sel])) * rtol * cond
 
 
-def krylov_plan(torch, nx, ny, H, rtol=1e-13, max_iters=20000, batch=32, **phys):
+def krylov_plan(torch, nx, ny, depth, rtol=1e-13, max_iters=20000, batch=32, **phys):
     from paper_2008_11607_gb300 import rexi
 
-    Hd = torch.from_numpy(np.ascontiguousarray(H, dtype=np.float64)).cuda()
+    Hd = torch.from_numpy(np.ascontiguousarray(depth, dtype=np.float64)).cuda()
     plan = rexi.Plan(nx, ny, depth=Hd, **phys)
     plan.set_krylov(rtol=rtol, max_iters=max_iters, term_batch=batch)
     return plan
@@ -76,7 +76,7 @@ def test_constant_depth_krylov_matches_fourier_path():
 
     nx, ny = 24, 20
     st = inputs.kminus3_field(nx, ny, seed=4)
-    plan_k = krylov_plan(torch, nx, ny, np.full((ny, nx), 1.3), rtol=1e-13, H=1.3)
+    plan_k = krylov_plan(torch, nx, ny, np.full((ny, nx), 1.3), rtol=1e-13)
     plan_f = rexi.Plan(nx, ny, H=1.3)
     # the Krylov plan uses the rigorous bound for rho; use the same dt for both
     dt = 25.0 / plan_k.rho
