@@ -277,6 +277,60 @@ def time_form(torch, rexi, form, states, steps, warmup, world, profile=True):
     return plan, dt, ms, prof, out
 
 
+KRYLOV_D = 1024
+KRYLOV_TAU_RHO = 400.0
+# algorithmic bytes per grid point per CG iteration of one term (FP64):
+# cg_apply_B reads r, p and writes t (3 x 48 B); cg_update reads t, x, p, r and
+# writes p, x, r (7 x 48 B); the depth field (8 B per kernel) is shared by all
+# terms and left out.
+KRYLOV_BYTES_PER_PT_ITER = {"fp64": 480}
+
+
+def krylov_measure(torch, rexi, inputs, form, n_terms, rtol, warm=1):
+    """Variable-depth workload (1024^2, H = 1 + 0.4 sin cos + 8 bumps, |k|^-3
+    height, tau rho = 400): one batch of the hardest terms |n| < n_terms
+    (nearest the resonance), CG to relative residual rtol."""
+    import numpy as np
+
+    n = KRYLOV_D
+    H = torch.from_numpy(inputs.variable_depth(n, n, seed=0)).cuda()
+    plan = rexi.Plan(n, n, depth=H, form=form)
+    plan.set_krylov(rtol=rtol, max_iters=20000, term_batch=n_terms)
+    dt = KRYLOV_TAU_RHO / plan.rho
+    x = torch.from_numpy(inputs.kminus3_field(n, n, seed=0)).cuda()
+    out = torch.empty_like(x)
+    ws = plan.workspace(dt)
+    for _ in range(warm):
+        plan.step(x, dt, out=out, workspace=ws, terms=(0, n_terms))
+    torch.cuda.synchronize()
+    plan.set_profiling(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    _, info = plan.step(x, dt, out=out, workspace=ws, terms=(0, n_terms), want_info=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ph, nsets, nl = plan.read_profile()
+    cg_ms = ph[1]
+    iters = int(info.krylov_term_iters)
+    bpp = KRYLOV_BYTES_PER_PT_ITER.get(form, 480)
+    gbs = bpp * n * n * iters / (cg_ms / 1e3) / 1e9
+    J = 2 * n_terms
+    return {
+        "workload": "LRSW variable depth %dx%d, H = 1 + 0.4 sin(2 pi x) cos(4 pi y) + 8 bumps (seed 0), |k|^-3 "
+                    "eta, tau*rho=%g (M=%d), REXII terms n = 0..%d (the %d nearest the resonance, J = %d poles) "
+                    "of %d, CG rtol=%g, form=%s" % (n, n, KRYLOV_TAU_RHO, info.M, n_terms - 1, n_terms, J,
+                                                   info.N + 1, rtol, form),
+        "value": n * n * J / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+        "cg_ms": cg_ms, "term_iters": iters, "max_iters": int(info.krylov_iters),
+        "max_rel_res": info.krylov_max_rel_res,
+        "roofline": {"kernel": "cg_apply_B + cg_update", "bound": "hbm", "achieved": gbs, "unit": "GB/s",
+                     "bytes_per_point_iteration": bpp},
+        "gpu_launches": nl,
+    }
+
+
 def run_ours(args):
     import torch
 
@@ -382,6 +436,12 @@ def run_ours(args):
             forms[form] = {"value": world * units / (fms / 1e3), "ms_per_step": fms, "steps": k,
                            "pole_ms": fprof[0][1] / max(fprof[1], 1)}
 
+    krylov = None
+    if not args.skip_krylov:
+        krylov = krylov_measure(torch, rexi, inputs, "fp64", args.krylov_terms, 1e-10)
+        krylov["roofline"]["peak"] = hbm_peak
+        krylov["roofline"]["frac"] = krylov["roofline"]["achieved"] / hbm_peak
+
     # CPU oracle on a bounded sample (rank 0, N = 1 only), also the accuracy check
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -402,7 +462,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32x2+f64" if args.form == "mixed" else "f64", "data": "synthetic",
             "config": cfg, "clocks": clocks, "e2e": e2e, "gpu_launches": nlaunch, "roofline": roofline,
-            "roofline_fft": roofline_fft, "phases_ms": phases, "forms": forms, "cpu_baseline": cpu,
+            "roofline_fft": roofline_fft, "phases_ms": phases, "forms": forms, "krylov": krylov,
+            "cpu_baseline": cpu,
             "accuracy": {"tolerance": 1e-8 if args.form == "mixed" else 1e-10,
                          "max_rel_err_vs_oracle_sampled": cpu["max_rel_err_vs_oracle"] if cpu else None},
         }
@@ -422,11 +483,24 @@ def main():
     ap.add_argument("--skip-forms", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-krylov", action="store_true")
+    ap.add_argument("--krylov-terms", type=int, default=8)
+    ap.add_argument("--krylov-only", action="store_true",
+                    help="run only the variable-depth measurement (profiling captures)")
     args = ap.parse_args()
     set_workload(args.grid, args.tau_rho)
     args.warmup = max(args.warmup, 3)  # timing rule: at least 3 untimed warm-up steps
     if args.impl == "reference":
         run_reference(args)
+    elif args.krylov_only:
+        import torch
+
+        from paper_2008_11607_gb300 import build as B
+
+        B.build()
+        from paper_2008_11607_gb300 import inputs, rexi
+
+        print(json.dumps(krylov_measure(torch, rexi, inputs, "fp64", args.krylov_terms, 1e-10)), flush=True)
     else:
         run_ours(args)
 

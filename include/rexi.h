@@ -78,6 +78,7 @@ typedef struct {
   int32_t krylov_iters;        /* Krylov path: largest iteration count over terms */
   int32_t krylov_unconverged;  /* Krylov path: terms that hit the iteration cap */
   double krylov_max_rel_res;   /* Krylov path: largest final relative residual */
+  int64_t krylov_term_iters;   /* Krylov path: CG iterations summed over all terms */
 } rexi_step_info;
 
 /* ------------------------------------------------------------------------ */
@@ -196,9 +197,11 @@ rexi_status rexi_workspace_size_host(rexi_plan_t plan, double dt, double tol, in
  * call records CUDA events on its own stream around its phases.
  * rexi_plan_read_profile waits for the recorded events, returns the summed
  * milliseconds per phase since the last read (ms[0] forward transform or
- * Krylov set-up, ms[1] the pole loop over all terms, ms[2] inverse
- * transform or final accumulation, ms[3] table upload), the number of
- * profiled calls and of kernels launched by them, then resets the sums. */
+ * Krylov set-up, ms[1] the pole loop over all terms (Krylov: the CG
+ * iterations), ms[2] inverse transform or final accumulation, ms[3] table
+ * upload), the number of profiled phase sets (one per call on the Fourier
+ * path, one per term batch on the Krylov path) and of kernels launched,
+ * then resets the sums. */
 rexi_status rexi_plan_set_profiling(rexi_plan_t plan, int32_t enable);
 rexi_status rexi_plan_read_profile(rexi_plan_t plan, double* ms4, int32_t* n_calls, int64_t* n_launches);
 

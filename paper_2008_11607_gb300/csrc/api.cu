@@ -593,8 +593,12 @@ rexi_status rexi_step(rexi_plan_t p, const void* in, void* out, double dt, doubl
   if (st != REXI_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (p->depth) {
+    KrylovHooks hooks;
+    hooks.mark = [](void* ctx, int i, cudaStream_t st) { prof_mark(static_cast<rexi_plan_s*>(ctx), i, st); };
+    hooks.ctx = p;
+    hooks.launches = &p->launches;
     st = krylov_step(&p->kry, p->form, p->h, M, in, out, dt, real_input, term_begin, term_end, ws, ws_bytes,
-                     s, info, false);
+                     s, info, false, hooks);
     if (info) { info->M = M; info->N = M + kL; info->tau_rho = dt * p->rho; info->rho = p->rho; }
     return st;
   }
@@ -612,7 +616,7 @@ rexi_status rexi_step_adjoint(rexi_plan_t p, const void* gout, void* gin, double
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (p->depth)
     return krylov_step(&p->kry, p->form, p->h, M, gout, gin, dt, real_input, 0, -1, ws, ws_bytes, s, nullptr,
-                       true);
+                       true, KrylovHooks());
   return fourier_step(p, gout, gin, dt, M, real_input, 0, -1, ws, ws_bytes, s, true);
 }
 

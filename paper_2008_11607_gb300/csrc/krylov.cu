@@ -407,7 +407,13 @@ size_t krylov_workspace_bytes(const KrylovSettings* k, int M, int real_input, in
 
 rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void* in, void* out, double dt,
                         int real_input, int term_begin, int term_end, void* ws, size_t ws_bytes, cudaStream_t s,
-                        rexi_step_info* info, bool adjoint) {
+                        rexi_step_info* info, bool adjoint, const KrylovHooks& hooks) {
+  auto mark = [&](int i) {
+    if (hooks.mark) hooks.mark(hooks.ctx, i, s);
+  };
+  auto count = [&](int64_t n) {
+    if (hooks.launches) *hooks.launches += n;
+  };
   if (form != REXI_FORM_FP64) {
     set_last_error("variable-depth path: only the FP64 form is available");
     return REXI_EUNSUPPORTED;
@@ -494,16 +500,21 @@ rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void
     }
   }
   int worst_iters = 0, unconverged = 0;
+  int64_t term_iters = 0;
   double worst_res = 0.0;
   const int check_every = 16;
   std::vector<TermScalars> hs(L.batch);
   for (size_t b0 = 0; b0 < terms.size(); b0 += L.batch) {
     const int nb = (int)std::min<size_t>(L.batch, terms.size() - b0);
+    mark(0);
     e = cudaMemcpyAsync(dsc, &terms[b0], nb * sizeof(TermScalars), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) break;
+    mark(1);
     dim3 grid(G.tiles_x, G.tiles_y, nb);
     cg_init<<<grid, THREADS, 0, s>>>(G, k->depth, src, real_input, X, R, P, vstride, dsc, partials, counters,
                                      k->rtol);
+    count(1);
+    mark(2);
     int it = 0;
     bool done = false;
     while (!done) {
@@ -512,6 +523,7 @@ rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void
         cg_update<<<grid, THREADS, 0, s>>>(G, k->depth, T, P, X, R, vstride, dsc, partials, counters, k->rtol,
                                            k->max_iters);
       }
+      count(2 * check_every);
       it += check_every;
       if ((e = cudaGetLastError()) != cudaSuccess) break;
       e = cudaMemcpyAsync(hs.data(), dsc, nb * sizeof(TermScalars), cudaMemcpyDeviceToHost, s);
@@ -523,14 +535,18 @@ rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void
       if (it > k->max_iters + check_every) done = true;  // the device caps every term at max_iters
     }
     if (e != cudaSuccess) break;
+    mark(3);
     for (int b = 0; b < nb; ++b) {
+      term_iters += hs[b].iters;
       worst_iters = std::max(worst_iters, hs[b].iters);
       if (hs[b].status != 1) ++unconverged;
       if (hs[b].gamma0 > 0) worst_res = std::max(worst_res, sqrt(hs[b].gamma / hs[b].gamma0));
     }
     dim3 g2(G.tiles_x, G.tiles_y, 1);
     cg_accumulate<<<g2, THREADS, 0, s>>>(G, k->depth, X, vstride, nb, dsc, acc, b0 == 0 ? 1 : 0);
+    count(1);
     if ((e = cudaGetLastError()) != cudaSuccess) break;
+    mark(4);
   }
   if (e != cudaSuccess) {
     set_last_error(cudaGetErrorString(e));
@@ -556,6 +572,7 @@ rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void
     info->krylov_iters = worst_iters;
     info->krylov_unconverged = unconverged;
     info->krylov_max_rel_res = worst_res;
+    info->krylov_term_iters = term_iters;
   }
   if (unconverged > 0) {
     set_last_error("variable-depth path: some terms reached the iteration cap");

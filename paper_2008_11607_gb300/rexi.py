@@ -36,6 +36,7 @@ class rexi_step_info(ctypes.Structure):
         ("krylov_iters", ctypes.c_int32),
         ("krylov_unconverged", ctypes.c_int32),
         ("krylov_max_rel_res", ctypes.c_double),
+        ("krylov_term_iters", ctypes.c_int64),
     ]
 
 
