@@ -25,10 +25,21 @@
 // in index order and updates the term's scalars.  The host polls the status
 // flags every few iterations.  A final kernel adds
 // Gamma_n (C1 x - C2 tau A x) over the batch into the FP64 accumulator.
+//
+// Forms.  FP64: every vector and stencil in FP64.  On this GPU the FP64 units
+// are the bottleneck of that form (one FP64 operation costs about as much
+// time as 11 bytes of HBM traffic), so the stencil constants are folded
+// (tau, 1/dx, g, f/4, the energy weight g/H) to keep FP64 work low.
+// MIXED: per term, iterative refinement in FP64 around an FP32 CG:
+//   x = 0, r = f;  repeat { solve N d = r in FP32 (complex64 vectors) to a
+//   loose relative residual;  x += d;  r = f - N x in FP64 }  until the FP64
+//   residual meets rtol.  The inner kernels move half the bytes of the FP64
+//   ones and their arithmetic is cheap, so they are bound by HBM bandwidth.
 #include <math.h>
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -51,32 +62,49 @@ struct TermScalars {
   int pad0, pad1;
 };
 
+// ---- complex arithmetic for float2 / double2 ------------------------------
+template <typename R> struct CT;
+template <> struct CT<double> { using T = double2; };
+template <> struct CT<float> { using T = float2; };
+template <typename R> using cplx = typename CT<R>::T;
+
+__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+template <typename R, typename V> __device__ __forceinline__ cplx<R> cvt(V v) { return mk((R)v.x, (R)v.y); }
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return mk(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+template <typename V> __device__ __forceinline__ auto cabs2(V a) -> decltype(a.x) { return fma(a.x, a.x, a.y * a.y); }
+
+// Stencil constants in precision R; tau is folded into every coefficient.
+template <typename R>
 struct Geom {
   int nx, ny, tiles_x, tiles_y;
-  double inv_dx, inv_dy, g, f, tau;
   size_t fstride;  // nx * ny
+  R tdx, tdy;      // tau / dx, tau / dy (times H per point in the eta row)
+  R tgdx, tgdy;    // tau g / dx, tau g / dy
+  R tf4;           // tau f / 4
+  const R* H;      // depth at eta points
+  const R* w;      // energy weight g / H
 };
 
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
-
-// Stencil of A at tile point (li, lj) of the shared arrays (with a halo of 1).
+// tau A at tile point (li, lj) of the shared arrays (halo of 1).
 // eta: -H (d_x^b u + d_y^b v);  u: -g d_x^f eta + f avg4(v);  v: -g d_y^f eta - f avg4(u)
-__device__ __forceinline__ void apply_A(const double2 (*E)[HX], const double2 (*U)[HX],
-                                        const double2 (*V)[HX], int li, int lj, double Hij,
-                                        const Geom& G, double2& ae, double2& au, double2& av) {
-  const double2 div = cadd(cscale(G.inv_dx, csub(U[lj][li], U[lj][li - 1])),
-                           cscale(G.inv_dy, csub(V[lj][li], V[lj - 1][li])));
-  ae = cscale(-Hij, div);
-  const double2 v4 = cadd(cadd(V[lj][li], V[lj][li + 1]), cadd(V[lj - 1][li], V[lj - 1][li + 1]));
-  au = cadd(cscale(-G.g * G.inv_dx, csub(E[lj][li + 1], E[lj][li])), cscale(0.25 * G.f, v4));
-  const double2 u4 = cadd(cadd(U[lj][li], U[lj][li - 1]), cadd(U[lj + 1][li], U[lj + 1][li - 1]));
-  av = csub(cscale(-G.g * G.inv_dy, csub(E[lj + 1][li], E[lj][li])), cscale(0.25 * G.f, u4));
+template <typename R>
+__device__ __forceinline__ void apply_tA(const cplx<R> (*E)[HX], const cplx<R> (*U)[HX], const cplx<R> (*V)[HX],
+                                         int li, int lj, R Hij, const Geom<R>& G, cplx<R>& ae, cplx<R>& au,
+                                         cplx<R>& av) {
+  const R hx = -Hij * G.tdx, hy = -Hij * G.tdy;
+  const cplx<R> du = csub(U[lj][li], U[lj][li - 1]), dv = csub(V[lj][li], V[lj - 1][li]);
+  ae = mk(fma(hx, du.x, hy * dv.x), fma(hx, du.y, hy * dv.y));
+  const cplx<R> v4 = cadd(cadd(V[lj][li], V[lj][li + 1]), cadd(V[lj - 1][li], V[lj - 1][li + 1]));
+  const cplx<R> de = csub(E[lj][li + 1], E[lj][li]);
+  au = mk(fma(G.tf4, v4.x, -G.tgdx * de.x), fma(G.tf4, v4.y, -G.tgdx * de.y));
+  const cplx<R> u4 = cadd(cadd(U[lj][li], U[lj][li - 1]), cadd(U[lj + 1][li], U[lj + 1][li - 1]));
+  const cplx<R> dn = csub(E[lj + 1][li], E[lj][li]);
+  av = mk(fma(-G.tf4, u4.x, -G.tgdy * dn.x), fma(-G.tf4, u4.y, -G.tgdy * dn.y));
 }
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -93,8 +121,8 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 // Last-block reduction over the tiles of one term.  Returns true in thread 0
 // of the last block, with *total the sum of all partials in index order.
-__device__ __forceinline__ bool last_block_total(double mine, double* partials, unsigned* counter,
-                                                 int ntiles, int tile, double* total) {
+__device__ __forceinline__ bool last_block_total(double mine, double* partials, unsigned* counter, int ntiles,
+                                                 int tile, double* total) {
   __shared__ bool is_last;
   if (threadIdx.x == 0) {
     partials[tile] = mine;
@@ -115,40 +143,80 @@ __device__ __forceinline__ bool last_block_total(double mine, double* partials, 
   return threadIdx.x == 0;
 }
 
-__device__ __forceinline__ size_t gidx(const Geom& G, int i, int j) {
+template <typename R>
+__device__ __forceinline__ size_t gidx(const Geom<R>& G, int i, int j) {
   i = (i + G.nx) % G.nx;
   j = (j + G.ny) % G.ny;
   return (size_t)j * G.nx + i;
 }
 
-// --- initialisation: x = 0, r = f (real part only for real input), p = 0, gamma0 = ||f||_W^2
-__global__ void __launch_bounds__(THREADS) cg_init(Geom G, const double* __restrict__ H,
-                                                   const double2* __restrict__ f, int real_input,
-                                                   double2* x, double2* r, double2* p, size_t vstride,
-                                                   TermScalars* sc, double* partials, unsigned* counters,
-                                                   double rtol) {
+// Loads a + beta b (3 fields, converted to precision R) on the tile plus halo.
+template <typename R, bool COMBINE, typename VA, typename VB>
+__device__ __forceinline__ void load_tile(const Geom<R>& G, const VA* a, const VB* b, R beta, cplx<R> (*E)[HX],
+                                          cplx<R> (*U)[HX], cplx<R> (*V)[HX]) {
+  const int i0 = blockIdx.x * TX - 1, j0 = blockIdx.y * TY - 1;
+  for (int k = threadIdx.x; k < HX * HY; k += THREADS) {
+    const int li = k % HX, lj = k / HX;
+    const size_t id = gidx(G, i0 + li, j0 + lj);
+    cplx<R> f3[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      cplx<R> v = cvt<R>(a[id + c * G.fstride]);
+      if (COMBINE) {
+        const cplx<R> q = cvt<R>(b[id + c * G.fstride]);
+        v = mk(fma(beta, q.x, v.x), fma(beta, q.y, v.y));
+      }
+      f3[c] = v;
+    }
+    E[lj][li] = f3[0];
+    U[lj][li] = f3[1];
+    V[lj][li] = f3[2];
+  }
+  __syncthreads();
+}
+
+// ---- kernels -----------------------------------------------------------------
+
+// x = 0, r = f (real part only for real input), p = 0, gamma0 = ||f||_W^2.
+// With `outer`, terms whose outer (refinement) status is not active are
+// marked done at once.
+template <typename R, typename VF>
+__global__ void __launch_bounds__(THREADS) cg_init(Geom<R> G, const VF* __restrict__ f, int real_input,
+                                                   cplx<R>* x, cplx<R>* r, cplx<R>* p, size_t vstride,
+                                                   size_t fterm_stride, TermScalars* sc, const TermScalars* outer,
+                                                   double* partials, unsigned* counters) {
   __shared__ double red[THREADS / 32];
   const int term = blockIdx.z;
+  if (outer && outer[term].status != 0) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+      sc[term].status = 1;
+      sc[term].iters = 0;
+    }
+    return;
+  }
   const int tile = blockIdx.y * G.tiles_x + blockIdx.x;
   const int ntiles = G.tiles_x * G.tiles_y;
-  double2* xb = x + (size_t)term * vstride;
-  double2* rb = r + (size_t)term * vstride;
-  double2* pb = p + (size_t)term * vstride;
+  cplx<R>* xb = x + (size_t)term * vstride;
+  cplx<R>* rb = r + (size_t)term * vstride;
+  cplx<R>* pb = p + (size_t)term * vstride;
+  const VF* fb = f + (size_t)term * fterm_stride;
+  const cplx<R> zero = mk((R)0, (R)0);
   double loc = 0.0;
   for (int k = threadIdx.x; k < TX * TY; k += THREADS) {
     const int i = blockIdx.x * TX + (k % TX), j = blockIdx.y * TY + (k / TX);
     if (i >= G.nx || j >= G.ny) continue;
     const size_t id = (size_t)j * G.nx + i;
-    const double w0 = G.g / H[id];
+    R acc = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      double2 v = f[id + c * G.fstride];
-      if (real_input) v.y = 0.0;
+      cplx<R> v = cvt<R>(fb[id + c * G.fstride]);
+      if (real_input) v.y = 0;
       rb[id + c * G.fstride] = v;
-      xb[id + c * G.fstride] = make_double2(0.0, 0.0);
-      pb[id + c * G.fstride] = make_double2(0.0, 0.0);
-      loc += (c == 0 ? w0 : 1.0) * cabs2(v);
+      xb[id + c * G.fstride] = zero;
+      pb[id + c * G.fstride] = zero;
+      acc += (c == 0 ? G.w[id] : (R)1) * cabs2(v);
     }
+    loc += (double)acc;
   }
   const double s = block_sum(loc, red);
   double tot;
@@ -163,62 +231,40 @@ __global__ void __launch_bounds__(THREADS) cg_init(Geom G, const double* __restr
   }
 }
 
-// Loads p_new = r + beta p (3 fields) on the tile plus halo into shared memory.
-template <bool UPDATE_P>
-__device__ __forceinline__ void load_tile(const Geom& G, const double2* a, const double2* b, double beta,
-                                          double2 (*E)[HX], double2 (*U)[HX], double2 (*V)[HX]) {
-  const int i0 = blockIdx.x * TX - 1, j0 = blockIdx.y * TY - 1;
-  for (int k = threadIdx.x; k < HX * HY; k += THREADS) {
-    const int li = k % HX, lj = k / HX;
-    const size_t id = gidx(G, i0 + li, j0 + lj);
-    double2 e = a[id], u = a[id + G.fstride], v = a[id + 2 * G.fstride];
-    if (UPDATE_P) {
-      const double2 pe = b[id], pu = b[id + G.fstride], pv = b[id + 2 * G.fstride];
-      e = make_double2(fma(beta, pe.x, e.x), fma(beta, pe.y, e.y));
-      u = make_double2(fma(beta, pu.x, u.x), fma(beta, pu.y, u.y));
-      v = make_double2(fma(beta, pv.x, v.x), fma(beta, pv.y, v.y));
-    }
-    E[lj][li] = e;
-    U[lj][li] = u;
-    V[lj][li] = v;
-  }
-  __syncthreads();
-}
-
-// t <- alpha_n p' + tau A p' with p' = r + beta p formed on the fly (p itself
-// is not written here: neighbouring tiles read p in their halo);
-// dot1 = ||t||_W^2 ; a = gamma / dot1
-__global__ void __launch_bounds__(THREADS) cg_apply_B(Geom G, const double* __restrict__ H, const double2* p,
-                                                      const double2* r, double2* t, size_t vstride,
-                                                      TermScalars* sc, double* partials, unsigned* counters) {
-  __shared__ double2 E[HY][HX], U[HY][HX], V[HY][HX];
+// t <- alpha_n p' + tau A p' with p' = a + beta b formed on the fly (nothing
+// that a neighbouring tile reads is written here); dot1 = ||t||_W^2 and
+// a = gamma / dot1.  beta is the term's CG beta, or 1 when unit_beta is set
+// (the refinement step t = B (x + d)).
+template <typename R, typename VA, typename VB>
+__global__ void __launch_bounds__(THREADS) cg_apply_B(Geom<R> G, const VA* a, const VB* b, cplx<R>* t,
+                                                      size_t vstride, size_t bstride, TermScalars* sc,
+                                                      double* partials, unsigned* counters, int unit_beta) {
+  __shared__ cplx<R> E[HY][HX], U[HY][HX], V[HY][HX];
   __shared__ double red[THREADS / 32];
   const int term = blockIdx.z;
   TermScalars& S = sc[term];
   if (S.status != 0) return;
   const int tile = blockIdx.y * G.tiles_x + blockIdx.x;
   const int ntiles = G.tiles_x * G.tiles_y;
-  const double2* pb = p + (size_t)term * vstride;
-  const double2* rb = r + (size_t)term * vstride;
-  double2* tb = t + (size_t)term * vstride;
-  load_tile<true>(G, rb, pb, S.beta, E, U, V);
-  const double2 al = S.alpha_n;
+  load_tile<R, true>(G, a + (size_t)term * vstride, b + (size_t)term * bstride, unit_beta ? (R)1 : (R)S.beta, E,
+                     U, V);
+  cplx<R>* tb = t + (size_t)term * vstride;
+  const cplx<R> al = cvt<R>(S.alpha_n);
   double loc = 0.0;
   for (int k = threadIdx.x; k < TX * TY; k += THREADS) {
     const int li = k % TX + 1, lj = k / TX + 1;
     const int i = blockIdx.x * TX + li - 1, j = blockIdx.y * TY + lj - 1;
     if (i >= G.nx || j >= G.ny) continue;
     const size_t id = (size_t)j * G.nx + i;
-    const double Hij = H[id];
-    double2 ae, au, av;
-    apply_A(E, U, V, li, lj, Hij, G, ae, au, av);
-    const double2 te = cadd(cmul(al, E[lj][li]), cscale(G.tau, ae));
-    const double2 tu = cadd(cmul(al, U[lj][li]), cscale(G.tau, au));
-    const double2 tv = cadd(cmul(al, V[lj][li]), cscale(G.tau, av));
+    cplx<R> ae, au, av;
+    apply_tA<R>(E, U, V, li, lj, G.H[id], G, ae, au, av);
+    const cplx<R> te = cadd(cmul(al, E[lj][li]), ae);
+    const cplx<R> tu = cadd(cmul(al, U[lj][li]), au);
+    const cplx<R> tv = cadd(cmul(al, V[lj][li]), av);
     tb[id] = te;
     tb[id + G.fstride] = tu;
     tb[id + 2 * G.fstride] = tv;
-    loc += (G.g / Hij) * cabs2(te) + cabs2(tu) + cabs2(tv);
+    loc += (double)(G.w[id] * cabs2(te) + cabs2(tu) + cabs2(tv));
   }
   const double s = block_sum(loc, red);
   double tot;
@@ -230,50 +276,47 @@ __global__ void __launch_bounds__(THREADS) cg_apply_B(Geom G, const double* __re
 
 // q = alpha_{-n} t - tau A t ; p <- r + beta p ; x += a p ; r -= a q ;
 // gamma_new = ||r||_W^2 ; convergence.  Only t is read across tile borders.
-__global__ void __launch_bounds__(THREADS) cg_update(Geom G, const double* __restrict__ H, const double2* t,
-                                                     double2* p, double2* x, double2* r, size_t vstride,
-                                                     TermScalars* sc, double* partials, unsigned* counters,
-                                                     double rtol, int max_iters) {
-  __shared__ double2 E[HY][HX], U[HY][HX], V[HY][HX];
+template <typename R>
+__global__ void __launch_bounds__(THREADS) cg_update(Geom<R> G, const cplx<R>* t, cplx<R>* p, cplx<R>* x,
+                                                     cplx<R>* r, size_t vstride, TermScalars* sc, double* partials,
+                                                     unsigned* counters, double rtol, int max_iters) {
+  __shared__ cplx<R> E[HY][HX], U[HY][HX], V[HY][HX];
   __shared__ double red[THREADS / 32];
   const int term = blockIdx.z;
   TermScalars& S = sc[term];
   if (S.status != 0) return;
   const int tile = blockIdx.y * G.tiles_x + blockIdx.x;
   const int ntiles = G.tiles_x * G.tiles_y;
-  const double2* tb = t + (size_t)term * vstride;
-  double2* pb = p + (size_t)term * vstride;
-  double2* xb = x + (size_t)term * vstride;
-  double2* rb = r + (size_t)term * vstride;
-  load_tile<false>(G, tb, nullptr, 0.0, E, U, V);
-  const double2 am = S.alpha_mn;
-  const double a = S.a;
-  const double beta = S.beta;
+  load_tile<R, false>(G, t + (size_t)term * vstride, (const cplx<R>*)nullptr, (R)0, E, U, V);
+  cplx<R>* pb = p + (size_t)term * vstride;
+  cplx<R>* xb = x + (size_t)term * vstride;
+  cplx<R>* rb = r + (size_t)term * vstride;
+  const cplx<R> am = cvt<R>(S.alpha_mn);
+  const R a = (R)S.a, beta = (R)S.beta;
   double loc = 0.0;
   for (int k = threadIdx.x; k < TX * TY; k += THREADS) {
     const int li = k % TX + 1, lj = k / TX + 1;
     const int i = blockIdx.x * TX + li - 1, j = blockIdx.y * TY + lj - 1;
     if (i >= G.nx || j >= G.ny) continue;
     const size_t id = (size_t)j * G.nx + i;
-    const double Hij = H[id];
-    double2 ae, au, av;
-    apply_A(E, U, V, li, lj, Hij, G, ae, au, av);
-    const double2 q[3] = {csub(cmul(am, E[lj][li]), cscale(G.tau, ae)),
-                          csub(cmul(am, U[lj][li]), cscale(G.tau, au)),
-                          csub(cmul(am, V[lj][li]), cscale(G.tau, av))};
+    cplx<R> ae, au, av;
+    apply_tA<R>(E, U, V, li, lj, G.H[id], G, ae, au, av);
+    const cplx<R> q[3] = {csub(cmul(am, E[lj][li]), ae), csub(cmul(am, U[lj][li]), au),
+                          csub(cmul(am, V[lj][li]), av)};
+    R acc = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const size_t o = id + c * G.fstride;
-      double2 xv = xb[o], rv = rb[o];
-      double2 pv = pb[o];
-      pv = make_double2(fma(beta, pv.x, rv.x), fma(beta, pv.y, rv.y));
+      cplx<R> xv = xb[o], rv = rb[o], pv = pb[o];
+      pv = mk(fma(beta, pv.x, rv.x), fma(beta, pv.y, rv.y));
       pb[o] = pv;
-      xv = make_double2(fma(a, pv.x, xv.x), fma(a, pv.y, xv.y));
-      rv = make_double2(fma(-a, q[c].x, rv.x), fma(-a, q[c].y, rv.y));
+      xv = mk(fma(a, pv.x, xv.x), fma(a, pv.y, xv.y));
+      rv = mk(fma(-a, q[c].x, rv.x), fma(-a, q[c].y, rv.y));
       xb[o] = xv;
       rb[o] = rv;
-      loc += (c == 0 ? G.g / Hij : 1.0) * cabs2(rv);
+      acc += (c == 0 ? G.w[id] : (R)1) * cabs2(rv);
     }
+    loc += (double)acc;
   }
   const double s = block_sum(loc, red);
   double tot;
@@ -288,29 +331,82 @@ __global__ void __launch_bounds__(THREADS) cg_update(Geom G, const double* __res
   }
 }
 
+// Refinement (FP64): x += d (pointwise) and r = f - B^* t with t = B (x + d);
+// gamma = ||r||_W^2 ; outer convergence against gamma0 = ||f||_W^2.
+__global__ void __launch_bounds__(THREADS) refine_residual(Geom<double> G, const double2* __restrict__ f,
+                                                           int real_input, const double2* t, const float2* d,
+                                                           double2* x, double2* r, size_t vstride, size_t dstride,
+                                                           TermScalars* sc, double* partials, unsigned* counters,
+                                                           double rtol, int max_outer) {
+  __shared__ double2 E[HY][HX], U[HY][HX], V[HY][HX];
+  __shared__ double red[THREADS / 32];
+  const int term = blockIdx.z;
+  TermScalars& S = sc[term];
+  if (S.status != 0) return;
+  const int tile = blockIdx.y * G.tiles_x + blockIdx.x;
+  const int ntiles = G.tiles_x * G.tiles_y;
+  load_tile<double, false>(G, t + (size_t)term * vstride, (const double2*)nullptr, 0.0, E, U, V);
+  double2* xb = x + (size_t)term * vstride;
+  double2* rb = r + (size_t)term * vstride;
+  const float2* db = d + (size_t)term * dstride;
+  const double2 am = S.alpha_mn;
+  double loc = 0.0;
+  for (int k = threadIdx.x; k < TX * TY; k += THREADS) {
+    const int li = k % TX + 1, lj = k / TX + 1;
+    const int i = blockIdx.x * TX + li - 1, j = blockIdx.y * TY + lj - 1;
+    if (i >= G.nx || j >= G.ny) continue;
+    const size_t id = (size_t)j * G.nx + i;
+    double2 ae, au, av;
+    apply_tA<double>(E, U, V, li, lj, G.H[id], G, ae, au, av);
+    const double2 q[3] = {csub(cmul(am, E[lj][li]), ae), csub(cmul(am, U[lj][li]), au),
+                          csub(cmul(am, V[lj][li]), av)};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t o = id + c * G.fstride;
+      const float2 dv = db[o];
+      const double2 xv = xb[o];
+      xb[o] = mk(xv.x + (double)dv.x, xv.y + (double)dv.y);
+      double2 fv = f[o];
+      if (real_input) fv.y = 0.0;
+      const double2 rv = csub(fv, q[c]);
+      rb[o] = rv;
+      loc += (c == 0 ? G.w[id] : 1.0) * cabs2(rv);
+    }
+  }
+  const double s = block_sum(loc, red);
+  double tot;
+  if (last_block_total(s, partials + (size_t)term * ntiles, counters + term, ntiles, tile, &tot)) {
+    S.gamma = tot;
+    S.iters += 1;  // refinement steps
+    if (tot <= rtol * rtol * S.gamma0)
+      S.status = 1;
+    else if (S.iters >= max_outer)
+      S.status = 2;
+  }
+}
+
 // acc += sum over the batch of Gamma_n (C1 x - C2 tau A x), batch order fixed.
-__global__ void __launch_bounds__(THREADS) cg_accumulate(Geom G, const double* __restrict__ H,
-                                                         const double2* x, size_t vstride, int nbatch,
-                                                         const TermScalars* sc, double2* acc, int first) {
+__global__ void __launch_bounds__(THREADS) cg_accumulate(Geom<double> G, const double2* x, size_t vstride,
+                                                         int nbatch, const TermScalars* sc, double2* acc,
+                                                         int first) {
   __shared__ double2 E[HY][HX], U[HY][HX], V[HY][HX];
   double2 s[2][3];
   for (int q = 0; q < 2; ++q)
     for (int c = 0; c < 3; ++c) s[q][c] = make_double2(0.0, 0.0);
   for (int b = 0; b < nbatch; ++b) {
     __syncthreads();
-    load_tile<false>(G, x + (size_t)b * vstride, nullptr, 0.0, E, U, V);
+    load_tile<double, false>(G, x + (size_t)b * vstride, (const double2*)nullptr, 0.0, E, U, V);
     const double2 c1 = sc[b].gC1, c2 = sc[b].gC2;
     int q = 0;
     for (int k = threadIdx.x; k < TX * TY; k += THREADS, ++q) {
       const int li = k % TX + 1, lj = k / TX + 1;
       const int i = blockIdx.x * TX + li - 1, j = blockIdx.y * TY + lj - 1;
       if (i >= G.nx || j >= G.ny) continue;
-      const double Hij = H[(size_t)j * G.nx + i];
       double2 ae, au, av;
-      apply_A(E, U, V, li, lj, Hij, G, ae, au, av);
-      s[q][0] = cadd(s[q][0], csub(cmul(c1, E[lj][li]), cmul(c2, cscale(G.tau, ae))));
-      s[q][1] = cadd(s[q][1], csub(cmul(c1, U[lj][li]), cmul(c2, cscale(G.tau, au))));
-      s[q][2] = cadd(s[q][2], csub(cmul(c1, V[lj][li]), cmul(c2, cscale(G.tau, av))));
+      apply_tA<double>(E, U, V, li, lj, G.H[(size_t)j * G.nx + i], G, ae, au, av);
+      s[q][0] = cadd(s[q][0], csub(cmul(c1, E[lj][li]), cmul(c2, ae)));
+      s[q][1] = cadd(s[q][1], csub(cmul(c1, U[lj][li]), cmul(c2, au)));
+      s[q][2] = cadd(s[q][2], csub(cmul(c1, V[lj][li]), cmul(c2, av)));
     }
   }
   int q = 0;
@@ -333,48 +429,65 @@ __global__ void finish_output(const double2* acc, double2* out, size_t n3, int r
   out[i] = v;
 }
 
-// Diagonal scaling used by the adjoint: out_eta = s * in_eta * (H / g)^e, others copied.
-__global__ void scale_eta(const double2* in, double2* out, const double* H, size_t nk, double g, int inverse,
-                          int real_in) {
+// Energy-weight scaling used by the adjoint: eta *= w (inverse: eta /= w).
+__global__ void scale_eta(const double2* in, double2* out, const double* w, size_t nk, int inverse, int real_in) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 3 * nk) return;
   double2 v = in[i];
   if (real_in) v.y = 0.0;
   if (i < nk) {
-    const double w = g / H[i];  // energy weight of eta
-    const double s = inverse ? 1.0 / w : w;
+    const double s = inverse ? 1.0 / w[i] : w[i];
     v.x *= s;
     v.y *= s;
   }
   out[i] = v;
 }
 
+__global__ void depth_tables(const double* H, size_t nk, double g, double* w64, float* H32, float* w32) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nk) return;
+  const double w = g / H[i];
+  w64[i] = w;
+  H32[i] = (float)H[i];
+  w32[i] = (float)w;
+}
+
+// ---- workspace layout ------------------------------------------------------
+
 struct KLayout {
-  size_t acc_off, vec_off, vec_bytes, sc_off, part_off, cnt_off, tmp_off, total;
+  size_t acc_off, tmp_off, total;
+  size_t v64_off, v64_bytes;  // FP64 vectors per term: x, r, p, t
+  size_t v32_off, v32_bytes;  // FP32 vectors per term (mixed): d, r, p, t
+  size_t sc_off, sc32_off, part_off, cnt_off;
   int batch, ntiles;
 };
 
-KLayout layout(const KrylovSettings* k, int nterms, bool adjoint) {
+size_t al256(size_t v) { return (v + 255) / 256 * 256; }
+
+KLayout layout(const KrylovSettings* k, int nterms, int form) {
   KLayout L{};
   const size_t nk = (size_t)k->nx * k->ny;
-  const size_t state = 3 * nk * sizeof(double2);
-  auto al = [](size_t v) { return (v + 255) / 256 * 256; };
   L.batch = std::max(1, std::min(k->term_batch, nterms));
   L.ntiles = ((k->nx + TX - 1) / TX) * ((k->ny + TY - 1) / TY);
   size_t off = 0;
   L.acc_off = off;
-  off += al(state);
+  off += al256(3 * nk * sizeof(double2));
   L.tmp_off = off;  // adjoint: scaled input
-  if (adjoint) off += al(state);
-  L.vec_off = off;
-  L.vec_bytes = al(state);
-  off += 4 * (size_t)L.batch * L.vec_bytes;  // x, r, p, t per term
+  off += al256(3 * nk * sizeof(double2));
+  L.v64_off = off;
+  L.v64_bytes = al256(3 * nk * sizeof(double2));
+  off += 4 * (size_t)L.batch * L.v64_bytes;
+  L.v32_off = off;
+  L.v32_bytes = al256(3 * nk * sizeof(float2));
+  if (form == REXI_FORM_MIXED) off += 4 * (size_t)L.batch * L.v32_bytes;
   L.sc_off = off;
-  off += al((size_t)L.batch * sizeof(TermScalars));
+  off += al256((size_t)L.batch * sizeof(TermScalars));
+  L.sc32_off = off;
+  off += al256((size_t)L.batch * sizeof(TermScalars));
   L.part_off = off;
-  off += al((size_t)L.batch * L.ntiles * sizeof(double));
+  off += al256((size_t)L.batch * L.ntiles * sizeof(double));
   L.cnt_off = off;
-  off += al((size_t)L.batch * sizeof(unsigned));
+  off += al256((size_t)L.batch * sizeof(unsigned));
   L.total = off;
   return L;
 }
@@ -382,6 +495,25 @@ KLayout layout(const KrylovSettings* k, int nterms, bool adjoint) {
 int n_terms_for(int M, int real_input) {
   const int N = M + kL;
   return real_input ? N + 1 : 2 * N + 1;
+}
+
+template <typename R>
+Geom<R> make_geom(const KrylovSettings* k, double tau, const R* H, const R* w) {
+  Geom<R> G;
+  G.nx = k->nx;
+  G.ny = k->ny;
+  G.tiles_x = (k->nx + TX - 1) / TX;
+  G.tiles_y = (k->ny + TY - 1) / TY;
+  G.fstride = (size_t)k->nx * k->ny;
+  const double idx = k->nx / k->Lx, idy = k->ny / k->Ly;
+  G.tdx = (R)(tau * idx);
+  G.tdy = (R)(tau * idy);
+  G.tgdx = (R)(tau * k->g * idx);
+  G.tgdy = (R)(tau * k->g * idy);
+  G.tf4 = (R)(0.25 * tau * k->f);
+  G.H = H;
+  G.w = w;
+  return G;
 }
 
 }  // namespace
@@ -396,13 +528,32 @@ rexi_status krylov_init(KrylovSettings* k, int nx, int ny, double Lx, double Ly,
   k->f = f;
   k->depth = depth;
   k->Hmean = Hmean;
+  const size_t nk = (size_t)nx * ny;
+  char* mem = nullptr;
+  const size_t bytes = al256(nk * sizeof(double)) + 2 * al256(nk * sizeof(float));
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+    set_last_error("cudaMalloc of the depth tables failed");
+    return REXI_ENOMEM;
+  }
+  k->dev_state = mem;
+  k->w64 = reinterpret_cast<double*>(mem);
+  k->H32 = reinterpret_cast<float*>(mem + al256(nk * sizeof(double)));
+  k->w32 = reinterpret_cast<float*>(mem + al256(nk * sizeof(double)) + al256(nk * sizeof(float)));
+  depth_tables<<<(unsigned)((nk + 255) / 256), 256>>>(depth, nk, g, k->w64, k->H32, k->w32);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    set_last_error("depth table kernel failed");
+    return REXI_ECUDA;
+  }
   return REXI_OK;
 }
 
-void krylov_destroy(KrylovSettings*) {}
+void krylov_destroy(KrylovSettings* k) {
+  if (k->dev_state) cudaFree(k->dev_state);
+  k->dev_state = nullptr;
+}
 
-size_t krylov_workspace_bytes(const KrylovSettings* k, int M, int real_input, int /*form*/) {
-  return layout(k, n_terms_for(M, real_input), true).total;
+size_t krylov_workspace_bytes(const KrylovSettings* k, int M, int real_input, int form) {
+  return layout(k, n_terms_for(M, real_input), form).total;
 }
 
 rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void* in, void* out, double dt,
@@ -414,10 +565,11 @@ rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void
   auto count = [&](int64_t n) {
     if (hooks.launches) *hooks.launches += n;
   };
-  if (form != REXI_FORM_FP64) {
-    set_last_error("variable-depth path: only the FP64 form is available");
+  if (form != REXI_FORM_FP64 && form != REXI_FORM_MIXED) {
+    set_last_error("variable-depth path: the plain form is Fourier-path only");
     return REXI_EUNSUPPORTED;
   }
+  const bool mixed = form == REXI_FORM_MIXED;
   const int N = M + kL;
   if (term_end < 0 || term_end > N + 1) term_end = N + 1;
   if (term_begin < 0 || term_begin > term_end) {
@@ -450,35 +602,32 @@ rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void
     t.gC2 = make_double2(-gam * ts.c2im[i], gam * ts.c2re[i]);
     terms.push_back(t);
   }
-  const KLayout L = layout(k, (int)std::max<size_t>(terms.size(), 1), adjoint);
+  const KLayout L = layout(k, (int)std::max<size_t>(terms.size(), 1), form);
   if (ws_bytes < L.total) {
     set_last_error("workspace too small for the variable-depth path");
     return REXI_ENOMEM;
   }
   char* base = static_cast<char*>(ws);
   double2* acc = reinterpret_cast<double2*>(base + L.acc_off);
-  double2* vecs = reinterpret_cast<double2*>(base + L.vec_off);
-  const size_t vstride = L.vec_bytes / sizeof(double2);
-  double2* X = vecs;
-  double2* R = vecs + (size_t)L.batch * vstride;
-  double2* P = vecs + 2 * (size_t)L.batch * vstride;
-  double2* T = vecs + 3 * (size_t)L.batch * vstride;
+  const size_t vs64 = L.v64_bytes / sizeof(double2);
+  double2* X = reinterpret_cast<double2*>(base + L.v64_off);
+  double2* R = X + (size_t)L.batch * vs64;
+  double2* P = X + 2 * (size_t)L.batch * vs64;
+  double2* T = X + 3 * (size_t)L.batch * vs64;
+  const size_t vs32 = L.v32_bytes / sizeof(float2);
+  float2* D32 = reinterpret_cast<float2*>(base + L.v32_off);
+  float2* R32 = D32 + (size_t)L.batch * vs32;
+  float2* P32 = D32 + 2 * (size_t)L.batch * vs32;
+  float2* T32 = D32 + 3 * (size_t)L.batch * vs32;
   TermScalars* dsc = reinterpret_cast<TermScalars*>(base + L.sc_off);
+  TermScalars* dsc32 = reinterpret_cast<TermScalars*>(base + L.sc32_off);
   double* partials = reinterpret_cast<double*>(base + L.part_off);
   unsigned* counters = reinterpret_cast<unsigned*>(base + L.cnt_off);
 
-  Geom G;
-  G.nx = k->nx;
-  G.ny = k->ny;
-  G.tiles_x = (k->nx + TX - 1) / TX;
-  G.tiles_y = (k->ny + TY - 1) / TY;
-  G.inv_dx = k->nx / k->Lx;
-  G.inv_dy = k->ny / k->Ly;
-  G.g = k->g;
-  G.f = k->f;
   // adjoint: r(tau A)^H = r(tau A^T) = W r(-tau A) W^{-1} with W = diag(g/H, 1, 1)
-  G.tau = adjoint ? -dt : dt;
-  G.fstride = nk;
+  const double tau = adjoint ? -dt : dt;
+  const Geom<double> G = make_geom<double>(k, tau, k->depth, k->w64);
+  const Geom<float> G32 = make_geom<float>(k, tau, k->H32, k->w32);
 
   const double2* src = static_cast<const double2*>(in);
   cudaError_t e;
@@ -486,7 +635,8 @@ rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void
   const unsigned ebl = (unsigned)((n3 + eb - 1) / eb);
   if (adjoint) {
     double2* tmp = reinterpret_cast<double2*>(base + L.tmp_off);
-    scale_eta<<<ebl, eb, 0, s>>>(src, tmp, k->depth, nk, k->g, 1, real_input);
+    scale_eta<<<ebl, eb, 0, s>>>(src, tmp, k->w64, nk, 1, real_input);
+    count(1);
     src = tmp;
   }
   if ((e = cudaMemsetAsync(counters, 0, (size_t)L.batch * sizeof(unsigned), s)) != cudaSuccess) {
@@ -503,47 +653,82 @@ rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void
   int64_t term_iters = 0;
   double worst_res = 0.0;
   const int check_every = 16;
-  std::vector<TermScalars> hs(L.batch);
+  std::vector<TermScalars> hs(L.batch), hs32(L.batch);
+
+  // CG iterations on (sc, vectors) until every term of the batch has stopped
+  auto run_cg = [&](const auto& geom, auto* Xv, auto* Rv, auto* Pv, auto* Tv, size_t vs, TermScalars* sc, int nb,
+                    double rtol, std::vector<TermScalars>& host) -> cudaError_t {
+    using Rt = typename std::remove_const<decltype(geom.tdx)>::type;
+    dim3 grid(geom.tiles_x, geom.tiles_y, nb);
+    int it = 0;
+    for (;;) {
+      for (int c = 0; c < check_every; ++c) {
+        cg_apply_B<Rt><<<grid, THREADS, 0, s>>>(geom, Rv, Pv, Tv, vs, vs, sc, partials, counters, 0);
+        cg_update<Rt><<<grid, THREADS, 0, s>>>(geom, Tv, Pv, Xv, Rv, vs, sc, partials, counters, rtol,
+                                               k->max_iters);
+      }
+      count(2 * check_every);
+      it += check_every;
+      cudaError_t err = cudaGetLastError();
+      if (err == cudaSuccess)
+        err = cudaMemcpyAsync(host.data(), sc, nb * sizeof(TermScalars), cudaMemcpyDeviceToHost, s);
+      if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+      if (err != cudaSuccess) return err;
+      bool done = true;
+      for (int b = 0; b < nb; ++b)
+        if (host[b].status == 0) done = false;
+      if (done || it > k->max_iters + check_every) break;
+    }
+    for (int b = 0; b < nb; ++b) term_iters += host[b].iters;
+    return cudaSuccess;
+  };
+
   for (size_t b0 = 0; b0 < terms.size(); b0 += L.batch) {
     const int nb = (int)std::min<size_t>(L.batch, terms.size() - b0);
     mark(0);
     e = cudaMemcpyAsync(dsc, &terms[b0], nb * sizeof(TermScalars), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dsc32, &terms[b0], nb * sizeof(TermScalars), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) break;
     mark(1);
     dim3 grid(G.tiles_x, G.tiles_y, nb);
-    cg_init<<<grid, THREADS, 0, s>>>(G, k->depth, src, real_input, X, R, P, vstride, dsc, partials, counters,
-                                     k->rtol);
+    cg_init<double, double2><<<grid, THREADS, 0, s>>>(G, src, real_input, X, R, P, vs64, 0, dsc, nullptr,
+                                                      partials, counters);
     count(1);
     mark(2);
-    int it = 0;
-    bool done = false;
-    while (!done) {
-      for (int c = 0; c < check_every; ++c) {
-        cg_apply_B<<<grid, THREADS, 0, s>>>(G, k->depth, P, R, T, vstride, dsc, partials, counters);
-        cg_update<<<grid, THREADS, 0, s>>>(G, k->depth, T, P, X, R, vstride, dsc, partials, counters, k->rtol,
-                                           k->max_iters);
-      }
-      count(2 * check_every);
-      it += check_every;
-      if ((e = cudaGetLastError()) != cudaSuccess) break;
-      e = cudaMemcpyAsync(hs.data(), dsc, nb * sizeof(TermScalars), cudaMemcpyDeviceToHost, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (!mixed) {
+      e = run_cg(G, X, R, P, T, vs64, dsc, nb, k->rtol, hs);
       if (e != cudaSuccess) break;
-      done = true;
-      for (int b = 0; b < nb; ++b)
-        if (hs[b].status == 0) done = false;
-      if (it > k->max_iters + check_every) done = true;  // the device caps every term at max_iters
+    } else {
+      // iterative refinement: FP32 CG on N d = r, then x += d, r = f - N x in FP64
+      for (int outer = 0;; ++outer) {
+        cg_init<float, double2><<<grid, THREADS, 0, s>>>(G32, R, 0, D32, R32, P32, vs32, vs64, dsc32, dsc,
+                                                         partials, counters);
+        count(1);
+        e = run_cg(G32, D32, R32, P32, T32, vs32, dsc32, nb, k->inner_rtol, hs32);
+        if (e != cudaSuccess) break;
+        cg_apply_B<double><<<grid, THREADS, 0, s>>>(G, X, D32, T, vs64, vs32, dsc, partials, counters, 1);
+        refine_residual<<<grid, THREADS, 0, s>>>(G, src, real_input, T, D32, X, R, vs64, vs32, dsc, partials,
+                                                 counters, k->rtol, k->max_outer);
+        count(2);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), dsc, nb * sizeof(TermScalars), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) break;
+        bool done = true;
+        for (int b = 0; b < nb; ++b)
+          if (hs[b].status == 0) done = false;
+        if (done || outer > k->max_outer) break;
+      }
+      if (e != cudaSuccess) break;
     }
-    if (e != cudaSuccess) break;
     mark(3);
     for (int b = 0; b < nb; ++b) {
-      term_iters += hs[b].iters;
-      worst_iters = std::max(worst_iters, hs[b].iters);
+      worst_iters = std::max(worst_iters, mixed ? hs32[b].iters : hs[b].iters);
       if (hs[b].status != 1) ++unconverged;
       if (hs[b].gamma0 > 0) worst_res = std::max(worst_res, sqrt(hs[b].gamma / hs[b].gamma0));
     }
     dim3 g2(G.tiles_x, G.tiles_y, 1);
-    cg_accumulate<<<g2, THREADS, 0, s>>>(G, k->depth, X, vstride, nb, dsc, acc, b0 == 0 ? 1 : 0);
+    cg_accumulate<<<g2, THREADS, 0, s>>>(G, X, vs64, nb, dsc, acc, b0 == 0 ? 1 : 0);
     count(1);
     if ((e = cudaGetLastError()) != cudaSuccess) break;
     mark(4);
@@ -553,12 +738,15 @@ rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void
     return REXI_ECUDA;
   }
   if (adjoint) {
-    scale_eta<<<ebl, eb, 0, s>>>(acc, static_cast<double2*>(out), k->depth, nk, k->g, 0, 0);
+    scale_eta<<<ebl, eb, 0, s>>>(acc, static_cast<double2*>(out), k->w64, nk, 0, 0);
+    count(1);
     if (real_input) {
       finish_output<<<ebl, eb, 0, s>>>(static_cast<double2*>(out), static_cast<double2*>(out), n3, 1);
+      count(1);
     }
   } else {
     finish_output<<<ebl, eb, 0, s>>>(acc, static_cast<double2*>(out), n3, real_input);
+    count(1);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) {
     set_last_error(cudaGetErrorString(e));

@@ -11,10 +11,15 @@ struct KrylovSettings {
   int nx = 0, ny = 0;
   double Lx = 1, Ly = 1, g = 1, f = 1, Hmean = 1;
   const double* depth = nullptr;
-  double rtol = 1e-10;
-  int max_iters = 20000;
-  int term_batch = 64;
-  void* dev_state = nullptr;  // plan-owned device scalars (flags, counters)
+  double rtol = 1e-10;        // relative residual target per term (energy norm)
+  int max_iters = 20000;      // CG iteration cap per term (per inner solve in the mixed form)
+  int term_batch = 64;        // terms solved together in one launch
+  double inner_rtol = 1e-4;   // mixed form: FP32 inner solve target per refinement step
+  int max_outer = 30;         // mixed form: refinement steps cap
+  void* dev_state = nullptr;  // plan-owned device tables below
+  double* w64 = nullptr;      // energy weight g / H (FP64)
+  float* H32 = nullptr;       // depth (FP32 copy for the inner solver)
+  float* w32 = nullptr;       // energy weight (FP32)
 };
 
 // Optional instrumentation from the plan: phase marks (0..4 per term batch)

@@ -32,17 +32,18 @@ def error_bound(M, rtol, H, g=1.0, real_input=True, h=0.5):
     return float(np.sum(gam[sel] * per[sel])) * rtol * cond
 
 
-def krylov_plan(torch, nx, ny, depth, rtol=1e-13, max_iters=20000, batch=32, **phys):
+def krylov_plan(torch, nx, ny, depth, rtol=1e-13, max_iters=20000, batch=32, form="fp64", **phys):
     from paper_2008_11607_gb300 import rexi
 
     Hd = torch.from_numpy(np.ascontiguousarray(depth, dtype=np.float64)).cuda()
-    plan = rexi.Plan(nx, ny, depth=Hd, **phys)
+    plan = rexi.Plan(nx, ny, depth=Hd, form=form, **phys)
     plan.set_krylov(rtol=rtol, max_iters=max_iters, term_batch=batch)
     return plan
 
 
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
 @pytest.mark.parametrize("case", ["12x10_real", "16x16_complex", "9x14_phys"])
-def test_variable_depth_against_sparse_oracle(case):
+def test_variable_depth_against_sparse_oracle(case, form):
     torch = torch_cuda()
     phys = {}
     if case == "12x10_real":
@@ -57,7 +58,7 @@ def test_variable_depth_against_sparse_oracle(case):
         phys = dict(Lx=1.4, Ly=0.9, g=1.7, f=0.5)
     H = inputs.variable_depth(nx, ny, seed=3)
     rtol = 1e-13
-    plan = krylov_plan(torch, nx, ny, H, rtol=rtol, **phys)
+    plan = krylov_plan(torch, nx, ny, H, rtol=rtol, form=form, **phys)
     dt = 20.0 / plan.rho
     out, info = plan.step(to_dev(torch, st), dt, real_input=real, want_info=True)
     out = out.cpu().numpy()
@@ -85,11 +86,12 @@ def test_constant_depth_krylov_matches_fourier_path():
     assert rel_l2(a, b) < 1e-10
 
 
-def test_krylov_adjoint_dot_product():
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_krylov_adjoint_dot_product(form):
     torch = torch_cuda()
     nx, ny = 14, 12
     H = inputs.variable_depth(nx, ny, seed=6)
-    plan = krylov_plan(torch, nx, ny, H, rtol=1e-13)
+    plan = krylov_plan(torch, nx, ny, H, rtol=1e-13, form=form)
     dt = 15.0 / plan.rho
     x = inputs.complex_random_state(nx, ny, seed=7)
     y = inputs.complex_random_state(nx, ny, seed=8)
@@ -133,7 +135,8 @@ def test_krylov_term_slices_and_iteration_cap():
     assert e.value.status == rexi.REXI_EINVAL
 
 
-def test_downscaled_config3_against_oracle():
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_downscaled_config3_against_oracle(form):
     """The variable-depth workload (H = 1 + 0.4 sin(2 pi x) cos(4 pi y) + 8 bumps,
     |k|^-3 height) on a 48 x 48 replica with tau rho = 100 and all terms."""
     torch = torch_cuda()
@@ -141,7 +144,7 @@ def test_downscaled_config3_against_oracle():
     H = inputs.variable_depth(n, n, seed=0)
     st = inputs.kminus3_field(n, n, seed=0)
     rtol = 1e-12
-    plan = krylov_plan(torch, n, n, H, rtol=rtol, batch=64)
+    plan = krylov_plan(torch, n, n, H, rtol=rtol, batch=64, form=form)
     dt = 100.0 / plan.rho
     out, info = plan.step(to_dev(torch, st), dt, want_info=True)
     assert info.krylov_unconverged == 0
@@ -150,7 +153,8 @@ def test_downscaled_config3_against_oracle():
     assert rel_l2(out.cpu().numpy(), ref) < max(1e-10, error_bound(info.M, rtol, H))
 
 
-def test_full_size_1024_constant_depth_slice_matches_fourier():
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_full_size_1024_constant_depth_slice_matches_fourier(form):
     """1024 x 1024, tau rho = 400 (the variable-depth workload's size and pole
     count) with constant depth, hardest terms |n| < 6 (near resonance), against
     the Fourier path on the same slice."""
@@ -159,7 +163,7 @@ def test_full_size_1024_constant_depth_slice_matches_fourier():
 
     n = 1024
     st = inputs.kminus3_field(n, n, seed=0)
-    plan_k = krylov_plan(torch, n, n, np.ones((n, n)), rtol=1e-12, batch=6)
+    plan_k = krylov_plan(torch, n, n, np.ones((n, n)), rtol=1e-12, batch=6, form=form)
     plan_f = rexi.Plan(n, n)
     dt = 400.0 / plan_k.rho
     x = to_dev(torch, st)
