@@ -142,6 +142,18 @@ def rexi_coeffs(tau_rho, tol=1e-10, h=0.5, real_input=True):
     return M.value, p[0::2] + 1j * p[1::2], w[0::2] + 1j * w[1::2]
 
 
+def term_partition(n_terms, world, rank):
+    """Contiguous slice [begin, end) of the REXII term indices |n| = 0..n_terms-1
+    for `rank` of `world` devices, balanced by count.  Each device passes it to
+    rexi_step as term_begin/term_end; the step is linear in the terms, so the
+    outputs sum (one all-reduce) to the full step."""
+    if world < 1 or not (0 <= rank < world):
+        raise ValueError("bad world/rank")
+    base, extra = divmod(int(n_terms), int(world))
+    begin = rank * base + min(rank, extra)
+    return begin, begin + base + (1 if rank < extra else 0)
+
+
 # ---- plans and the step -----------------------------------------------------
 
 def _ptr(t):
