@@ -111,6 +111,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();  // red may still be read by thread 0 of a previous call
   if (l == 0) red[w] = v;
   __syncthreads();
   double s = 0.0;
@@ -119,10 +120,13 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;  // valid in thread 0
 }
 
-// Last-block reduction over the tiles of one term.  Returns true in thread 0
-// of the last block, with *total the sum of all partials in index order.
+// Last-block reduction over the tiles of one term.  Every block writes its
+// partial and takes a ticket; the block that takes the last ticket sums all
+// partials (each thread a fixed strided subset, then the fixed-order block
+// reduction, so the result does not depend on scheduling) and returns true in
+// its thread 0 with *total set.  No block waits for another.
 __device__ __forceinline__ bool last_block_total(double mine, double* partials, unsigned* counter, int ntiles,
-                                                 int tile, double* total) {
+                                                 int tile, double* total, double* red) {
   __shared__ bool is_last;
   if (threadIdx.x == 0) {
     partials[tile] = mine;
@@ -131,22 +135,33 @@ __device__ __forceinline__ bool last_block_total(double mine, double* partials, 
     is_last = (ticket == (unsigned)ntiles - 1);
   }
   __syncthreads();
-  if (!is_last) return false;
+  if (!is_last) return false;  // uniform across the block
+  __threadfence();
+  const volatile double* vp = partials;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < ntiles; i += THREADS) s += vp[i];
+  s = block_sum(s, red);
   if (threadIdx.x == 0) {
-    __threadfence();
-    double s = 0.0;
-    const volatile double* vp = partials;
-    for (int i = 0; i < ntiles; ++i) s += vp[i];
     *total = s;
     *counter = 0u;
   }
   return threadIdx.x == 0;
 }
 
+// Periodic index; tiles reach at most one halo point beyond the grid when the
+// grid is wider than a tile, so two compares replace the division there.
 template <typename R>
 __device__ __forceinline__ size_t gidx(const Geom<R>& G, int i, int j) {
-  i = (i + G.nx) % G.nx;
-  j = (j + G.ny) % G.ny;
+  if (G.nx > TX) {
+    i = i < 0 ? i + G.nx : (i >= G.nx ? i - G.nx : i);
+  } else {
+    i = (i + G.nx) % G.nx;
+  }
+  if (G.ny > TY) {
+    j = j < 0 ? j + G.ny : (j >= G.ny ? j - G.ny : j);
+  } else {
+    j = (j + G.ny) % G.ny;
+  }
   return (size_t)j * G.nx + i;
 }
 
@@ -220,7 +235,7 @@ __global__ void __launch_bounds__(THREADS) cg_init(Geom<R> G, const VF* __restri
   }
   const double s = block_sum(loc, red);
   double tot;
-  if (last_block_total(s, partials + (size_t)term * ntiles, counters + term, ntiles, tile, &tot)) {
+  if (last_block_total(s, partials + (size_t)term * ntiles, counters + term, ntiles, tile, &tot, red)) {
     TermScalars& S = sc[term];
     S.gamma = tot;
     S.gamma0 = tot;
@@ -268,7 +283,7 @@ __global__ void __launch_bounds__(THREADS) cg_apply_B(Geom<R> G, const VA* a, co
   }
   const double s = block_sum(loc, red);
   double tot;
-  if (last_block_total(s, partials + (size_t)term * ntiles, counters + term, ntiles, tile, &tot)) {
+  if (last_block_total(s, partials + (size_t)term * ntiles, counters + term, ntiles, tile, &tot, red)) {
     S.dot1 = tot;
     S.a = tot > 0.0 ? S.gamma / tot : 0.0;
   }
@@ -320,7 +335,7 @@ __global__ void __launch_bounds__(THREADS) cg_update(Geom<R> G, const cplx<R>* t
   }
   const double s = block_sum(loc, red);
   double tot;
-  if (last_block_total(s, partials + (size_t)term * ntiles, counters + term, ntiles, tile, &tot)) {
+  if (last_block_total(s, partials + (size_t)term * ntiles, counters + term, ntiles, tile, &tot, red)) {
     S.beta = S.gamma > 0.0 ? tot / S.gamma : 0.0;
     S.gamma = tot;
     S.iters += 1;
@@ -375,7 +390,7 @@ __global__ void __launch_bounds__(THREADS) refine_residual(Geom<double> G, const
   }
   const double s = block_sum(loc, red);
   double tot;
-  if (last_block_total(s, partials + (size_t)term * ntiles, counters + term, ntiles, tile, &tot)) {
+  if (last_block_total(s, partials + (size_t)term * ntiles, counters + term, ntiles, tile, &tot, red)) {
     S.gamma = tot;
     S.iters += 1;  // refinement steps
     if (tot <= rtol * rtol * S.gamma0)
