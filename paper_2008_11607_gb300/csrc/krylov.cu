@@ -107,12 +107,15 @@ __device__ __forceinline__ void apply_tA(const cplx<R> (*E)[HX], const cplx<R> (
   av = mk(fma(-G.tf4, u4.x, -G.tgdy * dn.x), fma(-G.tf4, u4.y, -G.tgdy * dn.y));
 }
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
+// Block sum: warp shuffles in the type of v (FP32 for the FP32 kernels, so
+// that they issue no FP64 work per point), then FP64 across warps.
+template <typename T>
+__device__ __forceinline__ double block_sum(T v, double* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();  // red may still be read by thread 0 of a previous call
-  if (l == 0) red[w] = v;
+  if (l == 0) red[w] = (double)v;
   __syncthreads();
   double s = 0.0;
   if (threadIdx.x == 0)
@@ -216,7 +219,7 @@ __global__ void __launch_bounds__(THREADS) cg_init(Geom<R> G, const VF* __restri
   cplx<R>* pb = p + (size_t)term * vstride;
   const VF* fb = f + (size_t)term * fterm_stride;
   const cplx<R> zero = mk((R)0, (R)0);
-  double loc = 0.0;
+  R loc = 0;
   for (int k = threadIdx.x; k < TX * TY; k += THREADS) {
     const int i = blockIdx.x * TX + (k % TX), j = blockIdx.y * TY + (k / TX);
     if (i >= G.nx || j >= G.ny) continue;
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(THREADS) cg_init(Geom<R> G, const VF* __restri
       pb[id + c * G.fstride] = zero;
       acc += (c == 0 ? G.w[id] : (R)1) * cabs2(v);
     }
-    loc += (double)acc;
+    loc += acc;
   }
   const double s = block_sum(loc, red);
   double tot;
@@ -261,25 +264,39 @@ __global__ void __launch_bounds__(THREADS) cg_apply_B(Geom<R> G, const VA* a, co
   if (S.status != 0) return;
   const int tile = blockIdx.y * G.tiles_x + blockIdx.x;
   const int ntiles = G.tiles_x * G.tiles_y;
+  // per-point coefficients first, so their loads overlap the tile load
+  constexpr int PP = TX * TY / THREADS;
+  R Hp[PP], wp[PP];
+#pragma unroll
+  for (int q = 0; q < PP; ++q) {
+    const int k = threadIdx.x + q * THREADS;
+    const int i = blockIdx.x * TX + k % TX, j = blockIdx.y * TY + k / TX;
+    const bool ok = i < G.nx && j < G.ny;
+    const size_t id = ok ? (size_t)j * G.nx + i : 0;
+    Hp[q] = G.H[id];
+    wp[q] = G.w[id];
+  }
   load_tile<R, true>(G, a + (size_t)term * vstride, b + (size_t)term * bstride, unit_beta ? (R)1 : (R)S.beta, E,
                      U, V);
   cplx<R>* tb = t + (size_t)term * vstride;
   const cplx<R> al = cvt<R>(S.alpha_n);
-  double loc = 0.0;
-  for (int k = threadIdx.x; k < TX * TY; k += THREADS) {
+  R loc = 0;
+#pragma unroll
+  for (int q = 0; q < PP; ++q) {
+    const int k = threadIdx.x + q * THREADS;
     const int li = k % TX + 1, lj = k / TX + 1;
     const int i = blockIdx.x * TX + li - 1, j = blockIdx.y * TY + lj - 1;
     if (i >= G.nx || j >= G.ny) continue;
     const size_t id = (size_t)j * G.nx + i;
     cplx<R> ae, au, av;
-    apply_tA<R>(E, U, V, li, lj, G.H[id], G, ae, au, av);
+    apply_tA<R>(E, U, V, li, lj, Hp[q], G, ae, au, av);
     const cplx<R> te = cadd(cmul(al, E[lj][li]), ae);
     const cplx<R> tu = cadd(cmul(al, U[lj][li]), au);
     const cplx<R> tv = cadd(cmul(al, V[lj][li]), av);
     tb[id] = te;
     tb[id + G.fstride] = tu;
     tb[id + 2 * G.fstride] = tv;
-    loc += (double)(G.w[id] * cabs2(te) + cabs2(tu) + cabs2(tv));
+    loc += wp[q] * cabs2(te) + cabs2(tu) + cabs2(tv);
   }
   const double s = block_sum(loc, red);
   double tot;
@@ -302,36 +319,56 @@ __global__ void __launch_bounds__(THREADS) cg_update(Geom<R> G, const cplx<R>* t
   if (S.status != 0) return;
   const int tile = blockIdx.y * G.tiles_x + blockIdx.x;
   const int ntiles = G.tiles_x * G.tiles_y;
-  load_tile<R, false>(G, t + (size_t)term * vstride, (const cplx<R>*)nullptr, (R)0, E, U, V);
   cplx<R>* pb = p + (size_t)term * vstride;
   cplx<R>* xb = x + (size_t)term * vstride;
   cplx<R>* rb = r + (size_t)term * vstride;
+  // pointwise operands first, so their loads overlap the tile load
+  constexpr int PP = TX * TY / THREADS;
+  cplx<R> xv[PP][3], rv[PP][3], pv[PP][3];
+  R Hp[PP], wp[PP];
+#pragma unroll
+  for (int q = 0; q < PP; ++q) {
+    const int k = threadIdx.x + q * THREADS;
+    const int i = blockIdx.x * TX + k % TX, j = blockIdx.y * TY + k / TX;
+    const bool ok = i < G.nx && j < G.ny;
+    const size_t id = ok ? (size_t)j * G.nx + i : 0;
+    Hp[q] = G.H[id];
+    wp[q] = G.w[id];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      xv[q][c] = xb[id + c * G.fstride];
+      rv[q][c] = rb[id + c * G.fstride];
+      pv[q][c] = pb[id + c * G.fstride];
+    }
+  }
+  load_tile<R, false>(G, t + (size_t)term * vstride, (const cplx<R>*)nullptr, (R)0, E, U, V);
   const cplx<R> am = cvt<R>(S.alpha_mn);
   const R a = (R)S.a, beta = (R)S.beta;
-  double loc = 0.0;
-  for (int k = threadIdx.x; k < TX * TY; k += THREADS) {
+  R loc = 0;
+#pragma unroll
+  for (int q = 0; q < PP; ++q) {
+    const int k = threadIdx.x + q * THREADS;
     const int li = k % TX + 1, lj = k / TX + 1;
     const int i = blockIdx.x * TX + li - 1, j = blockIdx.y * TY + lj - 1;
     if (i >= G.nx || j >= G.ny) continue;
     const size_t id = (size_t)j * G.nx + i;
     cplx<R> ae, au, av;
-    apply_tA<R>(E, U, V, li, lj, G.H[id], G, ae, au, av);
-    const cplx<R> q[3] = {csub(cmul(am, E[lj][li]), ae), csub(cmul(am, U[lj][li]), au),
-                          csub(cmul(am, V[lj][li]), av)};
+    apply_tA<R>(E, U, V, li, lj, Hp[q], G, ae, au, av);
+    const cplx<R> qv[3] = {csub(cmul(am, E[lj][li]), ae), csub(cmul(am, U[lj][li]), au),
+                           csub(cmul(am, V[lj][li]), av)};
     R acc = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const size_t o = id + c * G.fstride;
-      cplx<R> xv = xb[o], rv = rb[o], pv = pb[o];
-      pv = mk(fma(beta, pv.x, rv.x), fma(beta, pv.y, rv.y));
-      pb[o] = pv;
-      xv = mk(fma(a, pv.x, xv.x), fma(a, pv.y, xv.y));
-      rv = mk(fma(-a, q[c].x, rv.x), fma(-a, q[c].y, rv.y));
-      xb[o] = xv;
-      rb[o] = rv;
-      acc += (c == 0 ? G.w[id] : (R)1) * cabs2(rv);
+      const cplx<R> pn = mk(fma(beta, pv[q][c].x, rv[q][c].x), fma(beta, pv[q][c].y, rv[q][c].y));
+      const cplx<R> xn = mk(fma(a, pn.x, xv[q][c].x), fma(a, pn.y, xv[q][c].y));
+      const cplx<R> rn = mk(fma(-a, qv[c].x, rv[q][c].x), fma(-a, qv[c].y, rv[q][c].y));
+      pb[o] = pn;
+      xb[o] = xn;
+      rb[o] = rn;
+      acc += (c == 0 ? wp[q] : (R)1) * cabs2(rn);
     }
-    loc += (double)acc;
+    loc += acc;
   }
   const double s = block_sum(loc, red);
   double tot;
