@@ -227,6 +227,57 @@ rexi_status rexi_step_noalloc(int32_t nx, int32_t ny, double Lx, double Ly, doub
                               double h, const void* in_dev, void* out_dev, double dt, double tol,
                               int32_t real_input, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batched serving launch.                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Many independent constant-depth instances advanced together, each with its
+ * own grid (nx[i] x ny[i]) and time step dt[i] (so its own pole count), with
+ * shared Lx, Ly, g, f, H, tol, h and form (REXI_FORM_FP64 or REXI_FORM_MIXED).
+ * Each instance computes exactly what rexi_step computes for it.
+ * States are packed in one device buffer: instance i occupies
+ * 3 * nx[i] * ny[i] complex128 values from element offsets[i]
+ * (rexi_batch_layout); instances of equal size are packed next to each other.
+ * rexi_batch_create allocates device tables (coefficients, work list). */
+typedef struct rexi_batch_s* rexi_batch_t;
+
+enum {
+  REXI_BATCH_PERSISTENT = 0,  /* one persistent pole kernel over all instances, whole step replayed from a CUDA graph */
+  REXI_BATCH_PER_INSTANCE = 1 /* FFT, pole and inverse-FFT launches instance by instance */
+};
+
+rexi_status rexi_batch_create(rexi_batch_t* batch, int32_t n, const int32_t* nx, const int32_t* ny,
+                              const double* dt, double Lx, double Ly, double g, double f, double H, double tol,
+                              int32_t form, double h);
+void rexi_batch_destroy(rexi_batch_t batch);
+
+/* offsets: NULL or n + 1 entries (element offsets, last = total); M_out: NULL
+ * or n pole counts; workspace_bytes: device workspace rexi_batch_step needs. */
+rexi_status rexi_batch_layout(rexi_batch_t batch, int64_t* offsets, int32_t* M_out, size_t* workspace_bytes);
+
+/* One step of every instance: out = r(dt_i A_i) in for each i.  The
+ * persistent mode captures its launch sequence in a CUDA graph on the first
+ * call for given buffers and replays it afterwards (on a stream owned by the
+ * batch, ordered after `stream` and before later work on `stream` by events);
+ * the buffers must not move between calls that should reuse the graph.
+ * `in` and `out` may be the same buffer. */
+rexi_status rexi_batch_step(rexi_batch_t batch, const void* in_dev, void* out_dev, int32_t real_input,
+                            void* workspace_dev, size_t workspace_bytes, int32_t mode, void* stream);
+
+/* Times the persistent mode for CTA sizes {64, 128, 256} x pairs per thread
+ * {1, 2} on the given buffers (a few steps each; results are overwritten) and
+ * keeps the fastest.  Outputs (each nullable): the chosen configuration and
+ * its time per step in milliseconds. */
+rexi_status rexi_batch_autotune(rexi_batch_t batch, const void* in_dev, void* out_dev, int32_t real_input,
+                                void* workspace_dev, size_t workspace_bytes, void* stream, int32_t* threads,
+                                int32_t* pairs_per_thread, double* best_ms);
+
+/* Current configuration and counters (each nullable): CTA size, pairs per
+ * thread, persistent CTAs launched, work items, sum over instances of
+ * wavenumber pairs x scalar terms, kernels launched so far. */
+rexi_status rexi_batch_info(rexi_batch_t batch, int32_t* threads, int32_t* pairs_per_thread, int32_t* ctas,
+                            int32_t* n_items, int64_t* terms_pairs, int64_t* launches);
+
 /* Human-readable name of a status code (static string). */
 const char* rexi_status_string(rexi_status status);
 

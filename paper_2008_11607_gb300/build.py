@@ -36,7 +36,7 @@ def _compile(src, verbose):
 
 def build(verbose=False, force=False):
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
-    hdrs = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    hdrs = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
     if not force and os.path.exists(LIB):
         newest = max(os.path.getmtime(f) for f in srcs + hdrs + [__file__])
         if os.path.getmtime(LIB) >= newest:

@@ -1,0 +1,606 @@
+// Batched serving launch: many independent constant-depth instances (own grid
+// size, own time step, hence own pole count) advanced together.
+//
+// Work is split into items of `threads * pairs_per_thread` wavenumber pairs of
+// one instance; an item costs (pairs x scalar terms).  Items are sorted by
+// cost, largest first, and one persistent kernel (a few CTAs per SM) pulls
+// them from an atomic counter, so that small and large instances fill the GPU
+// together instead of one small launch after another.  The forward and
+// inverse FFTs run once per distinct grid size over all instances of that
+// size (they are packed next to each other).  The whole sequence is captured
+// once in a CUDA graph on a stream owned by the batch and replayed.  The
+// persistent kernel's CTA size and pairs per thread are chosen by timing the
+// candidates (rexi_batch_autotune).  The per-instance mode launches the
+// single-instance kernels instance by instance, for comparison.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "internal.h"
+#include "pole_common.cuh"
+
+namespace rexi {
+namespace {
+
+struct InstDesc {
+  long long spec_off;  // first element of this instance's spectrum (field 0)
+  int nx, ny, nterms, pad;
+  double inv_dx, inv_dy, tau, q, R0re, R0im, grid;
+  float q_hi, q_lo;
+  long long table_off;  // first table entry (3 x 16 bytes per term)
+  const double2* half_x;
+  const double2* half_y;
+};
+
+struct WorkItem {
+  int inst, pair_begin;
+};
+
+struct SizeGroup {
+  int nx, ny;
+  std::vector<int> insts;  // packed consecutively
+  FftPlan1D fx, fy;
+  long long first_off;     // element offset of the group's first state
+};
+
+}  // namespace
+}  // namespace rexi
+
+struct rexi_batch_s {
+  int n = 0, form = REXI_FORM_FP64;
+  double Lx = 1, Ly = 1, g = 1, f = 1, H = 1, tol = 1e-10, h = 0.5;
+  std::vector<int> nx, ny, M;
+  std::vector<double> dt, rho;
+  std::vector<long long> offsets;  // per instance, complex128 elements; offsets[n] = total
+  std::vector<rexi::SizeGroup> groups;
+  std::map<int, std::pair<double2*, double2*>> axis_tables;  // n -> (twiddles, half angles), device
+  // device data owned by the batch
+  void* d_tables = nullptr;      // coefficient tables of all instances
+  rexi::InstDesc* d_desc = nullptr;
+  rexi::WorkItem* d_items = nullptr;
+  int n_items = 0;
+  int item_pairs = 0;            // pairs per work item the items were built for
+  std::vector<rexi::InstDesc> h_desc;
+  long long total_terms_pairs = 0;
+  // launch configuration of the persistent kernel
+  int threads = 128, ppt = 1, ctas = 0;
+  // graph replay
+  cudaStream_t own = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const void* g_in = nullptr;
+  void* g_out = nullptr;
+  void* g_ws = nullptr;
+  int g_real = -1, g_threads = 0, g_ppt = 0;
+  int64_t launches = 0;
+};
+
+namespace rexi {
+namespace {
+
+// ---- persistent kernel ------------------------------------------------------
+
+template <int FORM, int PPT>
+__global__ void batch_pole_kernel(double2* spec, const InstDesc* __restrict__ desc,
+                                  const WorkItem* __restrict__ items, int n_items, unsigned* counter,
+                                  const void* __restrict__ tables, double g, double f, double H, int adjoint) {
+  __shared__ float4 st[kChunk * 3];  // 48 bytes per term, both forms
+  __shared__ int s_item;
+  __shared__ InstDesc D;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) return;
+    if (threadIdx.x == 0) D = desc[items[it].inst];
+    __syncthreads();
+    SymbolParams sp;
+    sp.nx = D.nx;
+    sp.ny = D.ny;
+    sp.inv_dx = D.inv_dx;
+    sp.inv_dy = D.inv_dy;
+    sp.g = g;
+    sp.f = f;
+    sp.H = H;
+    sp.half_x = D.half_x;
+    sp.half_y = D.half_y;
+    const int npairs = D.nx * (D.ny / 2 + 1);
+    int kx[PPT], ky[PPT], kx2[PPT], ky2[PPT];
+    bool active[PPT];
+    Symbol S[PPT];
+    double x[PPT];
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) {
+      const int p = items[it].pair_begin + u * blockDim.x + threadIdx.x;
+      kx[u] = ky[u] = kx2[u] = ky2[u] = 0;
+      active[u] = p < npairs && pair_of(p, D.nx, D.ny, kx[u], ky[u], kx2[u], ky2[u]);
+      S[u] = symbol_at(sp, active[u] ? kx[u] : 0, active[u] ? ky[u] : 0);
+      x[u] = D.tau * S[u].omega;
+    }
+    double ar[PPT], ai[PPT];
+    float arh[PPT], arl[PPT], aih[PPT], ail[PPT], Xh[PPT], Xl[PPT];
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) {
+      ar[u] = ai[u] = 0.0;
+      arh[u] = arl[u] = aih[u] = ail[u] = 0.f;
+      const double xg = rint(x[u] / D.grid) * D.grid;
+      Xh[u] = (float)xg;
+      Xl[u] = (float)(x[u] - xg);
+    }
+    const float4* tb = reinterpret_cast<const float4*>(tables) + D.table_off * 3;
+    for (int t0 = 0; t0 < D.nterms; t0 += kChunk) {
+      const int cnt = min(kChunk, D.nterms - t0);
+      __syncthreads();
+      for (int i = threadIdx.x; i < cnt * 3; i += blockDim.x) st[i] = tb[(size_t)t0 * 3 + i];
+      __syncthreads();
+      if (FORM == REXI_FORM_FP64) {
+        const double2* sd = reinterpret_cast<const double2*>(st);
+#pragma unroll 2
+        for (int t = 0; t < cnt; ++t)
+#pragma unroll
+          for (int u = 0; u < PPT; ++u) fp64_term(sd + 3 * t, x[u], D.q, ar[u], ai[u]);
+      } else {
+#pragma unroll 2
+        for (int t = 0; t < cnt; ++t)
+#pragma unroll
+          for (int u = 0; u < PPT; ++u)
+            df_term(st + 3 * t, Xh[u], Xl[u], D.q_hi, D.q_lo, arh[u], arl[u], aih[u], ail[u]);
+      }
+    }
+    double2* sp_inst = spec + D.spec_off;
+    const size_t fstride = (size_t)D.nx * D.ny;
+    const double2 R0 = make_double2(D.R0re, D.R0im);
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) {
+      if (!active[u]) continue;
+      const double2 Rp = FORM == REXI_FORM_FP64
+                             ? make_double2(ar[u], ai[u])
+                             : make_double2((double)arh[u] + (double)arl[u], (double)aih[u] + (double)ail[u]);
+      combine(sp_inst, (size_t)ky[u] * D.nx + kx[u], fstride, S[u], sp, false, adjoint != 0, R0, Rp);
+      if (kx2[u] != kx[u] || ky2[u] != ky[u])
+        combine(sp_inst, (size_t)ky2[u] * D.nx + kx2[u], fstride, S[u], sp, true, adjoint != 0, R0, Rp);
+    }
+  }
+}
+
+template <int FORM, int PPT>
+cudaError_t launch_persistent(rexi_batch_s* b, double2* spec, unsigned* counter, int threads, cudaStream_t s) {
+  auto kern = batch_pole_kernel<FORM, PPT>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int ctas = std::max(1, std::min(per_sm * sms, b->n_items));
+  b->ctas = ctas;
+  kern<<<ctas, threads, 0, s>>>(spec, b->d_desc, b->d_items, b->n_items, counter, b->d_tables, b->g, b->f, b->H,
+                                0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pole(rexi_batch_s* b, double2* spec, unsigned* counter, cudaStream_t s) {
+  if (b->form == REXI_FORM_FP64)
+    return b->ppt == 2 ? launch_persistent<REXI_FORM_FP64, 2>(b, spec, counter, b->threads, s)
+                       : launch_persistent<REXI_FORM_FP64, 1>(b, spec, counter, b->threads, s);
+  return b->ppt == 2 ? launch_persistent<REXI_FORM_MIXED, 2>(b, spec, counter, b->threads, s)
+                     : launch_persistent<REXI_FORM_MIXED, 1>(b, spec, counter, b->threads, s);
+}
+
+size_t al256(size_t v) { return (v + 255) / 256 * 256; }
+
+// Workspace: [counter (256 B)][packed spectrum]
+size_t batch_ws_bytes(const rexi_batch_s* b) { return 256 + al256((size_t)b->offsets[b->n] * sizeof(double2)); }
+
+// (Re)build the work items for the current item size, largest cost first.
+cudaError_t build_items(rexi_batch_s* b) {
+  const int item_pairs = b->threads * b->ppt;
+  if (item_pairs == b->item_pairs && b->d_items) return cudaSuccess;
+  struct Cost {
+    long long cost;
+    WorkItem w;
+  };
+  std::vector<Cost> v;
+  for (int i = 0; i < b->n; ++i) {
+    const int np = b->nx[i] * (b->ny[i] / 2 + 1);
+    for (int p = 0; p < np; p += item_pairs) {
+      const long long pairs = std::min(item_pairs, np - p);
+      v.push_back({pairs * (long long)b->h_desc[i].nterms, {i, p}});
+    }
+  }
+  std::stable_sort(v.begin(), v.end(), [](const Cost& a, const Cost& c) { return a.cost > c.cost; });
+  std::vector<WorkItem> items(v.size());
+  for (size_t k = 0; k < v.size(); ++k) items[k] = v[k].w;
+  if (b->d_items) cudaFree(b->d_items);
+  b->d_items = nullptr;
+  cudaError_t e = cudaMalloc(&b->d_items, items.size() * sizeof(WorkItem));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
+  b->n_items = (int)items.size();
+  b->item_pairs = item_pairs;
+  return e;
+}
+
+// The whole persistent-mode step on stream s.
+cudaError_t enqueue_persistent(rexi_batch_s* b, const double2* in, double2* out, int real_input, char* ws,
+                               cudaStream_t s) {
+  unsigned* counter = reinterpret_cast<unsigned*>(ws);
+  double2* spec = reinterpret_cast<double2*>(ws + 256);
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+  for (auto& G : b->groups) {
+    if (e != cudaSuccess) return e;
+    const int nf = 3 * (int)G.insts.size();
+    e = fft2d(in + G.first_off, spec + G.first_off, nf, G.fx, G.fy, -1, 1.0, real_input, 0, s);
+  }
+  if (e != cudaSuccess) return e;
+  e = launch_pole(b, spec, counter, s);
+  for (auto& G : b->groups) {
+    if (e != cudaSuccess) return e;
+    const int nf = 3 * (int)G.insts.size();
+    e = fft2d(spec + G.first_off, out + G.first_off, nf, G.fx, G.fy, +1, 1.0 / ((double)G.nx * G.ny), 0,
+              real_input, s);
+  }
+  return e;
+}
+
+void reset_graph(rexi_batch_s* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+}
+
+}  // namespace
+}  // namespace rexi
+
+using namespace rexi;
+
+extern "C" {
+
+void rexi_batch_destroy(rexi_batch_t b) {
+  if (!b) return;
+  if (b->own) cudaStreamSynchronize(b->own);
+  reset_graph(b);
+  if (b->own) cudaStreamDestroy(b->own);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  for (auto& kv : b->axis_tables) {
+    cudaFree(kv.second.first);
+    cudaFree(kv.second.second);
+  }
+  cudaFree(b->d_tables);
+  cudaFree(b->d_desc);
+  cudaFree(b->d_items);
+  delete b;
+}
+
+rexi_status rexi_batch_create(rexi_batch_t* out, int32_t n, const int32_t* nx, const int32_t* ny, const double* dt,
+                              double Lx, double Ly, double g, double f, double H, double tol, int32_t form,
+                              double h) {
+  set_last_error("");
+  if (!out || n < 1 || !nx || !ny || !dt) {
+    set_last_error("rexi_batch_create: NULL argument or n < 1");
+    return REXI_EINVAL;
+  }
+  *out = nullptr;
+  if (!(Lx > 0 && Ly > 0 && g > 0 && H > 0 && isfinite(f)) || !valid_h(h) || !valid_tol(tol) ||
+      (form != REXI_FORM_FP64 && form != REXI_FORM_MIXED)) {
+    set_last_error("rexi_batch_create: bad physics, h, tol or form (FP64 or MIXED)");
+    return REXI_EINVAL;
+  }
+  rexi_batch_s* b = new rexi_batch_s();
+  b->n = n;
+  b->form = form;
+  b->Lx = Lx; b->Ly = Ly; b->g = g; b->f = f; b->H = H; b->tol = tol; b->h = h;
+  auto bail = [&](rexi_status st, const char* msg) {
+    set_last_error(msg);
+    rexi_batch_destroy(b);
+    return st;
+  };
+  std::map<std::pair<int, int>, int> gidx;
+  for (int i = 0; i < n; ++i) {
+    FftPlan1D px, py;
+    if (!fft_factor(nx[i], &px) || !fft_factor(ny[i], &py) || !(dt[i] >= 0.0) || !isfinite(dt[i]))
+      return bail(REXI_EINVAL, "rexi_batch_create: an instance has an unsupported grid or a bad dt");
+    b->nx.push_back(nx[i]);
+    b->ny.push_back(ny[i]);
+    b->dt.push_back(dt[i]);
+    auto key = std::make_pair(nx[i], ny[i]);
+    if (!gidx.count(key)) {
+      gidx[key] = (int)b->groups.size();
+      SizeGroup G;
+      G.nx = nx[i];
+      G.ny = ny[i];
+      G.fx = px;
+      G.fy = py;
+      b->groups.push_back(G);
+    }
+    b->groups[gidx[key]].insts.push_back(i);
+  }
+  // axis tables per distinct length
+  for (auto& G : b->groups) {
+    for (int len : {G.nx, G.ny}) {
+      if (b->axis_tables.count(len)) continue;
+      std::vector<double2> tw(len), half(len);
+      for (int t = 0; t < len; ++t) {
+        const double a = 2.0 * M_PI * t / len, c = M_PI * t / len;
+        tw[t] = make_double2(cos(a), -sin(a));
+        half[t] = make_double2(cos(c), sin(c));
+      }
+      double2 *dtw = nullptr, *dhalf = nullptr;
+      if (cudaMalloc(&dtw, len * sizeof(double2)) != cudaSuccess ||
+          cudaMalloc(&dhalf, len * sizeof(double2)) != cudaSuccess) {
+        cudaFree(dtw);
+        return bail(REXI_ENOMEM, "rexi_batch_create: table allocation failed");
+      }
+      b->axis_tables[len] = {dtw, dhalf};
+      cudaMemcpy(dtw, tw.data(), len * sizeof(double2), cudaMemcpyHostToDevice);
+      cudaMemcpy(dhalf, half.data(), len * sizeof(double2), cudaMemcpyHostToDevice);
+    }
+    G.fx.tw = b->axis_tables[G.nx].first;
+    G.fy.tw = b->axis_tables[G.ny].first;
+  }
+  // packed layout, group by group
+  b->offsets.assign(n + 1, 0);
+  long long off = 0;
+  for (auto& G : b->groups) {
+    G.first_off = off;
+    for (int i : G.insts) {
+      b->offsets[i] = off;
+      off += 3LL * G.nx * G.ny;
+    }
+  }
+  b->offsets[n] = off;
+  // per-instance rho, pole count and coefficient tables
+  b->h_desc.resize(n);
+  std::vector<float> tab;  // 12 floats = 48 bytes per term (FP64 tables reinterpret the same bytes)
+  const double mu = table_mu(), hmu = h * mu, q = hmu * hmu;
+  for (int i = 0; i < n; ++i) {
+    const int X = b->nx[i], Y = b->ny[i];
+    const double dx = Lx / X, dy = Ly / Y;
+    const double2* hx = nullptr;
+    const double2* hy = nullptr;
+    double best = 0.0;
+    for (int ky = 0; ky < Y; ++ky) {
+      const double sy = sin(M_PI * ky / Y), cy = cos(M_PI * ky / Y);
+      for (int kx = 0; kx < X; ++kx) {
+        const double sx = sin(M_PI * kx / X), cx = cos(M_PI * kx / X);
+        best = std::max(best, g * H * (4 * sx * sx / (dx * dx) + 4 * sy * sy / (dy * dy)) + f * f * cx * cx * cy * cy);
+      }
+    }
+    const double rho = sqrt(best);
+    const int M = pole_count(dt[i] * rho, h, tol);
+    if (M < 0) return bail(REXI_EINVAL, "rexi_batch_create: pole-count rule rejected an instance");
+    b->rho.push_back(rho);
+    b->M.push_back(M);
+    TermSet ts;
+    rexii_terms(M, h, &ts);
+    const int N = M + kL, nterms = 2 * N + 1;
+    InstDesc& D = b->h_desc[i];
+    memset(&D, 0, sizeof(D));
+    D.spec_off = b->offsets[i];
+    D.nx = X;
+    D.ny = Y;
+    D.nterms = nterms;
+    D.inv_dx = 1.0 / dx;
+    D.inv_dy = 1.0 / dy;
+    D.tau = dt[i];
+    D.q = q;
+    D.q_hi = (float)q;
+    D.q_lo = (float)(q - (double)D.q_hi);
+    D.table_off = (long long)(tab.size() / 12);
+    hx = b->axis_tables[X].second;
+    hy = b->axis_tables[Y].second;
+    D.half_x = hx;
+    D.half_y = hy;
+    const double span = dt[i] * rho + h * N + 4.0;
+    if (form == REXI_FORM_MIXED && span > 4.0e6)
+      return bail(REXI_EINVAL, "rexi_batch_create: dt*rho too large for the mixed form");
+    int gexp = 0;
+    while (ldexp(1.0, 23 - gexp) > span && gexp < 60) ++gexp;
+    D.grid = ldexp(1.0, -(gexp - 1));
+    double R0r = 0, R0i = 0;
+    for (int nn = -N; nn <= N; ++nn) {
+      const int k = nn + N;
+      const double hn = h * nn, d = q + hn * hn;
+      const double Ar = ts.c1re[k] * hmu, Ai = ts.c1im[k] * hmu, Br = ts.c2re[k], Bi = ts.c2im[k];
+      R0r += (Ar + Br * hn) / d;
+      R0i += (Ai + Bi * hn) / d;
+      float e[12];
+      if (form == REXI_FORM_FP64) {
+        const double dd[6] = {hn, Ar, Ai, Br, Bi, 0.0};
+        memcpy(e, dd, sizeof(dd));
+      } else {
+        auto split = [](double v, float& hi, float& lo) {
+          hi = (float)v;
+          lo = (float)(v - (double)hi);
+        };
+        const double hg = rint(hn / D.grid) * D.grid;
+        float Arh, Arl, Aih, Ail, Brh, Brl, Bih, Bil;
+        split(Ar, Arh, Arl);
+        split(Ai, Aih, Ail);
+        split(Br, Brh, Brl);
+        split(Bi, Bih, Bil);
+        const float v[12] = {(float)hg, Arh, Aih, Brh, Bih, Arl, Ail, Brl, Bil, (float)(hn - hg), 0.f, 0.f};
+        memcpy(e, v, sizeof(v));
+      }
+      tab.insert(tab.end(), e, e + 12);
+    }
+    D.R0re = R0r;
+    D.R0im = R0i;
+    b->total_terms_pairs += (long long)X * (Y / 2 + 1) * nterms;
+  }
+  if (cudaMalloc(&b->d_tables, tab.size() * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&b->d_desc, n * sizeof(InstDesc)) != cudaSuccess)
+    return bail(REXI_ENOMEM, "rexi_batch_create: device allocation failed");
+  cudaMemcpy(b->d_tables, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice);
+  cudaMemcpy(b->d_desc, b->h_desc.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice);
+  if (build_items(b) != cudaSuccess) return bail(REXI_ENOMEM, "rexi_batch_create: work list allocation failed");
+  if (cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return bail(REXI_ECUDA, "rexi_batch_create: stream or event creation failed");
+  *out = b;
+  return REXI_OK;
+}
+
+rexi_status rexi_batch_layout(rexi_batch_t b, int64_t* offsets, int32_t* M_out, size_t* workspace_bytes) {
+  set_last_error("");
+  if (!b) return REXI_EINVAL;
+  if (offsets)
+    for (int i = 0; i <= b->n; ++i) offsets[i] = b->offsets[i];
+  if (M_out)
+    for (int i = 0; i < b->n; ++i) M_out[i] = b->M[i];
+  if (workspace_bytes) *workspace_bytes = batch_ws_bytes(b);
+  return REXI_OK;
+}
+
+rexi_status rexi_batch_step(rexi_batch_t b, const void* in, void* out, int32_t real_input, void* ws, size_t ws_bytes,
+                            int32_t mode, void* stream) {
+  set_last_error("");
+  if (!b || !in || !out || !ws) {
+    set_last_error("rexi_batch_step: NULL argument");
+    return REXI_EINVAL;
+  }
+  if (((uintptr_t)in | (uintptr_t)out) & 15 || (uintptr_t)ws & 255) {
+    set_last_error("rexi_batch_step: misaligned buffer");
+    return REXI_EINVAL;
+  }
+  if (ws_bytes < batch_ws_bytes(b)) {
+    set_last_error("rexi_batch_step: workspace too small");
+    return REXI_ENOMEM;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const double2* in2 = static_cast<const double2*>(in);
+  double2* out2 = static_cast<double2*>(out);
+  char* wsc = static_cast<char*>(ws);
+  cudaError_t e = cudaSuccess;
+  if (mode == REXI_BATCH_PER_INSTANCE) {
+    double2* spec = reinterpret_cast<double2*>(wsc + 256);
+    for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
+      const InstDesc& D = b->h_desc[i];
+      FftPlan1D fx, fy;
+      fft_factor(D.nx, &fx);
+      fft_factor(D.ny, &fy);
+      fx.tw = b->axis_tables[D.nx].first;
+      fy.tw = b->axis_tables[D.ny].first;
+      double2* sp_i = spec + D.spec_off;
+      e = fft2d(in2 + D.spec_off, sp_i, 3, fx, fy, -1, 1.0, real_input, 0, s);
+      SymbolParams sp;
+      sp.nx = D.nx; sp.ny = D.ny; sp.inv_dx = D.inv_dx; sp.inv_dy = D.inv_dy;
+      sp.g = b->g; sp.f = b->f; sp.H = b->H; sp.half_x = D.half_x; sp.half_y = D.half_y;
+      FusedScalars fs;
+      fs.tau = D.tau; fs.q = D.q; fs.R0re = D.R0re; fs.R0im = D.R0im; fs.nterms = D.nterms; fs.adjoint = 0;
+      const float* tab = static_cast<const float*>(b->d_tables) + D.table_off * 12;
+      if (e == cudaSuccess)
+        e = b->form == REXI_FORM_FP64 ? pole_fused_fp64(sp_i, sp, reinterpret_cast<const double*>(tab), fs, s)
+                                      : pole_fused_mixed(sp_i, sp, tab, fs, D.grid, s);
+      if (e == cudaSuccess)
+        e = fft2d(sp_i, out2 + D.spec_off, 3, fx, fy, +1, 1.0 / ((double)D.nx * D.ny), 0, real_input, s);
+      b->launches += 5;
+    }
+  } else if (mode == REXI_BATCH_PERSISTENT) {
+    const bool same = b->exec && b->g_in == in && b->g_out == out && b->g_ws == ws && b->g_real == real_input &&
+                      b->g_threads == b->threads && b->g_ppt == b->ppt;
+    if (!same) {
+      reset_graph(b);
+      if ((e = build_items(b)) != cudaSuccess) {
+        set_last_error(cudaGetErrorString(e));
+        return REXI_ECUDA;
+      }
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t e2 = enqueue_persistent(b, in2, out2, real_input, wsc, b->own);
+        e = cudaStreamEndCapture(b->own, &graph);
+        if (e2 != cudaSuccess) e = e2;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        set_last_error(cudaGetErrorString(e));
+        return REXI_ECUDA;
+      }
+      b->g_in = in; b->g_out = out; b->g_ws = ws; b->g_real = real_input;
+      b->g_threads = b->threads; b->g_ppt = b->ppt;
+    }
+    // order the graph after the caller's stream and the caller's stream after the graph
+    e = cudaEventRecord(b->ev_in, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->own, b->ev_in, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->own);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev_out, b->own);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_out, 0);
+    b->launches += 1 + 4 * (int64_t)b->groups.size();
+  } else {
+    set_last_error("rexi_batch_step: unknown mode");
+    return REXI_EINVAL;
+  }
+  if (e != cudaSuccess) {
+    set_last_error(cudaGetErrorString(e));
+    return REXI_ECUDA;
+  }
+  return REXI_OK;
+}
+
+rexi_status rexi_batch_autotune(rexi_batch_t b, const void* in, void* out, int32_t real_input, void* ws,
+                                size_t ws_bytes, void* stream, int32_t* threads_out, int32_t* ppt_out,
+                                double* best_ms_out) {
+  set_last_error("");
+  if (!b) return REXI_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int cand_t[3] = {64, 128, 256};
+  const int cand_p[2] = {1, 2};
+  double best = 1e300;
+  int bt = b->threads, bp = b->ppt;
+  rexi_status st = REXI_OK;
+  for (int ti : cand_t) {
+    for (int pi : cand_p) {
+      b->threads = ti;
+      b->ppt = pi;
+      // first call captures the graph; time the next two replays
+      st = rexi_batch_step(b, in, out, real_input, ws, ws_bytes, REXI_BATCH_PERSISTENT, stream);
+      if (st != REXI_OK) break;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 2 && st == REXI_OK; ++r)
+        st = rexi_batch_step(b, in, out, real_input, ws, ws_bytes, REXI_BATCH_PERSISTENT, stream);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (st != REXI_OK) break;
+      if (ms / 2 < best) {
+        best = ms / 2;
+        bt = ti;
+        bp = pi;
+      }
+    }
+    if (st != REXI_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->threads = bt;
+  b->ppt = bp;
+  if (threads_out) *threads_out = bt;
+  if (ppt_out) *ppt_out = bp;
+  if (best_ms_out) *best_ms_out = best;
+  return st;
+}
+
+rexi_status rexi_batch_info(rexi_batch_t b, int32_t* threads, int32_t* ppt, int32_t* ctas, int32_t* n_items,
+                            int64_t* terms_pairs, int64_t* launches) {
+  if (!b) return REXI_EINVAL;
+  if (threads) *threads = b->threads;
+  if (ppt) *ppt = b->ppt;
+  if (ctas) *ctas = b->ctas;
+  if (n_items) *n_items = b->n_items;
+  if (terms_pairs) *terms_pairs = b->total_terms_pairs;
+  if (launches) *launches = b->launches;
+  return REXI_OK;
+}
+
+}  // extern "C"

@@ -27,122 +27,10 @@
 //    g3 = Gamma_n (C2 g1 + (C1 - C2 alpha_{-n}) g2) written to HBM for a chunk
 //    of terms, then a separate reduction pass over the chunk.
 #include "internal.h"
+#include "pole_common.cuh"
 
 namespace rexi {
 
-// ---------------------------------------------------------------------------
-// Symbol of the C-grid operator at wavenumber k (half-angle form, no
-// cancellation for small k).  With c = cos(theta/2), s = sin(theta/2):
-//   forward difference  (e^{i theta} - 1)/dx  = (2 s / dx)(-s + i c)
-//   backward difference (1 - e^{-i theta})/dx = (2 s / dx)( s + i c)
-//   P = (1 + e^{i theta_x})(1 + e^{-i theta_y}) / 4 = cx cy (cx + i sx)(cy - i sy)
-//   omega^2 = g H (4 sx^2/dx^2 + 4 sy^2/dy^2) + f^2 cx^2 cy^2
-struct Symbol {
-  double2 dxf, dyf, dxb, dyb, P;
-  double omega;
-};
-
-__device__ __forceinline__ Symbol symbol_at(const SymbolParams& sp, int kx, int ky) {
-  const double2 hx = sp.half_x[kx];
-  const double2 hy = sp.half_y[ky];
-  const double cx = hx.x, sx = hx.y, cy = hy.x, sy = hy.y;
-  Symbol S;
-  const double ax = 2.0 * sx * sp.inv_dx, ay = 2.0 * sy * sp.inv_dy;
-  S.dxf = make_double2(-ax * sx, ax * cx);
-  S.dxb = make_double2(ax * sx, ax * cx);
-  S.dyf = make_double2(-ay * sy, ay * cy);
-  S.dyb = make_double2(ay * sy, ay * cy);
-  const double cc = cx * cy;
-  S.P = make_double2(cc * (cx * cy + sx * sy), cc * (sx * cy - cx * sy));
-  const double w2 = sp.g * sp.H * (ax * ax + ay * ay) + sp.f * sp.f * cc * cc;
-  S.omega = sqrt(w2);
-  return S;
-}
-
-__device__ __forceinline__ double2 cm(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 cj(double2 a) { return make_double2(a.x, -a.y); }
-__device__ __forceinline__ double2 ca(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 cs(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 cr(double a, double2 b) { return make_double2(a * b.x, a * b.y); }
-
-// y = B f (conj_sym: use conj(B), the symbol at -k; adjoint: use B^H).
-__device__ __forceinline__ void apply_B(const Symbol& S, const SymbolParams& sp, bool conj_sym,
-                                        bool adjoint, const double2 f[3], double2 y[3]) {
-  double2 dxf = S.dxf, dyf = S.dyf, dxb = S.dxb, dyb = S.dyb, P = S.P;
-  if (conj_sym) {
-    dxf = cj(dxf); dyf = cj(dyf); dxb = cj(dxb); dyb = cj(dyb); P = cj(P);
-  }
-  if (!adjoint) {
-    // [[0, -H dxb, -H dyb], [-g dxf, 0, f P], [-g dyf, -f conj(P), 0]]
-    y[0] = cr(-sp.H, ca(cm(dxb, f[1]), cm(dyb, f[2])));
-    y[1] = cs(cr(sp.f, cm(P, f[2])), cr(sp.g, cm(dxf, f[0])));
-    y[2] = cs(cr(-sp.g, cm(dyf, f[0])), cr(sp.f, cm(cj(P), f[1])));
-  } else {
-    // B^H = [[0, -g conj(dxf), -g conj(dyf)], [-H conj(dxb), 0, -f P], [-H conj(dyb), f conj(P), 0]]
-    y[0] = cr(-sp.g, ca(cm(cj(dxf), f[1]), cm(cj(dyf), f[2])));
-    y[1] = cs(cr(-sp.H, cm(cj(dxb), f[0])), cr(sp.f, cm(P, f[2])));
-    y[2] = ca(cr(-sp.H, cm(cj(dyb), f[0])), cr(sp.f, cm(cj(P), f[1])));
-  }
-}
-
-// out = R0 f + Im(R+) Bt f + (R0 - Re R+) Bt^2 f, Bt = B / omega, in place on
-// the three fields of wavenumber index `idx` (field stride fs).
-__device__ __forceinline__ void combine(double2* spec, size_t idx, size_t fs, const Symbol& S,
-                                        const SymbolParams& sp, bool conj_sym, bool adjoint,
-                                        double2 R0, double2 Rp) {
-  double2 f[3], y1[3], y2[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) f[c] = spec[idx + c * fs];
-  double2 c0 = adjoint ? cj(R0) : R0;
-  double2 out[3];
-  if (S.omega > 0.0) {
-    const double inv = 1.0 / S.omega;
-    apply_B(S, sp, conj_sym, adjoint, f, y1);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) y1[c] = cr(inv, y1[c]);
-    apply_B(S, sp, conj_sym, adjoint, y1, y2);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) y2[c] = cr(inv, y2[c]);
-    const double a1 = Rp.y;
-    double2 a2 = make_double2(R0.x - Rp.x, R0.y);
-    if (adjoint) a2 = cj(a2);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) out[c] = ca(ca(cm(c0, f[c]), cr(a1, y1[c])), cm(a2, y2[c]));
-  } else {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) out[c] = cm(c0, f[c]);
-  }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) spec[idx + c * fs] = out[c];
-}
-
-// Map thread -> wavenumber pair.  Pairs (k, -k) with ky in [0, ny/2]; in the
-// self-conjugate rows (ky = 0, and ky = ny/2 for even ny) only kx <= nx/2.
-__device__ __forceinline__ bool pair_of(int p, int nx, int ny, int& kx, int& ky, int& kx2, int& ky2) {
-  ky = p / nx;
-  kx = p - ky * nx;
-  if (ky > ny / 2) return false;
-  const bool selfrow = (ky == 0) || (2 * ky == ny);
-  if (selfrow && kx > nx / 2) return false;
-  kx2 = kx == 0 ? 0 : nx - kx;
-  ky2 = ky == 0 ? 0 : ny - ky;
-  return true;
-}
-
-// ---------------------------------------------------------------------------
-// FP64 fused pole loop.
-// Table (per scalar term, 6 doubles): h n, A_re, A_im, B_re, B_im, 0 with
-// A = c1_n h mu, B = c2_n.
-
-__device__ __forceinline__ double rcp_seed(double d) {
-  double r;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
-  return r;
-}
-
-constexpr int kChunk = 256;  // terms staged in shared memory at a time
 
 __global__ void __launch_bounds__(128) pole_fused_fp64_kernel(double2* spec, SymbolParams sp,
                                                               const double* __restrict__ table,
@@ -162,16 +50,7 @@ __global__ void __launch_bounds__(128) pole_fused_fp64_kernel(double2* spec, Sym
     for (int i = threadIdx.x; i < cnt * 3; i += blockDim.x) st[i] = tb[(size_t)t0 * 3 + i];
     __syncthreads();
 #pragma unroll 4
-    for (int t = 0; t < cnt; ++t) {
-      const double2 e0 = st[3 * t], e1 = st[3 * t + 1], e2 = st[3 * t + 2];
-      // e0 = (h n, A_re), e1 = (A_im, B_re), e2 = (B_im, 0)
-      const double y = x + e0.x;
-      const double d = fma(y, y, q);
-      const double r0 = rcp_seed(d);
-      const double r = fma(r0, fma(-d, r0, 1.0), r0);  // one Newton-Raphson step
-      accr = fma(fma(e1.y, y, e0.y), r, accr);
-      acci = fma(fma(e2.x, y, e1.x), r, acci);
-    }
+    for (int t = 0; t < cnt; ++t) fp64_term(st + 3 * t, x, q, accr, acci);
   }
   if (!active) return;
   const double2 R0 = make_double2(fs.R0re, fs.R0im);
@@ -194,25 +73,7 @@ cudaError_t pole_fused_fp64(double2* spec, const SymbolParams& sp, const double*
 }
 
 // ---------------------------------------------------------------------------
-// Double-float fused pole loop.
-// A value v is carried as an unevaluated sum hi + lo of two FP32 numbers.
-// Error-free transformations (Knuth TwoSum, Dekker TwoProduct via FMA); the
-// _rn intrinsics keep the compiler from contracting or reassociating them.
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {  // |a| >= |b| or a == 0
-  s = __fadd_rn(a, b);
-  e = __fsub_rn(b, __fsub_rn(s, a));
-}
-__device__ __forceinline__ float rcp_approx_f32(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
+// Double-float fused pole loop (helpers in pole_common.cuh).
 
 // Table (per scalar term, 12 floats):
 //  [hn_hi, Ar_hi, Ai_hi, Br_hi], [Bi_hi, Ar_lo, Ai_lo, Br_lo], [Bi_lo, hn_lo, 0, 0]
@@ -238,52 +99,7 @@ __global__ void __launch_bounds__(128) pole_fused_mixed_kernel(double2* spec, Sy
     for (int i = threadIdx.x; i < cnt * 3; i += blockDim.x) st[i] = table[(size_t)t0 * 3 + i];
     __syncthreads();
 #pragma unroll 2
-    for (int t = 0; t < cnt; ++t) {
-      const float4 e0 = st[3 * t], e1 = st[3 * t + 1], e2 = st[3 * t + 2];
-      // y = x + h n: exact high part, then renormalise
-      float y_h, y_l;
-      fast_two_sum(__fadd_rn(X_hi, e0.x), __fadd_rn(X_lo, e2.y), y_h, y_l);
-      // d = q + y^2
-      const float p_h = __fmul_rn(y_h, y_h);
-      const float p_l = __fmaf_rn(y_h, y_h, -p_h);
-      float d_h, d_e;
-      two_sum(q_hi, p_h, d_h, d_e);
-      const float d_l = __fadd_rn(__fadd_rn(d_e, p_l), __fmaf_rn(2.0f * y_h, y_l, q_lo));
-      // r = 1/d: FP32 seed, one Newton-Raphson correction carried in the low part
-      const float r0 = rcp_approx_f32(d_h);
-      float tcorr = __fmaf_rn(-d_h, r0, 1.0f);
-      tcorr = __fmaf_rn(-d_l, r0, tcorr);
-      const float r_l = __fmul_rn(r0, tcorr);
-      // N = A + B y (real and imaginary parts), then T = N r, acc += T
-      {
-        const float t_h = __fmul_rn(e0.w, y_h);
-        const float t_l = __fmaf_rn(e0.w, y_h, -t_h);
-        const float cross = __fmaf_rn(e0.w, y_l, __fmul_rn(e1.w, y_h));
-        float n_h, n_e;
-        two_sum(e0.y, t_h, n_h, n_e);
-        const float n_l = __fadd_rn(__fadd_rn(n_e, t_l), __fadd_rn(cross, e1.y));
-        const float T_h = __fmul_rn(n_h, r0);
-        const float T_l = __fadd_rn(__fmaf_rn(n_h, r0, -T_h), __fmaf_rn(n_h, r_l, __fmul_rn(n_l, r0)));
-        float s, e;
-        two_sum(ar_h, T_h, s, e);
-        ar_h = s;
-        ar_l = __fadd_rn(ar_l, __fadd_rn(e, T_l));
-      }
-      {
-        const float t_h = __fmul_rn(e1.x, y_h);
-        const float t_l = __fmaf_rn(e1.x, y_h, -t_h);
-        const float cross = __fmaf_rn(e1.x, y_l, __fmul_rn(e2.x, y_h));
-        float n_h, n_e;
-        two_sum(e0.z, t_h, n_h, n_e);
-        const float n_l = __fadd_rn(__fadd_rn(n_e, t_l), __fadd_rn(cross, e1.z));
-        const float T_h = __fmul_rn(n_h, r0);
-        const float T_l = __fadd_rn(__fmaf_rn(n_h, r0, -T_h), __fmaf_rn(n_h, r_l, __fmul_rn(n_l, r0)));
-        float s, e;
-        two_sum(ai_h, T_h, s, e);
-        ai_h = s;
-        ai_l = __fadd_rn(ai_l, __fadd_rn(e, T_l));
-      }
-    }
+    for (int t = 0; t < cnt; ++t) df_term(st + 3 * t, X_hi, X_lo, q_hi, q_lo, ar_h, ar_l, ai_h, ai_l);
   }
   if (!active) return;
   const double2 R0 = make_double2(fs.R0re, fs.R0im);

@@ -19,6 +19,9 @@ REXI_ENOCONV = -4
 REXI_ETIMEOUT = -5
 REXI_EUNSUPPORTED = -6
 
+REXI_BATCH_PERSISTENT = 0
+REXI_BATCH_PER_INSTANCE = 1
+
 REXI_FORM_FP64 = 0
 REXI_FORM_MIXED = 1
 REXI_FORM_PLAIN = 2
@@ -66,6 +69,14 @@ SIGNATURES = {
     "rexi_plan_read_profile": (_c_int, [_vp, _dp, _ip, ctypes.POINTER(ctypes.c_int64)]),
     "rexi_step_noalloc": (_c_int, [_c_int, _c_int, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _c_dbl, _vp, _vp,
                                    _c_dbl, _c_dbl, _c_int, _vp]),
+    "rexi_batch_create": (_c_int, [ctypes.POINTER(_vp), _c_int, _ip, _ip, _dp, _c_dbl, _c_dbl, _c_dbl, _c_dbl,
+                                   _c_dbl, _c_dbl, _c_int, _c_dbl]),
+    "rexi_batch_destroy": (None, [_vp]),
+    "rexi_batch_layout": (_c_int, [_vp, ctypes.POINTER(ctypes.c_int64), _ip, ctypes.POINTER(ctypes.c_size_t)]),
+    "rexi_batch_step": (_c_int, [_vp, _vp, _vp, _c_int, _vp, ctypes.c_size_t, _c_int, _vp]),
+    "rexi_batch_autotune": (_c_int, [_vp, _vp, _vp, _c_int, _vp, ctypes.c_size_t, _vp, _ip, _ip, _dp]),
+    "rexi_batch_info": (_c_int, [_vp, _ip, _ip, _ip, _ip, ctypes.POINTER(ctypes.c_int64),
+                                 ctypes.POINTER(ctypes.c_int64)]),
     "rexi_status_string": (ctypes.c_char_p, [_c_int]),
     "rexi_version": (ctypes.c_char_p, []),
     "rexi_last_error_message": (ctypes.c_char_p, []),
@@ -273,3 +284,91 @@ class Plan:
                                          _ptr(workspace), workspace.numel(), _stream_handle(stream))
         _check(st, "rexi_step_adjoint")
         return out
+
+
+class Batch:
+    """Owns one rexi_batch_t: many constant-depth instances stepped together.
+
+    ``sizes`` is a list of (nx, ny), ``dts`` the per-instance time steps.
+    ``pack``/``unpack`` move per-instance (3, ny, nx) tensors in and out of the
+    packed device buffer (plain tensor copies; the step itself is one call)."""
+
+    def __init__(self, sizes, dts, Lx=1.0, Ly=1.0, g=1.0, f=1.0, H=1.0, tol=1e-10, form="fp64", h=0.5):
+        import numpy as np
+
+        lib = load()
+        self._lib = lib
+        self.n = len(sizes)
+        self.sizes = [(int(a), int(b)) for a, b in sizes]
+        nx = (ctypes.c_int32 * self.n)(*[s[0] for s in self.sizes])
+        ny = (ctypes.c_int32 * self.n)(*[s[1] for s in self.sizes])
+        dt = (ctypes.c_double * self.n)(*[float(d) for d in dts])
+        handle = ctypes.c_void_p()
+        _check(lib.rexi_batch_create(ctypes.byref(handle), self.n, nx, ny, dt, Lx, Ly, g, f, H, tol,
+                                     FORMS[form] if isinstance(form, str) else int(form), h), "rexi_batch_create")
+        self._h = handle
+        offs = (ctypes.c_int64 * (self.n + 1))()
+        Ms = (ctypes.c_int32 * self.n)()
+        ws = ctypes.c_size_t()
+        _check(lib.rexi_batch_layout(handle, offs, Ms, ctypes.byref(ws)), "rexi_batch_layout")
+        self.offsets = np.array(offs[:], dtype=np.int64)
+        self.M = list(Ms[:])
+        self.workspace_bytes = ws.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.rexi_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def empty(self, device="cuda"):
+        import torch
+
+        return torch.empty(int(self.offsets[-1]), dtype=torch.complex128, device=device)
+
+    def workspace(self, device="cuda"):
+        import torch
+
+        return torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=device)
+
+    def pack(self, states, out=None):
+        buf = self.empty(states[0].device) if out is None else out
+        for i, (nx, ny) in enumerate(self.sizes):
+            buf[int(self.offsets[i]):int(self.offsets[i]) + 3 * nx * ny].copy_(states[i].reshape(-1))
+        return buf
+
+    def unpack(self, buf):
+        return [buf[int(self.offsets[i]):int(self.offsets[i]) + 3 * nx * ny].view(3, ny, nx)
+                for i, (nx, ny) in enumerate(self.sizes)]
+
+    def step(self, packed_in, packed_out=None, workspace=None, real_input=True, mode=REXI_BATCH_PERSISTENT,
+             stream=None):
+        if packed_out is None:
+            packed_out = packed_in.new_empty(packed_in.shape)
+        if workspace is None:
+            workspace = self.workspace(packed_in.device)
+        _check(self._lib.rexi_batch_step(self._h, _ptr(packed_in), _ptr(packed_out), int(real_input),
+                                         _ptr(workspace), workspace.numel(), int(mode), _stream_handle(stream)),
+               "rexi_batch_step")
+        return packed_out
+
+    def autotune(self, packed_in, packed_out, workspace, real_input=True, stream=None):
+        t = ctypes.c_int32()
+        p = ctypes.c_int32()
+        ms = ctypes.c_double()
+        _check(self._lib.rexi_batch_autotune(self._h, _ptr(packed_in), _ptr(packed_out), int(real_input),
+                                             _ptr(workspace), workspace.numel(), _stream_handle(stream),
+                                             ctypes.byref(t), ctypes.byref(p), ctypes.byref(ms)),
+               "rexi_batch_autotune")
+        return t.value, p.value, ms.value
+
+    def info(self):
+        vals = [ctypes.c_int32() for _ in range(4)] + [ctypes.c_int64(), ctypes.c_int64()]
+        _check(self._lib.rexi_batch_info(self._h, *[ctypes.byref(v) for v in vals]), "rexi_batch_info")
+        keys = ["threads", "pairs_per_thread", "ctas", "n_items", "terms_pairs", "launches"]
+        return {k: v.value for k, v in zip(keys, vals)}

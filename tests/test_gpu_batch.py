@@ -1,0 +1,105 @@
+"""Batched serving launch: every instance of a batch must equal what the
+single-instance step computes for it (and, for a small instance, the oracle),
+in both the persistent (graph-replayed) mode and the per-instance mode."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import coeffs as C
+from paper_2008_11607_gb300 import inputs
+from tests.gpu_util import TOL, oracle_step, rel_l2, to_dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def make_batch(torch, sizes, tau_rhos, form, seed0=0, real=True):
+    from paper_2008_11607_gb300 import rexi
+
+    plans = [rexi.Plan(nx, ny, form=form) for nx, ny in sizes]
+    dts = [tr / p.rho for tr, p in zip(tau_rhos, plans)]
+    b = rexi.Batch(sizes, dts, form=form)
+    if real:
+        states = [to_dev(torch, inputs.kminus3_field(nx, ny, seed=seed0 + i)) for i, (nx, ny) in enumerate(sizes)]
+    else:
+        states = [to_dev(torch, inputs.complex_random_state(nx, ny, seed=seed0 + i)) for i, (nx, ny) in enumerate(sizes)]
+    return b, plans, dts, states
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+@pytest.mark.parametrize("real", [True, False])
+def test_small_batch_matches_single_instance(form, real):
+    torch = torch_cuda()
+    from paper_2008_11607_gb300 import rexi
+
+    sizes = [(16, 16), (24, 20), (16, 16), (12, 18), (32, 32), (9, 15)]
+    trs = [10.0, 30.0, 5.0, 20.0, 40.0, 12.0]
+    b, plans, dts, states = make_batch(torch, sizes, trs, form, real=real)
+    packed = b.pack(states)
+    ws = b.workspace()
+    refs = [p.step(s, dt, real_input=real) for p, s, dt in zip(plans, states, dts)]
+    for mode in (rexi.REXI_BATCH_PERSISTENT, rexi.REXI_BATCH_PER_INSTANCE):
+        out = b.step(packed, workspace=ws, real_input=real, mode=mode)
+        torch.cuda.synchronize()
+        for o, r in zip(b.unpack(out), refs):
+            assert rel_l2(o.cpu().numpy(), r.cpu().numpy()) < 1e-13
+    assert b.M == [C.pole_count_M(tr, 0.5, 1e-10) for tr in trs]
+    # one instance against the oracle
+    st = states[1].cpu().numpy()
+    ref = oracle_step(st, dts[1], b.M[1], real_input=real)
+    assert rel_l2(b.unpack(out)[1].cpu().numpy(), ref) < TOL[form]
+
+
+def test_graph_replay_and_autotune():
+    torch = torch_cuda()
+    from paper_2008_11607_gb300 import rexi
+
+    sizes = [(32, 32), (48, 48), (32, 32), (20, 24)]
+    trs = [25.0, 60.0, 8.0, 15.0]
+    b, plans, dts, states = make_batch(torch, sizes, trs, "mixed", seed0=10)
+    packed = b.pack(states)
+    out = b.empty()
+    ws = b.workspace()
+    b.step(packed, out, ws)  # captures the graph
+    # new data in the same buffers: the replayed graph must see it
+    states2 = [to_dev(torch, inputs.kminus3_field(nx, ny, seed=100 + i)) for i, (nx, ny) in enumerate(sizes)]
+    b.pack(states2, out=packed)
+    b.step(packed, out, ws)
+    torch.cuda.synchronize()
+    for o, p, s, dt in zip(b.unpack(out), plans, states2, dts):
+        assert rel_l2(o.cpu().numpy(), p.step(s, dt).cpu().numpy()) < 1e-13
+    t, ppt, ms = b.autotune(packed, out, ws)
+    assert t in (64, 128, 256) and ppt in (1, 2) and ms > 0
+    b.pack(states2, out=packed)
+    b.step(packed, out, ws)
+    torch.cuda.synchronize()
+    info = b.info()
+    assert info["threads"] == t and info["pairs_per_thread"] == ppt and info["n_items"] > 0
+    for o, p, s, dt in zip(b.unpack(out), plans, states2, dts):
+        assert rel_l2(o.cpu().numpy(), p.step(s, dt).cpu().numpy()) < 1e-13
+
+
+def test_serving_mix_96_instances():
+    """The serving workload: 96 instances, D uniform from {128, 192, 256, 384,
+    512}, tau rho log-uniform in [20, 800], |k|^-3 fields with seeds 0..95,
+    mixed form, persistent mode (autotuned) and per-instance mode, every
+    instance against the single-instance step."""
+    torch = torch_cuda()
+    from paper_2008_11607_gb300 import rexi
+
+    mix = inputs.batched_instances()
+    sizes = [(m["nx"], m["ny"]) for m in mix]
+    trs = [m["tau_rho"] for m in mix]
+    b, plans, dts, _ = make_batch(torch, sizes, trs, "mixed")
+    states = [to_dev(torch, inputs.kminus3_field(m["nx"], m["ny"], seed=m["seed"])) for m in mix]
+    packed = b.pack(states)
+    out = b.empty()
+    ws = b.workspace()
+    b.autotune(packed, out, ws)
+    b.step(packed, out, ws)
+    out2 = b.step(packed, workspace=ws, mode=rexi.REXI_BATCH_PER_INSTANCE)
+    torch.cuda.synchronize()
+    for o, o2, p, s, dt in zip(b.unpack(out), b.unpack(out2), plans, states, dts):
+        r = p.step(s, dt).cpu().numpy()
+        assert rel_l2(o.cpu().numpy(), r) < 1e-12
+        assert rel_l2(o2.cpu().numpy(), r) < 1e-12
