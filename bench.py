@@ -333,6 +333,52 @@ def krylov_measure(torch, rexi, inputs, form, n_terms, rtol, warm=1):
     }
 
 
+def batch_measure(torch, rexi, inputs, form="mixed", reps=5):
+    """Serving mix: 96 instances, D uniform from {128, 192, 256, 384, 512},
+    tau rho log-uniform in [20, 800], |k|^-3 fields (seeds 0..95), real input.
+    Persistent mode (autotuned, graph replay) against per-instance launches."""
+    mix = inputs.batched_instances()
+    sizes = [(m["nx"], m["ny"]) for m in mix]
+    dts = []
+    units = 0
+    for m in mix:
+        rho = rexi.Plan(m["nx"], m["ny"]).rho
+        dts.append(m["tau_rho"] / rho)
+        M = rexi.rexi_pole_count(m["tau_rho"], H_PARAM, TOL)
+        units += m["nx"] * m["ny"] * 2 * (M + 24 + 1)
+    b = rexi.Batch(sizes, dts, form=form, tol=TOL, h=H_PARAM)
+    states = [torch.from_numpy(inputs.kminus3_field(m["nx"], m["ny"], seed=m["seed"])).cuda() for m in mix]
+    packed = b.pack(states)
+    out = b.empty()
+    ws = b.workspace()
+    t, ppt, _ = b.autotune(packed, out, ws)
+    res = {}
+    for name, mode in (("persistent_graph", rexi.REXI_BATCH_PERSISTENT), ("per_instance", rexi.REXI_BATCH_PER_INSTANCE)):
+        for _ in range(3):
+            b.step(packed, out, ws, mode=mode)
+        torch.cuda.synchronize()
+        l0 = b.info()["launches"]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            b.step(packed, out, ws, mode=mode)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms_per_step": ms, "value": units / (ms / 1e3),
+                     "kernel_launches_per_step": (b.info()["launches"] - l0) / reps}
+    info = b.info()
+    return {
+        "workload": "96 constant-depth instances, D uniform from {128,192,256,384,512}, tau*rho log-uniform in "
+                    "[20, 800] (M %d..%d), |k|^-3 eta seeds 0-95, real input, form=%s" % (min(b.M), max(b.M), form),
+        "unit": UNIT, "units_per_step": units, "autotuned": {"threads": t, "pairs_per_thread": ppt,
+                                                             "ctas": info["ctas"], "work_items": info["n_items"]},
+        "terms_x_pairs": info["terms_pairs"], **res,
+        "speedup_persistent_vs_per_instance": res["per_instance"]["ms_per_step"] / res["persistent_graph"]["ms_per_step"],
+    }
+
+
 def run_ours(args):
     import torch
 
@@ -438,6 +484,10 @@ def run_ours(args):
             forms[form] = {"value": world * units / (fms / 1e3), "ms_per_step": fms, "steps": k,
                            "pole_ms": fprof[0][1] / max(fprof[1], 1)}
 
+    batched = None
+    if not args.skip_batch:
+        batched = batch_measure(torch, rexi, inputs)
+
     krylov = None
     if not args.skip_krylov:
         krylov = {}
@@ -467,7 +517,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32x2+f64" if args.form == "mixed" else "f64", "data": "synthetic",
             "config": cfg, "clocks": clocks, "e2e": e2e, "gpu_launches": nlaunch, "roofline": roofline,
-            "roofline_fft": roofline_fft, "phases_ms": phases, "forms": forms, "krylov": krylov,
+            "roofline_fft": roofline_fft, "phases_ms": phases, "forms": forms, "batched": batched, "krylov": krylov,
             "cpu_baseline": cpu,
             "accuracy": {"tolerance": 1e-8 if args.form == "mixed" else 1e-10,
                          "max_rel_err_vs_oracle_sampled": cpu["max_rel_err_vs_oracle"] if cpu else None},
@@ -489,6 +539,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-krylov", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--batch-only", action="store_true", help="run only the serving-mix measurement")
     ap.add_argument("--krylov-terms", type=int, default=8)
     ap.add_argument("--krylov-form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--krylov-only", action="store_true",
@@ -498,6 +550,15 @@ def main():
     args.warmup = max(args.warmup, 3)  # timing rule: at least 3 untimed warm-up steps
     if args.impl == "reference":
         run_reference(args)
+    elif args.batch_only:
+        import torch
+
+        from paper_2008_11607_gb300 import build as B
+
+        B.build()
+        from paper_2008_11607_gb300 import inputs, rexi
+
+        print(json.dumps(batch_measure(torch, rexi, inputs)), flush=True)
     elif args.krylov_only:
         import torch
 
