@@ -178,6 +178,20 @@ rexi_status rexi_step_adjoint(rexi_plan_t plan, const void* grad_out_dev, void* 
                               double dt, double tol, int32_t real_input, void* workspace_dev,
                               size_t workspace_bytes, void* stream);
 
+/* Gradient with respect to the depth field (variable-depth plans only;
+ * REXI_EUNSUPPORTED otherwise).  For out = r(dt A(H)) in and a real loss L
+ * with grad_out = dL/d out (complex convention dL/dRe + i dL/dIm), ADDS dL/dH
+ * to grad_depth_dev (ny * nx FP64 values at eta points, device).  With the
+ * single-shift form r(dt A) = sum_j beta_j (dt A - z_j)^{-1} and H entering A
+ * only through the eta row, (A v)_eta = -H div v:
+ *   dL/dH_k = dt Re sum_j beta_j conj(y_j,eta,k) (div x_j)_k,
+ *   x_j = (dt A - z_j)^{-1} in,  y_j = (dt A - z_j)^{-H} grad_out;
+ * both are recovered per REXII term from two CG solves with the pair
+ * operator.  Same workspace as rexi_step; info as for rexi_step. */
+rexi_status rexi_step_grad_depth(rexi_plan_t plan, const void* in_dev, const void* grad_out_dev,
+                                 double* grad_depth_dev, double dt, double tol, int32_t real_input,
+                                 void* workspace_dev, size_t workspace_bytes, void* stream, rexi_step_info* info);
+
 /* out = r(dt A) in with HOST buffers: copies `in_host` to the device
  * workspace, runs rexi_step there and copies the result back into
  * `out_host`, all on `stream`, then synchronises the stream so that

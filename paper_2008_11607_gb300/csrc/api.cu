@@ -683,3 +683,26 @@ rexi_status rexi_plan_read_profile(rexi_plan_t p, double* ms4, int32_t* n_calls,
 }
 
 }  // extern "C"
+
+extern "C" rexi_status rexi_step_grad_depth(rexi_plan_t p, const void* in, const void* gout, double* grad_depth,
+                                           double dt, double tol, int32_t real_input, void* ws, size_t ws_bytes,
+                                           void* stream, rexi_step_info* info) {
+  g_err[0] = 0;
+  int M = 0;
+  rexi_status st = check_step_args(p, in, const_cast<void*>(gout), dt, tol, ws, &M);
+  if (st != REXI_OK) return st;
+  if (!p->depth) return fail(REXI_EUNSUPPORTED, "depth gradient needs a variable-depth plan");
+  if (!grad_depth || ((uintptr_t)grad_depth & 7)) return fail(REXI_EINVAL, "grad_depth must be 8-byte aligned");
+  KrylovHooks hooks;
+  hooks.mark = [](void* ctx, int i, cudaStream_t s) { prof_mark(static_cast<rexi_plan_s*>(ctx), i, s); };
+  hooks.ctx = p;
+  hooks.launches = &p->launches;
+  st = krylov_grad_depth(&p->kry, p->form, p->h, M, in, gout, grad_depth, dt, real_input, ws, ws_bytes,
+                         static_cast<cudaStream_t>(stream), info, hooks);
+  if (info) {
+    info->M = M;
+    info->tau_rho = dt * p->rho;
+    info->rho = p->rho;
+  }
+  return st;
+}

@@ -60,6 +60,7 @@ struct TermScalars {
   double gamma, gamma0, dot1, a, beta;
   int iters, status;          // status 0 active, 1 converged, 2 iteration cap
   int pad0, pad1;
+  double2 gP, gQ;             // single-shift weights of the term's two poles (depth gradient)
 };
 
 // ---- complex arithmetic for float2 / double2 ------------------------------
@@ -86,6 +87,7 @@ struct Geom {
   R tdx, tdy;      // tau / dx, tau / dy (times H per point in the eta row)
   R tgdx, tgdy;    // tau g / dx, tau g / dy
   R tf4;           // tau f / 4
+  R idx, idy;      // 1 / dx, 1 / dy
   const R* H;      // depth at eta points
   const R* w;      // energy weight g / H
 };
@@ -504,6 +506,77 @@ __global__ void depth_tables(const double* H, size_t nk, double g, double* w64, 
   w32[i] = (float)w;
 }
 
+// ---- depth gradient ------------------------------------------------------------
+// For one REXII term with x = N^{-1} f and y = N^{-1} W^{-1} G (both CG solves
+// with N = B^* B), the term's two single-shift poles contribute
+//   tau Re[ Gamma Q w conj((B y)_eta) div(B^* x) - Gamma P w conj((B^* y)_eta) div(B x) ]
+// to dL/dH at each eta point (B = alpha_n + tau A, B^* = alpha_{-n} - tau A,
+// w = g/H, P and Q the partial-fraction weights).  Stage 1 forms the u, v
+// components of B^* x and B x and the eta components of B y and B^* y; stage 2
+// takes the divergences and sums over the batch in a fixed order.
+
+// out1 fields: (B* x)_u, (B* x)_v, (B y)_eta ; out2 fields: (B x)_u, (B x)_v, (B* y)_eta
+__global__ void __launch_bounds__(THREADS) grad_stage1(Geom<double> G, const double2* xs, const double2* ys,
+                                                       double2* out1, double2* out2, size_t vstride,
+                                                       const TermScalars* sc) {
+  __shared__ double2 E[HY][HX], U[HY][HX], V[HY][HX];
+  const int term = blockIdx.z;
+  const TermScalars& S = sc[term];
+  const double2 al = S.alpha_n, am = S.alpha_mn;
+  double2* o1 = out1 + (size_t)term * vstride;
+  double2* o2 = out2 + (size_t)term * vstride;
+  load_tile<double, false>(G, xs + (size_t)term * vstride, (const double2*)nullptr, 0.0, E, U, V);
+  for (int k = threadIdx.x; k < TX * TY; k += THREADS) {
+    const int li = k % TX + 1, lj = k / TX + 1;
+    const int i = blockIdx.x * TX + li - 1, j = blockIdx.y * TY + lj - 1;
+    if (i >= G.nx || j >= G.ny) continue;
+    const size_t id = (size_t)j * G.nx + i;
+    double2 ae, au, av;
+    apply_tA<double>(E, U, V, li, lj, G.H[id], G, ae, au, av);
+    o1[id] = csub(cmul(am, U[lj][li]), au);
+    o1[id + G.fstride] = csub(cmul(am, V[lj][li]), av);
+    o2[id] = cadd(cmul(al, U[lj][li]), au);
+    o2[id + G.fstride] = cadd(cmul(al, V[lj][li]), av);
+  }
+  __syncthreads();
+  load_tile<double, false>(G, ys + (size_t)term * vstride, (const double2*)nullptr, 0.0, E, U, V);
+  for (int k = threadIdx.x; k < TX * TY; k += THREADS) {
+    const int li = k % TX + 1, lj = k / TX + 1;
+    const int i = blockIdx.x * TX + li - 1, j = blockIdx.y * TY + lj - 1;
+    if (i >= G.nx || j >= G.ny) continue;
+    const size_t id = (size_t)j * G.nx + i;
+    double2 ae, au, av;
+    apply_tA<double>(E, U, V, li, lj, G.H[id], G, ae, au, av);
+    o1[id + 2 * G.fstride] = cadd(cmul(al, E[lj][li]), ae);
+    o2[id + 2 * G.fstride] = csub(cmul(am, E[lj][li]), ae);
+  }
+}
+
+__global__ void grad_stage2(Geom<double> G, const double2* out1, const double2* out2, size_t vstride, int nbatch,
+                            const TermScalars* sc, double tau, double* grad) {
+  const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= G.fstride) return;
+  const int i = (int)(id % G.nx), j = (int)(id / G.nx);
+  const size_t iw = (size_t)j * G.nx + (i == 0 ? G.nx - 1 : i - 1);
+  const size_t js = (size_t)(j == 0 ? G.ny - 1 : j - 1) * G.nx + i;
+  const size_t F = G.fstride;
+  const double w = G.w[id];
+  double acc = 0.0;
+  for (int b = 0; b < nbatch; ++b) {
+    const double2* a = out1 + (size_t)b * vstride;
+    const double2* c = out2 + (size_t)b * vstride;
+    const double2 div1 = cadd(mk(G.idx * (a[id].x - a[iw].x), G.idx * (a[id].y - a[iw].y)),
+                              mk(G.idy * (a[F + id].x - a[F + js].x), G.idy * (a[F + id].y - a[F + js].y)));
+    const double2 div2 = cadd(mk(G.idx * (c[id].x - c[iw].x), G.idx * (c[id].y - c[iw].y)),
+                              mk(G.idy * (c[F + id].x - c[F + js].x), G.idy * (c[F + id].y - c[F + js].y)));
+    const double2 s1 = a[2 * F + id], s2 = c[2 * F + id];
+    const double2 t1 = cmul(sc[b].gQ, cmul(mk(s1.x, -s1.y), div1));
+    const double2 t2 = cmul(sc[b].gP, cmul(mk(s2.x, -s2.y), div2));
+    acc += w * (t1.x - t2.x);
+  }
+  grad[id] += tau * acc;
+}
+
 // ---- workspace layout ------------------------------------------------------
 
 struct KLayout {
@@ -528,7 +601,7 @@ KLayout layout(const KrylovSettings* k, int nterms, int form) {
   off += al256(3 * nk * sizeof(double2));
   L.v64_off = off;
   L.v64_bytes = al256(3 * nk * sizeof(double2));
-  off += 4 * (size_t)L.batch * L.v64_bytes;
+  off += 5 * (size_t)L.batch * L.v64_bytes;  // x, r, p, t and a saved solution (depth gradient)
   L.v32_off = off;
   L.v32_bytes = al256(3 * nk * sizeof(float2));
   if (form == REXI_FORM_MIXED) off += 4 * (size_t)L.batch * L.v32_bytes;
@@ -563,6 +636,8 @@ Geom<R> make_geom(const KrylovSettings* k, double tau, const R* H, const R* w) {
   G.tgdx = (R)(tau * k->g * idx);
   G.tgdy = (R)(tau * k->g * idy);
   G.tf4 = (R)(0.25 * tau * k->f);
+  G.idx = (R)idx;
+  G.idy = (R)idy;
   G.H = H;
   G.w = w;
   return G;
@@ -608,116 +683,124 @@ size_t krylov_workspace_bytes(const KrylovSettings* k, int M, int real_input, in
   return layout(k, n_terms_for(M, real_input), form).total;
 }
 
-rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void* in, void* out, double dt,
-                        int real_input, int term_begin, int term_end, void* ws, size_t ws_bytes, cudaStream_t s,
-                        rexi_step_info* info, bool adjoint, const KrylovHooks& hooks) {
-  auto mark = [&](int i) {
-    if (hooks.mark) hooks.mark(hooks.ctx, i, s);
-  };
-  auto count = [&](int64_t n) {
-    if (hooks.launches) *hooks.launches += n;
-  };
-  if (form != REXI_FORM_FP64 && form != REXI_FORM_MIXED) {
-    set_last_error("variable-depth path: the plain form is Fourier-path only");
-    return REXI_EUNSUPPORTED;
-  }
-  const bool mixed = form == REXI_FORM_MIXED;
-  const int N = M + kL;
-  if (term_end < 0 || term_end > N + 1) term_end = N + 1;
-  if (term_begin < 0 || term_begin > term_end) {
-    set_last_error("bad term range");
-    return REXI_EINVAL;
-  }
-  const size_t nk = (size_t)k->nx * k->ny;
-  const size_t n3 = 3 * nk;
-  if ((const char*)in < (const char*)out + n3 * sizeof(double2) &&
-      (const char*)out < (const char*)in + n3 * sizeof(double2)) {
-    set_last_error("variable-depth path: input and output must not overlap");
-    return REXI_EINVAL;
-  }
-  // term list: n = 0..N (real input, Gamma) or -N..N, restricted to |n| in [term_begin, term_end)
-  TermSet ts;
-  rexii_terms(M, h, &ts);
-  const double hmu = h * ts.mu;
-  std::vector<TermScalars> terms;
-  for (int n = real_input ? 0 : -N; n <= N; ++n) {
-    const int an = n < 0 ? -n : n;
-    if (an < term_begin || an >= term_end) continue;
-    const int i = n + N;
-    const double gam = (real_input && n > 0) ? 2.0 : 1.0;
-    TermScalars t;
-    memset(&t, 0, sizeof(t));
-    t.alpha_n = make_double2(hmu, h * n);
-    t.alpha_mn = make_double2(hmu, -h * n);
-    // C1 = c1 h mu + c2 h n,  C2 = i c2
-    t.gC1 = make_double2(gam * (ts.c1re[i] * hmu + ts.c2re[i] * h * n), gam * (ts.c1im[i] * hmu + ts.c2im[i] * h * n));
-    t.gC2 = make_double2(-gam * ts.c2im[i], gam * ts.c2re[i]);
-    terms.push_back(t);
-  }
-  const KLayout L = layout(k, (int)std::max<size_t>(terms.size(), 1), form);
-  if (ws_bytes < L.total) {
-    set_last_error("workspace too small for the variable-depth path");
-    return REXI_ENOMEM;
-  }
-  char* base = static_cast<char*>(ws);
-  double2* acc = reinterpret_cast<double2*>(base + L.acc_off);
-  const size_t vs64 = L.v64_bytes / sizeof(double2);
-  double2* X = reinterpret_cast<double2*>(base + L.v64_off);
-  double2* R = X + (size_t)L.batch * vs64;
-  double2* P = X + 2 * (size_t)L.batch * vs64;
-  double2* T = X + 3 * (size_t)L.batch * vs64;
-  const size_t vs32 = L.v32_bytes / sizeof(float2);
-  float2* D32 = reinterpret_cast<float2*>(base + L.v32_off);
-  float2* R32 = D32 + (size_t)L.batch * vs32;
-  float2* P32 = D32 + 2 * (size_t)L.batch * vs32;
-  float2* T32 = D32 + 3 * (size_t)L.batch * vs32;
-  TermScalars* dsc = reinterpret_cast<TermScalars*>(base + L.sc_off);
-  TermScalars* dsc32 = reinterpret_cast<TermScalars*>(base + L.sc32_off);
-  double* partials = reinterpret_cast<double*>(base + L.part_off);
-  unsigned* counters = reinterpret_cast<unsigned*>(base + L.cnt_off);
+namespace {
 
-  // adjoint: r(tau A)^H = r(tau A^T) = W r(-tau A) W^{-1} with W = diag(g/H, 1, 1)
-  const double tau = adjoint ? -dt : dt;
-  const Geom<double> G = make_geom<double>(k, tau, k->depth, k->w64);
-  const Geom<float> G32 = make_geom<float>(k, tau, k->H32, k->w32);
-
-  const double2* src = static_cast<const double2*>(in);
-  cudaError_t e;
-  const int eb = 256;
-  const unsigned ebl = (unsigned)((n3 + eb - 1) / eb);
-  if (adjoint) {
-    double2* tmp = reinterpret_cast<double2*>(base + L.tmp_off);
-    scale_eta<<<ebl, eb, 0, s>>>(src, tmp, k->w64, nk, 1, real_input);
-    count(1);
-    src = tmp;
-  }
-  if ((e = cudaMemsetAsync(counters, 0, (size_t)L.batch * sizeof(unsigned), s)) != cudaSuccess) {
-    set_last_error(cudaGetErrorString(e));
-    return REXI_ECUDA;
-  }
-  if (terms.empty()) {
-    if ((e = cudaMemsetAsync(acc, 0, n3 * sizeof(double2), s)) != cudaSuccess) {
-      set_last_error(cudaGetErrorString(e));
-      return REXI_ECUDA;
-    }
-  }
+// One call of the Krylov path: the term list, the carve-up of the workspace
+// and the CG driver for one batch of terms (FP64, or FP32 with FP64
+// refinement).  The solution of the batch's pair systems is left in X.
+struct KrylovRun {
+  KrylovSettings* k = nullptr;
+  bool mixed = false;
+  cudaStream_t s = nullptr;
+  const KrylovHooks* hooks = nullptr;
+  KLayout L{};
+  char* base = nullptr;
+  double2 *acc = nullptr, *tmp = nullptr, *X = nullptr, *R = nullptr, *P = nullptr, *T = nullptr, *XS = nullptr;
+  float2 *D32 = nullptr, *R32 = nullptr, *P32 = nullptr, *T32 = nullptr;
+  size_t vs64 = 0, vs32 = 0;
+  TermScalars *dsc = nullptr, *dsc32 = nullptr;
+  double* partials = nullptr;
+  unsigned* counters = nullptr;
+  Geom<double> G{};
+  Geom<float> G32{};
+  std::vector<TermScalars> terms, hs, hs32;
   int worst_iters = 0, unconverged = 0;
   int64_t term_iters = 0;
   double worst_res = 0.0;
-  const int check_every = 16;
-  std::vector<TermScalars> hs(L.batch), hs32(L.batch);
+  static constexpr int check_every = 16;
 
-  // CG iterations on (sc, vectors) until every term of the batch has stopped
-  auto run_cg = [&](const auto& geom, auto* Xv, auto* Rv, auto* Pv, auto* Tv, size_t vs, TermScalars* sc, int nb,
-                    double rtol, std::vector<TermScalars>& host) -> cudaError_t {
-    using Rt = typename std::remove_const<decltype(geom.tdx)>::type;
+  void mark(int i) {
+    if (hooks && hooks->mark) hooks->mark(hooks->ctx, i, s);
+  }
+  void count(int64_t n) {
+    if (hooks && hooks->launches) *hooks->launches += n;
+  }
+
+  rexi_status setup(KrylovSettings* kk, int form, double h, int M, double tau, int real_input, int tb, int te,
+                    void* ws, size_t ws_bytes, cudaStream_t st, const KrylovHooks* hk) {
+    k = kk;
+    s = st;
+    hooks = hk;
+    if (form != REXI_FORM_FP64 && form != REXI_FORM_MIXED) {
+      set_last_error("variable-depth path: the plain form is Fourier-path only");
+      return REXI_EUNSUPPORTED;
+    }
+    mixed = form == REXI_FORM_MIXED;
+    const int N = M + kL;
+    if (te < 0 || te > N + 1) te = N + 1;
+    if (tb < 0 || tb > te) {
+      set_last_error("bad term range");
+      return REXI_EINVAL;
+    }
+    // n = 0..N (real input, Gamma) or -N..N, restricted to |n| in [tb, te)
+    TermSet ts;
+    rexii_terms(M, h, &ts);
+    const double hmu = h * ts.mu;
+    for (int n = real_input ? 0 : -N; n <= N; ++n) {
+      const int an = n < 0 ? -n : n;
+      if (an < tb || an >= te) continue;
+      const int i = n + N;
+      const double gam = (real_input && n > 0) ? 2.0 : 1.0;
+      TermScalars t;
+      memset(&t, 0, sizeof(t));
+      t.alpha_n = make_double2(hmu, h * n);
+      t.alpha_mn = make_double2(hmu, -h * n);
+      // C1 = c1 h mu + c2 h n,  C2 = i c2
+      const double C1r = ts.c1re[i] * hmu + ts.c2re[i] * h * n, C1i = ts.c1im[i] * hmu + ts.c2im[i] * h * n;
+      const double C2r = -ts.c2im[i], C2i = ts.c2re[i];
+      t.gC1 = make_double2(gam * C1r, gam * C1i);
+      t.gC2 = make_double2(gam * C2r, gam * C2i);
+      // P = (C1 - C2 alpha_{-n}) / (2 h mu),  Q = (C1 + C2 alpha_n) / (2 h mu)
+      const double inv2 = 1.0 / (2.0 * hmu), hn = h * n;
+      t.gP = make_double2(gam * (C1r - (C2r * hmu + C2i * hn)) * inv2, gam * (C1i - (-C2r * hn + C2i * hmu)) * inv2);
+      t.gQ = make_double2(gam * (C1r + (C2r * hmu - C2i * hn)) * inv2, gam * (C1i + (C2r * hn + C2i * hmu)) * inv2);
+      terms.push_back(t);
+    }
+    L = layout(k, (int)std::max<size_t>(terms.size(), 1), form);
+    if (ws_bytes < L.total) {
+      set_last_error("workspace too small for the variable-depth path");
+      return REXI_ENOMEM;
+    }
+    base = static_cast<char*>(ws);
+    acc = reinterpret_cast<double2*>(base + L.acc_off);
+    tmp = reinterpret_cast<double2*>(base + L.tmp_off);
+    vs64 = L.v64_bytes / sizeof(double2);
+    X = reinterpret_cast<double2*>(base + L.v64_off);
+    R = X + (size_t)L.batch * vs64;
+    P = X + 2 * (size_t)L.batch * vs64;
+    T = X + 3 * (size_t)L.batch * vs64;
+    XS = X + 4 * (size_t)L.batch * vs64;
+    vs32 = L.v32_bytes / sizeof(float2);
+    D32 = reinterpret_cast<float2*>(base + L.v32_off);
+    R32 = D32 + (size_t)L.batch * vs32;
+    P32 = D32 + 2 * (size_t)L.batch * vs32;
+    T32 = D32 + 3 * (size_t)L.batch * vs32;
+    dsc = reinterpret_cast<TermScalars*>(base + L.sc_off);
+    dsc32 = reinterpret_cast<TermScalars*>(base + L.sc32_off);
+    partials = reinterpret_cast<double*>(base + L.part_off);
+    counters = reinterpret_cast<unsigned*>(base + L.cnt_off);
+    G = make_geom<double>(k, tau, k->depth, k->w64);
+    G32 = make_geom<float>(k, tau, k->H32, k->w32);
+    hs.resize(L.batch);
+    hs32.resize(L.batch);
+    cudaError_t e = cudaMemsetAsync(counters, 0, (size_t)L.batch * sizeof(unsigned), s);
+    if (e != cudaSuccess) {
+      set_last_error(cudaGetErrorString(e));
+      return REXI_ECUDA;
+    }
+    return REXI_OK;
+  }
+
+  // CG iterations on (sc, vectors) until every term of the batch has stopped.
+  template <typename Rt>
+  cudaError_t run_cg(const Geom<Rt>& geom, cplx<Rt>* Xv, cplx<Rt>* Rv, cplx<Rt>* Pv, cplx<Rt>* Tv, size_t vs,
+                     TermScalars* sc, int nb, double rtol, std::vector<TermScalars>& host) {
     dim3 grid(geom.tiles_x, geom.tiles_y, nb);
     int it = 0;
     for (;;) {
       for (int c = 0; c < check_every; ++c) {
         cg_apply_B<Rt><<<grid, THREADS, 0, s>>>(geom, Rv, Pv, Tv, vs, vs, sc, partials, counters, 0);
-        cg_update<Rt><<<grid, THREADS, 0, s>>>(geom, Tv, Pv, Xv, Rv, vs, sc, partials, counters, rtol,
-                                               k->max_iters);
+        cg_update<Rt><<<grid, THREADS, 0, s>>>(geom, Tv, Pv, Xv, Rv, vs, sc, partials, counters, rtol, k->max_iters);
       }
       count(2 * check_every);
       it += check_every;
@@ -733,45 +816,43 @@ rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void
     }
     for (int b = 0; b < nb; ++b) term_iters += host[b].iters;
     return cudaSuccess;
-  };
+  }
 
-  for (size_t b0 = 0; b0 < terms.size(); b0 += L.batch) {
-    const int nb = (int)std::min<size_t>(L.batch, terms.size() - b0);
-    mark(0);
-    e = cudaMemcpyAsync(dsc, &terms[b0], nb * sizeof(TermScalars), cudaMemcpyHostToDevice, s);
+  // Solves the pair systems of terms [b0, b0 + nb) for the right-hand side rhs.
+  cudaError_t solve_batch(size_t b0, int nb, const double2* rhs, int real_rhs) {
+    cudaError_t e = cudaMemcpyAsync(dsc, &terms[b0], nb * sizeof(TermScalars), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dsc32, &terms[b0], nb * sizeof(TermScalars), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) break;
+    if (e != cudaSuccess) return e;
     mark(1);
     dim3 grid(G.tiles_x, G.tiles_y, nb);
-    cg_init<double, double2><<<grid, THREADS, 0, s>>>(G, src, real_input, X, R, P, vs64, 0, dsc, nullptr,
-                                                      partials, counters);
+    cg_init<double, double2><<<grid, THREADS, 0, s>>>(G, rhs, real_rhs, X, R, P, vs64, 0, dsc, nullptr, partials,
+                                                      counters);
     count(1);
     mark(2);
     if (!mixed) {
-      e = run_cg(G, X, R, P, T, vs64, dsc, nb, k->rtol, hs);
-      if (e != cudaSuccess) break;
+      e = run_cg<double>(G, X, R, P, T, vs64, dsc, nb, k->rtol, hs);
+      if (e != cudaSuccess) return e;
     } else {
       // iterative refinement: FP32 CG on N d = r, then x += d, r = f - N x in FP64
       for (int outer = 0;; ++outer) {
-        cg_init<float, double2><<<grid, THREADS, 0, s>>>(G32, R, 0, D32, R32, P32, vs32, vs64, dsc32, dsc,
-                                                         partials, counters);
+        cg_init<float, double2><<<grid, THREADS, 0, s>>>(G32, R, 0, D32, R32, P32, vs32, vs64, dsc32, dsc, partials,
+                                                         counters);
         count(1);
-        e = run_cg(G32, D32, R32, P32, T32, vs32, dsc32, nb, k->inner_rtol, hs32);
-        if (e != cudaSuccess) break;
+        e = run_cg<float>(G32, D32, R32, P32, T32, vs32, dsc32, nb, k->inner_rtol, hs32);
+        if (e != cudaSuccess) return e;
         cg_apply_B<double><<<grid, THREADS, 0, s>>>(G, X, D32, T, vs64, vs32, dsc, partials, counters, 1);
-        refine_residual<<<grid, THREADS, 0, s>>>(G, src, real_input, T, D32, X, R, vs64, vs32, dsc, partials,
-                                                 counters, k->rtol, k->max_outer);
+        refine_residual<<<grid, THREADS, 0, s>>>(G, rhs, real_rhs, T, D32, X, R, vs64, vs32, dsc, partials, counters,
+                                                 k->rtol, k->max_outer);
         count(2);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), dsc, nb * sizeof(TermScalars), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) break;
+        if (e != cudaSuccess) return e;
         bool done = true;
         for (int b = 0; b < nb; ++b)
           if (hs[b].status == 0) done = false;
         if (done || outer > k->max_outer) break;
       }
-      if (e != cudaSuccess) break;
     }
     mark(3);
     for (int b = 0; b < nb; ++b) {
@@ -779,32 +860,12 @@ rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void
       if (hs[b].status != 1) ++unconverged;
       if (hs[b].gamma0 > 0) worst_res = std::max(worst_res, sqrt(hs[b].gamma / hs[b].gamma0));
     }
-    dim3 g2(G.tiles_x, G.tiles_y, 1);
-    cg_accumulate<<<g2, THREADS, 0, s>>>(G, X, vs64, nb, dsc, acc, b0 == 0 ? 1 : 0);
-    count(1);
-    if ((e = cudaGetLastError()) != cudaSuccess) break;
-    mark(4);
+    return cudaSuccess;
   }
-  if (e != cudaSuccess) {
-    set_last_error(cudaGetErrorString(e));
-    return REXI_ECUDA;
-  }
-  if (adjoint) {
-    scale_eta<<<ebl, eb, 0, s>>>(acc, static_cast<double2*>(out), k->w64, nk, 0, 0);
-    count(1);
-    if (real_input) {
-      finish_output<<<ebl, eb, 0, s>>>(static_cast<double2*>(out), static_cast<double2*>(out), n3, 1);
-      count(1);
-    }
-  } else {
-    finish_output<<<ebl, eb, 0, s>>>(acc, static_cast<double2*>(out), n3, real_input);
-    count(1);
-  }
-  if ((e = cudaGetLastError()) != cudaSuccess) {
-    set_last_error(cudaGetErrorString(e));
-    return REXI_ECUDA;
-  }
-  if (info) {
+
+  void fill_info(rexi_step_info* info, int M, int real_input) const {
+    if (!info) return;
+    const int N = M + kL;
     memset(info, 0, sizeof(*info));
     info->N = N;
     info->n_terms = n_terms_for(M, real_input);
@@ -814,8 +875,106 @@ rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void
     info->krylov_max_rel_res = worst_res;
     info->krylov_term_iters = term_iters;
   }
-  if (unconverged > 0) {
+};
+
+rexi_status cuda_status(cudaError_t e) {
+  set_last_error(cudaGetErrorString(e));
+  return REXI_ECUDA;
+}
+
+bool overlaps(const void* a, const void* b, size_t bytes) {
+  return (const char*)a < (const char*)b + bytes && (const char*)b < (const char*)a + bytes;
+}
+
+}  // namespace
+
+rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void* in, void* out, double dt,
+                        int real_input, int term_begin, int term_end, void* ws, size_t ws_bytes, cudaStream_t s,
+                        rexi_step_info* info, bool adjoint, const KrylovHooks& hooks) {
+  const size_t nk = (size_t)k->nx * k->ny, n3 = 3 * nk;
+  if (overlaps(in, out, n3 * sizeof(double2))) {
+    set_last_error("variable-depth path: input and output must not overlap");
+    return REXI_EINVAL;
+  }
+  KrylovRun run;
+  // adjoint: r(tau A)^H = r(tau A^T) = W r(-tau A) W^{-1} with W = diag(g/H, 1, 1)
+  rexi_status st = run.setup(k, form, h, M, adjoint ? -dt : dt, real_input, term_begin, term_end, ws, ws_bytes, s,
+                             &hooks);
+  if (st != REXI_OK) return st;
+  const double2* src = static_cast<const double2*>(in);
+  const unsigned ebl = (unsigned)((n3 + 255) / 256);
+  cudaError_t e = cudaSuccess;
+  if (adjoint) {
+    scale_eta<<<ebl, 256, 0, s>>>(src, run.tmp, k->w64, nk, 1, real_input);
+    run.count(1);
+    src = run.tmp;
+  }
+  if (run.terms.empty()) e = cudaMemsetAsync(run.acc, 0, n3 * sizeof(double2), s);
+  for (size_t b0 = 0; b0 < run.terms.size() && e == cudaSuccess; b0 += run.L.batch) {
+    const int nb = (int)std::min<size_t>(run.L.batch, run.terms.size() - b0);
+    run.mark(0);
+    e = run.solve_batch(b0, nb, src, real_input);
+    if (e != cudaSuccess) break;
+    cg_accumulate<<<dim3(run.G.tiles_x, run.G.tiles_y, 1), THREADS, 0, s>>>(run.G, run.X, run.vs64, nb, run.dsc,
+                                                                            run.acc, b0 == 0 ? 1 : 0);
+    run.count(1);
+    e = cudaGetLastError();
+    run.mark(4);
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  double2* o = static_cast<double2*>(out);
+  if (adjoint) {
+    scale_eta<<<ebl, 256, 0, s>>>(run.acc, o, k->w64, nk, 0, 0);
+    run.count(1);
+    if (real_input) {
+      finish_output<<<ebl, 256, 0, s>>>(o, o, n3, 1);
+      run.count(1);
+    }
+  } else {
+    finish_output<<<ebl, 256, 0, s>>>(run.acc, o, n3, real_input);
+    run.count(1);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+  if (info) run.fill_info(info, M, real_input);
+  if (run.unconverged > 0) {
     set_last_error("variable-depth path: some terms reached the iteration cap");
+    return REXI_ENOCONV;
+  }
+  return REXI_OK;
+}
+
+rexi_status krylov_grad_depth(KrylovSettings* k, int form, double h, int M, const void* f_in, const void* g_out,
+                              double* grad_depth, double dt, int real_input, void* ws, size_t ws_bytes,
+                              cudaStream_t s, rexi_step_info* info, const KrylovHooks& hooks) {
+  const size_t nk = (size_t)k->nx * k->ny, n3 = 3 * nk;
+  KrylovRun run;
+  rexi_status st = run.setup(k, form, h, M, dt, real_input, 0, -1, ws, ws_bytes, s, &hooks);
+  if (st != REXI_OK) return st;
+  const unsigned ebl = (unsigned)((n3 + 255) / 256);
+  // adjoint right-hand side W^{-1} G
+  scale_eta<<<ebl, 256, 0, s>>>(static_cast<const double2*>(g_out), run.tmp, k->w64, nk, 1, real_input);
+  run.count(1);
+  cudaError_t e = cudaGetLastError();
+  for (size_t b0 = 0; b0 < run.terms.size() && e == cudaSuccess; b0 += run.L.batch) {
+    const int nb = (int)std::min<size_t>(run.L.batch, run.terms.size() - b0);
+    run.mark(0);
+    e = run.solve_batch(b0, nb, static_cast<const double2*>(f_in), real_input);  // x = N^{-1} f
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(run.XS, run.X, (size_t)nb * run.vs64 * sizeof(double2), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = run.solve_batch(b0, nb, run.tmp, 0);  // y = N^{-1} W^{-1} G
+    if (e != cudaSuccess) break;
+    grad_stage1<<<dim3(run.G.tiles_x, run.G.tiles_y, nb), THREADS, 0, s>>>(run.G, run.XS, run.X, run.R, run.P,
+                                                                           run.vs64, run.dsc);
+    grad_stage2<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(run.G, run.R, run.P, run.vs64, nb, run.dsc, dt,
+                                                             grad_depth);
+    run.count(2);
+    e = cudaGetLastError();
+    run.mark(4);
+  }
+  if (e != cudaSuccess) return cuda_status(e);
+  if (info) run.fill_info(info, M, real_input);
+  if (run.unconverged > 0) {
+    set_last_error("depth gradient: some terms reached the iteration cap");
     return REXI_ENOCONV;
   }
   return REXI_OK;

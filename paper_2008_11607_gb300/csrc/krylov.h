@@ -37,5 +37,9 @@ size_t krylov_workspace_bytes(const KrylovSettings* k, int M, int real_input, in
 rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void* in, void* out, double dt,
                         int real_input, int term_begin, int term_end, void* ws, size_t ws_bytes,
                         cudaStream_t s, rexi_step_info* info, bool adjoint, const KrylovHooks& hooks);
+// grad_depth += dL/dH for out = r(dt A(H)) f_in and G = dL/d out.
+rexi_status krylov_grad_depth(KrylovSettings* k, int form, double h, int M, const void* f_in, const void* g_out,
+                              double* grad_depth, double dt, int real_input, void* ws, size_t ws_bytes,
+                              cudaStream_t s, rexi_step_info* info, const KrylovHooks& hooks);
 
 }  // namespace rexi

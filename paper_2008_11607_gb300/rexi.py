@@ -62,6 +62,8 @@ SIGNATURES = {
     "rexi_step": (_c_int, [_vp, _vp, _vp, _c_dbl, _c_dbl, _c_int, _c_int, _c_int, _vp, ctypes.c_size_t, _vp,
                            ctypes.POINTER(rexi_step_info)]),
     "rexi_step_adjoint": (_c_int, [_vp, _vp, _vp, _c_dbl, _c_dbl, _c_int, _vp, ctypes.c_size_t, _vp]),
+    "rexi_step_grad_depth": (_c_int, [_vp, _vp, _vp, _vp, _c_dbl, _c_dbl, _c_int, _vp, ctypes.c_size_t, _vp,
+                                      ctypes.POINTER(rexi_step_info)]),
     "rexi_step_host": (_c_int, [_vp, _vp, _vp, _c_dbl, _c_dbl, _c_int, _vp, ctypes.c_size_t, _vp,
                                 ctypes.POINTER(rexi_step_info)]),
     "rexi_workspace_size_host": (_c_int, [_vp, _c_dbl, _c_dbl, _c_int, ctypes.POINTER(ctypes.c_size_t)]),
@@ -272,6 +274,22 @@ class Plan:
         _check(self._lib.rexi_plan_read_profile(self._h, ms, ctypes.byref(n), ctypes.byref(L)),
                "rexi_plan_read_profile")
         return list(ms), n.value, L.value
+
+    def grad_depth(self, state, grad_out, dt, tol=1e-10, real_input=True, grad=None, workspace=None, stream=None,
+                   want_info=False):
+        """grad += dL/dH for out = r(dt A(H)) state and grad_out = dL/d out (variable depth)."""
+        import torch
+
+        if grad is None:
+            grad = torch.zeros((self.ny, self.nx), dtype=torch.float64, device=state.device)
+        if workspace is None:
+            workspace = self.workspace(dt, tol, real_input, device=state.device)
+        info = rexi_step_info() if want_info else None
+        st = self._lib.rexi_step_grad_depth(self._h, _ptr(state), _ptr(grad_out), _ptr(grad), dt, tol,
+                                            int(real_input), _ptr(workspace), workspace.numel(),
+                                            _stream_handle(stream), ctypes.byref(info) if info is not None else None)
+        _check(st, "rexi_step_grad_depth")
+        return (grad, info) if want_info else grad
 
     def step_adjoint(self, grad_out, dt, tol=1e-10, real_input=True, out=None, workspace=None, stream=None):
         import torch
