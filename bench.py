@@ -379,6 +379,70 @@ def batch_measure(torch, rexi, inputs, form="mixed", reps=5):
     }
 
 
+def adjoint_measure(torch, rexi, inputs, form="mixed", n=512, steps=8, tau_rho=200.3, every=2, rtol=1e-12,
+                    fd_dirs=1):
+    """Differentiation workload: variable depth (as the 1024^2 workload), n^2
+    grid, `steps` REXII steps of tau rho ~ 200, loss 1/2 ||eta(T) - eta_target||^2
+    (|k|^-3 target, seed 1000), gradients with respect to the initial state and
+    the depth field through the checkpointed rollout (every `every` steps);
+    central differences (step 1e-6) along `fd_dirs` random state and depth
+    directions."""
+    import numpy as np
+
+    from paper_2008_11607_gb300.autograd import rexi_rollout
+
+    H = inputs.variable_depth(n, n, seed=0)
+    Hd = torch.from_numpy(H).cuda()
+
+    def mkplan(Hx):
+        p = rexi.Plan(n, n, depth=Hx, form=form, h=H_PARAM)
+        p.set_krylov(rtol=rtol, max_iters=20000, term_batch=64)
+        return p
+
+    plan = mkplan(Hd)
+    dt = tau_rho / plan.rho
+    x0 = torch.from_numpy(inputs.kminus3_field(n, n, seed=0)).cuda()
+    tgt = torch.from_numpy(inputs.kminus3_field(n, n, seed=1000)[0].real).cuda()
+    x = x0.clone().requires_grad_(True)
+    Hd.requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sT = rexi_rollout(x, plan, dt, steps, every=every, depth=Hd)
+    loss = 0.5 * torch.sum((sT[0].real - tgt) ** 2)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    gx, gH = torch.autograd.grad(loss, [x, Hd])
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+
+    def loss_of(p, xx):
+        s = xx
+        for _ in range(steps):
+            s = p.step(s, dt, tol=TOL)
+        return 0.5 * float(torch.sum((s[0].real - tgt) ** 2))
+
+    rng = np.random.default_rng(7)
+    eps = 1e-6
+    checks = []
+    for _ in range(fd_dirs):
+        d = torch.from_numpy(rng.standard_normal((3, n, n))).cuda().to(torch.complex128)
+        fd = (loss_of(plan, x0 + eps * d) - loss_of(plan, x0 - eps * d)) / (2 * eps)
+        an = float(torch.sum(gx.real * d.real))
+        checks.append({"wrt": "state", "fd": fd, "adjoint": an, "rel_err": abs(fd - an) / abs(an)})
+        dh = rng.standard_normal((n, n))
+        Hp = torch.from_numpy(H + eps * dh).cuda()
+        Hm = torch.from_numpy(H - eps * dh).cuda()
+        fd = (loss_of(mkplan(Hp), x0) - loss_of(mkplan(Hm), x0)) / (2 * eps)
+        an = float(torch.sum(gH * torch.from_numpy(dh).cuda()))
+        checks.append({"wrt": "depth", "fd": fd, "adjoint": an, "rel_err": abs(fd - an) / abs(an)})
+    return {
+        "workload": "LRSW variable depth %dx%d (H = 1 + 0.4 sin(2 pi x) cos(4 pi y) + 8 bumps), %d REXII steps of "
+                    "tau*rho=%g, checkpoints every %d steps, loss 1/2||eta(T) - eta_target||^2, CG rtol %g, form=%s"
+                    % (n, n, steps, tau_rho, every, rtol, form),
+        "forward_s": t1 - t0, "backward_s": t2 - t1, "loss": float(loss), "fd_checks": checks,
+    }
+
+
 def run_ours(args):
     import torch
 
@@ -540,6 +604,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-krylov", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the differentiation workload (minutes at 512^2)")
+    ap.add_argument("--adjoint-grid", type=int, default=512)
     ap.add_argument("--batch-only", action="store_true", help="run only the serving-mix measurement")
     ap.add_argument("--krylov-terms", type=int, default=8)
     ap.add_argument("--krylov-form", default="mixed", choices=["mixed", "fp64"])
@@ -550,6 +617,15 @@ def main():
     args.warmup = max(args.warmup, 3)  # timing rule: at least 3 untimed warm-up steps
     if args.impl == "reference":
         run_reference(args)
+    elif args.adjoint_only:
+        import torch
+
+        from paper_2008_11607_gb300 import build as B
+
+        B.build()
+        from paper_2008_11607_gb300 import inputs, rexi
+
+        print(json.dumps(adjoint_measure(torch, rexi, inputs, n=args.adjoint_grid)), flush=True)
     elif args.batch_only:
         import torch
 
