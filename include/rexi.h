@@ -140,6 +140,22 @@ void rexi_plan_destroy(rexi_plan_t plan);
  * depth_dev at plan creation). */
 rexi_status rexi_spectral_radius(rexi_plan_t plan, double* rho_out);
 
+/* Spatial symbol of the constant-depth (Fourier) path:
+ * REXI_SYMBOL_CGRID (default): the staggered second-order operator above;
+ * REXI_SYMBOL_SPECTRAL: spectral derivatives on a collocated grid
+ *   (d/dx -> i k', k' = 2 pi k / Lx with the signed wavenumber, Nyquist as
+ *   +n/2, no Coriolis averaging), the discretisation behind eq. lswRoh
+ *   (rho = sqrt(2 pi^2 D^2 + 1) for D x D on the unit square, H = g = f = 1).
+ * Recomputes rho.  Variable-depth plans accept only the C grid. */
+enum { REXI_SYMBOL_CGRID = 0, REXI_SYMBOL_SPECTRAL = 1 };
+rexi_status rexi_plan_set_symbol(rexi_plan_t plan, int32_t symbol);
+
+/* Override the spectral radius used by the pole-count rule (rho > 0), or
+ * restore the plan's own value (rho = 0).  The paper's wave scenarios take
+ * rho from the highest active Fourier mode instead of the grid (Section 4,
+ * text after eq. WAVESCENARIO1; Table tab:W8_M). */
+rexi_status rexi_plan_set_rho(rexi_plan_t plan, double rho);
+
 /* Krylov path settings (ignored by the FFT path): relative residual target
  * per term, iteration cap per term, number of terms solved together. */
 rexi_status rexi_plan_set_krylov(rexi_plan_t plan, double rtol, int32_t max_iters, int32_t term_batch);

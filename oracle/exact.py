@@ -29,8 +29,9 @@ def omega2_of(B):
     return float((-(B[0, 1] * B[1, 0]) - (B[0, 2] * B[2, 0]) - (B[1, 2] * B[2, 1])).real)
 
 
-def exp_closed_form(state, tau, Lx=1.0, Ly=1.0, g=1.0, f=1.0, H=1.0):
-    """e^{tau A} state for constant H; ``state`` is (3, ny, nx)."""
+def exp_closed_form(state, tau, Lx=1.0, Ly=1.0, g=1.0, f=1.0, H=1.0, symbol_fn=None):
+    """e^{tau A} state for constant H; ``state`` is (3, ny, nx).  ``symbol_fn``
+    (default: the C-grid symbol) maps (kx, ky, nx, ny, Lx, Ly, g, f, H) to B(k)."""
     state = np.asarray(state, dtype=np.complex128)
     _, ny, nx = state.shape
     fh = np.fft.fft2(state, axes=(1, 2))
@@ -38,7 +39,7 @@ def exp_closed_form(state, tau, Lx=1.0, Ly=1.0, g=1.0, f=1.0, H=1.0):
     I3 = np.eye(3)
     for ky in range(ny):
         for kx in range(nx):
-            B = op.symbol(kx, ky, nx, ny, Lx, Ly, g, f, H)
+            B = (symbol_fn or op.symbol)(kx, ky, nx, ny, Lx, Ly, g, f, H)
             w2 = omega2_of(B)
             w = math.sqrt(max(w2, 0.0))
             if w * tau < 1e-8:

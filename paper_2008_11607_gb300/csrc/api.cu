@@ -48,6 +48,8 @@ struct rexi_plan_s {
   const double* depth = nullptr;
   int form = REXI_FORM_FP64;
   double rho = 0.0;
+  double rho_natural = 0.0;  // rho of the discretisation (rho may be overridden)
+  int spectral = 0;
   double Hmax = 0.0, Hmean = 0.0;
   // Fourier path tables (device)
   FftPlan1D fx, fy;
@@ -263,6 +265,7 @@ rexi_status rexi_plan_create(rexi_plan_t* out, int32_t nx, int32_t ny, double Lx
       }
     }
     p->rho = sqrt(best);
+    p->rho_natural = p->rho;
     p->Hmax = H;
     p->Hmean = H;
   } else {
@@ -282,6 +285,7 @@ rexi_status rexi_plan_create(rexi_plan_t* out, int32_t nx, int32_t ny, double Lx
     p->Hmax = hmax;
     p->Hmean = hsum / (double)Hh.size();
     p->rho = sqrt(g * hmax * (4.0 / (dx * dx) + 4.0 / (dy * dy))) + fabs(f);
+    p->rho_natural = p->rho;
     st = krylov_init(&p->kry, nx, ny, Lx, Ly, g, f, depth, p->Hmean);
     if (st != REXI_OK) { rexi_plan_destroy(p); return st; }
   }
@@ -400,6 +404,7 @@ SymbolParams symbol_params(const rexi_plan_s* p) {
   sp.H = p->H;
   sp.half_x = p->half_x;
   sp.half_y = p->half_y;
+  sp.spectral = p->spectral;
   return sp;
 }
 
@@ -705,4 +710,39 @@ extern "C" rexi_status rexi_step_grad_depth(rexi_plan_t p, const void* in, const
     info->rho = p->rho;
   }
   return st;
+}
+
+extern "C" rexi_status rexi_plan_set_symbol(rexi_plan_t p, int32_t symbol) {
+  g_err[0] = 0;
+  if (!p || (symbol != REXI_SYMBOL_CGRID && symbol != REXI_SYMBOL_SPECTRAL)) return fail(REXI_EINVAL, "bad symbol");
+  if (p->depth && symbol != REXI_SYMBOL_CGRID) return fail(REXI_EUNSUPPORTED, "spectral symbol needs constant depth");
+  p->spectral = symbol == REXI_SYMBOL_SPECTRAL;
+  if (p->depth) return REXI_OK;
+  // rho: the largest omega over the discrete wavenumbers of the chosen symbol
+  double best = 0.0;
+  for (int ky = 0; ky < p->ny; ++ky) {
+    for (int kx = 0; kx < p->nx; ++kx) {
+      double w2;
+      if (p->spectral) {
+        const int sx = 2 * kx <= p->nx ? kx : kx - p->nx, sy = 2 * ky <= p->ny ? ky : ky - p->ny;
+        const double a = 2.0 * M_PI * sx / p->Lx, b = 2.0 * M_PI * sy / p->Ly;
+        w2 = p->g * p->H * (a * a + b * b) + p->f * p->f;
+      } else {
+        const double sx = sin(M_PI * kx / p->nx), cx = cos(M_PI * kx / p->nx);
+        const double sy = sin(M_PI * ky / p->ny), cy = cos(M_PI * ky / p->ny);
+        const double dx = p->Lx / p->nx, dy = p->Ly / p->ny;
+        w2 = p->g * p->H * (4 * sx * sx / (dx * dx) + 4 * sy * sy / (dy * dy)) + p->f * p->f * cx * cx * cy * cy;
+      }
+      best = std::max(best, w2);
+    }
+  }
+  p->rho = p->rho_natural = sqrt(best);
+  return REXI_OK;
+}
+
+extern "C" rexi_status rexi_plan_set_rho(rexi_plan_t p, double rho) {
+  g_err[0] = 0;
+  if (!p || !(rho >= 0.0) || !isfinite(rho)) return fail(REXI_EINVAL, "bad rho");
+  p->rho = rho > 0.0 ? rho : p->rho_natural;
+  return REXI_OK;
 }

@@ -52,6 +52,7 @@ struct SymbolParams {
   double inv_dx, inv_dy, g, f, H;
   const double2* half_x;  // (cos(pi k/nx), sin(pi k/nx)), k < nx
   const double2* half_y;
+  int spectral = 0;       // 1: spectral derivatives on a collocated grid (no averaging)
 };
 struct FusedScalars {
   double tau, q, R0re, R0im;  // q = (h mu)^2, R0 = r(0) over the selected terms

@@ -20,6 +20,20 @@ struct Symbol {
 };
 
 __device__ __forceinline__ Symbol symbol_at(const SymbolParams& sp, int kx, int ky) {
+  if (sp.spectral) {
+    // spectral derivative i k' with the signed wavenumber (Nyquist taken as +n/2),
+    // k' = 2 pi k_signed / L = 2 pi k_signed (1/dx) / n; no averaging (P = 1)
+    const int sx = 2 * kx <= sp.nx ? kx : kx - sp.nx;
+    const int sy = 2 * ky <= sp.ny ? ky : ky - sp.ny;
+    const double kxp = 6.283185307179586 * sx * sp.inv_dx / sp.nx;
+    const double kyp = 6.283185307179586 * sy * sp.inv_dy / sp.ny;
+    Symbol S;
+    S.dxf = S.dxb = make_double2(0.0, kxp);
+    S.dyf = S.dyb = make_double2(0.0, kyp);
+    S.P = make_double2(1.0, 0.0);
+    S.omega = sqrt(sp.g * sp.H * (kxp * kxp + kyp * kyp) + sp.f * sp.f);
+    return S;
+  }
   const double2 hx = sp.half_x[kx];
   const double2 hy = sp.half_y[ky];
   const double cx = hx.x, sx = hx.y, cy = hy.x, sy = hy.y;

@@ -83,3 +83,33 @@ def batched_instances(count=96, seed=0, sizes=(128, 192, 256, 384, 512), rho_ran
         tr = float(math.exp(rng.uniform(math.log(rho_range[0]), math.log(rho_range[1]))))
         out.append({"nx": D, "ny": D, "tau_rho": tr, "seed": i})
     return out
+
+
+def grid_points(nx, ny, Lx=1.0, Ly=1.0):
+    """Collocated points (i dx, j dy), shaped (ny, nx) (the spectral grid)."""
+    x = np.arange(nx) * (Lx / nx)
+    y = np.arange(ny) * (Ly / ny)
+    return np.meshgrid(x, y, indexing="xy")
+
+
+def paper_scenario(name, nx, ny):
+    """Initial states of Section 4 on the collocated grid: "ws1" (eq.
+    WAVESCENARIO1), "ws2" (eq. WAVESCENARIO2), "gaussian" (eq. GAUSSIANSCENARIO)."""
+    X, Y = grid_points(nx, ny)
+    pi = math.pi
+    s = np.zeros((3, ny, nx), dtype=np.complex128)
+    if name == "ws1":
+        s[0] = np.sin(4 * pi * X) * np.cos(2 * pi * Y) - 0.2 * np.cos(4 * pi * X) * np.sin(4 * pi * Y)
+        s[1] = np.cos(8 * pi * X) * np.cos(2 * pi * Y)
+        s[2] = np.cos(4 * pi * X) * np.cos(4 * pi * Y)
+    elif name == "ws2":
+        s[0] = np.sin(32 * pi * X) * np.cos(16 * pi * Y) - 0.2 * np.cos(32 * pi * X) * np.sin(32 * pi * Y)
+        s[1] = np.cos(64 * pi * X) * np.cos(16 * pi * Y)
+        s[2] = np.cos(32 * pi * X) * np.cos(32 * pi * Y)
+    elif name == "gaussian":
+        s[0] = np.exp(-100.0 * ((X - 0.5) ** 2 + (Y - 0.5) ** 2))
+        s[1] = 0.1 * np.sin(64 * pi * X) * np.sin(16 * pi * Y)
+        s[2] = 0.1 * np.sin(32 * pi * X) * np.sin(32 * pi * Y)
+    else:
+        raise ValueError(name)
+    return s

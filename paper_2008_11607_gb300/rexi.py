@@ -22,6 +22,9 @@ REXI_EUNSUPPORTED = -6
 REXI_BATCH_PERSISTENT = 0
 REXI_BATCH_PER_INSTANCE = 1
 
+REXI_SYMBOL_CGRID = 0
+REXI_SYMBOL_SPECTRAL = 1
+
 REXI_FORM_FP64 = 0
 REXI_FORM_MIXED = 1
 REXI_FORM_PLAIN = 2
@@ -58,6 +61,8 @@ SIGNATURES = {
     "rexi_plan_destroy": (None, [_vp]),
     "rexi_spectral_radius": (_c_int, [_vp, _dp]),
     "rexi_plan_set_krylov": (_c_int, [_vp, _c_dbl, _c_int, _c_int]),
+    "rexi_plan_set_symbol": (_c_int, [_vp, _c_int]),
+    "rexi_plan_set_rho": (_c_int, [_vp, _c_dbl]),
     "rexi_workspace_size": (_c_int, [_vp, _c_dbl, _c_dbl, _c_int, ctypes.POINTER(ctypes.c_size_t)]),
     "rexi_step": (_c_int, [_vp, _vp, _vp, _c_dbl, _c_dbl, _c_int, _c_int, _c_int, _vp, ctypes.c_size_t, _vp,
                            ctypes.POINTER(rexi_step_info)]),
@@ -213,6 +218,15 @@ class Plan:
         r = ctypes.c_double()
         _check(self._lib.rexi_spectral_radius(self._h, ctypes.byref(r)), "rexi_spectral_radius")
         return r.value
+
+    def set_symbol(self, symbol):
+        """"cgrid" or "spectral" (constant-depth plans)."""
+        code = {"cgrid": REXI_SYMBOL_CGRID, "spectral": REXI_SYMBOL_SPECTRAL}.get(symbol, symbol)
+        _check(self._lib.rexi_plan_set_symbol(self._h, int(code)), "rexi_plan_set_symbol")
+
+    def set_rho(self, rho):
+        """Override rho for the pole count (0 restores the plan's own value)."""
+        _check(self._lib.rexi_plan_set_rho(self._h, float(rho)), "rexi_plan_set_rho")
 
     def set_krylov(self, rtol=1e-10, max_iters=20000, term_batch=64):
         _check(self._lib.rexi_plan_set_krylov(self._h, rtol, max_iters, term_batch), "rexi_plan_set_krylov")

@@ -1,0 +1,72 @@
+"""Reproduction of Section 4 on the GPU with the spectral symbol: the paper's
+scenarios at D = 128 with the printed pole counts M, against the exact
+exponential of the discretised operator (closed form per wavenumber).  The
+spectral path itself is first checked against the oracle's dense operator."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import coeffs as C
+from oracle import exact as E
+from oracle import rexi as R
+from oracle import spectral as S
+from paper_2008_11607_gb300 import inputs
+from tests.gpu_util import rel_l2, to_dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed", "plain"])
+@pytest.mark.parametrize("nx,ny,real", [(8, 8, False), (9, 7, True), (6, 10, False)])
+def test_spectral_symbol_against_dense_oracle(form, nx, ny, real):
+    torch = torch_cuda()
+    from paper_2008_11607_gb300 import rexi
+
+    plan = rexi.Plan(nx, ny, form=form, f=0.8, g=1.2, H=0.9)
+    plan.set_symbol("spectral")
+    assert abs(plan.rho - S.spectral_radius(nx, ny, g=1.2, f=0.8, H=0.9)) < 1e-9
+    dt = 20.0 / plan.rho
+    st = inputs.kminus3_field(nx, ny, seed=1) if real else inputs.complex_random_state(nx, ny, seed=1)
+    out, info = plan.step(to_dev(torch, st), dt, real_input=real, want_info=True)
+    A = S.spectral_operator(nx, ny, g=1.2, f=0.8, H=0.9)
+    ref = R.rexii_apply_sparse(A, st.ravel(), dt, 0.5, info.M, real_input=real).reshape(st.shape)
+    assert rel_l2(out.cpu().numpy(), ref) < (1e-8 if form == "mixed" else 1e-10)
+
+
+def _rows():
+    with open(os.path.join(GOLDEN, "paper_errors.txt")) as fh:
+        for ln in fh:
+            if ln.strip() and not ln.startswith("#"):
+                p = ln.split()
+                yield p[0], float(p[1]), float(p[2]), int(p[3]), float(p[4])
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_paper_scenarios_d128(form):
+    torch = torch_cuda()
+    from paper_2008_11607_gb300 import rexi
+
+    D = 128
+    refs = {}
+    for scen, tau, h, M, printed in _rows():
+        plan = rexi.Plan(D, D, form=form, h=h)
+        plan.set_symbol("spectral")
+        # rho so that the paper's rule M = ceil(tau rho / h) + 11 (tol 1e-16) gives the printed M
+        plan.set_rho(((M - 11) - 0.5) * h / tau)
+        st = inputs.paper_scenario(scen, D, D)
+        out, info = plan.step(to_dev(torch, st), tau, tol=1e-16, want_info=True)
+        assert info.M == M
+        key = (scen, tau)
+        if key not in refs:
+            refs[key] = E.exp_closed_form(st, tau, symbol_fn=S.symbol).real
+        err = float(np.max(np.abs(out.cpu().numpy().real - refs[key])))
+        bound_ok = (M - 11) * h >= tau * S.spectral_radius(46, 46) if scen == "ws2" else True
+        if printed > 0.1:
+            assert err > 0.1, (scen, tau, h, M, err)        # below the accuracy bound: no approximation
+        elif h == 1.0:
+            assert 1e-13 < err < 1e-11, (scen, tau, h, M, err)  # h = 1 error floor (Appendix B aliasing)
+        else:
+            assert bound_ok and err < 1e-12, (scen, tau, h, M, err)
