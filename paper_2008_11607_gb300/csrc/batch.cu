@@ -162,7 +162,8 @@ __global__ void batch_pole_kernel(double2* spec, const InstDesc* __restrict__ de
                              : make_double2((double)arh[u] + (double)arl[u], (double)aih[u] + (double)ail[u]);
       combine(sp_inst, (size_t)ky[u] * D.nx + kx[u], fstride, S[u], sp, false, adjoint != 0, R0, Rp);
       if (kx2[u] != kx[u] || ky2[u] != ky[u])
-        combine(sp_inst, (size_t)ky2[u] * D.nx + kx2[u], fstride, S[u], sp, true, adjoint != 0, R0, Rp);
+        combine(sp_inst, (size_t)ky2[u] * D.nx + kx2[u], fstride, symbol_at(sp, kx2[u], ky2[u]), sp, false,
+                adjoint != 0, R0, Rp);
     }
   }
 }

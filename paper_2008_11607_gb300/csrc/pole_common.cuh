@@ -111,6 +111,9 @@ __device__ __forceinline__ void combine(double2* spec, size_t idx, size_t fs, co
 
 // Map thread -> wavenumber pair.  Pairs (k, -k) with ky in [0, ny/2]; in the
 // self-conjugate rows (ky = 0, and ky = ny/2 for even ny) only kx <= nx/2.
+// omega(-k) = omega(k), so one pole loop serves both; the combine step takes
+// each wavenumber's own symbol (for the spectral symbol the Nyquist
+// derivative i k' is not the conjugate of its partner's).
 __device__ __forceinline__ bool pair_of(int p, int nx, int ny, int& kx, int& ky, int& kx2, int& ky2) {
   ky = p / nx;
   kx = p - ky * nx;

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(128) pole_fused_fp64_kernel(double2* spec, Sym
   const bool adj = fs.adjoint != 0;
   combine(spec, (size_t)ky * sp.nx + kx, fstride, S, sp, false, adj, R0, Rp);
   if (kx2 != kx || ky2 != ky)
-    combine(spec, (size_t)ky2 * sp.nx + kx2, fstride, S, sp, true, adj, R0, Rp);
+    combine(spec, (size_t)ky2 * sp.nx + kx2, fstride, symbol_at(sp, kx2, ky2), sp, false, adj, R0, Rp);
 }
 
 static int pairs_count(int nx, int ny) { return nx * (ny / 2 + 1); }
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(128) pole_fused_mixed_kernel(double2* spec, Sy
   const bool adj = fs.adjoint != 0;
   combine(spec, (size_t)ky * sp.nx + kx, fstride, S, sp, false, adj, R0, Rp);
   if (kx2 != kx || ky2 != ky)
-    combine(spec, (size_t)ky2 * sp.nx + kx2, fstride, S, sp, true, adj, R0, Rp);
+    combine(spec, (size_t)ky2 * sp.nx + kx2, fstride, symbol_at(sp, kx2, ky2), sp, false, adj, R0, Rp);
 }
 
 cudaError_t pole_fused_mixed(double2* spec, const SymbolParams& sp, const float* table,
