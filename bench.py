@@ -39,12 +39,12 @@ METRIC = "grid-points×poles solved/sec and HBM GB/s vs roofline at stated error
 UNIT = "grid-points*poles/s"
 
 # Per-term work of the fused pole loops, counted from the kernel source
-# (csrc/pole_fft.cu).  mixed: 72 FP32 arithmetic instructions per term, 12 of
-# them FFMA -> 84 flops; fp64: 7 DFMA + 1 DADD -> 15 flops.  One MUFU
+# (csrc/pole_common.cuh).  mixed: 73 FP32 arithmetic instructions per term, 12
+# of them FFMA -> 85 flops; fp64: 8 DFMA + 1 DADD -> 17 flops.  One MUFU
 # reciprocal seed per term in both.
-FLOPS_PER_TERM = {"mixed": 84, "fp64": 15}
-FP32_INSTR_PER_TERM = 72
-FP64_INSTR_PER_TERM = 8
+FLOPS_PER_TERM = {"mixed": 85, "fp64": 17}
+FP32_INSTR_PER_TERM = 73
+FP64_INSTR_PER_TERM = 9
 # Peaks for ALU-bound kernels, derived from unit counts and the maximum clock:
 # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz; FP64 from the nominal
 # 1.25 TFLOP/s of this GPU.
@@ -55,7 +55,7 @@ PEAK_FP64_TFLOPS = 1.25
 # DRAM traffic of the pole kernel per launch from an ncu capture of this
 # kernel on the 2048^2 grid (profiles/pole_fused_mixed_2048_tau50.md: same grid and
 # bytes, fewer terms; traffic does not depend on the term count); None if not captured.
-NCU_POLE_TRAFFIC_BYTES = {"mixed": 342193152, "fp64": None}  # 201.50 MB read + 140.69 MB write
+NCU_POLE_TRAFFIC_BYTES = {"mixed": None, "fp64": None}
 
 
 def set_workload(grid, tau_rho):
@@ -485,11 +485,11 @@ def run_ours(args):
         # lane rate 152 SMs x 128 lanes x 2.07 GHz
         ops = terms * FP32_INSTR_PER_TERM
         peak = SMS * 128 * SM_MAX_GHZ / 1e3
-        conv = "FP32 operations per launch (FADD/FMUL/FFMA each 1; 72 per term) vs 152 SMs x 128 lanes x 2.07 GHz"
+        conv = "FP32 operations per launch (FADD/FMUL/FFMA each 1; 73 per term) vs 152 SMs x 128 lanes x 2.07 GHz"
     else:
         ops = terms * FP64_INSTR_PER_TERM
         peak = PEAK_FP64_TFLOPS / 2
-        conv = "FP64 operations per launch (DADD/DFMA each 1; 8 per term) vs nominal 1.25 TFLOP/s / 2"
+        conv = "FP64 operations per launch (DADD/DFMA each 1; 9 per term) vs nominal 1.25 TFLOP/s / 2"
     achieved = ops / t_pole / 1e12
     roofline = {
         "kernel": "pole_fused_%s_kernel" % args.form,

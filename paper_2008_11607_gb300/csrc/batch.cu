@@ -122,7 +122,7 @@ __global__ void batch_pole_kernel(double2* spec, const InstDesc* __restrict__ de
       x[u] = D.tau * S[u].omega;
     }
     double ar[PPT], ai[PPT];
-    float arh[PPT], arl[PPT], aih[PPT], ail[PPT], Xh[PPT], Xl[PPT];
+    float arh[PPT], arl[PPT], aih[PPT], ail[PPT], Xh[PPT], Xl[PPT], Xl2[PPT];
 #pragma unroll
     for (int u = 0; u < PPT; ++u) {
       ar[u] = ai[u] = 0.0;
@@ -130,6 +130,7 @@ __global__ void batch_pole_kernel(double2* spec, const InstDesc* __restrict__ de
       const double xg = rint(x[u] / D.grid) * D.grid;
       Xh[u] = (float)xg;
       Xl[u] = (float)(x[u] - xg);
+      Xl2[u] = (float)((x[u] - xg) - (double)Xl[u]);
     }
     const float4* tb = reinterpret_cast<const float4*>(tables) + D.table_off * 3;
     for (int t0 = 0; t0 < D.nterms; t0 += kChunk) {
@@ -148,7 +149,7 @@ __global__ void batch_pole_kernel(double2* spec, const InstDesc* __restrict__ de
         for (int t = 0; t < cnt; ++t)
 #pragma unroll
           for (int u = 0; u < PPT; ++u)
-            df_term(st + 3 * t, Xh[u], Xl[u], D.q_hi, D.q_lo, arh[u], arl[u], aih[u], ail[u]);
+            df_term(st + 3 * t, Xh[u], Xl[u], Xl2[u], D.q_hi, D.q_lo, arh[u], arl[u], aih[u], ail[u]);
       }
     }
     double2* sp_inst = spec + D.spec_off;

@@ -167,20 +167,26 @@ __device__ __forceinline__ void fp64_term(const double2* e, double x, double q, 
   const double y = x + e0.x;
   const double d = fma(y, y, q);
   const double r0 = rcp_seed(d);
-  const double r = fma(r0, fma(-d, r0, 1.0), r0);  // one Newton-Raphson step
+  // 1/d = r0 / (1 - e) with e = 1 - d r0; r0 (1 + e + e^2) leaves a relative
+  // error of order e^3 (a Newton-Raphson step plus its next term)
+  const double er = fma(-d, r0, 1.0);
+  const double r = fma(r0, fma(er, er, er), r0);
   accr = fma(fma(e1.y, y, e0.y), r, accr);
   acci = fma(fma(e2.x, y, e1.x), r, acci);
 }
 
-// One scalar REXII term in double-float arithmetic (see pole_fft.cu):
+// One scalar REXII term in double-float arithmetic (see pole_fft.cu).
+// x is split as X_hi (a multiple of the table's grid G) + X_lo + X_lo2 (FP32).
 // acc += (A + B y) / (q + y^2) with every quantity an FP32 (hi, lo) pair.
 // Table entry (3 float4): [hn_hi, Ar_hi, Ai_hi, Br_hi], [Bi_hi, Ar_lo, Ai_lo, Br_lo], [Bi_lo, hn_lo, 0, 0].
-__device__ __forceinline__ void df_term(const float4* ent, float X_hi, float X_lo, float q_hi, float q_lo,
-                                        float& ar_h, float& ar_l, float& ai_h, float& ai_l) {
+__device__ __forceinline__ void df_term(const float4* ent, float X_hi, float X_lo, float X_lo2, float q_hi,
+                                        float q_lo, float& ar_h, float& ar_l, float& ai_h, float& ai_l) {
   const float4 e0 = ent[0], e1 = ent[1], e2 = ent[2];
-  // y = x + h n: exact high part, then renormalise
+  // y = x + h n with x = X_hi + X_lo + X_lo2: the grid-aligned high parts add
+  // exactly, X_lo joins by an error-free FastTwoSum, the rest is far below it
   float y_h, y_l;
-  fast_two_sum(__fadd_rn(X_hi, e0.x), __fadd_rn(X_lo, e2.y), y_h, y_l);
+  fast_two_sum(__fadd_rn(X_hi, e0.x), X_lo, y_h, y_l);
+  y_l = __fadd_rn(y_l, __fadd_rn(X_lo2, e2.y));
   // d = q + y^2
   const float p_h = __fmul_rn(y_h, y_h);
   const float p_l = __fmaf_rn(y_h, y_h, -p_h);

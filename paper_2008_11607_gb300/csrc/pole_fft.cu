@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(128) pole_fused_mixed_kernel(double2* spec, Sy
   const double xg = rint(x / grid) * grid;
   const float X_hi = (float)xg;
   const float X_lo = (float)(x - xg);
+  const float X_lo2 = (float)((x - xg) - (double)X_lo);
   float ar_h = 0.f, ar_l = 0.f, ai_h = 0.f, ai_l = 0.f;
   for (int t0 = 0; t0 < fs.nterms; t0 += kChunk) {
     const int cnt = min(kChunk, fs.nterms - t0);
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(128) pole_fused_mixed_kernel(double2* spec, Sy
     for (int i = threadIdx.x; i < cnt * 3; i += blockDim.x) st[i] = table[(size_t)t0 * 3 + i];
     __syncthreads();
 #pragma unroll 2
-    for (int t = 0; t < cnt; ++t) df_term(st + 3 * t, X_hi, X_lo, q_hi, q_lo, ar_h, ar_l, ai_h, ai_l);
+    for (int t = 0; t < cnt; ++t) df_term(st + 3 * t, X_hi, X_lo, X_lo2, q_hi, q_lo, ar_h, ar_l, ai_h, ai_l);
   }
   if (!active) return;
   const double2 R0 = make_double2(fs.R0re, fs.R0im);

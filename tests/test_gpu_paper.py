@@ -69,4 +69,5 @@ def test_paper_scenarios_d128(form):
         elif h == 1.0:
             assert 1e-13 < err < 1e-11, (scen, tau, h, M, err)  # h = 1 error floor (Appendix B aliasing)
         else:
-            assert bound_ok and err < 1e-12, (scen, tau, h, M, err)
+            # converged rows: the paper prints 6e-15 .. 7.7e-13; allow 3x the larger scale
+            assert bound_ok and err < max(1e-12, 3 * printed), (scen, tau, h, M, err)
