@@ -481,7 +481,7 @@ def run_ours(args):
     t_pole = pole_ms / 1e3
     if args.form == "mixed":
         # every FP32 arithmetic operation counted once (the kernel is FADD-heavy:
-        # 60 of its 72 operations per term are single-flop), against the FP32
+        # 61 of its 73 operations per term are single-flop), against the FP32
         # lane rate 152 SMs x 128 lanes x 2.07 GHz
         ops = terms * FP32_INSTR_PER_TERM
         peak = SMS * 128 * SM_MAX_GHZ / 1e3
