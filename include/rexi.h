@@ -160,9 +160,40 @@ rexi_status rexi_plan_set_rho(rexi_plan_t plan, double rho);
  * per term, iteration cap per term, number of terms solved together. */
 rexi_status rexi_plan_set_krylov(rexi_plan_t plan, double rtol, int32_t max_iters, int32_t term_batch);
 
-/* Bytes of device workspace rexi_step needs for this plan, dt and tol. */
+/* Solver of the variable-depth path (REXI_EUNSUPPORTED on constant-depth
+ * plans):
+ * REXI_KRYLOV_CG (default): one pole-pair CG solve per REXII term, terms
+ *   batched (pair operator (alpha_{-n} - dt A)(alpha_n + dt A), Section 3's
+ *   reduced sum); computes in the plan's form.
+ * REXI_KRYLOV_SHARED: one Lanczos basis of K = -i dt A (self-adjoint in the
+ *   energy inner product) shared by every single-shift pole z_j of the step:
+ *   (dt A - z_j)^{-1} f = -i (K + i z_j)^{-1} f, and the Krylov space of a
+ *   shifted system does not depend on the shift.  Every pole's residual is a
+ *   multiple of the next Lanczos vector, so the error of the whole step is
+ *   ||f|| b_k phi(K) v_k for a rational function phi known from the Lanczos
+ *   scalars; the solver stops when b_k max |phi| over [-dt rho, dt rho]
+ *   (sampled, rho the plan's spectral radius) is <= rtol (from
+ *   rexi_plan_set_krylov, relative to ||f|| in the energy norm; max_iters
+ *   caps the Lanczos steps), then forms sum_j beta_j x_j = V_k c.  Lanczos
+ *   vectors that fit in workspace bytes beyond rexi_workspace_size (3 nx ny
+ *   complex values, or 3 nx ny real values for real input, rounded up to 256
+ *   bytes, each) are kept from the first pass; the rest are regenerated from
+ *   the stored scalars.  Real input runs the real form of the recurrence
+ *   (the vectors alternate between real and imaginary, a_j = 0).  FP64 in
+ *   every form.  Applies to rexi_step and rexi_step_adjoint; the depth gradient
+ *   always uses per-term CG. */
+enum { REXI_KRYLOV_CG = 0, REXI_KRYLOV_SHARED = 1 };
+rexi_status rexi_plan_set_krylov_method(rexi_plan_t plan, int32_t method);
+
+/* Bytes of device workspace rexi_step and rexi_step_adjoint need for this
+ * plan, dt and tol. */
 rexi_status rexi_workspace_size(rexi_plan_t plan, double dt, double tol, int32_t real_input,
                                 size_t* bytes);
+
+/* Bytes of device workspace rexi_step_grad_depth needs (variable-depth plans;
+ * REXI_EUNSUPPORTED otherwise). */
+rexi_status rexi_workspace_size_grad_depth(rexi_plan_t plan, double dt, double tol, int32_t real_input,
+                                           size_t* bytes);
 
 /* ------------------------------------------------------------------------ */
 /* The time step.                                                           */
@@ -203,7 +234,8 @@ rexi_status rexi_step_adjoint(rexi_plan_t plan, const void* grad_out_dev, void* 
  *   dL/dH_k = dt Re sum_j beta_j conj(y_j,eta,k) (div x_j)_k,
  *   x_j = (dt A - z_j)^{-1} in,  y_j = (dt A - z_j)^{-H} grad_out;
  * both are recovered per REXII term from two CG solves with the pair
- * operator.  Same workspace as rexi_step; info as for rexi_step. */
+ * operator.  Workspace: rexi_workspace_size_grad_depth bytes; info as for
+ * rexi_step. */
 rexi_status rexi_step_grad_depth(rexi_plan_t plan, const void* in_dev, const void* grad_out_dev,
                                  double* grad_depth_dev, double dt, double tol, int32_t real_input,
                                  void* workspace_dev, size_t workspace_bytes, void* stream, rexi_step_info* info);

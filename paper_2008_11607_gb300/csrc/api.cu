@@ -288,6 +288,7 @@ rexi_status rexi_plan_create(rexi_plan_t* out, int32_t nx, int32_t ny, double Lx
     p->rho_natural = p->rho;
     st = krylov_init(&p->kry, nx, ny, Lx, Ly, g, f, depth, p->Hmean);
     if (st != REXI_OK) { rexi_plan_destroy(p); return st; }
+    p->kry.rho_bound = p->rho_natural;
   }
   if (cudaEventCreateWithFlags(&p->staging_done, cudaEventDisableTiming) != cudaSuccess) {
     rexi_plan_destroy(p);
@@ -301,6 +302,14 @@ rexi_status rexi_spectral_radius(rexi_plan_t p, double* rho) {
   g_err[0] = 0;
   if (!p || !rho) return fail(REXI_EINVAL, "NULL argument");
   *rho = p->rho;
+  return REXI_OK;
+}
+
+rexi_status rexi_plan_set_krylov_method(rexi_plan_t p, int32_t method) {
+  g_err[0] = 0;
+  if (!p || (method != REXI_KRYLOV_CG && method != REXI_KRYLOV_SHARED)) return fail(REXI_EINVAL, "bad Krylov method");
+  if (!p->depth) return fail(REXI_EUNSUPPORTED, "Krylov method needs a variable-depth plan");
+  p->kry.method = method;
   return REXI_OK;
 }
 
@@ -589,6 +598,17 @@ rexi_status rexi_workspace_size(rexi_plan_t p, double dt, double tol, int32_t re
   return REXI_OK;
 }
 
+rexi_status rexi_workspace_size_grad_depth(rexi_plan_t p, double dt, double tol, int32_t real_input, size_t* bytes) {
+  g_err[0] = 0;
+  if (!p || !bytes) return fail(REXI_EINVAL, "NULL argument");
+  if (!p->depth) return fail(REXI_EUNSUPPORTED, "depth gradient needs a variable-depth plan");
+  if (!(dt >= 0.0) || !isfinite(dt)) return fail(REXI_EINVAL, "dt must be finite and >= 0");
+  const int M = pole_count(dt * p->rho, p->h, tol);
+  if (M < 0) return fail(REXI_EINVAL, "pole count rule rejected the arguments");
+  *bytes = krylov_grad_workspace_bytes(&p->kry, M, real_input, p->form);
+  return REXI_OK;
+}
+
 rexi_status rexi_step(rexi_plan_t p, const void* in, void* out, double dt, double tol, int32_t real_input,
                       int32_t term_begin, int32_t term_end, void* ws, size_t ws_bytes, void* stream,
                       rexi_step_info* info) {
@@ -744,5 +764,6 @@ extern "C" rexi_status rexi_plan_set_rho(rexi_plan_t p, double rho) {
   g_err[0] = 0;
   if (!p || !(rho >= 0.0) || !isfinite(rho)) return fail(REXI_EINVAL, "bad rho");
   p->rho = rho > 0.0 ? rho : p->rho_natural;
+  p->kry.rho_bound = p->rho;  // interval of the shared-Krylov error bound
   return REXI_OK;
 }

@@ -666,6 +666,12 @@ rexi_status krylov_init(KrylovSettings* k, int nx, int ny, double Lx, double Ly,
   k->w64 = reinterpret_cast<double*>(mem);
   k->H32 = reinterpret_cast<float*>(mem + al256(nk * sizeof(double)));
   k->w32 = reinterpret_cast<float*>(mem + al256(nk * sizeof(double)) + al256(nk * sizeof(float)));
+  if (cudaMallocHost(reinterpret_cast<void**>(&k->pinned), 8 * sizeof(double)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&k->ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&k->ev[1], cudaEventDisableTiming) != cudaSuccess) {
+    set_last_error("pinned buffer or event creation failed");
+    return REXI_ECUDA;
+  }
   depth_tables<<<(unsigned)((nk + 255) / 256), 256>>>(depth, nk, g, k->w64, k->H32, k->w32);
   if (cudaDeviceSynchronize() != cudaSuccess) {
     set_last_error("depth table kernel failed");
@@ -677,9 +683,20 @@ rexi_status krylov_init(KrylovSettings* k, int nx, int ny, double Lx, double Ly,
 void krylov_destroy(KrylovSettings* k) {
   if (k->dev_state) cudaFree(k->dev_state);
   k->dev_state = nullptr;
+  if (k->pinned) cudaFreeHost(k->pinned);
+  k->pinned = nullptr;
+  for (auto& e : k->ev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
 }
 
 size_t krylov_workspace_bytes(const KrylovSettings* k, int M, int real_input, int form) {
+  if (k->method == 1) return lanczos_workspace_bytes(k, M, real_input);
+  return layout(k, n_terms_for(M, real_input), form).total;
+}
+
+size_t krylov_grad_workspace_bytes(const KrylovSettings* k, int M, int real_input, int form) {
   return layout(k, n_terms_for(M, real_input), form).total;
 }
 
@@ -891,6 +908,9 @@ bool overlaps(const void* a, const void* b, size_t bytes) {
 rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void* in, void* out, double dt,
                         int real_input, int term_begin, int term_end, void* ws, size_t ws_bytes, cudaStream_t s,
                         rexi_step_info* info, bool adjoint, const KrylovHooks& hooks) {
+  if (k->method == 1)
+    return krylov_step_lanczos(k, h, M, in, out, dt, real_input, term_begin, term_end, ws, ws_bytes, s, info,
+                               adjoint, hooks);
   const size_t nk = (size_t)k->nx * k->ny, n3 = 3 * nk;
   if (overlaps(in, out, n3 * sizeof(double2))) {
     set_last_error("variable-depth path: input and output must not overlap");

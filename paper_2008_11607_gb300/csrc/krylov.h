@@ -16,6 +16,10 @@ struct KrylovSettings {
   int term_batch = 64;        // terms solved together in one launch
   double inner_rtol = 1e-4;   // mixed form: FP32 inner solve target per refinement step
   int max_outer = 30;         // mixed form: refinement steps cap
+  int method = 0;             // 0: CG per REXII term; 1: one Lanczos basis shared by all poles
+  double rho_bound = 0;       // upper bound of ||A||_W (the plan's own rho)
+  double* pinned = nullptr;   // small pinned host buffer (convergence checks)
+  cudaEvent_t ev[2] = {nullptr, nullptr};
   void* dev_state = nullptr;  // plan-owned device tables below
   double* w64 = nullptr;      // energy weight g / H (FP64)
   float* H32 = nullptr;       // depth (FP32 copy for the inner solver)
@@ -34,9 +38,15 @@ rexi_status krylov_init(KrylovSettings* k, int nx, int ny, double Lx, double Ly,
                         const double* depth, double Hmean);
 void krylov_destroy(KrylovSettings* k);
 size_t krylov_workspace_bytes(const KrylovSettings* k, int M, int real_input, int form);
+size_t krylov_grad_workspace_bytes(const KrylovSettings* k, int M, int real_input, int form);
 rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void* in, void* out, double dt,
                         int real_input, int term_begin, int term_end, void* ws, size_t ws_bytes,
                         cudaStream_t s, rexi_step_info* info, bool adjoint, const KrylovHooks& hooks);
+// Shared-Krylov (multi-shift Lanczos) variant of krylov_step (FP64).
+size_t lanczos_workspace_bytes(const KrylovSettings* k, int M, int real_input);
+rexi_status krylov_step_lanczos(KrylovSettings* k, double h, int M, const void* in, void* out, double dt,
+                                int real_input, int term_begin, int term_end, void* ws, size_t ws_bytes,
+                                cudaStream_t s, rexi_step_info* info, bool adjoint, const KrylovHooks& hooks);
 // grad_depth += dL/dH for out = r(dt A(H)) f_in and G = dL/d out.
 rexi_status krylov_grad_depth(KrylovSettings* k, int form, double h, int M, const void* f_in, const void* g_out,
                               double* grad_depth, double dt, int real_input, void* ws, size_t ws_bytes,

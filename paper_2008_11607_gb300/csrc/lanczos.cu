@@ -1,0 +1,841 @@
+// Variable-depth path, shared-Krylov method: every single-shift pole of the
+// rational approximation uses one Lanczos basis.
+//
+// With K = -i tau A, which is self-adjoint in the energy inner product
+// <a, b>_W = sum (g/H, 1, 1) conj(a) b (A is skew there), each pole term is
+//   (tau A - z_j)^{-1} f = -i (K + i z_j)^{-1} f,
+// a shifted system of one self-adjoint operator.  The Krylov space
+// span{f, K f, K^2 f, ...} does not depend on the shift, so k Lanczos steps
+// (K V_k = V_k T_k + b_k v_k e_{k-1}^T, T_k real symmetric tridiagonal) give
+// every pole its Galerkin solution x_j = ||f|| V_k (T_k + s_j)^{-1} e_0,
+// s_j = i z_j, at once.  The weighted sum over poles is
+//   sum_j beta_j (tau A - z_j)^{-1} f ~ V_k c,
+//   c = -i ||f|| sum_j beta_j (T_k + s_j)^{-1} e_0.
+// Error: every pole's residual is a multiple of v_k, so the error of the sum
+// is -i ||f|| b_k phi(K) v_k with the rational function
+//   phi(l) = sum_j beta_j y_j / (l + s_j),  y_j = e_{k-1}^T (T_k + s_j)^{-1} e_0,
+// and ||error|| <= ||f|| b_k max |phi| over the spectrum of K, which lies in
+// [-tau rho, tau rho] (rho >= ||A||_W).  For real input the step keeps only the
+// real part, which is the same sum over the conjugate-closed pole set
+// {z_j, conj z_j} with weights {beta_j / 2, conj beta_j / 2}; the bound uses
+// that set (its phi has no cancelling imaginary remainder).  The bound is
+// evaluated on the device every kChunk steps by sampling l at spacing d / 8,
+// d = h |mu| the distance of every pole from the real axis.
+//
+// One fused kernel per Lanczos step (v_j formed on the fly from w'_{j-1} and
+// v_{j-1}; both inner products of the step in one deterministic reduction,
+// b_{j+1}^2 = ||w'_j||^2 - a_j^2).  Vectors that fit in the caller's extra
+// workspace are kept; the rest of the basis is regenerated in a second pass
+// with the stored scalars (same operations in the same order, so the same
+// vectors).  FP64 throughout.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <complex>
+#include <vector>
+
+#include "internal.h"
+#include "krylov.h"
+
+namespace rexi {
+namespace {
+
+constexpr int TX = 32, TY = 16, THREADS = 256, HX = TX + 2, HY = TY + 2;
+constexpr int kChunk = 16;         // Lanczos steps between convergence checks
+constexpr int kCoarse = 8;         // coarse check: every 8th sample of the fine grid
+constexpr int kMinScratchPoles = 32;
+
+struct LGeom {
+  int nx, ny, tiles_x, tiles_y;
+  size_t fstride;
+  double tdx, tdy, tgdx, tgdy, tf4;  // tau folded in
+  const double* H;
+  const double* w;
+};
+
+__device__ __forceinline__ double2 ladd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 lsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+__device__ __forceinline__ size_t lidx(const LGeom& G, int i, int j) {
+  i = G.nx > TX ? (i < 0 ? i + G.nx : (i >= G.nx ? i - G.nx : i)) : (i + G.nx) % G.nx;
+  j = G.ny > TY ? (j < 0 ? j + G.ny : (j >= G.ny ? j - G.ny : j)) : (j + G.ny) % G.ny;
+  return (size_t)j * G.nx + i;
+}
+
+// Two block sums at once (result valid in thread 0).
+__device__ __forceinline__ double2 lblock_sum2(double2 v, double2* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double2 s = make_double2(0.0, 0.0);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < THREADS / 32; ++i) s = ladd(s, red[i]);
+  return s;
+}
+
+// Deterministic cross-block sum of two values (fixed order), finished by the
+// last block to arrive; returns true in that block's thread 0.
+__device__ __forceinline__ bool llast_block2(double2 mine, double2* partials, unsigned* counter, int ntiles, int tile,
+                                            double2* total, double2* red) {
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) {
+    partials[tile] = mine;
+    __threadfence();
+    is_last = atomicAdd(counter, 1u) == (unsigned)ntiles - 1;
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  const volatile double2* vp = partials;
+  double2 s = make_double2(0.0, 0.0);
+  for (int i = threadIdx.x; i < ntiles; i += THREADS) {
+    s.x += vp[i].x;
+    s.y += vp[i].y;
+  }
+  s = lblock_sum2(s, red);
+  if (threadIdx.x == 0) {
+    *total = s;
+    *counter = 0u;
+  }
+  return threadIdx.x == 0;
+}
+
+__device__ __forceinline__ double safe_inv(double b) { return b > 0.0 ? 1.0 / b : 0.0; }
+
+// Vector arithmetic for the two representations of a Lanczos vector: complex
+// (double2) in general, and real (double) for real input, where the vectors
+// alternate between purely real and purely imaginary (v_j = i^j u_j with u_j
+// real, a_j = 0) and the recurrence becomes u_{j+1} b_{j+1} = -tau A u_j + b_j u_{j-1}.
+__device__ __forceinline__ double vadd(double a, double b) { return a + b; }
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return ladd(a, b); }
+__device__ __forceinline__ double vsub(double a, double b) { return a - b; }
+__device__ __forceinline__ double2 vsub(double2 a, double2 b) { return lsub(a, b); }
+__device__ __forceinline__ double vscal(double s, double a) { return s * a; }
+__device__ __forceinline__ double2 vscal(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__device__ __forceinline__ double vfma(double s, double a, double b) { return fma(s, a, b); }
+__device__ __forceinline__ double2 vfma(double s, double2 a, double2 b) {
+  return make_double2(fma(s, a.x, b.x), fma(s, a.y, b.y));
+}
+__device__ __forceinline__ double vnrm2(double a) { return a * a; }
+__device__ __forceinline__ double vnrm2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
+__device__ __forceinline__ double vredot(double a, double b) { return a * b; }
+__device__ __forceinline__ double vredot(double2 a, double2 b) { return fma(a.x, b.x, a.y * b.y); }
+template <typename T>
+__device__ __forceinline__ T vzero() {
+  return T{};
+}
+// acc += c v (complex c; real vectors take c' = Re(i^j c), the real part of
+// c_j v_j = c_j i^j u_j)
+__device__ __forceinline__ double2 vcfma(double2 c, double2 v, double2 a) {
+  return make_double2(fma(c.x, v.x, fma(-c.y, v.y, a.x)), fma(c.x, v.y, fma(c.y, v.x, a.y)));
+}
+__device__ __forceinline__ double vcfma(double c, double v, double a) { return fma(c, v, a); }
+__device__ __forceinline__ double real_coeff(double2 c, int j) {
+  switch (j & 3) {
+    case 0: return c.x;
+    case 1: return -c.y;
+    case 2: return -c.x;
+    default: return c.y;
+  }
+}
+template <typename T>
+__device__ __forceinline__ T cvec_at(const double2* cvec, int j);
+template <>
+__device__ __forceinline__ double2 cvec_at<double2>(const double2* cvec, int j) {
+  return cvec[j];
+}
+template <>
+__device__ __forceinline__ double cvec_at<double>(const double2* cvec, int j) {
+  return real_coeff(cvec[j], j);
+}
+template <typename T>
+__device__ __forceinline__ T from_in(double2 v);
+template <>
+__device__ __forceinline__ double from_in<double>(double2 v) {
+  return v.x;
+}
+template <>
+__device__ __forceinline__ double2 from_in<double2>(double2 v) {
+  return v;
+}
+__device__ __forceinline__ double2 to_out(double v) { return make_double2(v, 0.0); }
+__device__ __forceinline__ double2 to_out(double2 v) { return v; }
+
+// s tau A t at a tile point (C-grid stencil: eta row -H div, momentum rows
+// -g grad eta and the four-point Coriolis average); s is folded into the
+// coefficients (c = s tau / dx etc.).
+struct StencilCoef {
+  double cdx, cdy, cgdx, cgdy, cf4;
+};
+template <typename T>
+__device__ __forceinline__ void apply_sA(const T (*E)[HX], const T (*U)[HX], const T (*V)[HX], int li, int lj,
+                                         double Hij, const StencilCoef& c, T out[3]) {
+  const double hx = -Hij * c.cdx, hy = -Hij * c.cdy;
+  out[0] = vfma(hx, vsub(U[lj][li], U[lj][li - 1]), vscal(hy, vsub(V[lj][li], V[lj - 1][li])));
+  const T v4 = vadd(vadd(V[lj][li], V[lj][li + 1]), vadd(V[lj - 1][li], V[lj - 1][li + 1]));
+  out[1] = vfma(c.cf4, v4, vscal(-c.cgdx, vsub(E[lj][li + 1], E[lj][li])));
+  const T u4 = vadd(vadd(U[lj][li], U[lj][li - 1]), vadd(U[lj + 1][li], U[lj + 1][li - 1]));
+  out[2] = vfma(-c.cf4, u4, vscal(-c.cgdy, vsub(E[lj + 1][li], E[lj][li])));
+}
+// the Lanczos operator applied to the scaled-stencil output: complex K = -i (tau A),
+// real -(tau A) (the sign is folded into the coefficients by the caller)
+__device__ __forceinline__ double2 op_out(double2 a) { return make_double2(a.y, -a.x); }
+__device__ __forceinline__ double op_out(double a) { return a; }
+
+// f0 = in (eta / w for the adjoint), imaginary parts dropped for real input;
+// beta[0] = ||f0||_W.
+template <typename T>
+__global__ void __launch_bounds__(THREADS) lz_init(LGeom G, const double2* in, int adjoint, T* f0, double* beta,
+                                                   double2* partials, unsigned* counter) {
+  __shared__ double2 red[THREADS / 32];
+  const int tile = blockIdx.y * G.tiles_x + blockIdx.x;
+  double loc = 0.0;
+  for (int k = threadIdx.x; k < TX * TY; k += THREADS) {
+    const int i = blockIdx.x * TX + k % TX, j = blockIdx.y * TY + k / TX;
+    if (i >= G.nx || j >= G.ny) continue;
+    const size_t id = (size_t)j * G.nx + i;
+    for (int c = 0; c < 3; ++c) {
+      T v = from_in<T>(in[id + c * G.fstride]);
+      if (adjoint && c == 0) v = vscal(1.0 / G.w[id], v);
+      f0[id + c * G.fstride] = v;
+      loc += (c == 0 ? G.w[id] : 1.0) * vnrm2(v);
+    }
+  }
+  const double2 s = lblock_sum2(make_double2(loc, 0.0), red);
+  double2 tot;
+  if (llast_block2(s, partials, counter, G.tiles_x * G.tiles_y, tile, &tot, red)) beta[0] = sqrt(tot.x);
+}
+
+// One Lanczos step j (complex: K = -i tau A, w'_j = K v_j - b_j v_{j-1};
+// real: w'_j = -tau A u_j + b_j u_{j-1}, a_j = 0).
+//   MODE 0 (first pass): v_j = (w'_{j-1} - a_{j-1} v_{j-1}) / b_j  (v_0 = f0 / b_0);
+//     the stencil runs on the unscaled tile with 1 / b_j folded into its
+//     coefficients; writes v_j, w'_j; a_j = Re <v_j, w'_j>_W (complex) and
+//     b_{j+1} = sqrt(||w'_j||_W^2 - a_j^2), one deterministic reduction.
+//   MODE 1 (second pass): as MODE 0 with the stored scalars, no reduction,
+//     and acc += c_j v_j.
+template <int MODE, typename T>
+__global__ void __launch_bounds__(THREADS) lz_step(LGeom G, int j, const T* __restrict__ wprev,
+                                                   const T* __restrict__ vprev, T* __restrict__ vout,
+                                                   T* __restrict__ wout, double* alpha,
+                                                   double* beta, double2* partials, unsigned* counter, T* acc,
+                                                   const double2* cvec) {
+  constexpr bool CPLX = sizeof(T) == sizeof(double2);
+  __shared__ T E[HY][HX], U[HY][HX], V[HY][HX];
+  __shared__ double2 red[THREADS / 32];
+  const double bj = beta[j];
+  const double sc = safe_inv(bj);
+  const double am = (CPLX && j > 0) ? alpha[j - 1] : 0.0;
+  const double sg = CPLX ? sc : -sc;  // real form: -(tau A)
+  StencilCoef cf;
+  cf.cdx = sg * G.tdx;
+  cf.cdy = sg * G.tdy;
+  cf.cgdx = sg * G.tgdx;
+  cf.cgdy = sg * G.tgdy;
+  cf.cf4 = sg * G.tf4;
+  const double bsign = CPLX ? -bj : bj;
+  const int i0 = blockIdx.x * TX - 1, j0 = blockIdx.y * TY - 1;
+  for (int k = threadIdx.x; k < HX * HY; k += THREADS) {
+    const int li = k % HX, lj = k / HX;
+    const size_t id = lidx(G, i0 + li, j0 + lj);
+    T t[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      t[c] = wprev[id + c * G.fstride];
+      if (CPLX && vprev) t[c] = vfma(-am, vprev[id + c * G.fstride], t[c]);
+    }
+    E[lj][li] = t[0];
+    U[lj][li] = t[1];
+    V[lj][li] = t[2];
+  }
+  __syncthreads();
+  T cj = vzero<T>();
+  if (MODE == 1) cj = cvec_at<T>(cvec, j);
+  double dot = 0.0, nrm = 0.0;
+  for (int k = threadIdx.x; k < TX * TY; k += THREADS) {
+    const int li = k % TX + 1, lj = k / TX + 1;
+    const int i = blockIdx.x * TX + li - 1, jj = blockIdx.y * TY + lj - 1;
+    if (i >= G.nx || jj >= G.ny) continue;
+    const size_t id = (size_t)jj * G.nx + i;
+    T ka[3];
+    apply_sA<T>(E, U, V, li, lj, G.H[id], cf, ka);
+    const T tc[3] = {E[lj][li], U[lj][li], V[lj][li]};
+    const double wt = G.w[id];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t o = id + c * G.fstride;
+      const T vc = vscal(sc, tc[c]);
+      const T vp = vprev ? vprev[o] : vzero<T>();
+      const T w = vfma(bsign, vp, op_out(ka[c]));
+      wout[o] = w;
+      vout[o] = vc;
+      if (MODE == 1) acc[o] = vcfma(cj, vc, acc[o]);
+      if (MODE == 0) {
+        const double wc = c == 0 ? wt : 1.0;
+        if (CPLX) dot += wc * vredot(vc, w);  // Re conj(v) w
+        nrm += wc * vnrm2(w);
+      }
+    }
+  }
+  if (MODE != 0) return;
+  const double2 s = lblock_sum2(make_double2(dot, nrm), red);
+  double2 tot;
+  if (llast_block2(s, partials, counter, G.tiles_x * G.tiles_y, blockIdx.y * G.tiles_x + blockIdx.x, &tot, red)) {
+    alpha[j] = tot.x;
+    beta[j + 1] = sqrt(fmax(tot.y - tot.x * tot.x, 0.0));
+  }
+}
+
+// acc = sum_{b < nb} c_b basis_b (acc = 0 for nb = 0); fixed summation order,
+// four vectors per pass for loads in flight.
+template <typename T>
+__global__ void lz_basis_sum(const T* __restrict__ basis, size_t vstride, int nb, const double2* cvec, T* acc,
+                             size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T a = vzero<T>();
+  int b = 0;
+  for (; b + 4 <= nb; b += 4) {
+    const T v0 = basis[(size_t)b * vstride + i], v1 = basis[(size_t)(b + 1) * vstride + i];
+    const T v2 = basis[(size_t)(b + 2) * vstride + i], v3 = basis[(size_t)(b + 3) * vstride + i];
+    a = vcfma(cvec_at<T>(cvec, b), v0, a);
+    a = vcfma(cvec_at<T>(cvec, b + 1), v1, a);
+    a = vcfma(cvec_at<T>(cvec, b + 2), v2, a);
+    a = vcfma(cvec_at<T>(cvec, b + 3), v3, a);
+  }
+  for (; b < nb; ++b) a = vcfma(cvec_at<T>(cvec, b), basis[(size_t)b * vstride + i], a);
+  acc[i] = a;
+}
+
+// out = acc (eta times w for the adjoint), real part only for real input.
+template <typename T>
+__global__ void lz_finish(const T* acc, double2* out, const double* w, size_t nk, int real_out, int adjoint) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 3 * nk) return;
+  double2 v = to_out(acc[i]);
+  if (adjoint && i < nk) {
+    v.x *= w[i];
+    v.y *= w[i];
+  }
+  if (real_out) v.y = 0.0;
+  out[i] = v;
+}
+
+__device__ __forceinline__ double2 cdivd(double2 a, double2 b) {
+  const double q = 1.0 / fma(b.x, b.x, b.y * b.y);
+  return make_double2(fma(a.x, b.x, a.y * b.y) * q, fma(a.y, b.x, -a.x * b.y) * q);
+}
+
+// Per pole p: forward elimination of (T + s_p) over the new steps [j0, j1);
+// wy_p = weight_p * e_{j1-1}^T (T_{j1} + s_p)^{-1} e_0 = weight_p g / d.
+__global__ void lz_poles_advance(int np, const double2* s, const double2* wgt, const double* alpha,
+                                 const double* beta, int j0, int j1, double2* dg, double2* wy) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  double2 d = dg[2 * p], g = dg[2 * p + 1];
+  const double2 sp = s[p];
+  for (int j = j0; j < j1; ++j) {
+    if (j == 0) {
+      d = make_double2(alpha[0] + sp.x, sp.y);
+      g = make_double2(1.0, 0.0);
+    } else {
+      const double b = beta[j];
+      const double2 m = cdivd(make_double2(b, 0.0), d);
+      d = make_double2(alpha[j] + sp.x - m.x * b, sp.y - m.y * b);
+      g = make_double2(-(m.x * g.x - m.y * g.y), -(m.x * g.y + m.y * g.x));
+    }
+  }
+  dg[2 * p] = d;
+  dg[2 * p + 1] = g;
+  const double2 y = cdivd(g, d), wp = wgt[p];
+  wy[p] = make_double2(wp.x * y.x - wp.y * y.y, wp.x * y.y + wp.y * y.x);
+}
+
+// 1 / x for x >= 1e-30 and below 1e30: FP32 hardware reciprocal as the seed,
+// two Newton-Raphson steps r <- r (2 - x r) in FP64 (relative error ~1e-16;
+// the bound needs a few digits after the cancellation inside phi).
+__device__ __forceinline__ double lrcp(double x) {
+  double r = (double)__frcp_rn((float)x);
+  r = fma(r, fma(-x, r, 1.0), r);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+
+// Partial sums of phi(l_m) = sum_p wy_p / (l_m + s_p) over the poles of group
+// blockIdx.y (G poles each) at samples l_m = -L + m dl, m = slot * stride:
+// part[group * nslot + slot].  With `gate`, runs only if
+// beta[jk] * (max of the gate pass) <= rtol.
+__global__ void __launch_bounds__(THREADS) lz_bound_part(int np, int G, const double2* s, const double2* wy,
+                                                         double L, double dl, int nslot, int stride,
+                                                         const double* beta, int jk, double rtol,
+                                                         const unsigned long long* gate, double2* part) {
+  if (gate && beta[jk] * __longlong_as_double((long long)*gate) > rtol) return;
+  __shared__ double2 ss[THREADS], sw[THREADS];
+  const int slot = blockIdx.x * THREADS + threadIdx.x;
+  const double lam = -L + (double)slot * stride * dl;
+  const int pb = blockIdx.y * G, pe = min(np, pb + G);
+  double re = 0.0, im = 0.0;
+  for (int p0 = pb; p0 < pe; p0 += THREADS) {
+    __syncthreads();
+    if (p0 + threadIdx.x < pe) {
+      ss[threadIdx.x] = s[p0 + threadIdx.x];
+      sw[threadIdx.x] = wy[p0 + threadIdx.x];
+    }
+    __syncthreads();
+    const int cnt = min(THREADS, pe - p0);
+    for (int q = 0; q < cnt; ++q) {
+      const double a = lam + ss[q].x, b = ss[q].y;
+      const double r = lrcp(fma(a, a, b * b));
+      re = fma(r, fma(sw[q].x, a, sw[q].y * b), re);   // Re w / (a + ib)
+      im = fma(r, fma(sw[q].y, a, -sw[q].x * b), im);  // Im w / (a + ib)
+    }
+  }
+  if (slot < nslot) part[(size_t)blockIdx.y * nslot + slot] = make_double2(re, im);
+}
+
+// max over slots of |sum over groups of part| (fixed order), as the bits of a
+// non-negative double (atomicMax on those bits is order-independent).
+__global__ void __launch_bounds__(THREADS) lz_bound_max(int groups, int nslot, const double2* part,
+                                                        const double* beta, int jk, double rtol,
+                                                        const unsigned long long* gate, unsigned long long* out) {
+  if (gate && beta[jk] * __longlong_as_double((long long)*gate) > rtol) return;
+  __shared__ double red[THREADS / 32];
+  const int slot = blockIdx.x * THREADS + threadIdx.x;
+  double v = 0.0;
+  if (slot < nslot) {
+    double re = 0.0, im = 0.0;
+    for (int g = 0; g < groups; ++g) {
+      const double2 t = part[(size_t)g * nslot + slot];
+      re += t.x;
+      im += t.y;
+    }
+    v = sqrt(fma(re, re, im * im));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int i = 0; i < THREADS / 32; ++i) b = fmax(b, red[i]);
+    atomicMax(out, (unsigned long long)__double_as_longlong(b));
+  }
+}
+
+// Coefficients of V c for the poles [p0, p0 + P): per pole the UL sweep of
+// (T_k + s_p) (psi_{k-1} = a_{k-1} + s_p, psi_i = a_i + s_p - b_{i+1}^2 / psi_{i+1})
+// gives y = (T_k + s_p)^{-1} e_0 forward (y_0 = 1 / psi_0,
+// y_{i+1} = -b_{i+1} y_i / psi_{i+1}); scratch[i P + q] = -i ||f|| weight_p y_i.
+__global__ void lz_coeff_solve(int p0, int P, const double2* s, const double2* wgt, const double* alpha,
+                               const double* beta, int kk, double2* scratch) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= P) return;
+  const double2 sp = s[p0 + q], wp = wgt[p0 + q];
+  double2 psi = make_double2(alpha[kk - 1] + sp.x, sp.y);
+  scratch[(size_t)(kk - 1) * P + q] = psi;
+  for (int i = kk - 2; i >= 0; --i) {
+    const double b2 = beta[i + 1] * beta[i + 1];
+    const double2 r = cdivd(make_double2(b2, 0.0), psi);
+    psi = make_double2(alpha[i] + sp.x - r.x, sp.y - r.y);
+    scratch[(size_t)i * P + q] = psi;
+  }
+  // scale = -i ||f|| weight
+  const double fn = beta[0];
+  const double2 sc = make_double2(fn * wp.y, -fn * wp.x);
+  double2 y = cdivd(make_double2(1.0, 0.0), scratch[q]);
+  scratch[q] = make_double2(sc.x * y.x - sc.y * y.y, sc.x * y.y + sc.y * y.x);
+  for (int i = 1; i < kk; ++i) {
+    const double2 ps = scratch[(size_t)i * P + q];
+    const double2 t = cdivd(y, ps);
+    y = make_double2(-beta[i] * t.x, -beta[i] * t.y);
+    scratch[(size_t)i * P + q] = make_double2(sc.x * y.x - sc.y * y.y, sc.x * y.y + sc.y * y.x);
+  }
+}
+
+// cvec[i] (+)= sum_q scratch[i P + q], one block per i, fixed order.
+__global__ void __launch_bounds__(THREADS) lz_coeff_sum(int P, const double2* scratch, double2* cvec, int first) {
+  __shared__ double2 red[THREADS / 32];
+  const int i = blockIdx.x;
+  double2 a = make_double2(0.0, 0.0);
+  for (int q = threadIdx.x; q < P; q += THREADS) a = ladd(a, scratch[(size_t)i * P + q]);
+  a = lblock_sum2(a, red);
+  if (threadIdx.x == 0) cvec[i] = first ? a : ladd(cvec[i], a);
+}
+
+size_t al(size_t v) { return (v + 255) / 256 * 256; }
+
+struct LLayout {
+  size_t vb, scratch_bytes, alpha, beta, cvec, partials, counter, maxslots, sb, wb, wy, dg, sc, wc, part, min_total;
+};
+
+// Error-bound sampling: spacing d / 4 over [-tau rho, tau rho], d = h |mu|;
+// with tau rho <= M h (pole-count rule) at most 8 M / |mu| + 2 samples.
+int nsamp_cap(int M) { return (int)std::ceil(8.0 * M / std::fabs(table_mu())) + 2; }
+// poles per group of the partial sums (at most 64 groups)
+int bound_group(int np_b) { return std::max(128, (np_b + 63) / 64); }
+
+LLayout lz_layout(const KrylovSettings* k, int np_b, int np_c, int M, size_t esize) {
+  LLayout L{};
+  const size_t nk = (size_t)k->nx * k->ny;
+  const size_t ntiles = (size_t)((k->nx + TX - 1) / TX) * ((k->ny + TY - 1) / TY);
+  const size_t nmax = (size_t)k->max_iters + 2;
+  L.vb = al(3 * nk * esize);
+  // f0 | acc vA vB wA wB (+ extra): the five vectors double as the coefficient
+  // scratch once the first pass is over
+  const size_t smin = (size_t)kMinScratchPoles * nmax * sizeof(double2);
+  L.scratch_bytes = std::max(5 * L.vb, al(smin));
+  size_t o = L.vb + L.scratch_bytes;
+  L.alpha = o;
+  o += al(nmax * sizeof(double));
+  L.beta = o;
+  o += al(nmax * sizeof(double));
+  L.cvec = o;
+  o += al(nmax * sizeof(double2));
+  L.partials = o;
+  o += al(ntiles * sizeof(double2));
+  L.counter = o;
+  o += 256;
+  L.maxslots = o;
+  o += 256;
+  L.sb = o;
+  o += al((size_t)np_b * sizeof(double2));
+  L.wb = o;
+  o += al((size_t)np_b * sizeof(double2));
+  L.wy = o;
+  o += al((size_t)np_b * sizeof(double2));
+  L.dg = o;
+  o += al((size_t)np_b * 2 * sizeof(double2));
+  L.sc = o;
+  o += al((size_t)np_c * sizeof(double2));
+  L.wc = o;
+  o += al((size_t)np_c * sizeof(double2));
+  L.part = o;  // bound_group keeps the group count at or below 64
+  o += al((size_t)64 * nsamp_cap(M) * sizeof(double2));
+  L.min_total = o;
+  return L;
+}
+
+int poles_c(int M, int real_input) {
+  const int N = M + kL;
+  return real_input ? 2 * (N + 1) : 2 * (2 * N + 1);
+}
+
+template <typename T>
+rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, void* out, double dt, int real_input,
+                         int term_begin, int term_end, void* ws, size_t ws_bytes, cudaStream_t s,
+                         rexi_step_info* info, bool adjoint, const KrylovHooks& hooks) {
+  using cd = std::complex<double>;
+  auto mark = [&](int i) {
+    if (hooks.mark) hooks.mark(hooks.ctx, i, s);
+  };
+  int64_t launches = 0;
+  const int N = M + kL;
+  if (term_end < 0 || term_end > N + 1) term_end = N + 1;
+  if (term_begin < 0 || term_begin > term_end) {
+    set_last_error("bad term range");
+    return REXI_EINVAL;
+  }
+  const size_t nk = (size_t)k->nx * k->ny, n3 = 3 * nk;
+  if ((const char*)in < (const char*)out + n3 * sizeof(double2) &&
+      (const char*)out < (const char*)in + n3 * sizeof(double2)) {
+    set_last_error("variable-depth path: input and output must not overlap");
+    return REXI_EINVAL;
+  }
+  if (!(k->rho_bound > 0.0) || !k->pinned) {
+    set_last_error("shared-Krylov method: plan has no spectral bound");
+    return REXI_EINVAL;
+  }
+  const int npc_max = poles_c(M, real_input);
+  const LLayout L = lz_layout(k, real_input ? 2 * npc_max : npc_max, npc_max, M, sizeof(T));
+  if (ws_bytes < L.min_total) {
+    set_last_error("workspace too small for the shared-Krylov method");
+    return REXI_ENOMEM;
+  }
+
+  // poles z_j and weights beta_j of the selected REXII terms (partial fractions
+  // of each term: z = alpha_{-n} with -Gamma P_n, z = -alpha_n with Gamma Q_n)
+  TermSet ts;
+  rexii_terms(M, h, &ts);
+  const double hmu = h * ts.mu;
+  std::vector<double2> sc, wc, sb, wb;
+  const cd I(0.0, 1.0);
+  auto push = [&](cd z, cd w) {
+    const cd sz = I * z;  // shift of K: (tau A - z)^{-1} = -i (K + i z)^{-1}
+    sc.push_back(make_double2(sz.real(), sz.imag()));
+    wc.push_back(make_double2(w.real(), w.imag()));
+    if (real_input) {  // conjugate-closed set for the error bound
+      const cd sz2 = I * std::conj(z);
+      sb.push_back(make_double2(sz.real(), sz.imag()));
+      wb.push_back(make_double2(0.5 * w.real(), 0.5 * w.imag()));
+      sb.push_back(make_double2(sz2.real(), sz2.imag()));
+      wb.push_back(make_double2(0.5 * w.real(), -0.5 * w.imag()));
+    }
+  };
+  for (int n = real_input ? 0 : -N; n <= N; ++n) {
+    const int an = n < 0 ? -n : n;
+    if (an < term_begin || an >= term_end) continue;
+    const int i = n + N;
+    const double gam = (real_input && n > 0) ? 2.0 : 1.0;
+    const cd C1(ts.c1re[i] * hmu + ts.c2re[i] * h * n, ts.c1im[i] * hmu + ts.c2im[i] * h * n);
+    const cd C2 = I * cd(ts.c2re[i], ts.c2im[i]);
+    const cd a_n(hmu, h * n), a_mn(hmu, -h * n);
+    const cd P = (C1 - C2 * a_mn) / (2.0 * hmu), Q = (C1 + C2 * a_n) / (2.0 * hmu);
+    push(a_mn, -gam * P);
+    push(-a_n, gam * Q);
+  }
+  if (!real_input) {
+    sb = sc;
+    wb = wc;
+  }
+  const int npc = (int)sc.size(), npb = (int)sb.size();
+
+  char* base = static_cast<char*>(ws);
+  T* f0 = reinterpret_cast<T*>(base);
+  T* acc = reinterpret_cast<T*>(base + L.vb);
+  T* vA = reinterpret_cast<T*>(base + 2 * L.vb);
+  T* vB = reinterpret_cast<T*>(base + 3 * L.vb);
+  T* wA = reinterpret_cast<T*>(base + 4 * L.vb);
+  T* wB = reinterpret_cast<T*>(base + 5 * L.vb);
+  double2* scratch = reinterpret_cast<double2*>(base + L.vb);
+  double* alpha = reinterpret_cast<double*>(base + L.alpha);
+  double* beta = reinterpret_cast<double*>(base + L.beta);
+  double2* cvec = reinterpret_cast<double2*>(base + L.cvec);
+  double2* partials = reinterpret_cast<double2*>(base + L.partials);
+  unsigned* counter = reinterpret_cast<unsigned*>(base + L.counter);
+  unsigned long long* maxslots = reinterpret_cast<unsigned long long*>(base + L.maxslots);
+  double2* d_sb = reinterpret_cast<double2*>(base + L.sb);
+  double2* d_wb = reinterpret_cast<double2*>(base + L.wb);
+  double2* d_wy = reinterpret_cast<double2*>(base + L.wy);
+  double2* d_dg = reinterpret_cast<double2*>(base + L.dg);
+  double2* d_sc = reinterpret_cast<double2*>(base + L.sc);
+  double2* d_wc = reinterpret_cast<double2*>(base + L.wc);
+  double2* d_part = reinterpret_cast<double2*>(base + L.part);
+  // Lanczos vectors kept in the caller's extra workspace
+  T* basis = reinterpret_cast<T*>(base + L.min_total);
+  const size_t vstride = L.vb / sizeof(T);
+  // kept vectors (at least two, or none); w'_{nbasis-1} goes to f0's buffer
+  // (f0 is read only by step 0) so that the second pass can resume the
+  // recurrence at step nbasis with exactly the first pass's operands
+  int nbasis = (int)std::min<size_t>((ws_bytes - L.min_total) / L.vb, (size_t)k->max_iters + 1);
+  if (nbasis < 2) nbasis = 0;
+  auto vptr = [&](int j) -> T* {
+    if (j < 0) return nullptr;
+    if (j < nbasis) return basis + (size_t)j * vstride;
+    return (j & 1) ? vB : vA;
+  };
+  auto wptr = [&](int j) -> T* { return (j < 0 || j == nbasis - 1) ? f0 : ((j & 1) ? wB : wA); };
+
+  const double tau = adjoint ? -dt : dt;
+  LGeom G_;
+  G_.nx = k->nx;
+  G_.ny = k->ny;
+  G_.tiles_x = (k->nx + TX - 1) / TX;
+  G_.tiles_y = (k->ny + TY - 1) / TY;
+  G_.fstride = nk;
+  const double idx = k->nx / k->Lx, idy = k->ny / k->Ly;
+  G_.tdx = tau * idx;
+  G_.tdy = tau * idy;
+  G_.tgdx = tau * k->g * idx;
+  G_.tgdy = tau * k->g * idy;
+  G_.tf4 = 0.25 * tau * k->f;
+  G_.H = k->depth;
+  G_.w = k->w64;
+  const dim3 grid(G_.tiles_x, G_.tiles_y, 1);
+  const unsigned ebl = (unsigned)((n3 + 255) / 256);
+
+  cudaError_t e = cudaSuccess;
+  mark(0);
+  if (npc == 0) {  // empty term slice
+    e = cudaMemsetAsync(out, 0, n3 * sizeof(double2), s);
+    mark(1);
+    mark(2);
+    mark(3);
+    mark(4);
+    if (e != cudaSuccess) {
+      set_last_error(cudaGetErrorString(e));
+      return REXI_ECUDA;
+    }
+    if (info) {
+      memset(info, 0, sizeof(*info));
+      info->N = N;
+      info->n_terms = real_input ? N + 1 : 2 * N + 1;
+      info->n_poles = npc_max;
+    }
+    return REXI_OK;
+  }
+  e = cudaMemcpyAsync(d_sb, sb.data(), npb * sizeof(double2), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_wb, wb.data(), npb * sizeof(double2), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_sc, sc.data(), npc * sizeof(double2), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_wc, wc.data(), npc * sizeof(double2), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+  mark(1);
+  if (e == cudaSuccess) {
+    lz_init<T><<<grid, THREADS, 0, s>>>(G_, static_cast<const double2*>(in), adjoint ? 1 : 0, f0, beta, partials,
+                                        counter);
+    ++launches;
+    e = cudaGetLastError();
+  }
+
+  // ---- first pass: Lanczos steps, convergence checked on the device ----
+  const double dist = std::fabs(hmu);  // every pole's distance from the real axis
+  const double Lh = std::fabs(tau) * k->rho_bound;
+  int nsamp = (int)std::min<double>(std::ceil(2.0 * Lh / (dist / 4.0)) + 1.0, (double)nsamp_cap(M));
+  nsamp = std::max(nsamp, 2);
+  const double dl = 2.0 * Lh / (nsamp - 1);
+  const int chunk = std::min(512, std::max(kChunk, npb / 256));
+  const int G = bound_group(npb), groups = (npb + G - 1) / G;
+  const int nslot_c = (nsamp + kCoarse - 1) / kCoarse, nslot_f = nsamp;
+  double* pin = k->pinned;
+  auto launch_chunk = [&](int c, int j0, int j1) -> cudaError_t {
+    for (int j = j0; j < j1; ++j)
+      lz_step<0, T><<<grid, THREADS, 0, s>>>(G_, j, wptr(j - 1), vptr(j - 1), vptr(j), wptr(j), alpha, beta,
+                                             partials, counter, nullptr, nullptr);
+    lz_poles_advance<<<(npb + 127) / 128, 128, 0, s>>>(npb, d_sb, d_wb, alpha, beta, j0, j1, d_dg, d_wy);
+    cudaError_t err = cudaMemsetAsync(maxslots, 0, 2 * sizeof(unsigned long long), s);
+    if (err != cudaSuccess) return err;
+    const dim3 gc((nslot_c + THREADS - 1) / THREADS, groups), gf((nslot_f + THREADS - 1) / THREADS, groups);
+    lz_bound_part<<<gc, THREADS, 0, s>>>(npb, G, d_sb, d_wy, Lh, dl, nslot_c, kCoarse, beta, j1, k->rtol, nullptr,
+                                         d_part);
+    lz_bound_max<<<gc.x, THREADS, 0, s>>>(groups, nslot_c, d_part, beta, j1, k->rtol, nullptr, maxslots);
+    lz_bound_part<<<gf, THREADS, 0, s>>>(npb, G, d_sb, d_wy, Lh, dl, nslot_f, 1, beta, j1, k->rtol, maxslots,
+                                         d_part);
+    lz_bound_max<<<gf.x, THREADS, 0, s>>>(groups, nslot_f, d_part, beta, j1, k->rtol, maxslots, maxslots + 1);
+    launches += (j1 - j0) + 5;
+    const int par = c & 1;
+    err = cudaMemcpyAsync(pin + 3 * par, beta + j1, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(pin + 3 * par + 1, maxslots, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaEventRecord(k->ev[par], s);
+    if (err == cudaSuccess) err = cudaGetLastError();
+    return err;
+  };
+  int kk = 0;
+  bool converged = false, nonfinite = false;
+  double bound = INFINITY;
+  auto evaluate = [&](int c, int j1) -> cudaError_t {
+    const int par = c & 1;
+    cudaError_t err = cudaEventSynchronize(k->ev[par]);
+    if (err != cudaSuccess) return err;
+    const double b = pin[3 * par], coarse = pin[3 * par + 1], fine = pin[3 * par + 2];
+    if (!std::isfinite(b) || !std::isfinite(coarse) || !std::isfinite(fine)) {
+      nonfinite = true;
+      return cudaSuccess;
+    }
+    bound = b * coarse > k->rtol ? b * coarse : b * fine;
+    if (bound <= k->rtol) {
+      converged = true;
+      kk = j1;
+    }
+    return cudaSuccess;
+  };
+  int pending = -1, pending_j1 = 0, steps_run = 0;
+  for (int c = 0; e == cudaSuccess; ++c) {
+    const int j0 = c * chunk;
+    if (j0 >= k->max_iters) break;
+    const int j1 = std::min(j0 + chunk, k->max_iters);
+    e = launch_chunk(c, j0, j1);
+    steps_run = j1;
+    if (e != cudaSuccess) break;
+    if (pending >= 0) {
+      e = evaluate(pending, pending_j1);
+      if (e != cudaSuccess || converged || nonfinite) break;
+    }
+    pending = c;
+    pending_j1 = j1;
+  }
+  if (e == cudaSuccess && !converged && !nonfinite && pending >= 0) e = evaluate(pending, pending_j1);
+  // the stream may still run one chunk past the converged step: harmless, the
+  // second pass uses steps < kk only
+  if (e != cudaSuccess) {
+    set_last_error(cudaGetErrorString(e));
+    return REXI_ECUDA;
+  }
+  if (nonfinite) {
+    set_last_error("shared-Krylov method: non-finite Lanczos scalars");
+    if (hooks.launches) *hooks.launches += launches;
+    return REXI_ENOCONV;
+  }
+  if (!converged) {
+    if (hooks.launches) *hooks.launches += launches;
+    if (info) {
+      memset(info, 0, sizeof(*info));
+      info->N = N;
+      info->krylov_iters = k->max_iters;
+      info->krylov_unconverged = npc;
+      info->krylov_max_rel_res = bound;
+    }
+    set_last_error("shared-Krylov method: step cap reached before the error bound");
+    return REXI_ENOCONV;
+  }
+  mark(2);
+
+  // ---- c = -i ||f|| sum_j beta_j (T_kk + s_j)^{-1} e_0, poles in chunks ----
+  const int P = (int)std::min<size_t>((size_t)npc, L.scratch_bytes / ((size_t)kk * sizeof(double2)));
+  for (int p0 = 0; p0 < npc && e == cudaSuccess; p0 += P) {
+    const int Pc = std::min(P, npc - p0);
+    lz_coeff_solve<<<(Pc + 127) / 128, 128, 0, s>>>(p0, Pc, d_sc, d_wc, alpha, beta, kk, scratch);
+    lz_coeff_sum<<<kk, THREADS, 0, s>>>(Pc, scratch, cvec, p0 == 0 ? 1 : 0);
+    launches += 2;
+    e = cudaGetLastError();
+  }
+  mark(3);
+
+  // ---- second pass: acc = V c from the kept vectors, the rest regenerated ----
+  const int nb = std::min(nbasis, kk);
+  if (e == cudaSuccess) {
+    lz_basis_sum<T><<<ebl, 256, 0, s>>>(basis, vstride, nb, cvec, acc, n3);
+    ++launches;
+  }
+  if (e == cudaSuccess && nb < kk) {
+    for (int j = nb; j < kk; ++j)
+      lz_step<1, T><<<grid, THREADS, 0, s>>>(G_, j, wptr(j - 1), vptr(j - 1), vptr(j), wptr(j), alpha, beta,
+                                             partials, counter, acc, cvec);
+    launches += kk - nb;
+  }
+  if (e == cudaSuccess) {
+    lz_finish<T><<<ebl, 256, 0, s>>>(acc, static_cast<double2*>(out), k->w64, nk, real_input, adjoint ? 1 : 0);
+    ++launches;
+    e = cudaGetLastError();
+  }
+  mark(4);
+  if (hooks.launches) *hooks.launches += launches;
+  if (e != cudaSuccess) {
+    set_last_error(cudaGetErrorString(e));
+    return REXI_ECUDA;
+  }
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->N = N;
+    info->n_terms = real_input ? N + 1 : 2 * N + 1;
+    info->n_poles = npc_max;
+    info->krylov_iters = kk;
+    info->krylov_unconverged = 0;
+    info->krylov_max_rel_res = bound;
+    info->krylov_term_iters = steps_run;  // first-pass steps, with the chunk run past convergence
+  }
+  return REXI_OK;
+}
+
+}  // namespace
+
+size_t lanczos_workspace_bytes(const KrylovSettings* k, int M, int real_input) {
+  const int npc = poles_c(M, real_input);
+  return lz_layout(k, real_input ? 2 * npc : npc, npc, M, real_input ? sizeof(double) : sizeof(double2)).min_total;
+}
+
+rexi_status krylov_step_lanczos(KrylovSettings* k, double h, int M, const void* in, void* out, double dt,
+                                int real_input, int term_begin, int term_end, void* ws, size_t ws_bytes,
+                                cudaStream_t s, rexi_step_info* info, bool adjoint, const KrylovHooks& hooks) {
+  if (real_input)
+    return lanczos_impl<double>(k, h, M, in, out, dt, 1, term_begin, term_end, ws, ws_bytes, s, info, adjoint,
+                                hooks);
+  return lanczos_impl<double2>(k, h, M, in, out, dt, 0, term_begin, term_end, ws, ws_bytes, s, info, adjoint, hooks);
+}
+
+}  // namespace rexi

@@ -30,6 +30,10 @@ REXI_FORM_MIXED = 1
 REXI_FORM_PLAIN = 2
 FORMS = {"fp64": REXI_FORM_FP64, "mixed": REXI_FORM_MIXED, "plain": REXI_FORM_PLAIN}
 
+REXI_KRYLOV_CG = 0
+REXI_KRYLOV_SHARED = 1
+KRYLOV_METHODS = {"cg": REXI_KRYLOV_CG, "shared": REXI_KRYLOV_SHARED}
+
 
 class rexi_step_info(ctypes.Structure):
     _fields_ = [
@@ -61,9 +65,11 @@ SIGNATURES = {
     "rexi_plan_destroy": (None, [_vp]),
     "rexi_spectral_radius": (_c_int, [_vp, _dp]),
     "rexi_plan_set_krylov": (_c_int, [_vp, _c_dbl, _c_int, _c_int]),
+    "rexi_plan_set_krylov_method": (_c_int, [_vp, _c_int]),
     "rexi_plan_set_symbol": (_c_int, [_vp, _c_int]),
     "rexi_plan_set_rho": (_c_int, [_vp, _c_dbl]),
     "rexi_workspace_size": (_c_int, [_vp, _c_dbl, _c_dbl, _c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "rexi_workspace_size_grad_depth": (_c_int, [_vp, _c_dbl, _c_dbl, _c_int, ctypes.POINTER(ctypes.c_size_t)]),
     "rexi_step": (_c_int, [_vp, _vp, _vp, _c_dbl, _c_dbl, _c_int, _c_int, _c_int, _vp, ctypes.c_size_t, _vp,
                            ctypes.POINTER(rexi_step_info)]),
     "rexi_step_adjoint": (_c_int, [_vp, _vp, _vp, _c_dbl, _c_dbl, _c_int, _vp, ctypes.c_size_t, _vp]),
@@ -231,16 +237,26 @@ class Plan:
     def set_krylov(self, rtol=1e-10, max_iters=20000, term_batch=64):
         _check(self._lib.rexi_plan_set_krylov(self._h, rtol, max_iters, term_batch), "rexi_plan_set_krylov")
 
-    def workspace_size(self, dt, tol=1e-10, real_input=True):
+    def set_krylov_method(self, method):
+        """Variable-depth solver: "cg" (one CG per REXII term) or "shared" (one Lanczos basis for all poles)."""
+        code = KRYLOV_METHODS[method] if isinstance(method, str) else int(method)
+        _check(self._lib.rexi_plan_set_krylov_method(self._h, code), "rexi_plan_set_krylov_method")
+
+    def krylov_vector_bytes(self, real_input=True):
+        """Bytes of one kept Lanczos vector of the shared-Krylov method (extra workspace beyond
+        workspace_size() holds as many as fit)."""
+        return (3 * self.nx * self.ny * (8 if real_input else 16) + 255) // 256 * 256
+
+    def workspace_size(self, dt, tol=1e-10, real_input=True, grad_depth=False):
         b = ctypes.c_size_t()
-        _check(self._lib.rexi_workspace_size(self._h, dt, tol, int(real_input), ctypes.byref(b)),
-               "rexi_workspace_size")
+        fn = "rexi_workspace_size_grad_depth" if grad_depth else "rexi_workspace_size"
+        _check(getattr(self._lib, fn)(self._h, dt, tol, int(real_input), ctypes.byref(b)), fn)
         return b.value
 
-    def workspace(self, dt, tol=1e-10, real_input=True, device=None):
+    def workspace(self, dt, tol=1e-10, real_input=True, device=None, grad_depth=False):
         import torch
 
-        n = self.workspace_size(dt, tol, real_input)
+        n = self.workspace_size(dt, tol, real_input, grad_depth=grad_depth)
         return torch.empty(max(n, 256), dtype=torch.uint8, device=device or "cuda")
 
     def step(self, state, dt, tol=1e-10, real_input=True, out=None, workspace=None, stream=None,
@@ -297,7 +313,7 @@ class Plan:
         if grad is None:
             grad = torch.zeros((self.ny, self.nx), dtype=torch.float64, device=state.device)
         if workspace is None:
-            workspace = self.workspace(dt, tol, real_input, device=state.device)
+            workspace = self.workspace(dt, tol, real_input, device=state.device, grad_depth=True)
         info = rexi_step_info() if want_info else None
         st = self._lib.rexi_step_grad_depth(self._h, _ptr(state), _ptr(grad_out), _ptr(grad), dt, tol,
                                             int(real_input), _ptr(workspace), workspace.numel(),
