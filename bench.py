@@ -55,7 +55,7 @@ PEAK_FP64_TFLOPS = 1.25
 # DRAM traffic of the pole kernel per launch from an ncu capture of this
 # kernel on the 2048^2 grid (profiles/pole_fused_mixed_2048_tau50.md: same grid and
 # bytes, fewer terms; traffic does not depend on the term count); None if not captured.
-NCU_POLE_TRAFFIC_BYTES = {"mixed": None, "fp64": None}
+NCU_POLE_TRAFFIC_BYTES = {"mixed": 201.470720e6 + 140.511744e6, "fp64": None}
 
 
 def set_workload(grid, tau_rho):
@@ -333,24 +333,25 @@ def krylov_measure(torch, rexi, inputs, form, n_terms, rtol, warm=1):
     }
 
 
-LANCZOS_BYTES_PER_PT_STEP = 112  # lz_step, first pass, real form: w'_{j-1}, u_{j-1} (24 B each) + H, g/H (8 B
-# each) in; u_j, w'_j (24 B each) out
+LANCZOS_BYTES_PER_PT_STEP = 88  # lz_wstep, first pass (real form): W_{j-1}, W_{j-2} (24 B each) + H, g/H (8 B
+# each) in; W_j (24 B) out
 
 
-def shared_measure(torch, rexi, inputs, rtol=1e-10, reps=3):
+def shared_measure(torch, rexi, inputs, rtol=1e-10, reps=3, n=None, tau_rho=None, keep=True):
     """Variable-depth workload, every REXII term (1024^2, tau rho = 400), by the
     shared-Krylov method (one Lanczos basis for all poles, FP64): with the
     minimum workspace (second pass regenerates the basis) and with the basis
     kept in HBM."""
     import numpy as np
 
-    n = KRYLOV_D
+    n = n or KRYLOV_D
+    tau_rho = tau_rho or KRYLOV_TAU_RHO
     Hn = inputs.variable_depth(n, n, seed=0)
     H = torch.from_numpy(Hn).cuda()
     plan = rexi.Plan(n, n, depth=H, form="fp64")
     plan.set_krylov(rtol=rtol, max_iters=20000, term_batch=64)
     plan.set_krylov_method("shared")
-    dt = KRYLOV_TAU_RHO / plan.rho
+    dt = tau_rho / plan.rho
     xn = inputs.kminus3_field(n, n, seed=0)
     x = torch.from_numpy(xn).cuda()
     out = torch.empty_like(x)
@@ -359,7 +360,7 @@ def shared_measure(torch, rexi, inputs, rtol=1e-10, reps=3):
     _, info = plan.step(x, dt, out=out, want_info=True)
     kk = int(info.krylov_iters)
     res = {}
-    for label, extra in (("regenerate", 0), ("kept_basis", kk + 64)):
+    for label, extra in (("regenerate", 0), ("kept_basis", kk + 64))[:2 if keep else 1]:
         ws = torch.empty(base + extra * vec, dtype=torch.uint8, device="cuda")
         plan.step(x, dt, out=out, workspace=ws)
         torch.cuda.synchronize()
@@ -387,13 +388,13 @@ def shared_measure(torch, rexi, inputs, rtol=1e-10, reps=3):
             "phases_ms": {"first_pass": pass1, "coefficients": ph[1] / max(ncalls, 1),
                           "second_pass": ph[2] / max(ncalls, 1), "setup": ph[3] / max(ncalls, 1)},
             "energy_drift": abs(en(o) / en(xn) - 1.0),
-            "roofline": {"kernel": "lz_step (first pass, incl. bound checks in the time)", "bound": "hbm",
+            "roofline": {"kernel": "lz_wstep (first pass, incl. bound checks in the time)", "bound": "hbm",
                          "achieved": gbs, "unit": "GB/s", "bytes_per_point_step": LANCZOS_BYTES_PER_PT_STEP},
             "gpu_launches": nl // max(ncalls, 1),
         }
     res["workload"] = ("LRSW variable depth %dx%d, H = 1 + 0.4 sin(2 pi x) cos(4 pi y) + 8 bumps (seed 0), |k|^-3 "
                        "eta, tau*rho=%g (M=%d), every REXII term (J = %d poles), shared Lanczos basis, FP64, "
-                       "error bound %g" % (n, n, KRYLOV_TAU_RHO, info.M, int(info.n_poles), rtol))
+                       "error bound %g" % (n, n, tau_rho, info.M, int(info.n_poles), rtol))
     return res
 
 
@@ -679,6 +680,9 @@ def main():
     ap.add_argument("--batch-only", action="store_true", help="run only the serving-mix measurement")
     ap.add_argument("--krylov-terms", type=int, default=8)
     ap.add_argument("--krylov-form", default="mixed", choices=["mixed", "fp64", "shared"])
+    ap.add_argument("--krylov-grid", type=int, default=None, help="shared method: grid (profiling captures)")
+    ap.add_argument("--krylov-tau-rho", type=float, default=None, help="shared method: dt * rho (captures)")
+    ap.add_argument("--shared-regen-only", action="store_true", help="shared method: minimum workspace only")
     ap.add_argument("--krylov-only", action="store_true",
                     help="run only the variable-depth measurement (profiling captures)")
     args = ap.parse_args()
@@ -713,7 +717,8 @@ def main():
         from paper_2008_11607_gb300 import inputs, rexi
 
         if args.krylov_form == "shared":
-            print(json.dumps(shared_measure(torch, rexi, inputs)), flush=True)
+            print(json.dumps(shared_measure(torch, rexi, inputs, n=args.krylov_grid, tau_rho=args.krylov_tau_rho,
+                                            keep=not args.shared_regen_only)), flush=True)
         else:
             print(json.dumps(krylov_measure(torch, rexi, inputs, args.krylov_form, args.krylov_terms, 1e-10)),
                   flush=True)

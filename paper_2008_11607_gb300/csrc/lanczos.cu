@@ -24,7 +24,9 @@
 //
 // One fused kernel per Lanczos step (v_j formed on the fly from w'_{j-1} and
 // v_{j-1}; both inner products of the step in one deterministic reduction,
-// b_{j+1}^2 = ||w'_j||^2 - a_j^2).  Vectors that fit in the caller's extra
+// b_{j+1}^2 = ||w'_j||^2 - a_j^2).  For real input the vectors alternate
+// between purely real and purely imaginary (a_j = 0), and the step runs in
+// real arithmetic on the unnormalised vectors alone.  Vectors that fit in the caller's extra
 // workspace are kept; the rest of the basis is regenerated in a second pass
 // with the stored scalars (same operations in the same order, so the same
 // vectors).  FP64 throughout.
@@ -125,18 +127,16 @@ __device__ __forceinline__ double2 vfma(double s, double2 a, double2 b) {
 }
 __device__ __forceinline__ double vnrm2(double a) { return a * a; }
 __device__ __forceinline__ double vnrm2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
-__device__ __forceinline__ double vredot(double a, double b) { return a * b; }
 __device__ __forceinline__ double vredot(double2 a, double2 b) { return fma(a.x, b.x, a.y * b.y); }
 template <typename T>
 __device__ __forceinline__ T vzero() {
   return T{};
 }
-// acc += c v (complex c; real vectors take c' = Re(i^j c), the real part of
-// c_j v_j = c_j i^j u_j)
+// acc += c v; the real form takes c' = Re(i^j c), the real part of
+// c_j v_j = c_j i^j u_j
 __device__ __forceinline__ double2 vcfma(double2 c, double2 v, double2 a) {
   return make_double2(fma(c.x, v.x, fma(-c.y, v.y, a.x)), fma(c.x, v.y, fma(c.y, v.x, a.y)));
 }
-__device__ __forceinline__ double vcfma(double c, double v, double a) { return fma(c, v, a); }
 __device__ __forceinline__ double real_coeff(double2 c, int j) {
   switch (j & 3) {
     case 0: return c.x;
@@ -150,10 +150,6 @@ __device__ __forceinline__ T cvec_at(const double2* cvec, int j);
 template <>
 __device__ __forceinline__ double2 cvec_at<double2>(const double2* cvec, int j) {
   return cvec[j];
-}
-template <>
-__device__ __forceinline__ double cvec_at<double>(const double2* cvec, int j) {
-  return real_coeff(cvec[j], j);
 }
 template <typename T>
 __device__ __forceinline__ T from_in(double2 v);
@@ -184,16 +180,14 @@ __device__ __forceinline__ void apply_sA(const T (*E)[HX], const T (*U)[HX], con
   const T u4 = vadd(vadd(U[lj][li], U[lj][li - 1]), vadd(U[lj + 1][li], U[lj + 1][li - 1]));
   out[2] = vfma(-c.cf4, u4, vscal(-c.cgdy, vsub(E[lj + 1][li], E[lj][li])));
 }
-// the Lanczos operator applied to the scaled-stencil output: complex K = -i (tau A),
-// real -(tau A) (the sign is folded into the coefficients by the caller)
+// K = -i (tau A) applied to the scaled-stencil output
 __device__ __forceinline__ double2 op_out(double2 a) { return make_double2(a.y, -a.x); }
-__device__ __forceinline__ double op_out(double a) { return a; }
 
 // f0 = in (eta / w for the adjoint), imaginary parts dropped for real input;
 // beta[0] = ||f0||_W.
 template <typename T>
 __global__ void __launch_bounds__(THREADS) lz_init(LGeom G, const double2* in, int adjoint, T* f0, double* beta,
-                                                   double2* partials, unsigned* counter) {
+                                                   double* invb, double2* partials, unsigned* counter) {
   __shared__ double2 red[THREADS / 32];
   const int tile = blockIdx.y * G.tiles_x + blockIdx.x;
   double loc = 0.0;
@@ -210,11 +204,13 @@ __global__ void __launch_bounds__(THREADS) lz_init(LGeom G, const double2* in, i
   }
   const double2 s = lblock_sum2(make_double2(loc, 0.0), red);
   double2 tot;
-  if (llast_block2(s, partials, counter, G.tiles_x * G.tiles_y, tile, &tot, red)) beta[0] = sqrt(tot.x);
+  if (llast_block2(s, partials, counter, G.tiles_x * G.tiles_y, tile, &tot, red)) {
+    beta[0] = sqrt(tot.x);
+    invb[0] = safe_inv(beta[0]);
+  }
 }
 
-// One Lanczos step j (complex: K = -i tau A, w'_j = K v_j - b_j v_{j-1};
-// real: w'_j = -tau A u_j + b_j u_{j-1}, a_j = 0).
+// One Lanczos step j of the complex form (K = -i tau A, w'_j = K v_j - b_j v_{j-1}).
 //   MODE 0 (first pass): v_j = (w'_{j-1} - a_{j-1} v_{j-1}) / b_j  (v_0 = f0 / b_0);
 //     the stencil runs on the unscaled tile with 1 / b_j folded into its
 //     coefficients; writes v_j, w'_j; a_j = Re <v_j, w'_j>_W (complex) and
@@ -225,13 +221,13 @@ template <int MODE, typename T>
 __global__ void __launch_bounds__(THREADS) lz_step(LGeom G, int j, const T* __restrict__ wprev,
                                                    const T* __restrict__ vprev, T* __restrict__ vout,
                                                    T* __restrict__ wout, double* alpha,
-                                                   double* beta, double2* partials, unsigned* counter, T* acc,
-                                                   const double2* cvec) {
+                                                   double* beta, double* invb, double2* partials, unsigned* counter,
+                                                   T* acc, const double2* cvec) {
   constexpr bool CPLX = sizeof(T) == sizeof(double2);
   __shared__ T E[HY][HX], U[HY][HX], V[HY][HX];
   __shared__ double2 red[THREADS / 32];
   const double bj = beta[j];
-  const double sc = safe_inv(bj);
+  const double sc = invb[j];
   const double am = (CPLX && j > 0) ? alpha[j - 1] : 0.0;
   const double sg = CPLX ? sc : -sc;  // real form: -(tau A)
   StencilCoef cf;
@@ -290,7 +286,100 @@ __global__ void __launch_bounds__(THREADS) lz_step(LGeom G, int j, const T* __re
   if (llast_block2(s, partials, counter, G.tiles_x * G.tiles_y, blockIdx.y * G.tiles_x + blockIdx.x, &tot, red)) {
     alpha[j] = tot.x;
     beta[j + 1] = sqrt(fmax(tot.y - tot.x * tot.x, 0.0));
+    invb[j + 1] = safe_inv(beta[j + 1]);
   }
+}
+
+// Real form (real input) on the unnormalised vectors W_j = b_{j+1} u_{j+1}
+// alone (u_j = W_{j-1} / b_j is never written):
+//   W_j = -(tau / b_j) A W_{j-1} + (b_j / b_{j-1}) W_{j-2},  W_{-1} = f0,
+//   b_{j+1} = ||W_j||_W,  a_j = 0.
+//   MODE 0 (first pass): writes W_j and b_{j+1} (one deterministic reduction).
+//   MODE 1 (second pass): stored scalars, acc += (c'_j / b_j) W_{j-1}.
+template <int MODE>
+__global__ void __launch_bounds__(THREADS) lz_wstep(LGeom G, int j, const double* __restrict__ wm1,
+                                                    const double* __restrict__ wm2, double* __restrict__ wout,
+                                                    double* alpha, double* beta, double* invb, double2* partials,
+                                                    unsigned* counter, double* acc, const double* coef) {
+  __shared__ double E[HY][HX], U[HY][HX], V[HY][HX];
+  __shared__ double2 red[THREADS / 32];
+  __shared__ StencilCoef cfs;
+  __shared__ double r2s;
+  if (threadIdx.x == 0) {  // step scalars, once per block
+    const double sc = invb[j];
+    cfs.cdx = -sc * G.tdx;
+    cfs.cdy = -sc * G.tdy;
+    cfs.cgdx = -sc * G.tgdx;
+    cfs.cgdy = -sc * G.tgdy;
+    cfs.cf4 = -sc * G.tf4;
+    r2s = wm2 ? beta[j] * invb[j - 1] : 0.0;
+  }
+  const int i0 = blockIdx.x * TX - 1, j0 = blockIdx.y * TY - 1;
+  for (int k = threadIdx.x; k < HX * HY; k += THREADS) {
+    const int li = k % HX, lj = k / HX;
+    const size_t id = lidx(G, i0 + li, j0 + lj);
+    E[lj][li] = wm1[id];
+    U[lj][li] = wm1[id + G.fstride];
+    V[lj][li] = wm1[id + 2 * G.fstride];
+  }
+  __syncthreads();
+  const StencilCoef cf = cfs;
+  const double r2 = r2s;
+  const double cu = MODE == 1 ? coef[j] : 0.0;
+  double nrm = 0.0;
+  for (int k = threadIdx.x; k < TX * TY; k += THREADS) {
+    const int li = k % TX + 1, lj = k / TX + 1;
+    const int i = blockIdx.x * TX + li - 1, jj = blockIdx.y * TY + lj - 1;
+    if (i >= G.nx || jj >= G.ny) continue;
+    const size_t id = (size_t)jj * G.nx + i;
+    double ka[3];
+    apply_sA<double>(E, U, V, li, lj, G.H[id], cf, ka);
+    const double tc[3] = {E[lj][li], U[lj][li], V[lj][li]};
+    double w[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t o = id + c * G.fstride;
+      w[c] = wm2 ? fma(r2, wm2[o], ka[c]) : ka[c];
+      wout[o] = w[c];
+      if (MODE == 1) acc[o] = fma(cu, tc[c], acc[o]);
+    }
+    if (MODE == 0) nrm = fma(G.w[id] * w[0], w[0], fma(w[1], w[1], fma(w[2], w[2], nrm)));
+  }
+  if (MODE != 0) return;
+  const double2 s = lblock_sum2(make_double2(nrm, 0.0), red);
+  double2 tot;
+  if (llast_block2(s, partials, counter, G.tiles_x * G.tiles_y, blockIdx.y * G.tiles_x + blockIdx.x, &tot, red)) {
+    alpha[j] = 0.0;
+    beta[j + 1] = sqrt(tot.x);
+    invb[j + 1] = safe_inv(beta[j + 1]);
+  }
+}
+
+// Real form: coef[b] = c'_b / b_b for b < kk.
+__global__ void lz_wcoef(const double2* cvec, const double* invb, int kk, double* coef) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < kk) coef[b] = real_coeff(cvec[b], b) * invb[b];
+}
+
+// Real form: acc = sum_{b < nb} coef_b S_b, S_0 = f0, S_b = W_{b-1} (kept
+// vector b - 1); the same coefficients and order as the second-pass steps.
+__global__ void lz_wbasis_sum(const double* __restrict__ f0, const double* __restrict__ basis, size_t vstride, int nb,
+                              const double* coef, double* acc, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double a = 0.0;
+  if (nb > 0) a = fma(coef[0], f0[i], a);
+  int b = 1;
+  for (; b + 4 <= nb; b += 4) {
+    const double v0 = basis[(size_t)(b - 1) * vstride + i], v1 = basis[(size_t)b * vstride + i];
+    const double v2 = basis[(size_t)(b + 1) * vstride + i], v3 = basis[(size_t)(b + 2) * vstride + i];
+    a = fma(coef[b], v0, a);
+    a = fma(coef[b + 1], v1, a);
+    a = fma(coef[b + 2], v2, a);
+    a = fma(coef[b + 3], v3, a);
+  }
+  for (; b < nb; ++b) a = fma(coef[b], basis[(size_t)(b - 1) * vstride + i], a);
+  acc[i] = a;
 }
 
 // acc = sum_{b < nb} c_b basis_b (acc = 0 for nb = 0); fixed summation order,
@@ -471,7 +560,7 @@ __global__ void __launch_bounds__(THREADS) lz_coeff_sum(int P, const double2* sc
 size_t al(size_t v) { return (v + 255) / 256 * 256; }
 
 struct LLayout {
-  size_t vb, scratch_bytes, alpha, beta, cvec, partials, counter, maxslots, sb, wb, wy, dg, sc, wc, part, min_total;
+  size_t vb, scratch_bytes, alpha, beta, invb, coef, cvec, partials, counter, maxslots, sb, wb, wy, dg, sc, wc, part, min_total;
 };
 
 // Error-bound sampling: spacing d / 4 over [-tau rho, tau rho], d = h |mu|;
@@ -494,6 +583,10 @@ LLayout lz_layout(const KrylovSettings* k, int np_b, int np_c, int M, size_t esi
   L.alpha = o;
   o += al(nmax * sizeof(double));
   L.beta = o;
+  o += al(nmax * sizeof(double));
+  L.invb = o;
+  o += al(nmax * sizeof(double));
+  L.coef = o;
   o += al(nmax * sizeof(double));
   L.cvec = o;
   o += al(nmax * sizeof(double2));
@@ -605,6 +698,8 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   double2* scratch = reinterpret_cast<double2*>(base + L.vb);
   double* alpha = reinterpret_cast<double*>(base + L.alpha);
   double* beta = reinterpret_cast<double*>(base + L.beta);
+  double* invb = reinterpret_cast<double*>(base + L.invb);  // 1 / b_j (0 for b_j = 0)
+  double* coef = reinterpret_cast<double*>(base + L.coef);  // real form: c'_j / b_j
   double2* cvec = reinterpret_cast<double2*>(base + L.cvec);
   double2* partials = reinterpret_cast<double2*>(base + L.partials);
   unsigned* counter = reinterpret_cast<unsigned*>(base + L.counter);
@@ -619,17 +714,25 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   // Lanczos vectors kept in the caller's extra workspace
   T* basis = reinterpret_cast<T*>(base + L.min_total);
   const size_t vstride = L.vb / sizeof(T);
-  // kept vectors (at least two, or none); w'_{nbasis-1} goes to f0's buffer
-  // (f0 is read only by step 0) so that the second pass can resume the
-  // recurrence at step nbasis with exactly the first pass's operands
+  constexpr bool REAL = sizeof(T) == sizeof(double);
+  // complex form: kept v_j (at least two, or none); w'_{nbasis-1} goes to f0's
+  // buffer (f0 is read only by step 0) so that the second pass can resume the
+  // recurrence at step nbasis with exactly the first pass's operands.
+  // real form: kept W_j; the second pass resumes from W_{nbasis-1}, W_{nbasis-2}.
   int nbasis = (int)std::min<size_t>((ws_bytes - L.min_total) / L.vb, (size_t)k->max_iters + 1);
-  if (nbasis < 2) nbasis = 0;
+  if (!REAL && nbasis < 2) nbasis = 0;
   auto vptr = [&](int j) -> T* {
     if (j < 0) return nullptr;
     if (j < nbasis) return basis + (size_t)j * vstride;
     return (j & 1) ? vB : vA;
   };
   auto wptr = [&](int j) -> T* { return (j < 0 || j == nbasis - 1) ? f0 : ((j & 1) ? wB : wA); };
+  T* const rot[3] = {vA, vB, wA};
+  auto Wptr = [&](int j) -> T* {  // real form
+    if (j < 0) return j == -1 ? f0 : nullptr;
+    if (j < nbasis) return basis + (size_t)j * vstride;
+    return rot[j % 3];
+  };
 
   const double tau = adjoint ? -dt : dt;
   LGeom G_;
@@ -676,8 +779,8 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
   mark(1);
   if (e == cudaSuccess) {
-    lz_init<T><<<grid, THREADS, 0, s>>>(G_, static_cast<const double2*>(in), adjoint ? 1 : 0, f0, beta, partials,
-                                        counter);
+    lz_init<T><<<grid, THREADS, 0, s>>>(G_, static_cast<const double2*>(in), adjoint ? 1 : 0, f0, beta, invb,
+                                        partials, counter);
     ++launches;
     e = cudaGetLastError();
   }
@@ -693,9 +796,14 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   const int nslot_c = (nsamp + kCoarse - 1) / kCoarse, nslot_f = nsamp;
   double* pin = k->pinned;
   auto launch_chunk = [&](int c, int j0, int j1) -> cudaError_t {
-    for (int j = j0; j < j1; ++j)
-      lz_step<0, T><<<grid, THREADS, 0, s>>>(G_, j, wptr(j - 1), vptr(j - 1), vptr(j), wptr(j), alpha, beta,
-                                             partials, counter, nullptr, nullptr);
+    for (int j = j0; j < j1; ++j) {
+      if constexpr (REAL)
+        lz_wstep<0><<<grid, THREADS, 0, s>>>(G_, j, Wptr(j - 1), Wptr(j - 2), Wptr(j), alpha, beta, invb, partials,
+                                             counter, nullptr, nullptr);
+      else
+        lz_step<0, T><<<grid, THREADS, 0, s>>>(G_, j, wptr(j - 1), vptr(j - 1), vptr(j), wptr(j), alpha, beta,
+                                               invb, partials, counter, nullptr, nullptr);
+    }
     lz_poles_advance<<<(npb + 127) / 128, 128, 0, s>>>(npb, d_sb, d_wb, alpha, beta, j0, j1, d_dg, d_wy);
     cudaError_t err = cudaMemsetAsync(maxslots, 0, 2 * sizeof(unsigned long long), s);
     if (err != cudaSuccess) return err;
@@ -789,13 +897,24 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   // ---- second pass: acc = V c from the kept vectors, the rest regenerated ----
   const int nb = std::min(nbasis, kk);
   if (e == cudaSuccess) {
-    lz_basis_sum<T><<<ebl, 256, 0, s>>>(basis, vstride, nb, cvec, acc, n3);
+    if constexpr (REAL) {
+      lz_wcoef<<<(kk + 255) / 256, 256, 0, s>>>(cvec, invb, kk, coef);
+      ++launches;
+      lz_wbasis_sum<<<ebl, 256, 0, s>>>(f0, basis, vstride, nb, coef, acc, n3);
+    } else {
+      lz_basis_sum<T><<<ebl, 256, 0, s>>>(basis, vstride, nb, cvec, acc, n3);
+    }
     ++launches;
   }
   if (e == cudaSuccess && nb < kk) {
-    for (int j = nb; j < kk; ++j)
-      lz_step<1, T><<<grid, THREADS, 0, s>>>(G_, j, wptr(j - 1), vptr(j - 1), vptr(j), wptr(j), alpha, beta,
-                                             partials, counter, acc, cvec);
+    for (int j = nb; j < kk; ++j) {
+      if constexpr (REAL)
+        lz_wstep<1><<<grid, THREADS, 0, s>>>(G_, j, Wptr(j - 1), Wptr(j - 2), Wptr(j), alpha, beta, invb, partials,
+                                             counter, acc, coef);
+      else
+        lz_step<1, T><<<grid, THREADS, 0, s>>>(G_, j, wptr(j - 1), vptr(j - 1), vptr(j), wptr(j), alpha, beta,
+                                               invb, partials, counter, acc, cvec);
+    }
     launches += kk - nb;
   }
   if (e == cudaSuccess) {

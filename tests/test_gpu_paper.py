@@ -70,7 +70,8 @@ def test_paper_scenarios_d128(form):
             assert 1e-13 < err < 1e-11, (scen, tau, h, M, err)  # h = 1 error floor (Appendix B aliasing)
         else:
             # converged rows: the paper prints 6e-15 .. 7.7e-13.  FP64 form: within 3x of that
-            # scale.  Double-float form: ~44 bits per term and a sum that cancels by ~30-60x
-            # leave ~1e-12, so 1e-11 (its stated tolerance is 1e-8).
-            lim = max(1e-12, 3 * printed) if form == "fp64" else 1e-11
+            # scale.  Double-float form: ~44 bits per term, and the rounding of the 2N + 1
+            # terms accumulates (measured 6e-16 M at M = 2677, 1.7e-15 M at M = 56885), so
+            # max(1e-11, 4e-15 M), far inside its stated tolerance of 1e-8.
+            lim = max(1e-12, 3 * printed) if form == "fp64" else min(1e-8, max(1e-11, 4e-15 * M))
             assert bound_ok and err < lim, (scen, tau, h, M, err)
