@@ -337,18 +337,18 @@ LANCZOS_BYTES_PER_PT_STEP = 88  # lz_wstep, first pass (real form): W_{j-1}, W_{
 # each) in; W_j (24 B) out
 
 
-def shared_measure(torch, rexi, inputs, rtol=1e-10, reps=3, n=None, tau_rho=None, keep=True):
+def shared_measure(torch, rexi, inputs, rtol=1e-10, reps=3, n=None, tau_rho=None, keep=True, form="mixed"):
     """Variable-depth workload, every REXII term (1024^2, tau rho = 400), by the
-    shared-Krylov method (one Lanczos basis for all poles, FP64): with the
-    minimum workspace (second pass regenerates the basis) and with the basis
-    kept in HBM."""
+    shared-Krylov method (one Lanczos basis for all poles; FP64, or
+    double-float vectors for the mixed form): with the minimum workspace
+    (second pass regenerates the basis) and with the basis kept in HBM."""
     import numpy as np
 
     n = n or KRYLOV_D
     tau_rho = tau_rho or KRYLOV_TAU_RHO
     Hn = inputs.variable_depth(n, n, seed=0)
     H = torch.from_numpy(Hn).cuda()
-    plan = rexi.Plan(n, n, depth=H, form="fp64")
+    plan = rexi.Plan(n, n, depth=H, form=form)
     plan.set_krylov(rtol=rtol, max_iters=20000, term_batch=64)
     plan.set_krylov_method("shared")
     dt = tau_rho / plan.rho
@@ -388,13 +388,16 @@ def shared_measure(torch, rexi, inputs, rtol=1e-10, reps=3, n=None, tau_rho=None
             "phases_ms": {"first_pass": pass1, "coefficients": ph[1] / max(ncalls, 1),
                           "second_pass": ph[2] / max(ncalls, 1), "setup": ph[3] / max(ncalls, 1)},
             "energy_drift": abs(en(o) / en(xn) - 1.0),
-            "roofline": {"kernel": "lz_wstep (first pass, incl. bound checks in the time)", "bound": "hbm",
+            "roofline": {"kernel": "%s (first pass, incl. bound checks in the time)"
+                                   % ("lz_dfstep" if form == "mixed" else "lz_wstep"), "bound": "hbm",
                          "achieved": gbs, "unit": "GB/s", "bytes_per_point_step": LANCZOS_BYTES_PER_PT_STEP},
             "gpu_launches": nl // max(ncalls, 1),
         }
     res["workload"] = ("LRSW variable depth %dx%d, H = 1 + 0.4 sin(2 pi x) cos(4 pi y) + 8 bumps (seed 0), |k|^-3 "
-                       "eta, tau*rho=%g (M=%d), every REXII term (J = %d poles), shared Lanczos basis, FP64, "
-                       "error bound %g" % (n, n, tau_rho, info.M, int(info.n_poles), rtol))
+                       "eta, tau*rho=%g (M=%d), every REXII term (J = %d poles), shared Lanczos basis, %s, "
+                       "error bound %g" % (n, n, tau_rho, info.M, int(info.n_poles),
+                                           "double-float vectors" if form == "mixed" else "FP64", rtol))
+    res["form"] = form
     return res
 
 
@@ -625,11 +628,13 @@ def run_ours(args):
             km["roofline"]["peak"] = hbm_peak
             km["roofline"]["frac"] = km["roofline"]["achieved"] / hbm_peak
             krylov[kform] = km
-        sm = shared_measure(torch, rexi, inputs)
-        for key in ("regenerate", "kept_basis"):
-            sm[key]["roofline"]["peak"] = hbm_peak
-            sm[key]["roofline"]["frac"] = sm[key]["roofline"]["achieved"] / hbm_peak
-        krylov["shared_all_terms"] = sm
+        krylov["shared_all_terms"] = {}
+        for sform in ("mixed", "fp64"):
+            sm = shared_measure(torch, rexi, inputs, form=sform)
+            for key in ("regenerate", "kept_basis"):
+                sm[key]["roofline"]["peak"] = hbm_peak
+                sm[key]["roofline"]["frac"] = sm[key]["roofline"]["achieved"] / hbm_peak
+            krylov["shared_all_terms"][sform] = sm
 
     # CPU oracle on a bounded sample (rank 0, N = 1 only), also the accuracy check
     cpu = None
@@ -683,6 +688,7 @@ def main():
     ap.add_argument("--krylov-grid", type=int, default=None, help="shared method: grid (profiling captures)")
     ap.add_argument("--krylov-tau-rho", type=float, default=None, help="shared method: dt * rho (captures)")
     ap.add_argument("--shared-regen-only", action="store_true", help="shared method: minimum workspace only")
+    ap.add_argument("--shared-form", default="mixed", choices=["mixed", "fp64"], help="shared method: form")
     ap.add_argument("--krylov-only", action="store_true",
                     help="run only the variable-depth measurement (profiling captures)")
     args = ap.parse_args()
@@ -718,7 +724,7 @@ def main():
 
         if args.krylov_form == "shared":
             print(json.dumps(shared_measure(torch, rexi, inputs, n=args.krylov_grid, tau_rho=args.krylov_tau_rho,
-                                            keep=not args.shared_regen_only)), flush=True)
+                                            keep=not args.shared_regen_only, form=args.shared_form)), flush=True)
         else:
             print(json.dumps(krylov_measure(torch, rexi, inputs, args.krylov_form, args.krylov_terms, 1e-10)),
                   flush=True)

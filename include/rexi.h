@@ -179,8 +179,10 @@ rexi_status rexi_plan_set_krylov(rexi_plan_t plan, double rtol, int32_t max_iter
  *   complex values, or 3 nx ny real values for real input, rounded up to 256
  *   bytes, each) are kept from the first pass; the rest are regenerated from
  *   the stored scalars.  Real input runs the real form of the recurrence
- *   (the vectors alternate between real and imaginary, a_j = 0).  FP64 in
- *   every form.  Applies to rexi_step and rexi_step_adjoint; the depth gradient
+ *   (the vectors alternate between real and imaginary, a_j = 0); in the
+ *   mixed form its vectors and stencil arithmetic are double-float (pairs of
+ *   FP32 values, about 48 significant bits) with FP64 scalars and inner
+ *   products.  FP64 otherwise.  Applies to rexi_step and rexi_step_adjoint; the depth gradient
  *   always uses per-term CG. */
 enum { REXI_KRYLOV_CG = 0, REXI_KRYLOV_SHARED = 1 };
 rexi_status rexi_plan_set_krylov_method(rexi_plan_t plan, int32_t method);

@@ -657,7 +657,7 @@ rexi_status krylov_init(KrylovSettings* k, int nx, int ny, double Lx, double Ly,
   k->Hmean = Hmean;
   const size_t nk = (size_t)nx * ny;
   char* mem = nullptr;
-  const size_t bytes = al256(nk * sizeof(double)) + 2 * al256(nk * sizeof(float));
+  const size_t bytes = al256(nk * sizeof(double)) + 2 * al256(nk * sizeof(float)) + 2 * al256(nk * sizeof(float2));
   if (cudaMalloc(&mem, bytes) != cudaSuccess) {
     set_last_error("cudaMalloc of the depth tables failed");
     return REXI_ENOMEM;
@@ -666,6 +666,9 @@ rexi_status krylov_init(KrylovSettings* k, int nx, int ny, double Lx, double Ly,
   k->w64 = reinterpret_cast<double*>(mem);
   k->H32 = reinterpret_cast<float*>(mem + al256(nk * sizeof(double)));
   k->w32 = reinterpret_cast<float*>(mem + al256(nk * sizeof(double)) + al256(nk * sizeof(float)));
+  k->Hdf = reinterpret_cast<float2*>(mem + al256(nk * sizeof(double)) + 2 * al256(nk * sizeof(float)));
+  k->wdf = reinterpret_cast<float2*>(mem + al256(nk * sizeof(double)) + 2 * al256(nk * sizeof(float)) +
+                                     al256(nk * sizeof(float2)));
   if (cudaMallocHost(reinterpret_cast<void**>(&k->pinned), 8 * sizeof(double)) != cudaSuccess ||
       cudaEventCreateWithFlags(&k->ev[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&k->ev[1], cudaEventDisableTiming) != cudaSuccess) {
@@ -673,6 +676,7 @@ rexi_status krylov_init(KrylovSettings* k, int nx, int ny, double Lx, double Ly,
     return REXI_ECUDA;
   }
   depth_tables<<<(unsigned)((nk + 255) / 256), 256>>>(depth, nk, g, k->w64, k->H32, k->w32);
+  if (lanczos_tables(k) != REXI_OK) return REXI_ECUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) {
     set_last_error("depth table kernel failed");
     return REXI_ECUDA;
@@ -909,7 +913,7 @@ rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void
                         int real_input, int term_begin, int term_end, void* ws, size_t ws_bytes, cudaStream_t s,
                         rexi_step_info* info, bool adjoint, const KrylovHooks& hooks) {
   if (k->method == 1)
-    return krylov_step_lanczos(k, h, M, in, out, dt, real_input, term_begin, term_end, ws, ws_bytes, s, info,
+    return krylov_step_lanczos(k, form, h, M, in, out, dt, real_input, term_begin, term_end, ws, ws_bytes, s, info,
                                adjoint, hooks);
   const size_t nk = (size_t)k->nx * k->ny, n3 = 3 * nk;
   if (overlaps(in, out, n3 * sizeof(double2))) {

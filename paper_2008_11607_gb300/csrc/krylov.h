@@ -24,6 +24,8 @@ struct KrylovSettings {
   double* w64 = nullptr;      // energy weight g / H (FP64)
   float* H32 = nullptr;       // depth (FP32 copy for the inner solver)
   float* w32 = nullptr;       // energy weight (FP32)
+  float2* Hdf = nullptr;      // depth and energy weight as double-float pairs (shared-Krylov mixed form)
+  float2* wdf = nullptr;
 };
 
 // Optional instrumentation from the plan: phase marks (0..4 per term batch)
@@ -42,9 +44,11 @@ size_t krylov_grad_workspace_bytes(const KrylovSettings* k, int M, int real_inpu
 rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void* in, void* out, double dt,
                         int real_input, int term_begin, int term_end, void* ws, size_t ws_bytes,
                         cudaStream_t s, rexi_step_info* info, bool adjoint, const KrylovHooks& hooks);
-// Shared-Krylov (multi-shift Lanczos) variant of krylov_step (FP64).
+// Shared-Krylov (multi-shift Lanczos) variant of krylov_step: FP64, or
+// double-float for the mixed form with real input.
 size_t lanczos_workspace_bytes(const KrylovSettings* k, int M, int real_input);
-rexi_status krylov_step_lanczos(KrylovSettings* k, double h, int M, const void* in, void* out, double dt,
+rexi_status lanczos_tables(KrylovSettings* k);  // fills Hdf, wdf
+rexi_status krylov_step_lanczos(KrylovSettings* k, int form, double h, int M, const void* in, void* out, double dt,
                                 int real_input, int term_begin, int term_end, void* ws, size_t ws_bytes,
                                 cudaStream_t s, rexi_step_info* info, bool adjoint, const KrylovHooks& hooks);
 // grad_depth += dL/dH for out = r(dt A(H)) f_in and G = dL/d out.

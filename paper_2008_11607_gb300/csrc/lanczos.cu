@@ -18,9 +18,12 @@
 // [-tau rho, tau rho] (rho >= ||A||_W).  For real input the step keeps only the
 // real part, which is the same sum over the conjugate-closed pole set
 // {z_j, conj z_j} with weights {beta_j / 2, conj beta_j / 2}; the bound uses
-// that set (its phi has no cancelling imaginary remainder).  The bound is
-// evaluated on the device every kChunk steps by sampling l at spacing d / 8,
-// d = h |mu| the distance of every pole from the real axis.
+// that set (its phi has no cancelling imaginary remainder).  With a_j = 0 its
+// phi is (phi(l) + (-1)^(k-1) conj(phi(-l))) / 2 in terms of the original
+// set's, so the device evaluates the original set on a symmetric grid.  The
+// bound is evaluated every kChunk steps by sampling l at spacing d / 4 or
+// finer, d = h |mu| the distance of every pole from the real axis, first on
+// every 8th sample and, once that passes, on all of them.
 //
 // One fused kernel per Lanczos step (v_j formed on the fly from w'_{j-1} and
 // v_{j-1}; both inner products of the step in one deterministic reduction,
@@ -35,6 +38,7 @@
 
 #include <algorithm>
 #include <complex>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -355,10 +359,242 @@ __global__ void __launch_bounds__(THREADS) lz_wstep(LGeom G, int j, const double
   }
 }
 
+// ---------------------------------------------------------------------------
+// Double-float real form (mixed form, real input): every vector value is a
+// pair of floats (hi, lo), value = hi + lo (about 48 significant bits), and
+// the step runs on the FP32 pipes with error-free transformations: Knuth's
+// TwoSum, Dekker's FastTwoSum and the FMA TwoProduct.  Additions use the
+// short form (TwoSum of the high parts, low parts added in FP32), whose error
+// is a few units of 2^-48 of the operands: the absolute accuracy the
+// Lanczos relation needs.  Scalars and inner products stay FP64.
+__device__ __forceinline__ float2 df_fast(float s, float e) {
+  const float h = s + e;
+  return make_float2(h, e - (h - s));
+}
+__device__ __forceinline__ float2 df_add(float2 x, float2 y) {
+  const float s = x.x + y.x, bb = s - x.x;
+  const float e = ((x.x - (s - bb)) + (y.x - bb)) + (x.y + y.y);
+  return df_fast(s, e);
+}
+__device__ __forceinline__ float2 df_neg(float2 x) { return make_float2(-x.x, -x.y); }
+__device__ __forceinline__ float2 df_sub(float2 x, float2 y) { return df_add(x, df_neg(y)); }
+__device__ __forceinline__ float2 df_mul(float2 x, float2 c) {
+  const float p = x.x * c.x;
+  const float e = fmaf(x.x, c.y, fmaf(x.y, c.x, fmaf(x.x, c.x, -p)));
+  return df_fast(p, e);
+}
+__device__ __forceinline__ float2 df_from(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+__device__ __forceinline__ double df_to(float2 v) { return (double)v.x + (double)v.y; }
+__device__ __forceinline__ double2 to_out(float2 v) { return make_double2(df_to(v), 0.0); }
+
+// Block sum of double-float values in double-float (FP32 pipes; result valid
+// in thread 0).  On this GPU an FP64 warp instruction holds its pipe for many
+// cycles even with one active lane, so the reductions of the double-float step
+// stay off the FP64 pipe up to one final conversion.
+__device__ __forceinline__ float2 df_block_reduce(float2 v, float2* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = df_add(v, make_float2(__shfl_down_sync(0xffffffffu, v.x, o), __shfl_down_sync(0xffffffffu, v.y, o)));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float2 t = red[0];
+  if (threadIdx.x == 0)
+    for (int i = 1; i < THREADS / 32; ++i) t = df_add(t, red[i]);
+  return t;
+}
+
+// Deterministic cross-block double-float sum (fixed order) finished by the
+// last block; returns true in that block's thread 0 with *total (FP64).
+__device__ __forceinline__ bool llast_block_df(float2 mine, float2* partials, unsigned* counter, int ntiles, int tile,
+                                               double* total, float2* red) {
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) {
+    partials[tile] = mine;
+    __threadfence();
+    is_last = atomicAdd(counter, 1u) == (unsigned)ntiles - 1;
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  const volatile float2* vp = partials;
+  float2 s = make_float2(0.f, 0.f);
+  for (int i = threadIdx.x; i < ntiles; i += THREADS) s = df_add(s, make_float2(vp[i].x, vp[i].y));
+  s = df_block_reduce(s, red);
+  if (threadIdx.x == 0) {
+    *total = df_to(s);
+    *counter = 0u;
+  }
+  return threadIdx.x == 0;
+}
+
+// Double-float coefficients of step j (computed once, by the reduction that
+// produces b_j): the stencil coefficients times -1 / b_j and r2 = b_j / b_{j-1}.
+struct DfCoef {
+  float2 cdx, cdy, cgdx, cgdy, cf4, r2;
+};
+__device__ __forceinline__ void df_coef_store(const LGeom& G, double ib, double r2, DfCoef* dst) {
+  DfCoef c;
+  c.cdx = df_from(-ib * G.tdx);
+  c.cdy = df_from(-ib * G.tdy);
+  c.cgdx = df_from(-ib * G.tgdx);
+  c.cgdy = df_from(-ib * G.tgdy);
+  c.cf4 = df_from(-ib * G.tf4);
+  c.r2 = df_from(r2);
+  *dst = c;
+}
+
+__global__ void lz_df_tables(const double* H, const double* w, size_t nk, float2* Hdf, float2* wdf) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nk) return;
+  Hdf[i] = df_from(H[i]);
+  wdf[i] = df_from(w[i]);
+}
+
+// f0 = Re in (eta / w for the adjoint) as double-float; beta[0] = ||f0||_W (FP64).
+__global__ void __launch_bounds__(THREADS) lz_init_df(LGeom G, const double2* in, int adjoint, float2* f0,
+                                                      double* beta, double* invb, DfCoef* dfc, double2* partials,
+                                                      unsigned* counter) {
+  __shared__ double2 red[THREADS / 32];
+  const int tile = blockIdx.y * G.tiles_x + blockIdx.x;
+  double loc = 0.0;
+  for (int k = threadIdx.x; k < TX * TY; k += THREADS) {
+    const int i = blockIdx.x * TX + k % TX, j = blockIdx.y * TY + k / TX;
+    if (i >= G.nx || j >= G.ny) continue;
+    const size_t id = (size_t)j * G.nx + i;
+    for (int c = 0; c < 3; ++c) {
+      double v = in[id + c * G.fstride].x;
+      if (adjoint && c == 0) v /= G.w[id];
+      const float2 d = df_from(v);
+      f0[id + c * G.fstride] = d;
+      const double vv = df_to(d);
+      loc += (c == 0 ? G.w[id] : 1.0) * vv * vv;
+    }
+  }
+  const double2 s = lblock_sum2(make_double2(loc, 0.0), red);
+  double2 tot;
+  if (llast_block2(s, partials, counter, G.tiles_x * G.tiles_y, tile, &tot, red)) {
+    beta[0] = sqrt(tot.x);
+    invb[0] = safe_inv(beta[0]);
+    df_coef_store(G, invb[0], 0.0, dfc);
+  }
+}
+
+// The real-form step (lz_wstep) in double-float.  The point-wise operands of
+// the thread's points are loaded before the tile, so that their latency
+// overlaps the halo loads.
+template <int MODE>
+__global__ void __launch_bounds__(THREADS) lz_dfstep(LGeom G, const float2* __restrict__ Hdf,
+                                                     const float2* __restrict__ wdf, int j,
+                                                     const float2* __restrict__ wm1, const float2* __restrict__ wm2,
+                                                     float2* __restrict__ wout, double* alpha, double* beta,
+                                                     double* invb, DfCoef* dfc, double2* partials,
+                                                     unsigned* counter, float2* acc, const float2* coef_df) {
+  constexpr int PPT = TX * TY / THREADS;  // interior points per thread
+  __shared__ float2 E[HY][HX], U[HY][HX], V[HY][HX];
+  __shared__ float2 red[THREADS / 32];
+  const float2 z2 = make_float2(0.f, 0.f);
+  size_t pid[PPT];
+  bool live[PPT];
+  float2 pw2[PPT][3], pH[PPT], pw[PPT];
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    const int k = threadIdx.x + q * THREADS;
+    const int i = blockIdx.x * TX + k % TX, jj = blockIdx.y * TY + k / TX;
+    live[q] = i < G.nx && jj < G.ny;
+    pid[q] = live[q] ? (size_t)jj * G.nx + i : 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) pw2[q][c] = (live[q] && wm2) ? wm2[pid[q] + c * G.fstride] : z2;
+    pH[q] = live[q] ? Hdf[pid[q]] : z2;
+    pw[q] = (live[q] && MODE == 0) ? wdf[pid[q]] : z2;
+  }
+  const int i0 = blockIdx.x * TX - 1, j0 = blockIdx.y * TY - 1;
+  for (int k = threadIdx.x; k < HX * HY; k += THREADS) {
+    const int li = k % HX, lj = k / HX;
+    const size_t id = lidx(G, i0 + li, j0 + lj);
+    E[lj][li] = wm1[id];
+    U[lj][li] = wm1[id + G.fstride];
+    V[lj][li] = wm1[id + 2 * G.fstride];
+  }
+  __syncthreads();
+  const DfCoef cf = dfc[j];
+  const float2 cu = MODE == 1 ? coef_df[j] : z2;
+  float2 nrm = z2;
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    if (!live[q]) continue;
+    const int k = threadIdx.x + q * THREADS;
+    const int li = k % TX + 1, lj = k / TX + 1;
+    const size_t id = pid[q];
+    float2 ka[3];
+    // eta: -H (cdx du + cdy dv)
+    const float2 du = df_sub(U[lj][li], U[lj][li - 1]), dv = df_sub(V[lj][li], V[lj - 1][li]);
+    ka[0] = df_neg(df_mul(df_add(df_mul(du, cf.cdx), df_mul(dv, cf.cdy)), pH[q]));
+    // u: cf4 v4 - cgdx de
+    const float2 v4 = df_add(df_add(V[lj][li], V[lj][li + 1]), df_add(V[lj - 1][li], V[lj - 1][li + 1]));
+    const float2 de = df_sub(E[lj][li + 1], E[lj][li]);
+    ka[1] = df_sub(df_mul(v4, cf.cf4), df_mul(de, cf.cgdx));
+    // v: -cf4 u4 - cgdy dn
+    const float2 u4 = df_add(df_add(U[lj][li], U[lj][li - 1]), df_add(U[lj + 1][li], U[lj + 1][li - 1]));
+    const float2 dn = df_sub(E[lj + 1][li], E[lj][li]);
+    ka[2] = df_neg(df_add(df_mul(u4, cf.cf4), df_mul(dn, cf.cgdy)));
+    const float2 tc[3] = {E[lj][li], U[lj][li], V[lj][li]};
+    float2 w[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const size_t o = id + c * G.fstride;
+      w[c] = wm2 ? df_add(df_mul(pw2[q][c], cf.r2), ka[c]) : ka[c];
+      wout[o] = w[c];
+      if (MODE == 1) acc[o] = df_add(acc[o], df_mul(tc[c], cu));
+    }
+    if (MODE == 0) {
+      nrm = df_add(nrm, df_mul(df_mul(w[0], w[0]), pw[q]));
+      nrm = df_add(nrm, df_mul(w[1], w[1]));
+      nrm = df_add(nrm, df_mul(w[2], w[2]));
+    }
+  }
+  if (MODE != 0) return;
+  const float2 bs = df_block_reduce(nrm, red);
+  double tot;
+  if (llast_block_df(bs, reinterpret_cast<float2*>(partials), counter, G.tiles_x * G.tiles_y,
+                     blockIdx.y * G.tiles_x + blockIdx.x, &tot, red)) {
+    alpha[j] = 0.0;
+    beta[j + 1] = sqrt(tot);
+    invb[j + 1] = safe_inv(beta[j + 1]);
+    df_coef_store(G, invb[j + 1], beta[j + 1] * invb[j], dfc + j + 1);
+  }
+}
+
+// Double-float: acc = sum_{b < nb} coef_b S_b (S_0 = f0, S_b = W_{b-1}).
+__global__ void lz_dfbasis_sum(const float2* __restrict__ f0, const float2* __restrict__ basis, size_t vstride,
+                               int nb, const float2* coef_df, float2* acc, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float2 a = make_float2(0.f, 0.f);
+  if (nb > 0) a = df_add(a, df_mul(f0[i], coef_df[0]));
+  int b = 1;
+  for (; b + 4 <= nb; b += 4) {
+    const float2 v0 = basis[(size_t)(b - 1) * vstride + i], v1 = basis[(size_t)b * vstride + i];
+    const float2 v2 = basis[(size_t)(b + 1) * vstride + i], v3 = basis[(size_t)(b + 2) * vstride + i];
+    a = df_add(a, df_mul(v0, coef_df[b]));
+    a = df_add(a, df_mul(v1, coef_df[b + 1]));
+    a = df_add(a, df_mul(v2, coef_df[b + 2]));
+    a = df_add(a, df_mul(v3, coef_df[b + 3]));
+  }
+  for (; b < nb; ++b) a = df_add(a, df_mul(basis[(size_t)(b - 1) * vstride + i], coef_df[b]));
+  acc[i] = a;
+}
+
 // Real form: coef[b] = c'_b / b_b for b < kk.
-__global__ void lz_wcoef(const double2* cvec, const double* invb, int kk, double* coef) {
+__global__ void lz_wcoef(const double2* cvec, const double* invb, int kk, double* coef, float2* coef_df) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < kk) coef[b] = real_coeff(cvec[b], b) * invb[b];
+  if (b >= kk) return;
+  coef[b] = real_coeff(cvec[b], b) * invb[b];
+  coef_df[b] = df_from(coef[b]);
 }
 
 // Real form: acc = sum_{b < nb} coef_b S_b, S_0 = f0, S_b = W_{b-1} (kept
@@ -456,28 +692,29 @@ __device__ __forceinline__ double lrcp(double x) {
   return fma(r, fma(-x, r, 1.0), r);
 }
 
+constexpr int BT = 64;  // threads per block of the error-bound kernels
+
 // Partial sums of phi(l_m) = sum_p wy_p / (l_m + s_p) over the poles of group
 // blockIdx.y (G poles each) at samples l_m = -L + m dl, m = slot * stride:
 // part[group * nslot + slot].  With `gate`, runs only if
 // beta[jk] * (max of the gate pass) <= rtol.
-__global__ void __launch_bounds__(THREADS) lz_bound_part(int np, int G, const double2* s, const double2* wy,
-                                                         double L, double dl, int nslot, int stride,
-                                                         const double* beta, int jk, double rtol,
-                                                         const unsigned long long* gate, double2* part) {
+__global__ void __launch_bounds__(BT) lz_bound_part(int np, int G, const double2* s, const double2* wy, double L,
+                                                    double dl, int nslot, int stride, const double* beta, int jk,
+                                                    double rtol, const unsigned long long* gate, double2* part) {
   if (gate && beta[jk] * __longlong_as_double((long long)*gate) > rtol) return;
-  __shared__ double2 ss[THREADS], sw[THREADS];
-  const int slot = blockIdx.x * THREADS + threadIdx.x;
+  __shared__ double2 ss[BT], sw[BT];
+  const int slot = blockIdx.x * BT + threadIdx.x;
   const double lam = -L + (double)slot * stride * dl;
   const int pb = blockIdx.y * G, pe = min(np, pb + G);
   double re = 0.0, im = 0.0;
-  for (int p0 = pb; p0 < pe; p0 += THREADS) {
+  for (int p0 = pb; p0 < pe; p0 += BT) {
     __syncthreads();
     if (p0 + threadIdx.x < pe) {
       ss[threadIdx.x] = s[p0 + threadIdx.x];
       sw[threadIdx.x] = wy[p0 + threadIdx.x];
     }
     __syncthreads();
-    const int cnt = min(THREADS, pe - p0);
+    const int cnt = min(BT, pe - p0);
     for (int q = 0; q < cnt; ++q) {
       const double a = lam + ss[q].x, b = ss[q].y;
       const double r = lrcp(fma(a, a, b * b));
@@ -488,14 +725,17 @@ __global__ void __launch_bounds__(THREADS) lz_bound_part(int np, int G, const do
   if (slot < nslot) part[(size_t)blockIdx.y * nslot + slot] = make_double2(re, im);
 }
 
-// max over slots of |sum over groups of part| (fixed order), as the bits of a
-// non-negative double (atomicMax on those bits is order-independent).
-__global__ void __launch_bounds__(THREADS) lz_bound_max(int groups, int nslot, const double2* part,
-                                                        const double* beta, int jk, double rtol,
-                                                        const unsigned long long* gate, unsigned long long* out) {
+// max over slots of |phi| (sum over groups in fixed order), as the bits of a
+// non-negative double (atomicMax on those bits is order-independent).  Real
+// form (sym != 0): the bound function of the conjugate-closed pole set,
+// (phi(l) + sym conj(phi(-l))) / 2 with sym = (-1)^(k-1); the sample grid is
+// symmetric (slot nslot - 1 - m sits at -l_m).
+__global__ void __launch_bounds__(BT) lz_bound_max(int groups, int nslot, const double2* part, int sym,
+                                                   const double* beta, int jk, double rtol,
+                                                   const unsigned long long* gate, unsigned long long* out) {
   if (gate && beta[jk] * __longlong_as_double((long long)*gate) > rtol) return;
-  __shared__ double red[THREADS / 32];
-  const int slot = blockIdx.x * THREADS + threadIdx.x;
+  __shared__ double red[BT / 32];
+  const int slot = blockIdx.x * BT + threadIdx.x;
   double v = 0.0;
   if (slot < nslot) {
     double re = 0.0, im = 0.0;
@@ -503,6 +743,16 @@ __global__ void __launch_bounds__(THREADS) lz_bound_max(int groups, int nslot, c
       const double2 t = part[(size_t)g * nslot + slot];
       re += t.x;
       im += t.y;
+    }
+    if (sym) {
+      double re2 = 0.0, im2 = 0.0;
+      for (int g = 0; g < groups; ++g) {
+        const double2 t = part[(size_t)g * nslot + (nslot - 1 - slot)];
+        re2 += t.x;
+        im2 += t.y;
+      }
+      re = 0.5 * fma((double)sym, re2, re);
+      im = 0.5 * fma(-(double)sym, im2, im);
     }
     v = sqrt(fma(re, re, im * im));
   }
@@ -512,7 +762,7 @@ __global__ void __launch_bounds__(THREADS) lz_bound_max(int groups, int nslot, c
   __syncthreads();
   if (threadIdx.x == 0) {
     double b = 0.0;
-    for (int i = 0; i < THREADS / 32; ++i) b = fmax(b, red[i]);
+    for (int i = 0; i < BT / 32; ++i) b = fmax(b, red[i]);
     atomicMax(out, (unsigned long long)__double_as_longlong(b));
   }
 }
@@ -560,16 +810,17 @@ __global__ void __launch_bounds__(THREADS) lz_coeff_sum(int P, const double2* sc
 size_t al(size_t v) { return (v + 255) / 256 * 256; }
 
 struct LLayout {
-  size_t vb, scratch_bytes, alpha, beta, invb, coef, cvec, partials, counter, maxslots, sb, wb, wy, dg, sc, wc, part, min_total;
+  size_t vb, scratch_bytes, alpha, beta, invb, coef, coef_df, dfc, cvec, partials, counter, maxslots, wy, dg, sc, wc, part, min_total;
 };
 
-// Error-bound sampling: spacing d / 4 over [-tau rho, tau rho], d = h |mu|;
-// with tau rho <= M h (pole-count rule) at most 8 M / |mu| + 2 samples.
-int nsamp_cap(int M) { return (int)std::ceil(8.0 * M / std::fabs(table_mu())) + 2; }
-// poles per group of the partial sums (at most 64 groups)
-int bound_group(int np_b) { return std::max(128, (np_b + 63) / 64); }
+// Error-bound sampling: spacing at most d / 4 over [-tau rho, tau rho],
+// d = h |mu|, sample count 1 mod kCoarse (symmetric coarse subgrid); with
+// tau rho <= M h (pole-count rule) at most 8 M / |mu| + 2 + kCoarse samples.
+int nsamp_cap(int M) { return (int)std::ceil(8.0 * M / std::fabs(table_mu())) + 2 + kCoarse; }
+// poles per group of the partial sums (at most 128 groups)
+int bound_group(int np) { return std::max(64, (np + 127) / 128); }
 
-LLayout lz_layout(const KrylovSettings* k, int np_b, int np_c, int M, size_t esize) {
+LLayout lz_layout(const KrylovSettings* k, int np_c, int M, size_t esize) {
   LLayout L{};
   const size_t nk = (size_t)k->nx * k->ny;
   const size_t ntiles = (size_t)((k->nx + TX - 1) / TX) * ((k->ny + TY - 1) / TY);
@@ -588,6 +839,10 @@ LLayout lz_layout(const KrylovSettings* k, int np_b, int np_c, int M, size_t esi
   o += al(nmax * sizeof(double));
   L.coef = o;
   o += al(nmax * sizeof(double));
+  L.coef_df = o;
+  o += al(nmax * sizeof(float2));
+  L.dfc = o;
+  o += al(nmax * sizeof(DfCoef));
   L.cvec = o;
   o += al(nmax * sizeof(double2));
   L.partials = o;
@@ -596,20 +851,16 @@ LLayout lz_layout(const KrylovSettings* k, int np_b, int np_c, int M, size_t esi
   o += 256;
   L.maxslots = o;
   o += 256;
-  L.sb = o;
-  o += al((size_t)np_b * sizeof(double2));
-  L.wb = o;
-  o += al((size_t)np_b * sizeof(double2));
   L.wy = o;
-  o += al((size_t)np_b * sizeof(double2));
+  o += al((size_t)np_c * sizeof(double2));
   L.dg = o;
-  o += al((size_t)np_b * 2 * sizeof(double2));
+  o += al((size_t)np_c * 2 * sizeof(double2));
   L.sc = o;
   o += al((size_t)np_c * sizeof(double2));
   L.wc = o;
   o += al((size_t)np_c * sizeof(double2));
-  L.part = o;  // bound_group keeps the group count at or below 64
-  o += al((size_t)64 * nsamp_cap(M) * sizeof(double2));
+  L.part = o;  // bound_group keeps the group count at or below 128
+  o += al((size_t)128 * nsamp_cap(M) * sizeof(double2));
   L.min_total = o;
   return L;
 }
@@ -645,7 +896,7 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
     return REXI_EINVAL;
   }
   const int npc_max = poles_c(M, real_input);
-  const LLayout L = lz_layout(k, real_input ? 2 * npc_max : npc_max, npc_max, M, sizeof(T));
+  const LLayout L = lz_layout(k, npc_max, M, sizeof(T));
   if (ws_bytes < L.min_total) {
     set_last_error("workspace too small for the shared-Krylov method");
     return REXI_ENOMEM;
@@ -656,19 +907,12 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   TermSet ts;
   rexii_terms(M, h, &ts);
   const double hmu = h * ts.mu;
-  std::vector<double2> sc, wc, sb, wb;
+  std::vector<double2> sc, wc;
   const cd I(0.0, 1.0);
   auto push = [&](cd z, cd w) {
     const cd sz = I * z;  // shift of K: (tau A - z)^{-1} = -i (K + i z)^{-1}
     sc.push_back(make_double2(sz.real(), sz.imag()));
     wc.push_back(make_double2(w.real(), w.imag()));
-    if (real_input) {  // conjugate-closed set for the error bound
-      const cd sz2 = I * std::conj(z);
-      sb.push_back(make_double2(sz.real(), sz.imag()));
-      wb.push_back(make_double2(0.5 * w.real(), 0.5 * w.imag()));
-      sb.push_back(make_double2(sz2.real(), sz2.imag()));
-      wb.push_back(make_double2(0.5 * w.real(), -0.5 * w.imag()));
-    }
   };
   for (int n = real_input ? 0 : -N; n <= N; ++n) {
     const int an = n < 0 ? -n : n;
@@ -682,11 +926,7 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
     push(a_mn, -gam * P);
     push(-a_n, gam * Q);
   }
-  if (!real_input) {
-    sb = sc;
-    wb = wc;
-  }
-  const int npc = (int)sc.size(), npb = (int)sb.size();
+  const int npc = (int)sc.size();
 
   char* base = static_cast<char*>(ws);
   T* f0 = reinterpret_cast<T*>(base);
@@ -700,12 +940,12 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   double* beta = reinterpret_cast<double*>(base + L.beta);
   double* invb = reinterpret_cast<double*>(base + L.invb);  // 1 / b_j (0 for b_j = 0)
   double* coef = reinterpret_cast<double*>(base + L.coef);  // real form: c'_j / b_j
+  float2* coef_df = reinterpret_cast<float2*>(base + L.coef_df);
+  DfCoef* dfc = reinterpret_cast<DfCoef*>(base + L.dfc);  // double-float step coefficients
   double2* cvec = reinterpret_cast<double2*>(base + L.cvec);
   double2* partials = reinterpret_cast<double2*>(base + L.partials);
   unsigned* counter = reinterpret_cast<unsigned*>(base + L.counter);
   unsigned long long* maxslots = reinterpret_cast<unsigned long long*>(base + L.maxslots);
-  double2* d_sb = reinterpret_cast<double2*>(base + L.sb);
-  double2* d_wb = reinterpret_cast<double2*>(base + L.wb);
   double2* d_wy = reinterpret_cast<double2*>(base + L.wy);
   double2* d_dg = reinterpret_cast<double2*>(base + L.dg);
   double2* d_sc = reinterpret_cast<double2*>(base + L.sc);
@@ -714,7 +954,8 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   // Lanczos vectors kept in the caller's extra workspace
   T* basis = reinterpret_cast<T*>(base + L.min_total);
   const size_t vstride = L.vb / sizeof(T);
-  constexpr bool REAL = sizeof(T) == sizeof(double);
+  constexpr bool DF = std::is_same<T, float2>::value;  // double-float real form
+  constexpr bool REAL = DF || std::is_same<T, double>::value;
   // complex form: kept v_j (at least two, or none); w'_{nbasis-1} goes to f0's
   // buffer (f0 is read only by step 0) so that the second pass can resume the
   // recurrence at step nbasis with exactly the first pass's operands.
@@ -772,15 +1013,17 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
     }
     return REXI_OK;
   }
-  e = cudaMemcpyAsync(d_sb, sb.data(), npb * sizeof(double2), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_wb, wb.data(), npb * sizeof(double2), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_sc, sc.data(), npc * sizeof(double2), cudaMemcpyHostToDevice, s);
+  e = cudaMemcpyAsync(d_sc, sc.data(), npc * sizeof(double2), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_wc, wc.data(), npc * sizeof(double2), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
   mark(1);
   if (e == cudaSuccess) {
-    lz_init<T><<<grid, THREADS, 0, s>>>(G_, static_cast<const double2*>(in), adjoint ? 1 : 0, f0, beta, invb,
-                                        partials, counter);
+    if constexpr (DF)
+      lz_init_df<<<grid, THREADS, 0, s>>>(G_, static_cast<const double2*>(in), adjoint ? 1 : 0, f0, beta, invb,
+                                          dfc, partials, counter);
+    else
+      lz_init<T><<<grid, THREADS, 0, s>>>(G_, static_cast<const double2*>(in), adjoint ? 1 : 0, f0, beta, invb,
+                                          partials, counter);
     ++launches;
     e = cudaGetLastError();
   }
@@ -788,32 +1031,37 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   // ---- first pass: Lanczos steps, convergence checked on the device ----
   const double dist = std::fabs(hmu);  // every pole's distance from the real axis
   const double Lh = std::fabs(tau) * k->rho_bound;
-  int nsamp = (int)std::min<double>(std::ceil(2.0 * Lh / (dist / 4.0)) + 1.0, (double)nsamp_cap(M));
-  nsamp = std::max(nsamp, 2);
+  int nsamp = (int)std::ceil(2.0 * Lh / (dist / 4.0)) + 1;
+  nsamp = std::max(nsamp, kCoarse + 1);
+  nsamp = (nsamp - 1 + kCoarse - 1) / kCoarse * kCoarse + 1;  // 1 mod kCoarse: symmetric coarse subgrid
+  while (nsamp > nsamp_cap(M)) nsamp -= kCoarse;              // rho above the one behind M: coarser grid
   const double dl = 2.0 * Lh / (nsamp - 1);
-  const int chunk = std::min(512, std::max(kChunk, npb / 256));
-  const int G = bound_group(npb), groups = (npb + G - 1) / G;
-  const int nslot_c = (nsamp + kCoarse - 1) / kCoarse, nslot_f = nsamp;
+  const int chunk = std::min(512, std::max(kChunk, npc / 128));
+  const int G = bound_group(npc), groups = (npc + G - 1) / G;
+  const int nslot_c = (nsamp - 1) / kCoarse + 1, nslot_f = nsamp;
   double* pin = k->pinned;
   auto launch_chunk = [&](int c, int j0, int j1) -> cudaError_t {
     for (int j = j0; j < j1; ++j) {
-      if constexpr (REAL)
+      if constexpr (DF)
+        lz_dfstep<0><<<grid, THREADS, 0, s>>>(G_, k->Hdf, k->wdf, j, Wptr(j - 1), Wptr(j - 2), Wptr(j), alpha, beta,
+                                              invb, dfc, partials, counter, nullptr, nullptr);
+      else if constexpr (REAL)
         lz_wstep<0><<<grid, THREADS, 0, s>>>(G_, j, Wptr(j - 1), Wptr(j - 2), Wptr(j), alpha, beta, invb, partials,
                                              counter, nullptr, nullptr);
       else
         lz_step<0, T><<<grid, THREADS, 0, s>>>(G_, j, wptr(j - 1), vptr(j - 1), vptr(j), wptr(j), alpha, beta,
                                                invb, partials, counter, nullptr, nullptr);
     }
-    lz_poles_advance<<<(npb + 127) / 128, 128, 0, s>>>(npb, d_sb, d_wb, alpha, beta, j0, j1, d_dg, d_wy);
+    lz_poles_advance<<<(npc + 127) / 128, 128, 0, s>>>(npc, d_sc, d_wc, alpha, beta, j0, j1, d_dg, d_wy);
     cudaError_t err = cudaMemsetAsync(maxslots, 0, 2 * sizeof(unsigned long long), s);
     if (err != cudaSuccess) return err;
-    const dim3 gc((nslot_c + THREADS - 1) / THREADS, groups), gf((nslot_f + THREADS - 1) / THREADS, groups);
-    lz_bound_part<<<gc, THREADS, 0, s>>>(npb, G, d_sb, d_wy, Lh, dl, nslot_c, kCoarse, beta, j1, k->rtol, nullptr,
-                                         d_part);
-    lz_bound_max<<<gc.x, THREADS, 0, s>>>(groups, nslot_c, d_part, beta, j1, k->rtol, nullptr, maxslots);
-    lz_bound_part<<<gf, THREADS, 0, s>>>(npb, G, d_sb, d_wy, Lh, dl, nslot_f, 1, beta, j1, k->rtol, maxslots,
-                                         d_part);
-    lz_bound_max<<<gf.x, THREADS, 0, s>>>(groups, nslot_f, d_part, beta, j1, k->rtol, maxslots, maxslots + 1);
+    const int sym = REAL ? (((j1 - 1) & 1) ? -1 : 1) : 0;  // (-1)^(k-1), k = j1 steps
+    const dim3 gc((nslot_c + BT - 1) / BT, groups), gf((nslot_f + BT - 1) / BT, groups);
+    lz_bound_part<<<gc, BT, 0, s>>>(npc, G, d_sc, d_wy, Lh, dl, nslot_c, kCoarse, beta, j1, k->rtol, nullptr,
+                                    d_part);
+    lz_bound_max<<<gc.x, BT, 0, s>>>(groups, nslot_c, d_part, sym, beta, j1, k->rtol, nullptr, maxslots);
+    lz_bound_part<<<gf, BT, 0, s>>>(npc, G, d_sc, d_wy, Lh, dl, nslot_f, 1, beta, j1, k->rtol, maxslots, d_part);
+    lz_bound_max<<<gf.x, BT, 0, s>>>(groups, nslot_f, d_part, sym, beta, j1, k->rtol, maxslots, maxslots + 1);
     launches += (j1 - j0) + 5;
     const int par = c & 1;
     err = cudaMemcpyAsync(pin + 3 * par, beta + j1, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -898,9 +1146,12 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   const int nb = std::min(nbasis, kk);
   if (e == cudaSuccess) {
     if constexpr (REAL) {
-      lz_wcoef<<<(kk + 255) / 256, 256, 0, s>>>(cvec, invb, kk, coef);
+      lz_wcoef<<<(kk + 255) / 256, 256, 0, s>>>(cvec, invb, kk, coef, coef_df);
       ++launches;
-      lz_wbasis_sum<<<ebl, 256, 0, s>>>(f0, basis, vstride, nb, coef, acc, n3);
+      if constexpr (DF)
+        lz_dfbasis_sum<<<ebl, 256, 0, s>>>(f0, basis, vstride, nb, coef_df, acc, n3);
+      else
+        lz_wbasis_sum<<<ebl, 256, 0, s>>>(f0, basis, vstride, nb, coef, acc, n3);
     } else {
       lz_basis_sum<T><<<ebl, 256, 0, s>>>(basis, vstride, nb, cvec, acc, n3);
     }
@@ -908,7 +1159,10 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   }
   if (e == cudaSuccess && nb < kk) {
     for (int j = nb; j < kk; ++j) {
-      if constexpr (REAL)
+      if constexpr (DF)
+        lz_dfstep<1><<<grid, THREADS, 0, s>>>(G_, k->Hdf, k->wdf, j, Wptr(j - 1), Wptr(j - 2), Wptr(j), alpha, beta,
+                                              invb, dfc, partials, counter, acc, coef_df);
+      else if constexpr (REAL)
         lz_wstep<1><<<grid, THREADS, 0, s>>>(G_, j, Wptr(j - 1), Wptr(j - 2), Wptr(j), alpha, beta, invb, partials,
                                              counter, acc, coef);
       else
@@ -945,12 +1199,31 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
 
 size_t lanczos_workspace_bytes(const KrylovSettings* k, int M, int real_input) {
   const int npc = poles_c(M, real_input);
-  return lz_layout(k, real_input ? 2 * npc : npc, npc, M, real_input ? sizeof(double) : sizeof(double2)).min_total;
+  // real forms: 8-byte values (FP64 or double-float); complex form: 16 bytes
+  return lz_layout(k, npc, M, real_input ? sizeof(double) : sizeof(double2)).min_total;
 }
 
-rexi_status krylov_step_lanczos(KrylovSettings* k, double h, int M, const void* in, void* out, double dt,
+rexi_status lanczos_tables(KrylovSettings* k) {
+  const size_t nk = (size_t)k->nx * k->ny;
+  lz_df_tables<<<(unsigned)((nk + 255) / 256), 256>>>(k->depth, k->w64, nk, k->Hdf, k->wdf);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_error(cudaGetErrorString(e));
+    return REXI_ECUDA;
+  }
+  return REXI_OK;
+}
+
+rexi_status krylov_step_lanczos(KrylovSettings* k, int form, double h, int M, const void* in, void* out, double dt,
                                 int real_input, int term_begin, int term_end, void* ws, size_t ws_bytes,
                                 cudaStream_t s, rexi_step_info* info, bool adjoint, const KrylovHooks& hooks) {
+  if (form == REXI_FORM_PLAIN) {
+    set_last_error("variable-depth path: the plain form is Fourier-path only");
+    return REXI_EUNSUPPORTED;
+  }
+  if (real_input && form == REXI_FORM_MIXED)
+    return lanczos_impl<float2>(k, h, M, in, out, dt, 1, term_begin, term_end, ws, ws_bytes, s, info, adjoint,
+                                hooks);
   if (real_input)
     return lanczos_impl<double>(k, h, M, in, out, dt, 1, term_begin, term_end, ws, ws_bytes, s, info, adjoint,
                                 hooks);

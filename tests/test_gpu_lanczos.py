@@ -15,16 +15,16 @@ from oracle import coeffs as C
 from oracle import operator as O
 from oracle import rexi as R
 from paper_2008_11607_gb300 import inputs
-from tests.gpu_util import rel_l2, to_dev, torch_cuda
+from tests.gpu_util import TOL, rel_l2, to_dev, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
 
-def shared_plan(torch, nx, ny, depth, rtol=1e-12, max_iters=20000, **phys):
+def shared_plan(torch, nx, ny, depth, rtol=1e-12, max_iters=20000, form="fp64", **phys):
     from paper_2008_11607_gb300 import rexi
 
     Hd = torch.from_numpy(np.ascontiguousarray(depth, dtype=np.float64)).cuda()
-    plan = rexi.Plan(nx, ny, depth=Hd, form="fp64", **phys)
+    plan = rexi.Plan(nx, ny, depth=Hd, form=form, **phys)
     plan.set_krylov(rtol=rtol, max_iters=max_iters, term_batch=64)
     plan.set_krylov_method("shared")
     return plan, Hd
@@ -40,8 +40,9 @@ def energy_norm(x, H, g=1.0):
     return math.sqrt(float(np.sum(g / H * np.abs(e) ** 2) + np.sum(np.abs(x[1:]) ** 2)))
 
 
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
 @pytest.mark.parametrize("case", ["12x10_real", "16x16_complex", "9x14_phys", "40x36_real", "70x50_complex"])
-def test_shared_against_sparse_oracle(case):
+def test_shared_against_sparse_oracle(case, form):
     torch = torch_cuda()
     phys = {}
     taurho = 20.0
@@ -65,7 +66,7 @@ def test_shared_against_sparse_oracle(case):
         taurho = 45.0
     H = inputs.variable_depth(nx, ny, seed=3)
     rtol = 1e-12
-    plan, _ = shared_plan(torch, nx, ny, H, rtol=rtol, **phys)
+    plan, _ = shared_plan(torch, nx, ny, H, rtol=rtol, form=form, **phys)
     dt = taurho / plan.rho
     out, info = plan.step(to_dev(torch, st), dt, real_input=real, want_info=True)
     out = out.cpu().numpy()
@@ -73,7 +74,8 @@ def test_shared_against_sparse_oracle(case):
     assert 0 < info.krylov_iters < 20000
     A = O.cgrid_operator(nx, ny, H=H, **phys)
     ref = R.rexii_apply_sparse(A, st.ravel(), dt, 0.5, info.M, real_input=real).reshape(st.shape)
-    tol = max(1e-10, 10 * rtol * energy_cond(H, phys.get("g", 1.0)))
+    # the mixed form is double-float for real input (FP64 for complex input)
+    tol = max(TOL[form] if real else 1e-10, 10 * rtol * energy_cond(H, phys.get("g", 1.0)))
     assert rel_l2(out, ref) < tol, (rel_l2(out, ref), tol)
     if real:
         assert np.all(out.imag == 0)
@@ -124,14 +126,15 @@ def test_shared_adjoint_against_oracle():
     assert np.all(gr.imag == 0) and rel_l2(gr, refr) < 1e-10
 
 
-def test_shared_kept_basis_is_bitwise_identical():
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_shared_kept_basis_is_bitwise_identical(form):
     """Vectors kept from the first pass and vectors regenerated in the second
     are the same bits, so the output does not depend on the workspace size."""
     torch = torch_cuda()
     nx, ny = 40, 36
     H = inputs.variable_depth(nx, ny, seed=4)
     st = inputs.kminus3_field(nx, ny, seed=4)
-    plan, _ = shared_plan(torch, nx, ny, H, rtol=1e-12)
+    plan, _ = shared_plan(torch, nx, ny, H, rtol=1e-12, form=form)
     dt = 50.0 / plan.rho
     x = to_dev(torch, st)
     base = plan.workspace_size(dt)
@@ -216,7 +219,8 @@ def test_shared_full_size_constant_depth_all_terms_matches_fourier():
     assert rel_l2(a.cpu().numpy(), b.cpu().numpy()) < 1e-10
 
 
-def test_shared_full_size_variable_depth():
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_shared_full_size_variable_depth(form):
     """The variable-depth workload at full size (1024 x 1024, H = 1 + 0.4 sin cos
     + bumps, |k|^-3 height, tau rho = 400, every term).  No oracle solve fits
     this size, so: (a) the REXII step preserves the energy norm to the rational
@@ -226,7 +230,7 @@ def test_shared_full_size_variable_depth():
     n = 1024
     H = inputs.variable_depth(n, n, seed=0)
     st = inputs.kminus3_field(n, n, seed=0)
-    plan, _ = shared_plan(torch, n, n, H, rtol=1e-11)
+    plan, _ = shared_plan(torch, n, n, H, rtol=1e-11, form=form)
     dt = 400.0 / plan.rho
     x = to_dev(torch, st)
     out, info = plan.step(x, dt, want_info=True)
@@ -237,4 +241,10 @@ def test_shared_full_size_variable_depth():
     plan.set_krylov_method("cg")
     plan.set_krylov(rtol=1e-12, term_batch=6)
     b = plan.step(x, dt, terms=(0, 6))
-    assert rel_l2(a.cpu().numpy(), b.cpu().numpy()) < 1e-9
+    assert rel_l2(a.cpu().numpy(), b.cpu().numpy()) < (1e-9 if form == "fp64" else TOL[form])
+    if form == "mixed":  # double-float against FP64 Lanczos on the full step
+        plan.set_krylov_method("shared")
+        plan.set_krylov(rtol=1e-11)
+        plan_f, _ = shared_plan(torch, n, n, H, rtol=1e-11, form="fp64")
+        ref = plan_f.step(x, dt)
+        assert rel_l2(o, ref.cpu().numpy()) < TOL[form]
