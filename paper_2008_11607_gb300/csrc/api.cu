@@ -55,6 +55,8 @@ struct rexi_plan_s {
   FftPlan1D fx, fy;
   double2* tw_x = nullptr;
   double2* tw_y = nullptr;
+  float4* twf_x = nullptr;  // double-float twiddles (mixed form)
+  float4* twf_y = nullptr;
   double2* half_x = nullptr;
   double2* half_y = nullptr;
   // coefficient staging (pinned host) guarded by an event
@@ -189,6 +191,8 @@ void rexi_plan_destroy(rexi_plan_t p) {
   }
   cudaFree(p->tw_x);
   cudaFree(p->tw_y);
+  cudaFree(p->twf_x);
+  cudaFree(p->twf_y);
   cudaFree(p->half_x);
   cudaFree(p->half_y);
   if (p->staging) cudaFreeHost(p->staging);
@@ -252,6 +256,18 @@ rexi_status rexi_plan_create(rexi_plan_t* out, int32_t nx, int32_t ny, double Lx
     }
     p->fx.tw = p->tw_x;
     p->fy.tw = p->tw_y;
+    {  // double-float twiddles for the mixed form's transforms
+      std::vector<double2> fx4(nx), fy4(ny);
+      split_twiddles(twx.data(), nx, reinterpret_cast<float4*>(fx4.data()));
+      split_twiddles(twy.data(), ny, reinterpret_cast<float4*>(fy4.data()));
+      if (!upload_table(fx4, reinterpret_cast<double2**>(&p->twf_x), &st) ||
+          !upload_table(fy4, reinterpret_cast<double2**>(&p->twf_y), &st)) {
+        rexi_plan_destroy(p);
+        return st;
+      }
+      p->fx.twf = p->twf_x;
+      p->fy.twf = p->twf_y;
+    }
     // rho(A): largest omega over the discrete wavenumbers (exact for constant depth)
     std::vector<double> sx2(nx), cx2(nx);
     for (int k = 0; k < nx; ++k) { sx2[k] = hx[k].y * hx[k].y; cx2[k] = hx[k].x * hx[k].x; }
@@ -444,7 +460,9 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
   auto forward = [&]() -> rexi_status {
     prof_mark(p, 1, s);
     // forward transform (imaginary parts dropped for real input)
-    CUDA_TRY(fft2d(in2, spec, 3, p->fx, p->fy, -1, 1.0, real_input, 0, s), "forward FFT");
+    CUDA_TRY(p->form == REXI_FORM_MIXED ? fft2d_df(in2, spec, 3, p->fx, p->fy, -1, 1.0, real_input, 0, s)
+                                        : fft2d(in2, spec, 3, p->fx, p->fy, -1, 1.0, real_input, 0, s),
+             "forward FFT");
     p->launches += 2;
     prof_mark(p, 2, s);
     return REXI_OK;
@@ -562,7 +580,9 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
   }
   prof_mark(p, 3, s);
   // inverse transform, 1/(nx ny), real part for real input
-  CUDA_TRY(fft2d(spec, static_cast<double2*>(out), 3, p->fx, p->fy, +1, 1.0 / (double)nk, 0, real_input, s),
+  CUDA_TRY(p->form == REXI_FORM_MIXED
+               ? fft2d_df(spec, static_cast<double2*>(out), 3, p->fx, p->fy, +1, 1.0 / (double)nk, 0, real_input, s)
+               : fft2d(spec, static_cast<double2*>(out), 3, p->fx, p->fy, +1, 1.0 / (double)nk, 0, real_input, s),
            "inverse FFT");
   p->launches += 2;
   prof_mark(p, 4, s);

@@ -57,6 +57,7 @@ struct rexi_batch_s {
   std::vector<long long> offsets;  // per instance, complex128 elements; offsets[n] = total
   std::vector<rexi::SizeGroup> groups;
   std::map<int, std::pair<double2*, double2*>> axis_tables;  // n -> (twiddles, half angles), device
+  std::map<int, float4*> axis_twf;                             // n -> double-float twiddles (mixed form)
   // device data owned by the batch
   void* d_tables = nullptr;      // coefficient tables of all instances
   rexi::InstDesc* d_desc = nullptr;
@@ -227,6 +228,13 @@ cudaError_t build_items(rexi_batch_s* b) {
   return e;
 }
 
+// FP64 transforms for the FP64 form, double-float ones for the mixed form.
+cudaError_t fft_any(const rexi_batch_s* b, const double2* in, double2* out, int nfields, const FftPlan1D& px,
+                    const FftPlan1D& py, int sign, double scale, int zero_imag_in, int real_out, cudaStream_t s) {
+  return b->form == REXI_FORM_MIXED ? fft2d_df(in, out, nfields, px, py, sign, scale, zero_imag_in, real_out, s)
+                                    : fft2d(in, out, nfields, px, py, sign, scale, zero_imag_in, real_out, s);
+}
+
 // The whole persistent-mode step on stream s.
 cudaError_t enqueue_persistent(rexi_batch_s* b, const double2* in, double2* out, int real_input, char* ws,
                                cudaStream_t s) {
@@ -236,15 +244,15 @@ cudaError_t enqueue_persistent(rexi_batch_s* b, const double2* in, double2* out,
   for (auto& G : b->groups) {
     if (e != cudaSuccess) return e;
     const int nf = 3 * (int)G.insts.size();
-    e = fft2d(in + G.first_off, spec + G.first_off, nf, G.fx, G.fy, -1, 1.0, real_input, 0, s);
+    e = fft_any(b, in + G.first_off, spec + G.first_off, nf, G.fx, G.fy, -1, 1.0, real_input, 0, s);
   }
   if (e != cudaSuccess) return e;
   e = launch_pole(b, spec, counter, s);
   for (auto& G : b->groups) {
     if (e != cudaSuccess) return e;
     const int nf = 3 * (int)G.insts.size();
-    e = fft2d(spec + G.first_off, out + G.first_off, nf, G.fx, G.fy, +1, 1.0 / ((double)G.nx * G.ny), 0,
-              real_input, s);
+    e = fft_any(b, spec + G.first_off, out + G.first_off, nf, G.fx, G.fy, +1, 1.0 / ((double)G.nx * G.ny), 0,
+                real_input, s);
   }
   return e;
 }
@@ -268,6 +276,7 @@ void rexi_batch_destroy(rexi_batch_t b) {
   if (b->own) cudaStreamDestroy(b->own);
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
+  for (auto& kv : b->axis_twf) cudaFree(kv.second);
   for (auto& kv : b->axis_tables) {
     cudaFree(kv.second.first);
     cudaFree(kv.second.second);
@@ -340,9 +349,18 @@ rexi_status rexi_batch_create(rexi_batch_t* out, int32_t n, const int32_t* nx, c
       b->axis_tables[len] = {dtw, dhalf};
       cudaMemcpy(dtw, tw.data(), len * sizeof(double2), cudaMemcpyHostToDevice);
       cudaMemcpy(dhalf, half.data(), len * sizeof(double2), cudaMemcpyHostToDevice);
+      std::vector<float4> twf(len);
+      split_twiddles(tw.data(), len, twf.data());
+      float4* dtwf = nullptr;
+      if (cudaMalloc(&dtwf, len * sizeof(float4)) != cudaSuccess)
+        return bail(REXI_ENOMEM, "rexi_batch_create: table allocation failed");
+      b->axis_twf[len] = dtwf;
+      cudaMemcpy(dtwf, twf.data(), len * sizeof(float4), cudaMemcpyHostToDevice);
     }
     G.fx.tw = b->axis_tables[G.nx].first;
     G.fy.tw = b->axis_tables[G.ny].first;
+    G.fx.twf = b->axis_twf[G.nx];
+    G.fy.twf = b->axis_twf[G.ny];
   }
   // packed layout, group by group
   b->offsets.assign(n + 1, 0);
@@ -488,8 +506,10 @@ rexi_status rexi_batch_step(rexi_batch_t b, const void* in, void* out, int32_t r
       fft_factor(D.ny, &fy);
       fx.tw = b->axis_tables[D.nx].first;
       fy.tw = b->axis_tables[D.ny].first;
+      fx.twf = b->axis_twf[D.nx];
+      fy.twf = b->axis_twf[D.ny];
       double2* sp_i = spec + D.spec_off;
-      e = fft2d(in2 + D.spec_off, sp_i, 3, fx, fy, -1, 1.0, real_input, 0, s);
+      e = fft_any(b, in2 + D.spec_off, sp_i, 3, fx, fy, -1, 1.0, real_input, 0, s);
       SymbolParams sp;
       sp.nx = D.nx; sp.ny = D.ny; sp.inv_dx = D.inv_dx; sp.inv_dy = D.inv_dy;
       sp.g = b->g; sp.f = b->f; sp.H = b->H; sp.half_x = D.half_x; sp.half_y = D.half_y;
@@ -500,7 +520,7 @@ rexi_status rexi_batch_step(rexi_batch_t b, const void* in, void* out, int32_t r
         e = b->form == REXI_FORM_FP64 ? pole_fused_fp64(sp_i, sp, reinterpret_cast<const double*>(tab), fs, s)
                                       : pole_fused_mixed(sp_i, sp, tab, fs, D.grid, s);
       if (e == cudaSuccess)
-        e = fft2d(sp_i, out2 + D.spec_off, 3, fx, fy, +1, 1.0 / ((double)D.nx * D.ny), 0, real_input, s);
+        e = fft_any(b, sp_i, out2 + D.spec_off, 3, fx, fy, +1, 1.0 / ((double)D.nx * D.ny), 0, real_input, s);
       b->launches += 5;
     }
   } else if (mode == REXI_BATCH_PERSISTENT) {

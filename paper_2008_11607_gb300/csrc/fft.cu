@@ -9,7 +9,16 @@
 // butterflies; any other prime factor (3, 5, 7, ... <= 127) uses a direct
 // DFT in which each thread computes one output.  Twiddles come from a host
 // table w[t] = exp(-2 pi i t / n) built in FP64; the inverse uses conj(w).
+//
+// The stages are templates over the complex value type: double2 (FP64) or
+// float4 = (re_hi, re_lo, im_hi, im_lo), a double-float complex number whose
+// arithmetic runs on the FP32 pipes with error-free transformations (Knuth's
+// TwoSum, Dekker's FastTwoSum, the FMA TwoProduct; about 48 significant
+// bits), for the mixed form: GB300 issues FP32 operations 58x faster than
+// FP64 ones.  The double-float transform reads and writes FP64 in HBM and
+// keeps the 16-byte double-float values between its row and column passes.
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -32,34 +41,97 @@ __device__ __forceinline__ double2 mul_si(double2 a) {
   return SIGN < 0 ? make_double2(a.y, -a.x) : make_double2(-a.y, a.x);
 }
 
+// ---- double-float complex (float4: re_hi, re_lo, im_hi, im_lo) ----
+__device__ __forceinline__ float2 f_fast(float s, float e) {
+  const float h = s + e;
+  return make_float2(h, e - (h - s));
+}
+__device__ __forceinline__ float2 f_add(float a, float al, float b, float bl) {
+  const float s = a + b, bb = s - a;
+  return f_fast(s, ((a - (s - bb)) + (b - bb)) + (al + bl));
+}
+// x * y for double-floats x = (a, al), y = (b, bl), as an unnormalised pair
+__device__ __forceinline__ float2 f_mul(float a, float al, float b, float bl) {
+  const float p = a * b;
+  return make_float2(p, fmaf(a, bl, fmaf(al, b, fmaf(a, b, -p))));
+}
+__device__ __forceinline__ float4 cadd(float4 a, float4 b) {
+  const float2 r = f_add(a.x, a.y, b.x, b.y), i = f_add(a.z, a.w, b.z, b.w);
+  return make_float4(r.x, r.y, i.x, i.y);
+}
+__device__ __forceinline__ float4 csub(float4 a, float4 b) {
+  const float2 r = f_add(a.x, a.y, -b.x, -b.y), i = f_add(a.z, a.w, -b.z, -b.w);
+  return make_float4(r.x, r.y, i.x, i.y);
+}
+__device__ __forceinline__ float4 cmul(float4 a, float4 w) {
+  const float2 rr = f_mul(a.x, a.y, w.x, w.y), ii = f_mul(a.z, a.w, w.z, w.w);
+  const float2 ri = f_mul(a.x, a.y, w.z, w.w), ir = f_mul(a.z, a.w, w.x, w.y);
+  const float2 re = f_add(rr.x, rr.y, -ii.x, -ii.y), im = f_add(ri.x, ri.y, ir.x, ir.y);
+  return make_float4(re.x, re.y, im.x, im.y);
+}
+template <int SIGN>
+__device__ __forceinline__ float4 mul_si(float4 a) {
+  return SIGN < 0 ? make_float4(a.z, a.w, -a.x, -a.y) : make_float4(-a.z, -a.w, a.x, a.y);
+}
+// (p + q) * h and (p - q) * h for the 8-point butterfly, h = 1/sqrt(2)
+constexpr double kHalfSqrt2 = 0.70710678118654752440;
+__device__ __forceinline__ double hmul_sum(double p, double q, int sgn) { return kHalfSqrt2 * (p + sgn * q); }
+__device__ __forceinline__ float2 hmul_sum(float2 p, float2 q, int sgn) {
+  constexpr float hh = (float)kHalfSqrt2;
+  constexpr float hl = (float)(kHalfSqrt2 - (double)hh);
+  const float2 t = f_add(p.x, p.y, sgn * q.x, sgn * q.y);
+  const float2 m = f_mul(t.x, t.y, hh, hl);
+  return f_fast(m.x, m.y);
+}
+__device__ __forceinline__ double re_of(double2 v) { return v.x; }
+__device__ __forceinline__ double im_of(double2 v) { return v.y; }
+__device__ __forceinline__ float2 re_of(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 im_of(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ double2 cpack(double re, double im) { return make_double2(re, im); }
+__device__ __forceinline__ float4 cpack(float2 re, float2 im) { return make_float4(re.x, re.y, im.x, im.y); }
+__device__ __forceinline__ double neg(double v) { return -v; }
+__device__ __forceinline__ float2 neg(float2 v) { return make_float2(-v.x, -v.y); }
+
 template <int SIGN>
 __device__ __forceinline__ double2 tw_load(const double2* tw, int idx) {
   double2 w = __ldg(tw + idx);
   if (SIGN > 0) w.y = -w.y;
   return w;
 }
+template <int SIGN>
+__device__ __forceinline__ float4 tw_load(const float4* tw, int idx) {
+  float4 w = __ldg(tw + idx);
+  if (SIGN > 0) {
+    w.z = -w.z;
+    w.w = -w.w;
+  }
+  return w;
+}
+template <typename T>
+__device__ __forceinline__ T czero() {
+  return T{};
+}
 
 // 2-, 4- and 8-point DFTs X_k = sum_r v_r e^{SIGN 2 pi i r k / R}, in place.
-template <int SIGN>
-__device__ __forceinline__ void dft2(double2* v) {
-  double2 a = v[0], b = v[1];
+template <int SIGN, typename T>
+__device__ __forceinline__ void dft2(T* v) {
+  T a = v[0], b = v[1];
   v[0] = cadd(a, b);
   v[1] = csub(a, b);
 }
-template <int SIGN>
-__device__ __forceinline__ void dft4(double2* v) {
-  double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-  double2 t2 = cadd(v[1], v[3]), t3 = mul_si<SIGN>(csub(v[1], v[3]));
+template <int SIGN, typename T>
+__device__ __forceinline__ void dft4(T* v) {
+  T t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+  T t2 = cadd(v[1], v[3]), t3 = mul_si<SIGN>(csub(v[1], v[3]));
   v[0] = cadd(t0, t2);
   v[2] = csub(t0, t2);
   v[1] = cadd(t1, t3);
   v[3] = csub(t1, t3);
 }
-template <int SIGN>
-__device__ __forceinline__ void dft8(double2* v) {
+template <int SIGN, typename T>
+__device__ __forceinline__ void dft8(T* v) {
   // X_{2m} = DFT4(v_r + v_{r+4}),  X_{2m+1} = DFT4((v_r - v_{r+4}) W^r),  W = e^{SIGN i pi/4}
-  const double h = 0.70710678118654752440;
-  double2 a[4], b[4];
+  T a[4], b[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     a[r] = cadd(v[r], v[r + 4]);
@@ -67,13 +139,13 @@ __device__ __forceinline__ void dft8(double2* v) {
   }
   // b1 *= h (1 + SIGN i), b2 *= SIGN i, b3 *= h (-1 + SIGN i)
   {
-    double2 z = b[1];
-    b[1] = SIGN < 0 ? make_double2(h * (z.x + z.y), h * (z.y - z.x))
-                    : make_double2(h * (z.x - z.y), h * (z.y + z.x));
+    T z = b[1];
+    b[1] = SIGN < 0 ? cpack(hmul_sum(re_of(z), im_of(z), 1), hmul_sum(im_of(z), re_of(z), -1))
+                    : cpack(hmul_sum(re_of(z), im_of(z), -1), hmul_sum(im_of(z), re_of(z), 1));
     b[2] = mul_si<SIGN>(b[2]);
     z = b[3];
-    b[3] = SIGN < 0 ? make_double2(h * (z.y - z.x), -h * (z.x + z.y))
-                    : make_double2(-h * (z.x + z.y), h * (z.x - z.y));
+    b[3] = SIGN < 0 ? cpack(hmul_sum(im_of(z), re_of(z), -1), neg(hmul_sum(re_of(z), im_of(z), 1)))
+                    : cpack(neg(hmul_sum(re_of(z), im_of(z), 1)), hmul_sum(re_of(z), im_of(z), -1));
   }
   dft4<SIGN>(a);
   dft4<SIGN>(b);
@@ -86,10 +158,9 @@ __device__ __forceinline__ void dft8(double2* v) {
 
 // One radix-R stage with register butterflies (R in {2, 4, 8}).
 // Element t of sequence b lives at b * sstride + t * estride.
-template <int SIGN, int R>
-__device__ __forceinline__ void stage_pow2(const double2* src, double2* dst, int n, int Ns, int nseq,
-                                           int sstride, int estride, bool seq_fastest,
-                                           const double2* tw) {
+template <int SIGN, int R, typename T>
+__device__ __forceinline__ void stage_pow2(const T* src, T* dst, int n, int Ns, int nseq, int sstride, int estride,
+                                           bool seq_fastest, const T* tw) {
   const int nb = n / R;
   const int total = nb * nseq;
   const int twstep = n / (Ns * R);
@@ -102,8 +173,8 @@ __device__ __forceinline__ void stage_pow2(const double2* src, double2* dst, int
       b = idx / nb;
       j = idx % nb;
     }
-    const double2* s = src + b * sstride;
-    double2 v[R];
+    const T* s = src + b * sstride;
+    T v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = s[(j + r * nb) * estride];
     const int jm = j % Ns;
@@ -114,7 +185,7 @@ __device__ __forceinline__ void stage_pow2(const double2* src, double2* dst, int
     if (R == 2) dft2<SIGN>(v);
     if (R == 4) dft4<SIGN>(v);
     if (R == 8) dft8<SIGN>(v);
-    double2* d = dst + b * sstride;
+    T* d = dst + b * sstride;
     const int base = (j - jm) * R + jm;
 #pragma unroll
     for (int r = 0; r < R; ++r) d[(base + r * Ns) * estride] = v[r];
@@ -123,10 +194,9 @@ __device__ __forceinline__ void stage_pow2(const double2* src, double2* dst, int
 
 // One radix-R stage for an arbitrary prime R: each thread produces one output
 // X[o] = sum_r x[j + r n/R] w^{r (j % Ns) n/(Ns R) + ((r k) mod R) n/R}.
-template <int SIGN>
-__device__ __forceinline__ void stage_generic(const double2* src, double2* dst, int n, int R, int Ns,
-                                              int nseq, int sstride, int estride, bool seq_fastest,
-                                              const double2* tw) {
+template <int SIGN, typename T>
+__device__ __forceinline__ void stage_generic(const T* src, T* dst, int n, int R, int Ns, int nseq, int sstride,
+                                              int estride, bool seq_fastest, const T* tw) {
   const int nb = n / R;
   const int total = n * nseq;
   const int twstep = n / (Ns * R);
@@ -142,8 +212,8 @@ __device__ __forceinline__ void stage_generic(const double2* src, double2* dst, 
     const int k = (o / Ns) % R;
     const int jm = o % Ns;
     const int j = (o / (Ns * R)) * Ns + jm;
-    const double2* s = src + b * sstride;
-    double2 acc = make_double2(0.0, 0.0);
+    const T* s = src + b * sstride;
+    T acc = czero<T>();
     int rk = 0;  // (r k) mod R
     for (int r = 0; r < R; ++r) {
       int t = r * jm * twstep + rk * nb;
@@ -157,11 +227,11 @@ __device__ __forceinline__ void stage_generic(const double2* src, double2* dst, 
 }
 
 // Runs all stages; returns the buffer holding the result.
-template <int SIGN>
-__device__ double2* run_stages(double2* b0, double2* b1, const StageList& st, int nseq, int sstride,
-                               int estride, bool seq_fastest, const double2* tw) {
-  double2* src = b0;
-  double2* dst = b1;
+template <int SIGN, typename T>
+__device__ T* run_stages(T* b0, T* b1, const StageList& st, int nseq, int sstride, int estride, bool seq_fastest,
+                         const T* tw) {
+  T* src = b0;
+  T* dst = b1;
   int Ns = 1;
   for (int s = 0; s < st.nstages; ++s) {
     const int R = st.radix[s];
@@ -175,80 +245,87 @@ __device__ double2* run_stages(double2* b0, double2* b1, const StageList& st, in
       stage_generic<SIGN>(src, dst, st.n, R, Ns, nseq, sstride, estride, seq_fastest, tw);
     __syncthreads();
     Ns *= R;
-    double2* t = src;
+    T* t = src;
     src = dst;
     dst = t;
   }
   return src;
 }
 
+// Conversions at the HBM boundary of a pass: FP64 in and out; double-float
+// values between the passes of the double-float transform.
+__device__ __forceinline__ void cvt(double2 v, int zero_imag, double2* o) {
+  if (zero_imag) v.y = 0.0;
+  *o = v;
+}
+__device__ __forceinline__ void cvt(double2 v, int zero_imag, float4* o) {
+  const float rh = (float)v.x, ih = zero_imag ? 0.f : (float)v.y;
+  *o = make_float4(rh, (float)(v.x - (double)rh), ih, zero_imag ? 0.f : (float)(v.y - (double)ih));
+}
+__device__ __forceinline__ void cvt(float4 v, int zero_imag, float4* o) {
+  if (zero_imag) v.z = v.w = 0.f;
+  *o = v;
+}
+__device__ __forceinline__ void out_cvt(double2 v, double scale, int real_out, double2* o) {
+  *o = make_double2(v.x * scale, real_out ? 0.0 : v.y * scale);
+}
+__device__ __forceinline__ void out_cvt(float4 v, double scale, int real_out, double2* o) {
+  const double re = (double)v.x + (double)v.y, im = (double)v.z + (double)v.w;
+  *o = make_double2(re * scale, real_out ? 0.0 : im * scale);
+}
+// between passes: scale 1, complex (the caller passes scale = 1, real_out = 0)
+__device__ __forceinline__ void out_cvt(float4 v, double, int, float4* o) { *o = v; }
+
 // Rows: `rpc` rows of length n per CTA.  `in` and `out` may alias (each CTA
-// reads all of its rows before writing them).
-template <int SIGN>
-__global__ void __launch_bounds__(256) fft_rows_kernel(const double2* in, double2* out, int nrows,
-                                                       int rpc, StageList st, const double2* tw,
-                                                       double scale, int zero_imag_in,
-                                                       int real_out) {
-  extern __shared__ double2 smem[];
+// reads all of its rows before writing them).  T: arithmetic type; TI, TO:
+// value types in HBM.
+template <int SIGN, typename T, typename TI, typename TO>
+__global__ void __launch_bounds__(256) fft_rows_kernel(const TI* in, TO* out, int nrows, int rpc, StageList st,
+                                                       const T* tw, double scale, int zero_imag_in, int real_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
   const int n = st.n;
-  double2* b0 = smem;
-  double2* b1 = smem + (size_t)rpc * n;
+  T* b0 = smem;
+  T* b1 = smem + (size_t)rpc * n;
   const long long row0 = (long long)blockIdx.x * rpc;
   const int nr = (int)min((long long)rpc, nrows - row0);
-  const double2* g_in = in + row0 * n;
+  const TI* g_in = in + row0 * n;
   for (int i = threadIdx.x; i < rpc * n; i += blockDim.x) {
-    double2 v = make_double2(0.0, 0.0);
-    if (i < nr * n) {
-      v = g_in[i];
-      if (zero_imag_in) v.y = 0.0;
-    }
+    T v = czero<T>();
+    if (i < nr * n) cvt(g_in[i], zero_imag_in, &v);
     b0[i] = v;
   }
   __syncthreads();
-  double2* res = run_stages<SIGN>(b0, b1, st, rpc, n, 1, false, tw);
-  double2* g_out = out + row0 * n;
-  for (int i = threadIdx.x; i < nr * n; i += blockDim.x) {
-    double2 v = res[i];
-    v.x *= scale;
-    v.y = real_out ? 0.0 : v.y * scale;
-    g_out[i] = v;
-  }
+  T* res = run_stages<SIGN>(b0, b1, st, rpc, n, 1, false, tw);
+  TO* g_out = out + row0 * n;
+  for (int i = threadIdx.x; i < nr * n; i += blockDim.x) out_cvt(res[i], scale, real_out, g_out + i);
 }
 
 // Columns: W adjacent columns of one field per CTA (blockIdx.y = field).
-template <int SIGN>
-__global__ void __launch_bounds__(256) fft_cols_kernel(const double2* in, double2* out, int nx,
-                                                       int W, StageList st, const double2* tw,
-                                                       double scale, int zero_imag_in,
-                                                       int real_out) {
-  extern __shared__ double2 smem[];
+template <int SIGN, typename T, typename TI, typename TO>
+__global__ void __launch_bounds__(256) fft_cols_kernel(const TI* in, TO* out, int nx, int W, StageList st,
+                                                       const T* tw, double scale, int zero_imag_in, int real_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
   const int ny = st.n;
-  double2* b0 = smem;
-  double2* b1 = smem + (size_t)W * ny;
+  T* b0 = smem;
+  T* b1 = smem + (size_t)W * ny;
   const int x0 = blockIdx.x * W;
   const int w = min(W, nx - x0);
   const size_t field_off = (size_t)blockIdx.y * nx * ny;
-  const double2* g_in = in + field_off + x0;
+  const TI* g_in = in + field_off + x0;
   for (int i = threadIdx.x; i < ny * W; i += blockDim.x) {
     const int t = i / W, c = i - t * W;
-    double2 v = make_double2(0.0, 0.0);
-    if (c < w) {
-      v = g_in[(size_t)t * nx + c];
-      if (zero_imag_in) v.y = 0.0;
-    }
+    T v = czero<T>();
+    if (c < w) cvt(g_in[(size_t)t * nx + c], zero_imag_in, &v);
     b0[i] = v;
   }
   __syncthreads();
-  double2* res = run_stages<SIGN>(b0, b1, st, W, 1, W, true, tw);
-  double2* g_out = out + field_off + x0;
+  T* res = run_stages<SIGN>(b0, b1, st, W, 1, W, true, tw);
+  TO* g_out = out + field_off + x0;
   for (int i = threadIdx.x; i < ny * W; i += blockDim.x) {
     const int t = i / W, c = i - t * W;
-    if (c < w) {
-      double2 v = res[i];
-      v.x *= scale;
-      v.y = real_out ? 0.0 : v.y * scale;
-      g_out[(size_t)t * nx + c] = v;
-    }
+    if (c < w) out_cvt(res[i], scale, real_out, g_out + (size_t)t * nx + c);
   }
 }
 
@@ -305,29 +382,34 @@ static cudaError_t allow_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int SIGN>
+// FP64 transform (T = double2), or double-float arithmetic (T = float4) with
+// double-float values between the passes (in `out`, 16 bytes per value like FP64).
+template <int SIGN, typename T>
 static cudaError_t fft2d_impl(const double2* in, double2* out, int nfields, const FftPlan1D& px,
-                              const FftPlan1D& py, double scale, int zero_imag_in, int real_out,
-                              cudaStream_t s) {
+                              const FftPlan1D& py, const T* twx, const T* twy, double scale, int zero_imag_in,
+                              int real_out, cudaStream_t s) {
+  constexpr bool DF = sizeof(T) == sizeof(float4) && !std::is_same<T, double2>::value;
+  using TM = typename std::conditional<DF, float4, double2>::type;  // between the passes
   const int nx = px.n, ny = py.n;
+  TM* mid = reinterpret_cast<TM*>(out);
   cudaError_t e;
   {
     const int rpc = rows_per_cta(nx);
     const int nrows = nfields * ny;
-    const size_t sm = 2 * (size_t)rpc * nx * sizeof(double2);
-    if ((e = allow_smem(fft_rows_kernel<SIGN>, sm)) != cudaSuccess) return e;
+    const size_t sm = 2 * (size_t)rpc * nx * sizeof(T);
+    auto k = fft_rows_kernel<SIGN, T, double2, TM>;
+    if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
     dim3 grid((nrows + rpc - 1) / rpc);
-    fft_rows_kernel<SIGN><<<grid, 256, sm, s>>>(in, out, nrows, rpc, to_stages(px), px.tw, 1.0,
-                                                zero_imag_in, 0);
+    k<<<grid, 256, sm, s>>>(in, mid, nrows, rpc, to_stages(px), twx, 1.0, zero_imag_in, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
     const int W = cols_per_cta(ny);
-    const size_t sm = 2 * (size_t)W * ny * sizeof(double2);
-    if ((e = allow_smem(fft_cols_kernel<SIGN>, sm)) != cudaSuccess) return e;
+    const size_t sm = 2 * (size_t)W * ny * sizeof(T);
+    auto k = fft_cols_kernel<SIGN, T, TM, double2>;
+    if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
     dim3 grid((nx + W - 1) / W, nfields);
-    fft_cols_kernel<SIGN><<<grid, 256, sm, s>>>(out, out, nx, W, to_stages(py), py.tw, scale, 0,
-                                                real_out);
+    k<<<grid, 256, sm, s>>>(mid, out, nx, W, to_stages(py), twy, scale, 0, real_out);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -336,8 +418,22 @@ static cudaError_t fft2d_impl(const double2* in, double2* out, int nfields, cons
 cudaError_t fft2d(const double2* in, double2* out, int nfields, const FftPlan1D& px,
                   const FftPlan1D& py, int sign, double scale, int zero_imag_in, int real_out,
                   cudaStream_t s) {
-  if (sign < 0) return fft2d_impl<-1>(in, out, nfields, px, py, scale, zero_imag_in, real_out, s);
-  return fft2d_impl<+1>(in, out, nfields, px, py, scale, zero_imag_in, real_out, s);
+  if (sign < 0) return fft2d_impl<-1>(in, out, nfields, px, py, px.tw, py.tw, scale, zero_imag_in, real_out, s);
+  return fft2d_impl<+1>(in, out, nfields, px, py, px.tw, py.tw, scale, zero_imag_in, real_out, s);
+}
+
+cudaError_t fft2d_df(const double2* in, double2* out, int nfields, const FftPlan1D& px, const FftPlan1D& py,
+                     int sign, double scale, int zero_imag_in, int real_out, cudaStream_t s) {
+  if (!px.twf || !py.twf) return fft2d(in, out, nfields, px, py, sign, scale, zero_imag_in, real_out, s);
+  if (sign < 0) return fft2d_impl<-1>(in, out, nfields, px, py, px.twf, py.twf, scale, zero_imag_in, real_out, s);
+  return fft2d_impl<+1>(in, out, nfields, px, py, px.twf, py.twf, scale, zero_imag_in, real_out, s);
+}
+
+void split_twiddles(const double2* tw, int n, float4* out) {
+  for (int t = 0; t < n; ++t) {
+    const float rh = (float)tw[t].x, ih = (float)tw[t].y;
+    out[t] = make_float4(rh, (float)(tw[t].x - (double)rh), ih, (float)(tw[t].y - (double)ih));
+  }
 }
 
 }  // namespace rexi

@@ -37,6 +37,7 @@ struct FftPlan1D {
   int nstages = 0;
   int radix[kMaxStages] = {0};
   const double2* tw = nullptr;  // device table w[t] = exp(-2 pi i t / n), t < n
+  const float4* twf = nullptr;  // the same as double-float pairs (re_hi, re_lo, im_hi, im_lo), or null
 };
 bool fft_factor(int n, FftPlan1D* p);  // fills n, nstages, radix; false if unsupported
 // Forward (sign -1) or inverse (sign +1, scaled by `scale`) 2-D transform of
@@ -45,6 +46,12 @@ bool fft_factor(int n, FftPlan1D* p);  // fills n, nstages, radix; false if unsu
 cudaError_t fft2d(const double2* in, double2* out, int nfields, const FftPlan1D& px,
                   const FftPlan1D& py, int sign, double scale, int zero_imag_in, int real_out,
                   cudaStream_t s);
+// The same in double-float arithmetic (FP32 pipes, about 48 significant bits)
+// when both plans carry double-float twiddles; FP64 otherwise.
+cudaError_t fft2d_df(const double2* in, double2* out, int nfields, const FftPlan1D& px,
+                     const FftPlan1D& py, int sign, double scale, int zero_imag_in, int real_out,
+                     cudaStream_t s);
+void split_twiddles(const double2* tw, int n, float4* out);  // host: FP64 table -> double-float
 
 // ---- Fourier-path pole kernels (pole_fft.cu) ------------------------------
 struct SymbolParams {
