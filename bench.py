@@ -448,13 +448,14 @@ def batch_measure(torch, rexi, inputs, form="mixed", reps=5):
 
 
 def adjoint_measure(torch, rexi, inputs, form="mixed", n=512, steps=8, tau_rho=200.3, every=2, rtol=1e-12,
-                    fd_dirs=1):
+                    fd_dirs=2, method="shared", warm=True):
     """Differentiation workload: variable depth (as the 1024^2 workload), n^2
     grid, `steps` REXII steps of tau rho ~ 200, loss 1/2 ||eta(T) - eta_target||^2
     (|k|^-3 target, seed 1000), gradients with respect to the initial state and
     the depth field through the checkpointed rollout (every `every` steps);
     central differences (step 1e-6) along `fd_dirs` random state and depth
-    directions."""
+    directions.  method: "shared" (one Lanczos basis for all poles; the depth
+    gradient from two kept bases) or "cg" (per-term CG)."""
     import numpy as np
 
     from paper_2008_11607_gb300.autograd import rexi_rollout
@@ -465,14 +466,20 @@ def adjoint_measure(torch, rexi, inputs, form="mixed", n=512, steps=8, tau_rho=2
     def mkplan(Hx):
         p = rexi.Plan(n, n, depth=Hx, form=form, h=H_PARAM)
         p.set_krylov(rtol=rtol, max_iters=20000, term_batch=64)
+        p.set_krylov_method(method)
         return p
 
     plan = mkplan(Hd)
     dt = tau_rho / plan.rho
     x0 = torch.from_numpy(inputs.kminus3_field(n, n, seed=0)).cuda()
     tgt = torch.from_numpy(inputs.kminus3_field(n, n, seed=1000)[0].real).cuda()
-    x = x0.clone().requires_grad_(True)
     Hd.requires_grad_(True)
+    if warm:  # one untimed forward + backward (module loading, allocator growth)
+        xw = x0.clone().requires_grad_(True)
+        sw = rexi_rollout(xw, plan, dt, steps, every=every, depth=Hd)
+        torch.autograd.grad(0.5 * torch.sum((sw[0].real - tgt) ** 2), [xw, Hd])
+    _, info = plan.step(x0, dt, want_info=True)
+    x = x0.clone().requires_grad_(True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sT = rexi_rollout(x, plan, dt, steps, every=every, depth=Hd)
@@ -505,9 +512,10 @@ def adjoint_measure(torch, rexi, inputs, form="mixed", n=512, steps=8, tau_rho=2
         checks.append({"wrt": "depth", "fd": fd, "adjoint": an, "rel_err": abs(fd - an) / abs(an)})
     return {
         "workload": "LRSW variable depth %dx%d (H = 1 + 0.4 sin(2 pi x) cos(4 pi y) + 8 bumps), %d REXII steps of "
-                    "tau*rho=%g, checkpoints every %d steps, loss 1/2||eta(T) - eta_target||^2, CG rtol %g, form=%s"
-                    % (n, n, steps, tau_rho, every, rtol, form),
-        "forward_s": t1 - t0, "backward_s": t2 - t1, "loss": float(loss), "fd_checks": checks,
+                    "tau*rho=%g, checkpoints every %d steps, loss 1/2||eta(T) - eta_target||^2, Krylov rtol %g, "
+                    "form=%s, method=%s" % (n, n, steps, tau_rho, every, rtol, form, method),
+        "forward_s": t1 - t0, "backward_s": t2 - t1, "loss": float(loss.detach()), "fd_checks": checks,
+        "krylov_iters_per_step": int(info.krylov_iters),
     }
 
 
@@ -636,6 +644,10 @@ def run_ours(args):
                 sm[key]["roofline"]["frac"] = sm[key]["roofline"]["achieved"] / hbm_peak
             krylov["shared_all_terms"][sform] = sm
 
+    differentiation = None
+    if not args.skip_adjoint:
+        differentiation = adjoint_measure(torch, rexi, inputs, n=args.adjoint_grid)
+
     # CPU oracle on a bounded sample (rank 0, N = 1 only), also the accuracy check
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
@@ -657,6 +669,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32x2+f64" if args.form == "mixed" else "f64", "data": "synthetic",
             "config": cfg, "clocks": clocks, "e2e": e2e, "gpu_launches": nlaunch, "roofline": roofline,
             "roofline_fft": roofline_fft, "phases_ms": phases, "forms": forms, "batched": batched, "krylov": krylov,
+            "differentiation": differentiation,
             "cpu_baseline": cpu,
             "accuracy": {"tolerance": 1e-8 if args.form == "mixed" else 1e-10,
                          "max_rel_err_vs_oracle_sampled": cpu["max_rel_err_vs_oracle"] if cpu else None},
@@ -682,6 +695,8 @@ def main():
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the differentiation workload (minutes at 512^2)")
     ap.add_argument("--adjoint-grid", type=int, default=512)
+    ap.add_argument("--adjoint-method", default="shared", choices=["shared", "cg"])
+    ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--batch-only", action="store_true", help="run only the serving-mix measurement")
     ap.add_argument("--krylov-terms", type=int, default=8)
     ap.add_argument("--krylov-form", default="mixed", choices=["mixed", "fp64", "shared"])
@@ -704,7 +719,8 @@ def main():
         B.build()
         from paper_2008_11607_gb300 import inputs, rexi
 
-        print(json.dumps(adjoint_measure(torch, rexi, inputs, n=args.adjoint_grid)), flush=True)
+        print(json.dumps(adjoint_measure(torch, rexi, inputs, n=args.adjoint_grid, method=args.adjoint_method)),
+              flush=True)
     elif args.batch_only:
         import torch
 

@@ -182,8 +182,12 @@ rexi_status rexi_plan_set_krylov(rexi_plan_t plan, double rtol, int32_t max_iter
  *   (the vectors alternate between real and imaginary, a_j = 0); in the
  *   mixed form its vectors and stencil arithmetic are double-float (pairs of
  *   FP32 values, about 48 significant bits) with FP64 scalars and inner
- *   products.  FP64 otherwise.  Applies to rexi_step and rexi_step_adjoint; the depth gradient
- *   always uses per-term CG. */
+ *   products.  FP64 otherwise.  Applies to rexi_step and rexi_step_adjoint,
+ *   and, for real input, to rexi_step_grad_depth: two Lanczos runs (on the
+ *   input and on W^{-1} grad_out), every vector kept, and the gradient as a
+ *   two-sided Galerkin form over the two bases (FP64; workspace from
+ *   rexi_workspace_size_grad_depth, about 2 (3 tau rho + 100) state-sized
+ *   real vectors).  Complex input keeps per-term CG for the gradient. */
 enum { REXI_KRYLOV_CG = 0, REXI_KRYLOV_SHARED = 1 };
 rexi_status rexi_plan_set_krylov_method(rexi_plan_t plan, int32_t method);
 
@@ -236,7 +240,9 @@ rexi_status rexi_step_adjoint(rexi_plan_t plan, const void* grad_out_dev, void* 
  *   dL/dH_k = dt Re sum_j beta_j conj(y_j,eta,k) (div x_j)_k,
  *   x_j = (dt A - z_j)^{-1} in,  y_j = (dt A - z_j)^{-H} grad_out;
  * both are recovered per REXII term from two CG solves with the pair
- * operator.  Workspace: rexi_workspace_size_grad_depth bytes; info as for
+ * operator (with the shared-Krylov method and real input: from two Lanczos
+ * bases, see rexi_plan_set_krylov_method).  Workspace:
+ * rexi_workspace_size_grad_depth bytes; info as for
  * rexi_step. */
 rexi_status rexi_step_grad_depth(rexi_plan_t plan, const void* in_dev, const void* grad_out_dev,
                                  double* grad_depth_dev, double dt, double tol, int32_t real_input,

@@ -625,7 +625,7 @@ rexi_status rexi_workspace_size_grad_depth(rexi_plan_t p, double dt, double tol,
   if (!(dt >= 0.0) || !isfinite(dt)) return fail(REXI_EINVAL, "dt must be finite and >= 0");
   const int M = pole_count(dt * p->rho, p->h, tol);
   if (M < 0) return fail(REXI_EINVAL, "pole count rule rejected the arguments");
-  *bytes = krylov_grad_workspace_bytes(&p->kry, M, real_input, p->form);
+  *bytes = krylov_grad_workspace_bytes(&p->kry, M, real_input, p->form, p->h);
   return REXI_OK;
 }
 

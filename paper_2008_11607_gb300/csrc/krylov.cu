@@ -700,7 +700,8 @@ size_t krylov_workspace_bytes(const KrylovSettings* k, int M, int real_input, in
   return layout(k, n_terms_for(M, real_input), form).total;
 }
 
-size_t krylov_grad_workspace_bytes(const KrylovSettings* k, int M, int real_input, int form) {
+size_t krylov_grad_workspace_bytes(const KrylovSettings* k, int M, int real_input, int form, double h) {
+  if (k->method == 1 && real_input) return lanczos_grad_workspace_bytes(k, M, h);
   return layout(k, n_terms_for(M, real_input), form).total;
 }
 
@@ -970,6 +971,8 @@ rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void
 rexi_status krylov_grad_depth(KrylovSettings* k, int form, double h, int M, const void* f_in, const void* g_out,
                               double* grad_depth, double dt, int real_input, void* ws, size_t ws_bytes,
                               cudaStream_t s, rexi_step_info* info, const KrylovHooks& hooks) {
+  if (k->method == 1 && real_input)
+    return krylov_grad_depth_lanczos(k, h, M, f_in, g_out, grad_depth, dt, ws, ws_bytes, s, info, hooks);
   const size_t nk = (size_t)k->nx * k->ny, n3 = 3 * nk;
   KrylovRun run;
   rexi_status st = run.setup(k, form, h, M, dt, real_input, 0, -1, ws, ws_bytes, s, &hooks);

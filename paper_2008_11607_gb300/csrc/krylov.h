@@ -40,7 +40,7 @@ rexi_status krylov_init(KrylovSettings* k, int nx, int ny, double Lx, double Ly,
                         const double* depth, double Hmean);
 void krylov_destroy(KrylovSettings* k);
 size_t krylov_workspace_bytes(const KrylovSettings* k, int M, int real_input, int form);
-size_t krylov_grad_workspace_bytes(const KrylovSettings* k, int M, int real_input, int form);
+size_t krylov_grad_workspace_bytes(const KrylovSettings* k, int M, int real_input, int form, double h);
 rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void* in, void* out, double dt,
                         int real_input, int term_begin, int term_end, void* ws, size_t ws_bytes,
                         cudaStream_t s, rexi_step_info* info, bool adjoint, const KrylovHooks& hooks);
@@ -48,6 +48,11 @@ rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void
 // double-float for the mixed form with real input.
 size_t lanczos_workspace_bytes(const KrylovSettings* k, int M, int real_input);
 rexi_status lanczos_tables(KrylovSettings* k);  // fills Hdf, wdf
+// Depth gradient from two kept Lanczos bases (real input; FP64).
+size_t lanczos_grad_workspace_bytes(const KrylovSettings* k, int M, double h);
+rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, double h, int M, const void* f_in, const void* g_out,
+                                      double* grad_depth, double dt, void* ws, size_t ws_bytes, cudaStream_t s,
+                                      rexi_step_info* info, const KrylovHooks& hooks);
 rexi_status krylov_step_lanczos(KrylovSettings* k, int form, double h, int M, const void* in, void* out, double dt,
                                 int real_input, int term_begin, int term_end, void* ws, size_t ws_bytes,
                                 cudaStream_t s, rexi_step_info* info, bool adjoint, const KrylovHooks& hooks);

@@ -1195,7 +1195,386 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   return REXI_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Depth gradient from two kept Lanczos bases (real input, FP64 real form).
+//
+// dL/dH_k = tau Re sum_j beta_j conj(y_j,eta,k) (div x_j)_k with
+// x_j = (tau A - z_j)^{-1} f and y_j = (tau A - z_j)^{-H} G.  A is W-skew, so
+// y_j = W (-tau A - conj z_j)^{-1} W^{-1} G: a Lanczos run on f (operator
+// K = -i tau A, shifts i z_j) and one on W^{-1} G (operator i tau A, shifts
+// i conj z_j) give x_j = -i ||f|| V c_j and y_j = -i ||W^{-1}G|| W V~ d_j with
+// c_j, d_j the resolvent columns of the two tridiagonal matrices.  With the
+// real-form vectors (v_b = i^b u_b) the gradient is
+//   grad_k = w_k sum_{a,b} u~_{eta,a,k} R_ab (div u_b)_k,
+//   R_ab = tau ||f|| ||W^{-1}G|| Re(i^{b-a} sum_j beta_j conj(d_ja) c_jb),
+// a two-sided Galerkin form whose middle matrix holds the divided differences
+// of r at pairs of Ritz values; it converges like the step itself (both runs
+// stop on the step's error bound), not like the single poles.
+
+// (T_k + s_p)^{-1} e_0 for every pole, out[i np + p] (UL sweep as lz_coeff_solve).
+__global__ void lz_resolvent(int np, const double2* s, const double* alpha, const double* beta, int kk,
+                             double2* out) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const double2 sp = s[p];
+  double2 psi = make_double2(alpha[kk - 1] + sp.x, sp.y);
+  out[(size_t)(kk - 1) * np + p] = psi;
+  for (int i = kk - 2; i >= 0; --i) {
+    const double2 r = cdivd(make_double2(beta[i + 1] * beta[i + 1], 0.0), psi);
+    psi = make_double2(alpha[i] + sp.x - r.x, sp.y - r.y);
+    out[(size_t)i * np + p] = psi;
+  }
+  double2 y = cdivd(make_double2(1.0, 0.0), out[p]);
+  out[p] = y;
+  for (int i = 1; i < kk; ++i) {
+    const double2 t = cdivd(y, out[(size_t)i * np + p]);
+    y = make_double2(-beta[i] * t.x, -beta[i] * t.y);
+    out[(size_t)i * np + p] = y;
+  }
+}
+
+// R[a kA + b] = tau b0A b0B invbB[a] invbA[b] Re(i^{b-a} sum_j w_j conj(DB[a][j]) CA[b][j]),
+// 16 x 16 tiles, poles in chunks of 16 through shared memory.
+__global__ void __launch_bounds__(256) lz_bilinear(int np, int kA, int kB, const double2* CA, const double2* DB,
+                                                   const double2* w, const double* betaA, const double* invbA,
+                                                   const double* betaB, const double* invbB, double tau, double* R) {
+  __shared__ double2 Ds[16][17], Cs[16][17];
+  const int ta = threadIdx.x / 16, tb = threadIdx.x % 16;
+  const int a = blockIdx.y * 16 + ta, b = blockIdx.x * 16 + tb;
+  double re = 0.0, im = 0.0;
+  for (int j0 = 0; j0 < np; j0 += 16) {
+    __syncthreads();
+    {
+      const int ra = blockIdx.y * 16 + ta, rb = blockIdx.x * 16 + ta, jj = j0 + tb;
+      Ds[ta][tb] = (ra < kB && jj < np) ? DB[(size_t)ra * np + jj] : make_double2(0.0, 0.0);
+      double2 c = (rb < kA && jj < np) ? CA[(size_t)rb * np + jj] : make_double2(0.0, 0.0);
+      if (jj < np) {
+        const double2 wj = w[jj];
+        c = make_double2(wj.x * c.x - wj.y * c.y, wj.x * c.y + wj.y * c.x);
+      }
+      Cs[ta][tb] = c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const double2 d = Ds[ta][q], c = Cs[tb][q];
+      re = fma(d.x, c.x, fma(d.y, c.y, re));  // conj(d) c
+      im = fma(d.x, c.y, fma(-d.y, c.x, im));
+    }
+  }
+  if (a < kB && b < kA)
+    R[(size_t)a * kA + b] =
+        tau * betaA[0] * betaB[0] * invbB[a] * invbA[b] * real_coeff(make_double2(re, im), (b - a) & 3);
+}
+
+// grad[p] += w[p] sum_b div(S_b)[p] sum_a R[a][b] S~_a,eta[p]; S_0 = f0, S_b = kept
+// W_{b-1} (run on f), the same for S~ (run on W^{-1} G).
+constexpr int kGB = 32, kGA = 64;
+__global__ void __launch_bounds__(256) lz_grad_contract(int nx, int ny, double idx, double idy, const double* f0,
+                                                        const double* basA, const double* g0, const double* basB,
+                                                        size_t vstride, int kA, int kB, const double* R,
+                                                        const double* w, double* grad) {
+  __shared__ double Rs[kGA][kGB];
+  const size_t nk = (size_t)nx * ny;
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = p < nk;
+  const int i = live ? (int)(p % nx) : 0, jrow = live ? (int)(p / nx) : 0;
+  const size_t pxm = (size_t)jrow * nx + (i == 0 ? nx - 1 : i - 1);
+  const size_t pym = (size_t)(jrow == 0 ? ny - 1 : jrow - 1) * nx + i;
+  double acc = 0.0;
+  for (int b0 = 0; b0 < kA; b0 += kGB) {
+    double z[kGB];
+#pragma unroll
+    for (int q = 0; q < kGB; ++q) z[q] = 0.0;
+    for (int a0 = 0; a0 < kB; a0 += kGA) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < kGA * kGB; t += blockDim.x) {
+        const int a = a0 + t / kGB, b = b0 + t % kGB;
+        Rs[t / kGB][t % kGB] = (a < kB && b < kA) ? R[(size_t)a * kA + b] : 0.0;
+      }
+      __syncthreads();
+      const int na = min(kGA, kB - a0);
+      for (int q = 0; q < na; ++q) {
+        const int a = a0 + q;
+        const double sv = live ? (a == 0 ? g0[p] : basB[(size_t)(a - 1) * vstride + p]) : 0.0;
+#pragma unroll
+        for (int bb = 0; bb < kGB; ++bb) z[bb] = fma(Rs[q][bb], sv, z[bb]);
+      }
+    }
+    if (!live) continue;
+    const int nbb = min(kGB, kA - b0);
+#pragma unroll
+    for (int bb = 0; bb < kGB; ++bb) {
+      if (bb >= nbb) break;
+      const int b = b0 + bb;
+      const double* S = b == 0 ? f0 : basA + (size_t)(b - 1) * vstride;
+      const double dv = (S[nk + p] - S[nk + pxm]) * idx + (S[2 * nk + p] - S[2 * nk + pym]) * idy;
+      acc = fma(z[bb], dv, acc);
+    }
+  }
+  if (live) grad[p] += w[p] * acc;
+}
+
+// Bytes of the gradient workspace; cap = kept Lanczos vectors per run.
+int grad_cap(const KrylovSettings* k, int M, double h) {
+  return (int)std::min<double>(k->max_iters, std::ceil(3.0 * M * h) + 100.0);
+}
+struct GLayout {
+  size_t vb, f0, g0, basA, basB, alA, beA, ibA, alB, beB, ibB, sA, wA, sB, wB, dg, wy, part, maxslots, partials,
+      counter, CA, DB, R, total;
+  int cap;
+};
+GLayout grad_layout(const KrylovSettings* k, int M, double h) {
+  GLayout L{};
+  const size_t nk = (size_t)k->nx * k->ny;
+  const size_t ntiles = (size_t)((k->nx + TX - 1) / TX) * ((k->ny + TY - 1) / TY);
+  const size_t nmax = (size_t)k->max_iters + 2;
+  const int np = poles_c(M, 1);
+  L.cap = grad_cap(k, M, h);
+  L.vb = al(3 * nk * sizeof(double));
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += al(bytes);
+    return at;
+  };
+  L.f0 = take(L.vb);
+  L.g0 = take(L.vb);
+  L.basA = take((size_t)L.cap * L.vb);
+  L.basB = take((size_t)L.cap * L.vb);
+  L.alA = take(nmax * sizeof(double));
+  L.beA = take(nmax * sizeof(double));
+  L.ibA = take(nmax * sizeof(double));
+  L.alB = take(nmax * sizeof(double));
+  L.beB = take(nmax * sizeof(double));
+  L.ibB = take(nmax * sizeof(double));
+  L.sA = take((size_t)np * sizeof(double2));
+  L.wA = take((size_t)np * sizeof(double2));
+  L.sB = take((size_t)np * sizeof(double2));
+  L.wB = take((size_t)np * sizeof(double2));
+  L.dg = take((size_t)np * 2 * sizeof(double2));
+  L.wy = take((size_t)np * sizeof(double2));
+  L.part = take((size_t)128 * nsamp_cap(M) * sizeof(double2));
+  L.maxslots = take(256);
+  L.partials = take(ntiles * sizeof(double2));
+  L.counter = take(256);
+  L.CA = take((size_t)L.cap * np * sizeof(double2));
+  L.DB = take((size_t)L.cap * np * sizeof(double2));
+  L.R = take((size_t)L.cap * L.cap * sizeof(double));
+  L.total = o;
+  return L;
+}
+
 }  // namespace
+
+size_t lanczos_grad_workspace_bytes(const KrylovSettings* k, int M, double h) { return grad_layout(k, M, h).total; }
+
+rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, double h, int M, const void* f_in, const void* g_out,
+                                      double* grad_depth, double dt, void* ws, size_t ws_bytes, cudaStream_t s,
+                                      rexi_step_info* info, const KrylovHooks& hooks) {
+  using cd = std::complex<double>;
+  auto mark = [&](int i) {
+    if (hooks.mark) hooks.mark(hooks.ctx, i, s);
+  };
+  int64_t launches = 0;
+  if (!(k->rho_bound > 0.0) || !k->pinned) {
+    set_last_error("shared-Krylov method: plan has no spectral bound");
+    return REXI_EINVAL;
+  }
+  const GLayout L = grad_layout(k, M, h);
+  if (ws_bytes < L.total) {
+    set_last_error("workspace too small for the shared-Krylov depth gradient");
+    return REXI_ENOMEM;
+  }
+  const int N = M + kL;
+  const size_t nk = (size_t)k->nx * k->ny;
+  // reduced (real-input) pole set: run on f uses shifts i z_j with beta_j, the run
+  // on W^{-1} G uses shifts i conj(z_j) with conj(beta_j)
+  TermSet ts;
+  rexii_terms(M, h, &ts);
+  const double hmu = h * ts.mu;
+  const cd I(0.0, 1.0);
+  std::vector<double2> sA, wA, sB, wB;
+  auto push = [&](cd z, cd w) {
+    const cd a = I * z, b = I * std::conj(z), wc = std::conj(w);
+    sA.push_back(make_double2(a.real(), a.imag()));
+    wA.push_back(make_double2(w.real(), w.imag()));
+    sB.push_back(make_double2(b.real(), b.imag()));
+    wB.push_back(make_double2(wc.real(), wc.imag()));
+  };
+  for (int n = 0; n <= N; ++n) {
+    const int i = n + N;
+    const double gam = n > 0 ? 2.0 : 1.0;
+    const cd C1(ts.c1re[i] * hmu + ts.c2re[i] * h * n, ts.c1im[i] * hmu + ts.c2im[i] * h * n);
+    const cd C2 = I * cd(ts.c2re[i], ts.c2im[i]);
+    const cd a_n(hmu, h * n), a_mn(hmu, -h * n);
+    const cd P = (C1 - C2 * a_mn) / (2.0 * hmu), Q = (C1 + C2 * a_n) / (2.0 * hmu);
+    push(a_mn, -gam * P);
+    push(-a_n, gam * Q);
+  }
+  const int np = (int)sA.size();
+  char* base = static_cast<char*>(ws);
+  auto D = [&](size_t off) { return reinterpret_cast<double*>(base + off); };
+  auto D2 = [&](size_t off) { return reinterpret_cast<double2*>(base + off); };
+  double2* partials = D2(L.partials);
+  unsigned* counter = reinterpret_cast<unsigned*>(base + L.counter);
+  unsigned long long* maxslots = reinterpret_cast<unsigned long long*>(base + L.maxslots);
+  const size_t vstride = L.vb / sizeof(double);
+
+  mark(0);
+  cudaError_t e = cudaMemcpyAsync(D2(L.sA), sA.data(), np * sizeof(double2), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(D2(L.wA), wA.data(), np * sizeof(double2), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(D2(L.sB), sB.data(), np * sizeof(double2), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(D2(L.wB), wB.data(), np * sizeof(double2), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+  mark(1);
+
+  const double dist = std::fabs(hmu);
+  const double Lh = std::fabs(dt) * k->rho_bound;
+  int nsamp = (int)std::ceil(2.0 * Lh / (dist / 4.0)) + 1;
+  nsamp = std::max(nsamp, kCoarse + 1);
+  nsamp = (nsamp - 1 + kCoarse - 1) / kCoarse * kCoarse + 1;
+  while (nsamp > nsamp_cap(M)) nsamp -= kCoarse;
+  const double dl = 2.0 * Lh / (nsamp - 1);
+  const int chunk = std::min(512, std::max(kChunk, np / 128));
+  const int Gp = bound_group(np), groups = (np + Gp - 1) / Gp;
+  const int nslot_c = (nsamp - 1) / kCoarse + 1, nslot_f = nsamp;
+  double* pin = k->pinned;
+
+  // One first pass with every vector kept (slot j = W_j); returns its step count.
+  auto keep_run = [&](double tau, const double2* src, int adjoint, double* f0, double* bas, double* alpha,
+                      double* beta, double* invb, const double2* d_s, const double2* d_w, int* kk_out,
+                      double* bound_out) -> rexi_status {
+    LGeom G;
+    G.nx = k->nx;
+    G.ny = k->ny;
+    G.tiles_x = (k->nx + TX - 1) / TX;
+    G.tiles_y = (k->ny + TY - 1) / TY;
+    G.fstride = nk;
+    const double idx = k->nx / k->Lx, idy = k->ny / k->Ly;
+    G.tdx = tau * idx;
+    G.tdy = tau * idy;
+    G.tgdx = tau * k->g * idx;
+    G.tgdy = tau * k->g * idy;
+    G.tf4 = 0.25 * tau * k->f;
+    G.H = k->depth;
+    G.w = k->w64;
+    const dim3 grid(G.tiles_x, G.tiles_y, 1);
+    auto W = [&](int j) -> double* { return j < -1 ? nullptr : (j == -1 ? f0 : bas + (size_t)j * vstride); };
+    lz_init<double><<<grid, THREADS, 0, s>>>(G, src, adjoint, f0, beta, invb, partials, counter);
+    ++launches;
+    cudaError_t err = cudaGetLastError();
+    bool converged = false, nonfinite = false;
+    int kk = 0, pending = -1, pending_j1 = 0;
+    double bound = INFINITY;
+    auto evaluate = [&](int c, int j1) -> cudaError_t {
+      const int par = c & 1;
+      cudaError_t er = cudaEventSynchronize(k->ev[par]);
+      if (er != cudaSuccess) return er;
+      const double b = pin[3 * par], coarse = pin[3 * par + 1], fine = pin[3 * par + 2];
+      if (!std::isfinite(b) || !std::isfinite(coarse) || !std::isfinite(fine)) {
+        nonfinite = true;
+        return cudaSuccess;
+      }
+      bound = b * coarse > k->rtol ? b * coarse : b * fine;
+      if (bound <= k->rtol) {
+        converged = true;
+        kk = j1;
+      }
+      return cudaSuccess;
+    };
+    for (int c = 0; err == cudaSuccess; ++c) {
+      const int j0 = c * chunk;
+      if (j0 >= L.cap) break;
+      const int j1 = std::min(j0 + chunk, L.cap);
+      for (int j = j0; j < j1; ++j)
+        lz_wstep<0><<<grid, THREADS, 0, s>>>(G, j, W(j - 1), W(j - 2), W(j), alpha, beta, invb, partials, counter,
+                                             nullptr, nullptr);
+      lz_poles_advance<<<(np + 127) / 128, 128, 0, s>>>(np, d_s, d_w, alpha, beta, j0, j1, D2(L.dg), D2(L.wy));
+      err = cudaMemsetAsync(maxslots, 0, 2 * sizeof(unsigned long long), s);
+      if (err != cudaSuccess) break;
+      const int sym = ((j1 - 1) & 1) ? -1 : 1;
+      const dim3 gc((nslot_c + BT - 1) / BT, groups), gf((nslot_f + BT - 1) / BT, groups);
+      lz_bound_part<<<gc, BT, 0, s>>>(np, Gp, d_s, D2(L.wy), Lh, dl, nslot_c, kCoarse, beta, j1, k->rtol, nullptr,
+                                      D2(L.part));
+      lz_bound_max<<<gc.x, BT, 0, s>>>(groups, nslot_c, D2(L.part), sym, beta, j1, k->rtol, nullptr, maxslots);
+      lz_bound_part<<<gf, BT, 0, s>>>(np, Gp, d_s, D2(L.wy), Lh, dl, nslot_f, 1, beta, j1, k->rtol, maxslots,
+                                      D2(L.part));
+      lz_bound_max<<<gf.x, BT, 0, s>>>(groups, nslot_f, D2(L.part), sym, beta, j1, k->rtol, maxslots,
+                                       maxslots + 1);
+      launches += (j1 - j0) + 5;
+      const int par = c & 1;
+      err = cudaMemcpyAsync(pin + 3 * par, beta + j1, sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (err == cudaSuccess)
+        err = cudaMemcpyAsync(pin + 3 * par + 1, maxslots, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (err == cudaSuccess) err = cudaEventRecord(k->ev[par], s);
+      if (err == cudaSuccess) err = cudaGetLastError();
+      if (err != cudaSuccess) break;
+      if (pending >= 0) {
+        err = evaluate(pending, pending_j1);
+        if (err != cudaSuccess || converged || nonfinite) break;
+      }
+      pending = c;
+      pending_j1 = j1;
+    }
+    if (err == cudaSuccess && !converged && !nonfinite && pending >= 0) err = evaluate(pending, pending_j1);
+    if (err != cudaSuccess) {
+      set_last_error(cudaGetErrorString(err));
+      return REXI_ECUDA;
+    }
+    *bound_out = bound;
+    if (!converged) {
+      set_last_error(nonfinite ? "shared-Krylov depth gradient: non-finite Lanczos scalars"
+                               : "shared-Krylov depth gradient: step cap reached before the error bound");
+      return REXI_ENOCONV;
+    }
+    *kk_out = kk;
+    return REXI_OK;
+  };
+
+  int kA = 0, kB = 0;
+  double bA = 0.0, bB = 0.0;
+  rexi_status st = e == cudaSuccess ? REXI_OK : REXI_ECUDA;
+  if (e != cudaSuccess) set_last_error(cudaGetErrorString(e));
+  if (st == REXI_OK)
+    st = keep_run(dt, static_cast<const double2*>(f_in), 0, D(L.f0), D(L.basA), D(L.alA), D(L.beA), D(L.ibA),
+                  D2(L.sA), D2(L.wA), &kA, &bA);
+  if (st == REXI_OK)  // W^{-1} G under -tau A
+    st = keep_run(-dt, static_cast<const double2*>(g_out), 1, D(L.g0), D(L.basB), D(L.alB), D(L.beB), D(L.ibB),
+                  D2(L.sB), D2(L.wB), &kB, &bB);
+  mark(2);
+  if (st == REXI_OK) {
+    lz_resolvent<<<(np + 127) / 128, 128, 0, s>>>(np, D2(L.sA), D(L.alA), D(L.beA), kA, D2(L.CA));
+    lz_resolvent<<<(np + 127) / 128, 128, 0, s>>>(np, D2(L.sB), D(L.alB), D(L.beB), kB, D2(L.DB));
+    lz_bilinear<<<dim3((kA + 15) / 16, (kB + 15) / 16), 256, 0, s>>>(np, kA, kB, D2(L.CA), D2(L.DB), D2(L.wA),
+                                                                     D(L.beA), D(L.ibA), D(L.beB), D(L.ibB), dt,
+                                                                     D(L.R));
+    launches += 3;
+    mark(3);
+    lz_grad_contract<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(
+        k->nx, k->ny, k->nx / k->Lx, k->ny / k->Ly, D(L.f0), D(L.basA), D(L.g0), D(L.basB), vstride, kA, kB,
+        D(L.R), k->w64, grad_depth);
+    ++launches;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      set_last_error(cudaGetErrorString(e));
+      st = REXI_ECUDA;
+    }
+  }
+  mark(4);
+  if (hooks.launches) *hooks.launches += launches;
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->N = N;
+    info->n_terms = N + 1;
+    info->n_poles = np;
+    info->krylov_iters = std::max(kA, kB);
+    info->krylov_unconverged = st == REXI_ENOCONV ? np : 0;
+    info->krylov_max_rel_res = std::max(bA, bB);
+    info->krylov_term_iters = (int64_t)kA + kB;
+  }
+  return st;
+}
 
 size_t lanczos_workspace_bytes(const KrylovSettings* k, int M, int real_input) {
   const int npc = poles_c(M, real_input);

@@ -17,13 +17,14 @@ from tests.gpu_util import rel_l2, to_dev, torch_cuda
 pytestmark = pytest.mark.gpu
 
 
-def plan_for(torch, H, form="fp64", rtol=1e-13):
+def plan_for(torch, H, form="fp64", rtol=1e-13, method="cg"):
     from paper_2008_11607_gb300 import rexi
 
     ny, nx = H.shape
     Hd = torch.from_numpy(np.ascontiguousarray(H, dtype=np.float64)).cuda()
     p = rexi.Plan(nx, ny, depth=Hd, form=form)
     p.set_krylov(rtol=rtol, max_iters=20000, term_batch=64)
+    p.set_krylov_method(method)
     return p, Hd
 
 
@@ -77,17 +78,18 @@ def _rollout_setup(torch, n=16, seed=0):
     return H, f0, target
 
 
-def test_rollout_gradients_central_differences():
+@pytest.mark.parametrize("method", ["cg", "shared"])
+def test_rollout_gradients_central_differences(method):
     """8 steps of tau rho = 20.3, checkpoints every 2 steps, loss
     1/2 ||eta(T) - eta_target||^2; 16 random state directions and 16 random
     depth directions, central differences with step 1e-6, agreement to 1e-6
-    relative."""
+    relative.  Per-term CG and the shared-Krylov method."""
     torch = torch_cuda()
     from paper_2008_11607_gb300.autograd import rexi_rollout
 
     n, steps = 16, 8
     H, f0, target = _rollout_setup(torch, n)
-    plan, Hd = plan_for(torch, H)
+    plan, Hd = plan_for(torch, H, method=method)
     dt = 20.3 / plan.rho
     tgt = torch.from_numpy(target).cuda()
 
@@ -113,8 +115,8 @@ def test_rollout_gradients_central_differences():
         assert abs(fd - an) <= 1e-6 * abs(an) + 1e-12, (fd, an)
     for _ in range(16):  # depth directions
         d = rng.standard_normal((n, n))
-        pp, _ = plan_for(torch, H + eps * d)
-        pm, _ = plan_for(torch, H - eps * d)
+        pp, _ = plan_for(torch, H + eps * d, method=method)
+        pm, _ = plan_for(torch, H - eps * d, method=method)
         fd = (loss_of(pp, base) - loss_of(pm, base)) / (2 * eps)
         an = float(torch.sum(gH * torch.from_numpy(d).cuda()))
         assert abs(fd - an) <= 1e-6 * abs(an) + 1e-12, (fd, an)

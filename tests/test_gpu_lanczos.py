@@ -248,3 +248,50 @@ def test_shared_full_size_variable_depth(form):
         plan_f, _ = shared_plan(torch, n, n, H, rtol=1e-11, form="fp64")
         ref = plan_f.step(x, dt)
         assert rel_l2(o, ref.cpu().numpy()) < TOL[form]
+
+
+@pytest.mark.parametrize("case", ["10x8", "40x36", "70x50"])
+def test_shared_grad_depth_against_oracle(case):
+    """Depth gradient from the two kept Lanczos bases (real input) against the
+    oracle's per-pole formula and against per-term CG."""
+    from oracle import adjoint as AD
+
+    torch = torch_cuda()
+    nx, ny = {"10x8": (10, 8), "40x36": (40, 36), "70x50": (70, 50)}[case]
+    taurho = {"10x8": 15.3, "40x36": 30.0, "70x50": 25.0}[case]
+    H = inputs.variable_depth(nx, ny, seed=2)
+    plan, _ = shared_plan(torch, nx, ny, H, rtol=1e-13)
+    dt = taurho / plan.rho
+    f0 = inputs.kminus3_field(nx, ny, seed=3)
+    G = inputs.complex_random_state(nx, ny, seed=4).real.astype(np.complex128)
+    got, info = plan.grad_depth(to_dev(torch, f0), to_dev(torch, G), dt, want_info=True)
+    assert 0 < info.krylov_iters < 20000
+    ref = AD.grad_depth_sparse(nx, ny, H, f0.ravel(), G.ravel(), dt, 0.5, info.M)
+    assert rel_l2(got.cpu().numpy(), ref) < 1e-9, rel_l2(got.cpu().numpy(), ref)
+    plan.set_krylov_method("cg")
+    cg = plan.grad_depth(to_dev(torch, f0), to_dev(torch, G), dt)
+    assert rel_l2(got.cpu().numpy(), cg.cpu().numpy()) < 1e-9
+
+
+def test_shared_autograd_rollout_matches_cg():
+    """A checkpointed 4-step rollout with the shared method gives the same state
+    and depth gradients as per-term CG."""
+    from paper_2008_11607_gb300.autograd import rexi_rollout
+
+    torch = torch_cuda()
+    n = 24
+    H = inputs.variable_depth(n, n, seed=0)
+    f0 = inputs.kminus3_field(n, n, seed=1)
+    target = torch.from_numpy(inputs.kminus3_field(n, n, seed=1000)[0].real.copy()).cuda()
+    grads = {}
+    for method in ("shared", "cg"):
+        plan, Hd = shared_plan(torch, n, n, H, rtol=1e-13)
+        plan.set_krylov_method(method)
+        Hd.requires_grad_(True)
+        x = to_dev(torch, f0).requires_grad_(True)
+        dt = 20.0 / plan.rho
+        out = rexi_rollout(x, plan, dt, 4, every=2, depth=Hd)
+        loss = 0.5 * torch.sum((out[0].real - target) ** 2)
+        grads[method] = [g.cpu().numpy() for g in torch.autograd.grad(loss, [x, Hd])]
+    for a, b in zip(grads["shared"], grads["cg"]):
+        assert rel_l2(a, b) < 1e-8
