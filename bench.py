@@ -38,10 +38,11 @@ N_SEEDS = 10
 METRIC = "grid-points×poles solved/sec and HBM GB/s vs roofline at stated error vs FP64 oracle"
 UNIT = "grid-points*poles/s"
 
-# Per-term work of the fused pole loops, counted from the kernel source
+# Per-term work of the pole-sum loops, counted from the kernel source
 # (csrc/pole_common.cuh).  mixed: 73 FP32 arithmetic instructions per term, 12
 # of them FFMA -> 85 flops; fp64: 8 DFMA + 1 DADD -> 17 flops.  One MUFU
-# reciprocal seed per term in both.
+# reciprocal seed per term in both.  The sum runs once per orbit of omega's
+# symmetries ((+-kx, +-ky) and kx <-> ky on the square grid).
 FLOPS_PER_TERM = {"mixed": 85, "fp64": 17}
 FP32_INSTR_PER_TERM = 73
 FP64_INSTR_PER_TERM = 9
@@ -52,10 +53,17 @@ SMS = 152
 SM_MAX_GHZ = 2.07
 PEAK_FP32_TFLOPS = SMS * 128 * 2 * SM_MAX_GHZ / 1e3
 PEAK_FP64_TFLOPS = 1.25
-# DRAM traffic of the pole kernel per launch from an ncu capture of this
-# kernel on the 2048^2 grid (profiles/pole_fused_mixed_2048_tau50.md: same grid and
-# bytes, fewer terms; traffic does not depend on the term count); None if not captured.
-NCU_POLE_TRAFFIC_BYTES = {"mixed": 201.470720e6 + 140.511744e6, "fp64": None}
+# DRAM traffic per launch of the pole-sum kernel and of the combine pass from
+# ncu captures on the 2048^2 grid (the traffic does not depend on the term
+# count); None where no capture of the current kernel exists.
+NCU_POLE_TRAFFIC_BYTES = {"mixed": None, "fp64": None}
+NCU_COMBINE_TRAFFIC_BYTES = None
+
+
+def orbit_count(n):
+    """Orbits of the n x n wavenumber grid under omega's symmetries."""
+    a = n // 2 + 1
+    return a * (a + 1) // 2
 
 
 def set_workload(grid, tau_rho):
@@ -440,9 +448,9 @@ def batch_measure(torch, rexi, inputs, form="mixed", reps=5):
     return {
         "workload": "96 constant-depth instances, D uniform from {128,192,256,384,512}, tau*rho log-uniform in "
                     "[20, 800] (M %d..%d), |k|^-3 eta seeds 0-95, real input, form=%s" % (min(b.M), max(b.M), form),
-        "unit": UNIT, "units_per_step": units, "autotuned": {"threads": t, "pairs_per_thread": ppt,
+        "unit": UNIT, "units_per_step": units, "autotuned": {"threads": t, "orbits_per_thread": ppt,
                                                              "ctas": info["ctas"], "work_items": info["n_items"]},
-        "terms_x_pairs": info["terms_pairs"], **res,
+        "terms_x_orbits": info["terms_orbits"], **res,
         "speedup_persistent_vs_per_instance": res["per_instance"]["ms_per_step"] / res["persistent_graph"]["ms_per_step"],
     }
 
@@ -550,10 +558,11 @@ def run_ours(args):
     ms_max = max_over_ranks(world, ms)
     value = world * units / (ms_max / 1e3)
     ms_phase, ncalls, nlaunch = prof
-    pole_ms = ms_phase[1] / max(ncalls, 1)
-    pairs = D * (D // 2 + 1)
+    combine_ms = ms_phase[4] / max(ncalls, 1)
+    pole_ms = ms_phase[1] / max(ncalls, 1) - combine_ms  # the pole-sum kernel alone
+    orbits = orbit_count(D)
     nterms = 2 * (M + 24) + 1
-    terms = pairs * nterms
+    terms = orbits * nterms
     t_pole = pole_ms / 1e3
     if args.form == "mixed":
         # every FP32 arithmetic operation counted once (the kernel is FADD-heavy:
@@ -568,16 +577,18 @@ def run_ours(args):
         conv = "FP64 operations per launch (DADD/DFMA each 1; 9 per term) vs nominal 1.25 TFLOP/s / 2"
     achieved = ops / t_pole / 1e12
     roofline = {
-        "kernel": "pole_fused_%s_kernel" % args.form,
+        "kernel": "pole_orbit_%s_kernel" % args.form,
         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
         "traffic": NCU_POLE_TRAFFIC_BYTES.get(args.form),
         "flop_convention": conv,
         "fma2_tflops": terms * FLOPS_PER_TERM[args.form] / t_pole / 1e12,
         "fma2_peak": PEAK_FP32_TFLOPS if args.form == "mixed" else PEAK_FP64_TFLOPS,
         "pole_ms_per_launch": pole_ms,
+        "orbits": orbits,
         "terms_per_launch": terms,
+        "peak_source": "derived from unit counts and the maximum SM clock (no measured ALU peak on file)",
     }
-    phases = {"forward_fft_ms": ms_phase[0] / max(ncalls, 1), "pole_ms": pole_ms,
+    phases = {"forward_fft_ms": ms_phase[0] / max(ncalls, 1), "pole_sum_ms": pole_ms, "combine_ms": combine_ms,
               "inverse_fft_ms": ms_phase[2] / max(ncalls, 1), "table_upload_ms": ms_phase[3] / max(ncalls, 1)}
     # HBM roofline of the FFT passes (2 passes each way, each reads + writes 3 fields)
     fft_bytes = 2 * 2 * 3 * D * D * 16
@@ -592,6 +603,13 @@ def run_ours(args):
                     "achieved": fwd_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": fwd_gbs / hbm_peak,
                     "traffic": None,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in mp else "fallback 6.8 TB/s"}
+    # combine pass: reads and writes the 3-field spectrum (96 B per wavenumber);
+    # the per-orbit sums it also reads are L2-resident and not counted
+    comb_bytes = 3 * D * D * 16 * 2
+    comb_gbs = comb_bytes / (combine_ms / 1e3) / 1e9 if combine_ms > 0 else None
+    roofline_combine = {"kernel": "pole_orbit_combine_kernel", "bound": "hbm", "achieved": comb_gbs,
+                        "peak": hbm_peak, "unit": "GB/s", "frac": comb_gbs / hbm_peak if comb_gbs else None,
+                        "traffic": NCU_COMBINE_TRAFFIC_BYTES, "algorithmic_bytes": comb_bytes}
 
     # end-to-end through the host-buffer C-ABI call (pinned host memory)
     e2e = None
@@ -668,7 +686,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32x2+f64" if args.form == "mixed" else "f64", "data": "synthetic",
             "config": cfg, "clocks": clocks, "e2e": e2e, "gpu_launches": nlaunch, "roofline": roofline,
-            "roofline_fft": roofline_fft, "phases_ms": phases, "forms": forms, "batched": batched, "krylov": krylov,
+            "roofline_fft": roofline_fft, "roofline_combine": roofline_combine, "phases_ms": phases, "forms": forms, "batched": batched, "krylov": krylov,
             "differentiation": differentiation,
             "cpu_baseline": cpu,
             "accuracy": {"tolerance": 1e-8 if args.form == "mixed" else 1e-10,

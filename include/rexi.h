@@ -265,15 +265,17 @@ rexi_status rexi_workspace_size_host(rexi_plan_t plan, double dt, double tol, in
 
 /* Device-side phase timing of rexi_step calls: with profiling enabled, each
  * call records CUDA events on its own stream around its phases.
- * rexi_plan_read_profile waits for the recorded events, returns the summed
- * milliseconds per phase since the last read (ms[0] forward transform or
- * Krylov set-up, ms[1] the pole loop over all terms (Krylov: the CG
- * iterations), ms[2] inverse transform or final accumulation, ms[3] table
- * upload), the number of profiled phase sets (one per call on the Fourier
- * path, one per term batch on the Krylov path) and of kernels launched,
- * then resets the sums. */
+ * rexi_plan_read_profile waits for the recorded events, fills ms5 (5
+ * doubles) with the summed milliseconds per phase since the last read
+ * (ms[0] forward transform or Krylov set-up, ms[1] the pole loop over all
+ * terms including the combine pass (Krylov: the CG iterations), ms[2]
+ * inverse transform or final accumulation, ms[3] table upload, ms[4] the
+ * part of ms[1] spent in the per-wavenumber combine pass of the FP64 and
+ * mixed Fourier forms, 0 elsewhere), returns the number of profiled phase
+ * sets (one per call on the Fourier path, one per term batch on the Krylov
+ * path) and of kernels launched, then resets the sums. */
 rexi_status rexi_plan_set_profiling(rexi_plan_t plan, int32_t enable);
-rexi_status rexi_plan_read_profile(rexi_plan_t plan, double* ms4, int32_t* n_calls, int64_t* n_launches);
+rexi_status rexi_plan_read_profile(rexi_plan_t plan, double* ms5, int32_t* n_calls, int64_t* n_launches);
 
 /* Constant-depth step that allocates nothing, for callers that may not
  * allocate device memory (code running inside another allocator's hooks or
@@ -312,7 +314,8 @@ rexi_status rexi_step_noalloc(int32_t nx, int32_t ny, double Lx, double Ly, doub
 typedef struct rexi_batch_s* rexi_batch_t;
 
 enum {
-  REXI_BATCH_PERSISTENT = 0,  /* one persistent pole kernel over all instances, whole step replayed from a CUDA graph */
+  REXI_BATCH_PERSISTENT = 0,  /* one persistent pole kernel over all instances, one combine launch, whole step
+                                 replayed from a CUDA graph */
   REXI_BATCH_PER_INSTANCE = 1 /* FFT, pole and inverse-FFT launches instance by instance */
 };
 
@@ -334,19 +337,22 @@ rexi_status rexi_batch_layout(rexi_batch_t batch, int64_t* offsets, int32_t* M_o
 rexi_status rexi_batch_step(rexi_batch_t batch, const void* in_dev, void* out_dev, int32_t real_input,
                             void* workspace_dev, size_t workspace_bytes, int32_t mode, void* stream);
 
-/* Times the persistent mode for CTA sizes {64, 128, 256} x pairs per thread
- * {1, 2} on the given buffers (a few steps each; results are overwritten) and
- * keeps the fastest.  Outputs (each nullable): the chosen configuration and
- * its time per step in milliseconds. */
+/* Times the persistent mode for CTA sizes {64, 128, 256} x orbits per
+ * thread {1, 2} on the given buffers (a few steps each; results are
+ * overwritten) and keeps the fastest.  An orbit is the set of wavenumbers
+ * (+-kx, +-ky), and (+-ky, +-kx) on square grids with equal spacing, which
+ * share omega(k) and hence the pole sum.  Outputs (each nullable): the chosen
+ * configuration and its time per step in milliseconds. */
 rexi_status rexi_batch_autotune(rexi_batch_t batch, const void* in_dev, void* out_dev, int32_t real_input,
                                 void* workspace_dev, size_t workspace_bytes, void* stream, int32_t* threads,
-                                int32_t* pairs_per_thread, double* best_ms);
+                                int32_t* orbits_per_thread, double* best_ms);
 
-/* Current configuration and counters (each nullable): CTA size, pairs per
+/* Current configuration and counters (each nullable): CTA size, orbits per
  * thread, persistent CTAs launched, work items, sum over instances of
- * wavenumber pairs x scalar terms, kernels launched so far. */
-rexi_status rexi_batch_info(rexi_batch_t batch, int32_t* threads, int32_t* pairs_per_thread, int32_t* ctas,
-                            int32_t* n_items, int64_t* terms_pairs, int64_t* launches);
+ * wavenumber orbits x scalar terms (the pole-sum evaluations of one step),
+ * kernels launched so far. */
+rexi_status rexi_batch_info(rexi_batch_t batch, int32_t* threads, int32_t* orbits_per_thread, int32_t* ctas,
+                            int32_t* n_items, int64_t* terms_orbits, int64_t* launches);
 
 /* Human-readable name of a status code (static string). */
 const char* rexi_status_string(rexi_status status);

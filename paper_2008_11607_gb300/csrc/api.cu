@@ -57,6 +57,11 @@ struct rexi_plan_s {
   double2* tw_y = nullptr;
   float4* twf_x = nullptr;  // double-float twiddles (mixed form)
   float4* twf_y = nullptr;
+  // half-length x plan for real input (nx = 2 m even, m >= 2)
+  FftPlan1D fxh;
+  bool r2c = false;
+  double2* tw_xh = nullptr;
+  float4* twf_xh = nullptr;
   double2* half_x = nullptr;
   double2* half_y = nullptr;
   // coefficient staging (pinned host) guarded by an event
@@ -66,8 +71,10 @@ struct rexi_plan_s {
   bool staging_pending = false;
   // Krylov path
   KrylovSettings kry;
-  // profiling: per call 5 events (start, after upload, after forward, after poles, end)
+  // profiling: per call 6 events (start, after upload, after forward, after
+  // poles, end, and between the pole sum and the combine pass)
   bool prof_on = false;
+  bool prof_mid = false;
   std::vector<std::vector<cudaEvent_t>> prof_pool;
   size_t prof_used = 0;
   int64_t launches = 0;
@@ -79,12 +86,16 @@ void prof_mark(rexi_plan_s* p, int i, cudaStream_t s) {
   if (!p->prof_on) return;
   if (i == 0) {
     if (p->prof_used == p->prof_pool.size()) {
-      std::vector<cudaEvent_t> set(5, nullptr);
+      std::vector<cudaEvent_t> set(6, nullptr);
       for (auto& e : set) cudaEventCreate(&e);
       p->prof_pool.push_back(set);
     }
     ++p->prof_used;
+    p->prof_mid = false;
   }
+  if (i == 5) p->prof_mid = true;
+  // paths without a separate combine pass: the combine phase is empty
+  if (i == 3 && !p->prof_mid) cudaEventRecord(p->prof_pool[p->prof_used - 1][5], s);
   cudaEventRecord(p->prof_pool[p->prof_used - 1][i], s);
 }
 }  // namespace
@@ -193,6 +204,8 @@ void rexi_plan_destroy(rexi_plan_t p) {
   cudaFree(p->tw_y);
   cudaFree(p->twf_x);
   cudaFree(p->twf_y);
+  cudaFree(p->tw_xh);
+  cudaFree(p->twf_xh);
   cudaFree(p->half_x);
   cudaFree(p->half_y);
   if (p->staging) cudaFreeHost(p->staging);
@@ -267,6 +280,22 @@ rexi_status rexi_plan_create(rexi_plan_t* out, int32_t nx, int32_t ny, double Lx
       }
       p->fx.twf = p->twf_x;
       p->fy.twf = p->twf_y;
+    }
+    if (nx % 2 == 0 && fft_factor(nx / 2, &p->fxh)) {  // real-input transforms along x
+      const int m = nx / 2;
+      std::vector<double2> twh(m), twh4(m);
+      for (int t = 0; t < m; ++t) {
+        const double a = 2.0 * M_PI * (double)t / (double)m;
+        twh[t] = make_double2(cos(a), -sin(a));
+      }
+      split_twiddles(twh.data(), m, reinterpret_cast<float4*>(twh4.data()));
+      if (!upload_table(twh, &p->tw_xh, &st) || !upload_table(twh4, reinterpret_cast<double2**>(&p->twf_xh), &st)) {
+        rexi_plan_destroy(p);
+        return st;
+      }
+      p->fxh.tw = p->tw_xh;
+      p->fxh.twf = p->twf_xh;
+      p->r2c = true;
     }
     // rho(A): largest omega over the discrete wavenumbers (exact for constant depth)
     std::vector<double> sx2(nx), cx2(nx);
@@ -347,9 +376,11 @@ rexi_status rexi_plan_set_krylov(rexi_plan_t p, double rtol, int32_t max_iters, 
 namespace {
 
 struct FourierLayout {
-  int M, N, nterms_scalar, nterms_plain;
-  size_t table_off, table_bytes, spec_off, acc_off, chunk_off, chunk_terms, total;
+  int M, N, nterms_scalar, nterms_plain, slice_cap;
+  size_t table_off, table_bytes, spec_off, acc_off, chunk_off, chunk_terms, part_off, total;
 };
+
+SymbolParams symbol_params(const rexi_plan_s* p);
 
 constexpr size_t kPlainChunkBudget = size_t(8) << 30;  // bytes of materialised terms per chunk
 
@@ -370,6 +401,14 @@ FourierLayout fourier_layout(const rexi_plan_s* p, int M, int real_input) {
   L.acc_off = end;
   L.chunk_off = end;
   L.chunk_terms = 0;
+  L.part_off = end;
+  L.slice_cap = 0;
+  if (p->form != REXI_FORM_PLAIN) {
+    // per-orbit partial sums of the pole loop, one row per term slice
+    const OrbitParams op = orbit_params(symbol_params(p));
+    L.slice_cap = orbit_slice_cap(op.norb);
+    end += align_up((size_t)L.slice_cap * op.norb * sizeof(double2), 256);
+  }
   if (p->form == REXI_FORM_PLAIN) {
     L.acc_off = end;
     end += align_up(nk3 * sizeof(double2), 256);
@@ -455,13 +494,19 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
   const size_t nk = (size_t)p->nx * p->ny;
   rexi_status st;
 
+  // real input on the C-grid: half spectrum (kx = 0..nx/2) through real
+  // transforms along x; the pole step there is the Hermitian part of the
+  // full-spectrum step (the real part the full path takes at the end)
+  const bool half = real_input && p->r2c && !p->spectral && p->form != REXI_FORM_PLAIN;
+  const int df = p->form == REXI_FORM_MIXED ? 1 : 0;
   prof_mark(p, 0, s);
   const double2* in2 = static_cast<const double2*>(in);
   auto forward = [&]() -> rexi_status {
     prof_mark(p, 1, s);
     // forward transform (imaginary parts dropped for real input)
-    CUDA_TRY(p->form == REXI_FORM_MIXED ? fft2d_df(in2, spec, 3, p->fx, p->fy, -1, 1.0, real_input, 0, s)
-                                        : fft2d(in2, spec, 3, p->fx, p->fy, -1, 1.0, real_input, 0, s),
+    CUDA_TRY(half ? fft2d_r2c(in2, spec, 3, p->fx, p->fxh, p->fy, df, s)
+             : df ? fft2d_df(in2, spec, 3, p->fx, p->fy, -1, 1.0, real_input, 0, s)
+                  : fft2d(in2, spec, 3, p->fx, p->fy, -1, 1.0, real_input, 0, s),
              "forward FFT");
     p->launches += 2;
     prof_mark(p, 2, s);
@@ -487,6 +532,14 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
     fs.R0im = R0i;
     fs.nterms = (int)sel.size();
     fs.adjoint = adjoint ? 1 : 0;
+    // With the real part of the step taken (real input), r(0) enters through
+    // its real part: Re r(tau B) = Re(R0) I + Im(R+) Bt + (Re R0 - Re R+) Bt^2
+    // on the C-grid, where B(-k) = conj B(k).
+    if (half) fs.R0im = 0.0;
+    const int row_len = half ? p->nx / 2 + 1 : p->nx;
+    const OrbitParams op = orbit_params(sp);
+    const int slices = pole_orbit_slices(p->form, op.norb, fs.nterms, L.slice_cap);
+    double2* part = reinterpret_cast<double2*>(base + L.part_off);
     if (p->form == REXI_FORM_FP64) {
       std::vector<double> tab(6 * std::max<size_t>(sel.size(), 1), 0.0);
       for (size_t t = 0; t < sel.size(); ++t) {
@@ -501,9 +554,11 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
       }
       if ((st = stage_upload(p, tab.data(), tab.size() * sizeof(double), base + L.table_off, s)) != REXI_OK) return st;
       if ((st = forward()) != REXI_OK) return st;
-      CUDA_TRY(pole_fused_fp64(spec, sp, reinterpret_cast<const double*>(base + L.table_off), fs, s),
-               "pole_fused_fp64");
-      p->launches += 1;
+      CUDA_TRY(pole_orbits_fp64(part, slices, sp, op, reinterpret_cast<const double*>(base + L.table_off), fs, s),
+               "pole_orbits_fp64");
+      prof_mark(p, 5, s);
+      CUDA_TRY(pole_orbit_combine(spec, part, slices, sp, op, fs, row_len, s), "pole_orbit_combine");
+      p->launches += 2;
     } else {
       // grid G = 2^-g so that |x| + h N < 2^24 G: x <= tau rho
       const double span = dt * p->rho + h * N + 4.0;
@@ -532,9 +587,11 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
       }
       if ((st = stage_upload(p, tab.data(), tab.size() * sizeof(float), base + L.table_off, s)) != REXI_OK) return st;
       if ((st = forward()) != REXI_OK) return st;
-      CUDA_TRY(pole_fused_mixed(spec, sp, reinterpret_cast<const float*>(base + L.table_off), fs, G, s),
-               "pole_fused_mixed");
-      p->launches += 1;
+      CUDA_TRY(pole_orbits_mixed(part, slices, sp, op, reinterpret_cast<const float*>(base + L.table_off), fs, G, s),
+               "pole_orbits_mixed");
+      prof_mark(p, 5, s);
+      CUDA_TRY(pole_orbit_combine(spec, part, slices, sp, op, fs, row_len, s), "pole_orbit_combine");
+      p->launches += 2;
     }
   } else {
     // plain form: terms n = 0..N (real) or -N..N (complex), |n| in [tb, te)
@@ -580,9 +637,9 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
   }
   prof_mark(p, 3, s);
   // inverse transform, 1/(nx ny), real part for real input
-  CUDA_TRY(p->form == REXI_FORM_MIXED
-               ? fft2d_df(spec, static_cast<double2*>(out), 3, p->fx, p->fy, +1, 1.0 / (double)nk, 0, real_input, s)
-               : fft2d(spec, static_cast<double2*>(out), 3, p->fx, p->fy, +1, 1.0 / (double)nk, 0, real_input, s),
+  CUDA_TRY(half ? fft2d_c2r(spec, static_cast<double2*>(out), 3, p->fx, p->fxh, p->fy, 1.0 / (double)nk, df, s)
+           : df ? fft2d_df(spec, static_cast<double2*>(out), 3, p->fx, p->fy, +1, 1.0 / (double)nk, 0, real_input, s)
+                : fft2d(spec, static_cast<double2*>(out), 3, p->fx, p->fy, +1, 1.0 / (double)nk, 0, real_input, s),
            "inverse FFT");
   p->launches += 2;
   prof_mark(p, 4, s);
@@ -706,18 +763,18 @@ rexi_status rexi_plan_set_profiling(rexi_plan_t p, int32_t enable) {
   return REXI_OK;
 }
 
-rexi_status rexi_plan_read_profile(rexi_plan_t p, double* ms4, int32_t* n_calls, int64_t* n_launches) {
+rexi_status rexi_plan_read_profile(rexi_plan_t p, double* ms5, int32_t* n_calls, int64_t* n_launches) {
   g_err[0] = 0;
-  if (!p || !ms4) return fail(REXI_EINVAL, "NULL argument");
-  for (int i = 0; i < 4; ++i) ms4[i] = 0.0;
+  if (!p || !ms5) return fail(REXI_EINVAL, "NULL argument");
+  for (int i = 0; i < 5; ++i) ms5[i] = 0.0;
   for (size_t k = 0; k < p->prof_used; ++k) {
     auto& e = p->prof_pool[k];
     CUDA_TRY(cudaEventSynchronize(e[4]), "profile event");
     float t;
-    const int map[4][2] = {{1, 2}, {2, 3}, {3, 4}, {0, 1}};
-    for (int ph = 0; ph < 4; ++ph) {
+    const int map[5][2] = {{1, 2}, {2, 3}, {3, 4}, {0, 1}, {5, 3}};
+    for (int ph = 0; ph < 5; ++ph) {
       CUDA_TRY(cudaEventElapsedTime(&t, e[map[ph][0]], e[map[ph][1]]), "profile elapsed");
-      ms4[ph] += t;
+      ms5[ph] += t;
     }
   }
   if (n_calls) *n_calls = (int32_t)p->prof_used;

@@ -1,15 +1,19 @@
 // Batched serving launch: many independent constant-depth instances (own grid
 // size, own time step, hence own pole count) advanced together.
 //
-// Work is split into items of `threads * pairs_per_thread` wavenumber pairs of
-// one instance; an item costs (pairs x scalar terms).  Items are sorted by
-// cost, largest first, and one persistent kernel (a few CTAs per SM) pulls
-// them from an atomic counter, so that small and large instances fill the GPU
-// together instead of one small launch after another.  The forward and
+// The pole sum depends on a wavenumber only through omega(k), so it is
+// evaluated once per orbit of omega's symmetries (k -> -k per axis, and
+// kx <-> ky on square grids; see OrbitParams).  Work is split into items of
+// `threads * orbits_per_thread` orbits of one instance; an item costs
+// (orbits x scalar terms).  Items are sorted by cost, largest first, and one
+// persistent kernel (a few CTAs per SM) pulls them from an atomic counter, so
+// that small and large instances fill the GPU together instead of one small
+// launch after another; it writes R+ per orbit, and one combine launch over
+// every wavenumber of every instance applies r(tau B).  The forward and
 // inverse FFTs run once per distinct grid size over all instances of that
 // size (they are packed next to each other).  The whole sequence is captured
 // once in a CUDA graph on a stream owned by the batch and replayed.  The
-// persistent kernel's CTA size and pairs per thread are chosen by timing the
+// persistent kernel's CTA size and orbits per thread are chosen by timing the
 // candidates (rexi_batch_autotune).  The per-instance mode launches the
 // single-instance kernels instance by instance, for comparison.
 #include <math.h>
@@ -27,7 +31,9 @@ namespace {
 
 struct InstDesc {
   long long spec_off;  // first element of this instance's spectrum (field 0)
+  long long orb_off;   // first entry of this instance's per-orbit R+ table
   int nx, ny, nterms, pad;
+  int ax, ay, sym, norb;  // OrbitParams of the instance's grid
   double inv_dx, inv_dy, tau, q, R0re, R0im, grid;
   float q_hi, q_lo;
   long long table_off;  // first table entry (3 x 16 bytes per term)
@@ -36,7 +42,7 @@ struct InstDesc {
 };
 
 struct WorkItem {
-  int inst, pair_begin;
+  int inst, orbit_begin;
 };
 
 struct SizeGroup {
@@ -63,9 +69,12 @@ struct rexi_batch_s {
   rexi::InstDesc* d_desc = nullptr;
   rexi::WorkItem* d_items = nullptr;
   int n_items = 0;
-  int item_pairs = 0;            // pairs per work item the items were built for
+  int item_orbits = 0;           // orbits per work item the items were built for
+  int* d_blk = nullptr;          // first combine block of each instance (n + 1 entries)
+  int combine_blocks = 0;
+  long long total_orbits = 0;
   std::vector<rexi::InstDesc> h_desc;
-  long long total_terms_pairs = 0;
+  long long total_terms_orbits = 0;
   // launch configuration of the persistent kernel
   int threads = 128, ppt = 1, ctas = 0;
   // graph replay
@@ -85,9 +94,9 @@ namespace {
 // ---- persistent kernel ------------------------------------------------------
 
 template <int FORM, int PPT>
-__global__ void batch_pole_kernel(double2* spec, const InstDesc* __restrict__ desc,
+__global__ void batch_pole_kernel(double2* orb, const InstDesc* __restrict__ desc,
                                   const WorkItem* __restrict__ items, int n_items, unsigned* counter,
-                                  const void* __restrict__ tables, double g, double f, double H, int adjoint) {
+                                  const void* __restrict__ tables, double g, double f, double H) {
   __shared__ float4 st[kChunk * 3];  // 48 bytes per term, both forms
   __shared__ int s_item;
   __shared__ InstDesc D;
@@ -109,18 +118,19 @@ __global__ void batch_pole_kernel(double2* spec, const InstDesc* __restrict__ de
     sp.H = H;
     sp.half_x = D.half_x;
     sp.half_y = D.half_y;
-    const int npairs = D.nx * (D.ny / 2 + 1);
-    int kx[PPT], ky[PPT], kx2[PPT], ky2[PPT];
-    bool active[PPT];
-    Symbol S[PPT];
+    OrbitParams op;
+    op.ax = D.ax;
+    op.ay = D.ay;
+    op.sym = D.sym;
+    op.norb = D.norb;
+    int o[PPT];
     double x[PPT];
 #pragma unroll
     for (int u = 0; u < PPT; ++u) {
-      const int p = items[it].pair_begin + u * blockDim.x + threadIdx.x;
-      kx[u] = ky[u] = kx2[u] = ky2[u] = 0;
-      active[u] = p < npairs && pair_of(p, D.nx, D.ny, kx[u], ky[u], kx2[u], ky2[u]);
-      S[u] = symbol_at(sp, active[u] ? kx[u] : 0, active[u] ? ky[u] : 0);
-      x[u] = D.tau * S[u].omega;
+      o[u] = items[it].orbit_begin + u * blockDim.x + threadIdx.x;
+      int a = 0, b = 0;
+      if (o[u] < D.norb) orbit_rep(op, o[u], a, b);
+      x[u] = D.tau * symbol_at(sp, a, b).omega;
     }
     double ar[PPT], ai[PPT];
     float arh[PPT], arl[PPT], aih[PPT], ail[PPT], Xh[PPT], Xl[PPT], Xl2[PPT];
@@ -153,25 +163,55 @@ __global__ void batch_pole_kernel(double2* spec, const InstDesc* __restrict__ de
             df_term(st + 3 * t, Xh[u], Xl[u], Xl2[u], D.q_hi, D.q_lo, arh[u], arl[u], aih[u], ail[u]);
       }
     }
-    double2* sp_inst = spec + D.spec_off;
-    const size_t fstride = (size_t)D.nx * D.ny;
-    const double2 R0 = make_double2(D.R0re, D.R0im);
 #pragma unroll
     for (int u = 0; u < PPT; ++u) {
-      if (!active[u]) continue;
-      const double2 Rp = FORM == REXI_FORM_FP64
-                             ? make_double2(ar[u], ai[u])
-                             : make_double2((double)arh[u] + (double)arl[u], (double)aih[u] + (double)ail[u]);
-      combine(sp_inst, (size_t)ky[u] * D.nx + kx[u], fstride, S[u], sp, false, adjoint != 0, R0, Rp);
-      if (kx2[u] != kx[u] || ky2[u] != ky[u])
-        combine(sp_inst, (size_t)ky2[u] * D.nx + kx2[u], fstride, symbol_at(sp, kx2[u], ky2[u]), sp, false,
-                adjoint != 0, R0, Rp);
+      if (o[u] >= D.norb) continue;
+      orb[D.orb_off + o[u]] = FORM == REXI_FORM_FP64
+                                  ? make_double2(ar[u], ai[u])
+                                  : make_double2((double)arh[u] + (double)arl[u], (double)aih[u] + (double)ail[u]);
     }
   }
 }
 
+// r(tau B) at every wavenumber of every instance from its orbit's R+.
+// Instance i owns combine blocks [blk[i], blk[i + 1]).
+__global__ void __launch_bounds__(256) batch_combine_kernel(double2* spec, const double2* __restrict__ orb,
+                                                            const InstDesc* __restrict__ desc,
+                                                            const int* __restrict__ blk, int n, double g, double f,
+                                                            double H, int adjoint) {
+  int lo = 0, hi = n - 1;  // last instance with blk[i] <= blockIdx.x
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (blk[mid] <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
+  }
+  const InstDesc& D = desc[lo];
+  const int nk = D.nx * D.ny;
+  const int k = ((int)blockIdx.x - blk[lo]) * blockDim.x + threadIdx.x;
+  if (k >= nk) return;
+  SymbolParams sp;
+  sp.nx = D.nx;
+  sp.ny = D.ny;
+  sp.inv_dx = D.inv_dx;
+  sp.inv_dy = D.inv_dy;
+  sp.g = g;
+  sp.f = f;
+  sp.H = H;
+  sp.half_x = D.half_x;
+  sp.half_y = D.half_y;
+  OrbitParams op;
+  op.ax = D.ax;
+  op.ay = D.ay;
+  op.sym = D.sym;
+  op.norb = D.norb;
+  const int ky = k / D.nx, kx = k - ky * D.nx;
+  const double2 Rp = orb[D.orb_off + orbit_of(op, D.nx, D.ny, kx, ky)];
+  combine(spec + D.spec_off, (size_t)k, (size_t)nk, symbol_at(sp, kx, ky), sp, false, adjoint != 0,
+          make_double2(D.R0re, D.R0im), Rp);
+}
+
 template <int FORM, int PPT>
-cudaError_t launch_persistent(rexi_batch_s* b, double2* spec, unsigned* counter, int threads, cudaStream_t s) {
+cudaError_t launch_persistent(rexi_batch_s* b, double2* orb, unsigned* counter, int threads, cudaStream_t s) {
   auto kern = batch_pole_kernel<FORM, PPT>;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
@@ -181,38 +221,52 @@ cudaError_t launch_persistent(rexi_batch_s* b, double2* spec, unsigned* counter,
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int ctas = std::max(1, std::min(per_sm * sms, b->n_items));
   b->ctas = ctas;
-  kern<<<ctas, threads, 0, s>>>(spec, b->d_desc, b->d_items, b->n_items, counter, b->d_tables, b->g, b->f, b->H,
-                                0);
+  kern<<<ctas, threads, 0, s>>>(orb, b->d_desc, b->d_items, b->n_items, counter, b->d_tables, b->g, b->f, b->H);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pole(rexi_batch_s* b, double2* spec, unsigned* counter, cudaStream_t s) {
+cudaError_t launch_pole(rexi_batch_s* b, double2* orb, unsigned* counter, cudaStream_t s) {
   if (b->form == REXI_FORM_FP64)
-    return b->ppt == 2 ? launch_persistent<REXI_FORM_FP64, 2>(b, spec, counter, b->threads, s)
-                       : launch_persistent<REXI_FORM_FP64, 1>(b, spec, counter, b->threads, s);
-  return b->ppt == 2 ? launch_persistent<REXI_FORM_MIXED, 2>(b, spec, counter, b->threads, s)
-                     : launch_persistent<REXI_FORM_MIXED, 1>(b, spec, counter, b->threads, s);
+    return b->ppt == 2 ? launch_persistent<REXI_FORM_FP64, 2>(b, orb, counter, b->threads, s)
+                       : launch_persistent<REXI_FORM_FP64, 1>(b, orb, counter, b->threads, s);
+  return b->ppt == 2 ? launch_persistent<REXI_FORM_MIXED, 2>(b, orb, counter, b->threads, s)
+                     : launch_persistent<REXI_FORM_MIXED, 1>(b, orb, counter, b->threads, s);
+}
+
+cudaError_t launch_combine(rexi_batch_s* b, double2* spec, const double2* orb, cudaStream_t s) {
+  batch_combine_kernel<<<b->combine_blocks, 256, 0, s>>>(spec, orb, b->d_desc, b->d_blk, b->n, b->g, b->f, b->H, 0);
+  return cudaGetLastError();
 }
 
 size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 
-// Workspace: [counter (256 B)][packed spectrum]
-size_t batch_ws_bytes(const rexi_batch_s* b) { return 256 + al256((size_t)b->offsets[b->n] * sizeof(double2)); }
+// Workspace: [counter (256 B)][packed spectrum][per-orbit R+ of every instance]
+size_t batch_spec_bytes(const rexi_batch_s* b) { return al256((size_t)b->offsets[b->n] * sizeof(double2)); }
+// The R+ region also serves the per-instance mode, one instance at a time,
+// with that instance's term slices.
+size_t batch_orb_entries(const rexi_batch_s* b) {
+  size_t m = (size_t)b->total_orbits;
+  for (const auto& D : b->h_desc) m = std::max(m, (size_t)orbit_slice_cap(D.norb) * D.norb);
+  return m;
+}
+size_t batch_ws_bytes(const rexi_batch_s* b) {
+  return 256 + batch_spec_bytes(b) + al256(batch_orb_entries(b) * sizeof(double2));
+}
 
 // (Re)build the work items for the current item size, largest cost first.
 cudaError_t build_items(rexi_batch_s* b) {
-  const int item_pairs = b->threads * b->ppt;
-  if (item_pairs == b->item_pairs && b->d_items) return cudaSuccess;
+  const int item_orbits = b->threads * b->ppt;
+  if (item_orbits == b->item_orbits && b->d_items) return cudaSuccess;
   struct Cost {
     long long cost;
     WorkItem w;
   };
   std::vector<Cost> v;
   for (int i = 0; i < b->n; ++i) {
-    const int np = b->nx[i] * (b->ny[i] / 2 + 1);
-    for (int p = 0; p < np; p += item_pairs) {
-      const long long pairs = std::min(item_pairs, np - p);
-      v.push_back({pairs * (long long)b->h_desc[i].nterms, {i, p}});
+    const int no = b->h_desc[i].norb;
+    for (int p = 0; p < no; p += item_orbits) {
+      const long long orbits = std::min(item_orbits, no - p);
+      v.push_back({orbits * (long long)b->h_desc[i].nterms, {i, p}});
     }
   }
   std::stable_sort(v.begin(), v.end(), [](const Cost& a, const Cost& c) { return a.cost > c.cost; });
@@ -224,7 +278,7 @@ cudaError_t build_items(rexi_batch_s* b) {
   if (e != cudaSuccess) return e;
   e = cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice);
   b->n_items = (int)items.size();
-  b->item_pairs = item_pairs;
+  b->item_orbits = item_orbits;
   return e;
 }
 
@@ -240,6 +294,7 @@ cudaError_t enqueue_persistent(rexi_batch_s* b, const double2* in, double2* out,
                                cudaStream_t s) {
   unsigned* counter = reinterpret_cast<unsigned*>(ws);
   double2* spec = reinterpret_cast<double2*>(ws + 256);
+  double2* orb = reinterpret_cast<double2*>(ws + 256 + batch_spec_bytes(b));
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
   for (auto& G : b->groups) {
     if (e != cudaSuccess) return e;
@@ -247,7 +302,8 @@ cudaError_t enqueue_persistent(rexi_batch_s* b, const double2* in, double2* out,
     e = fft_any(b, in + G.first_off, spec + G.first_off, nf, G.fx, G.fy, -1, 1.0, real_input, 0, s);
   }
   if (e != cudaSuccess) return e;
-  e = launch_pole(b, spec, counter, s);
+  e = launch_pole(b, orb, counter, s);
+  if (e == cudaSuccess) e = launch_combine(b, spec, orb, s);
   for (auto& G : b->groups) {
     if (e != cudaSuccess) return e;
     const int nf = 3 * (int)G.insts.size();
@@ -284,6 +340,7 @@ void rexi_batch_destroy(rexi_batch_t b) {
   cudaFree(b->d_tables);
   cudaFree(b->d_desc);
   cudaFree(b->d_items);
+  cudaFree(b->d_blk);
   delete b;
 }
 
@@ -450,11 +507,28 @@ rexi_status rexi_batch_create(rexi_batch_t* out, int32_t n, const int32_t* nx, c
     }
     D.R0re = R0r;
     D.R0im = R0i;
-    b->total_terms_pairs += (long long)X * (Y / 2 + 1) * nterms;
+    SymbolParams spi;
+    spi.nx = X;
+    spi.ny = Y;
+    spi.inv_dx = D.inv_dx;
+    spi.inv_dy = D.inv_dy;
+    const OrbitParams op = orbit_params(spi);
+    D.ax = op.ax;
+    D.ay = op.ay;
+    D.sym = op.sym;
+    D.norb = op.norb;
+    D.orb_off = b->total_orbits;
+    b->total_orbits += op.norb;
+    b->total_terms_orbits += (long long)op.norb * nterms;
   }
+  std::vector<int> blk(n + 1, 0);
+  for (int i = 0; i < n; ++i) blk[i + 1] = blk[i] + (b->nx[i] * b->ny[i] + 255) / 256;
+  b->combine_blocks = blk[n];
   if (cudaMalloc(&b->d_tables, tab.size() * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&b->d_desc, n * sizeof(InstDesc)) != cudaSuccess)
+      cudaMalloc(&b->d_desc, n * sizeof(InstDesc)) != cudaSuccess ||
+      cudaMalloc(&b->d_blk, (n + 1) * sizeof(int)) != cudaSuccess)
     return bail(REXI_ENOMEM, "rexi_batch_create: device allocation failed");
+  cudaMemcpy(b->d_blk, blk.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice);
   cudaMemcpy(b->d_tables, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice);
   cudaMemcpy(b->d_desc, b->h_desc.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice);
   if (build_items(b) != cudaSuccess) return bail(REXI_ENOMEM, "rexi_batch_create: work list allocation failed");
@@ -499,6 +573,7 @@ rexi_status rexi_batch_step(rexi_batch_t b, const void* in, void* out, int32_t r
   cudaError_t e = cudaSuccess;
   if (mode == REXI_BATCH_PER_INSTANCE) {
     double2* spec = reinterpret_cast<double2*>(wsc + 256);
+    double2* orb = reinterpret_cast<double2*>(wsc + 256 + batch_spec_bytes(b));
     for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
       const InstDesc& D = b->h_desc[i];
       FftPlan1D fx, fy;
@@ -516,12 +591,18 @@ rexi_status rexi_batch_step(rexi_batch_t b, const void* in, void* out, int32_t r
       FusedScalars fs;
       fs.tau = D.tau; fs.q = D.q; fs.R0re = D.R0re; fs.R0im = D.R0im; fs.nterms = D.nterms; fs.adjoint = 0;
       const float* tab = static_cast<const float*>(b->d_tables) + D.table_off * 12;
+      // the single-instance kernels, term slices as rexi_step chooses them
+      OrbitParams op;
+      op.ax = D.ax; op.ay = D.ay; op.sym = D.sym; op.norb = D.norb;
+      const int slices = pole_orbit_slices(b->form, op.norb, D.nterms, orbit_slice_cap(op.norb));
       if (e == cudaSuccess)
-        e = b->form == REXI_FORM_FP64 ? pole_fused_fp64(sp_i, sp, reinterpret_cast<const double*>(tab), fs, s)
-                                      : pole_fused_mixed(sp_i, sp, tab, fs, D.grid, s);
+        e = b->form == REXI_FORM_FP64
+                ? pole_orbits_fp64(orb, slices, sp, op, reinterpret_cast<const double*>(tab), fs, s)
+                : pole_orbits_mixed(orb, slices, sp, op, tab, fs, D.grid, s);
+      if (e == cudaSuccess) e = pole_orbit_combine(sp_i, orb, slices, sp, op, fs, D.nx, s);
       if (e == cudaSuccess)
         e = fft_any(b, sp_i, out2 + D.spec_off, 3, fx, fy, +1, 1.0 / ((double)D.nx * D.ny), 0, real_input, s);
-      b->launches += 5;
+      b->launches += 6;
     }
   } else if (mode == REXI_BATCH_PERSISTENT) {
     const bool same = b->exec && b->g_in == in && b->g_out == out && b->g_ws == ws && b->g_real == real_input &&
@@ -554,7 +635,7 @@ rexi_status rexi_batch_step(rexi_batch_t b, const void* in, void* out, int32_t r
     if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->own);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev_out, b->own);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->ev_out, 0);
-    b->launches += 1 + 4 * (int64_t)b->groups.size();
+    b->launches += 2 + 4 * (int64_t)b->groups.size();
   } else {
     set_last_error("rexi_batch_step: unknown mode");
     return REXI_EINVAL;
@@ -614,13 +695,13 @@ rexi_status rexi_batch_autotune(rexi_batch_t b, const void* in, void* out, int32
 }
 
 rexi_status rexi_batch_info(rexi_batch_t b, int32_t* threads, int32_t* ppt, int32_t* ctas, int32_t* n_items,
-                            int64_t* terms_pairs, int64_t* launches) {
+                            int64_t* terms_orbits, int64_t* launches) {
   if (!b) return REXI_EINVAL;
   if (threads) *threads = b->threads;
   if (ppt) *ppt = b->ppt;
   if (ctas) *ctas = b->ctas;
   if (n_items) *n_items = b->n_items;
-  if (terms_pairs) *terms_pairs = b->total_terms_pairs;
+  if (terms_orbits) *terms_orbits = b->total_terms_orbits;
   if (launches) *launches = b->launches;
   return REXI_OK;
 }

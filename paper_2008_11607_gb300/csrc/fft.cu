@@ -329,6 +329,103 @@ __global__ void __launch_bounds__(256) fft_cols_kernel(const TI* in, TO* out, in
   }
 }
 
+// ---------------------------------------------------------------------------
+// Real input along x.  A real row x[0..n) (n = 2m) is transformed as the
+// m-point complex sequence z[t] = x[2t] + i x[2t+1]: with Z = DFT_m(z), the
+// DFTs of the even and odd samples are E[k] = (Z[k] + conj Z[m-k])/2 and
+// O[k] = -i (Z[k] - conj Z[m-k])/2, and X[k] = E[k] + w^k O[k], w = e^{-2 pi i/n},
+// for k = 0..m (the other half of X is its conjugate mirror).  The inverse
+// forms Z[k] = (X[k] + conj X[m-k]) + i w^{-k} (X[k] - conj X[m-k]) for
+// k < m, and the unnormalised inverse m-point transform of Z is n (x[2t] +
+// i x[2t+1]).  Only half of the spectrum is transformed along y and handled
+// by the pole step.
+
+__device__ __forceinline__ double2 conj_of(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ float4 conj_of(float4 a) { return make_float4(a.x, a.y, -a.z, -a.w); }
+__device__ __forceinline__ double2 half_of(double2 a) { return make_double2(0.5 * a.x, 0.5 * a.y); }
+__device__ __forceinline__ float4 half_of(float4 a) {  // exact: scaling by a power of two
+  return make_float4(0.5f * a.x, 0.5f * a.y, 0.5f * a.z, 0.5f * a.w);
+}
+__device__ __forceinline__ void real_pair(const double2* g, double2* v) { *v = make_double2(g[0].x, g[1].x); }
+__device__ __forceinline__ void real_pair(const double2* g, float4* v) {
+  cvt(make_double2(g[0].x, g[1].x), 0, v);
+}
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(float4 v) {
+  return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
+
+// Forward, rows: `rpc` real rows of length 2m per CTA -> m + 1 spectrum values each.
+template <typename T, typename TO>
+__global__ void __launch_bounds__(256) fft_rows_r2c_kernel(const double2* in, TO* out, int nrows, int rpc,
+                                                           StageList st, const T* tw_half, const T* tw_full) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  const int m = st.n, n = 2 * m;
+  T* b0 = smem;
+  T* b1 = smem + (size_t)rpc * m;
+  const long long row0 = (long long)blockIdx.x * rpc;
+  const int nr = (int)min((long long)rpc, nrows - row0);
+  const double2* g_in = in + row0 * n;
+  for (int i = threadIdx.x; i < rpc * m; i += blockDim.x) {
+    T v = czero<T>();
+    if (i < nr * m) real_pair(g_in + 2 * (size_t)i, &v);
+    b0[i] = v;
+  }
+  __syncthreads();
+  const T* res = run_stages<-1>(b0, b1, st, rpc, m, 1, false, tw_half);
+  TO* g_out = out + row0 * (m + 1);
+  for (int i = threadIdx.x; i < nr * (m + 1); i += blockDim.x) {
+    const int r = i / (m + 1), k = i - r * (m + 1);
+    const T* zr = res + (size_t)r * m;
+    const T zk = zr[k == m ? 0 : k];
+    const T zc = conj_of(zr[k == 0 ? 0 : m - k]);
+    const T e = half_of(cadd(zk, zc));
+    const T o = half_of(mul_si<-1>(csub(zk, zc)));
+    const T x = cadd(e, cmul(o, tw_load<-1>(tw_full, k)));
+    out_cvt(x, 1.0, 0, g_out + i);
+  }
+}
+
+// Inverse, rows: m + 1 spectrum values per row -> 2m real values (imaginary 0), scaled.
+template <typename T, typename TI>
+__global__ void __launch_bounds__(256) fft_rows_c2r_kernel(const TI* in, double2* out, int nrows, int rpc,
+                                                           StageList st, const T* tw_half, const T* tw_full,
+                                                           double scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  const int m = st.n, n = 2 * m;
+  T* b0 = smem;
+  T* b1 = smem + (size_t)rpc * m;
+  const long long row0 = (long long)blockIdx.x * rpc;
+  const int nr = (int)min((long long)rpc, nrows - row0);
+  // each thread forms Z[k] from X[k] and X[m - k] (the second read of a row
+  // hits the cache lines of the first)
+  const TI* g_in = in + row0 * (m + 1);
+  for (int i = threadIdx.x; i < rpc * m; i += blockDim.x) {
+    T v = czero<T>();
+    if (i < nr * m) {
+      const int r = i / m, k = i - r * m;
+      T a, b;
+      cvt(g_in[(size_t)r * (m + 1) + k], 0, &a);
+      cvt(g_in[(size_t)r * (m + 1) + (m - k)], 0, &b);
+      const T bc = conj_of(b);
+      const T e = cadd(a, bc);
+      const T o = cmul(csub(a, bc), tw_load<+1>(tw_full, k));
+      v = cadd(e, mul_si<+1>(o));
+    }
+    b0[i] = v;
+  }
+  __syncthreads();
+  const T* res = run_stages<+1>(b0, b1, st, rpc, m, 1, false, tw_half);
+  double2* g_out = out + row0 * n;
+  for (int i = threadIdx.x; i < nr * m; i += blockDim.x) {
+    const double2 z = to_d2(res[i]);
+    g_out[2 * (size_t)i] = make_double2(z.x * scale, 0.0);
+    g_out[2 * (size_t)i + 1] = make_double2(z.y * scale, 0.0);
+  }
+}
+
 bool fft_factor(int n, FftPlan1D* p) {
   if (n < 2 || n > 4096) return false;
   p->n = n;
@@ -413,6 +510,86 @@ static cudaError_t fft2d_impl(const double2* in, double2* out, int nfields, cons
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// Real-input transforms: forward rows (half-length complex + split), then
+// columns of the half spectrum; inverse columns, then rows (merge +
+// half-length complex).  T: arithmetic type, TM: value type of the
+// intermediate in HBM.
+template <typename T>
+static cudaError_t fft2d_r2c_impl(const double2* in, double2* spec, int nfields, const FftPlan1D& px,
+                                  const FftPlan1D& pxh, const FftPlan1D& py, const T* twx, const T* twxh,
+                                  const T* twy, cudaStream_t s) {
+  constexpr bool DF = !std::is_same<T, double2>::value;
+  using TM = typename std::conditional<DF, float4, double2>::type;
+  const int m = pxh.n, ny = py.n;
+  TM* mid = reinterpret_cast<TM*>(spec);
+  cudaError_t e;
+  {
+    const int rpc = rows_per_cta(m);
+    const int nrows = nfields * ny;
+    const size_t sm = 2 * (size_t)rpc * m * sizeof(T);
+    auto k = fft_rows_r2c_kernel<T, TM>;
+    if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
+    k<<<(nrows + rpc - 1) / rpc, 256, sm, s>>>(in, mid, nrows, rpc, to_stages(pxh), twxh, twx);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  {
+    const int W = cols_per_cta(ny);
+    const size_t sm = 2 * (size_t)W * ny * sizeof(T);
+    auto k = fft_cols_kernel<-1, T, TM, double2>;
+    if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
+    dim3 grid((m + 1 + W - 1) / W, nfields);
+    k<<<grid, 256, sm, s>>>(mid, spec, m + 1, W, to_stages(py), twy, 1.0, 0, 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  (void)px;
+  return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t fft2d_c2r_impl(double2* spec, double2* out, int nfields, const FftPlan1D& px,
+                                  const FftPlan1D& pxh, const FftPlan1D& py, const T* twx, const T* twxh,
+                                  const T* twy, double scale, cudaStream_t s) {
+  constexpr bool DF = !std::is_same<T, double2>::value;
+  using TM = typename std::conditional<DF, float4, double2>::type;
+  const int m = pxh.n, ny = py.n;
+  TM* mid = reinterpret_cast<TM*>(spec);
+  cudaError_t e;
+  {
+    const int W = cols_per_cta(ny);
+    const size_t sm = 2 * (size_t)W * ny * sizeof(T);
+    auto k = fft_cols_kernel<+1, T, double2, TM>;
+    if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
+    dim3 grid((m + 1 + W - 1) / W, nfields);
+    k<<<grid, 256, sm, s>>>(spec, mid, m + 1, W, to_stages(py), twy, 1.0, 0, 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  {
+    const int rpc = rows_per_cta(m);
+    const int nrows = nfields * ny;
+    const size_t sm = 2 * (size_t)rpc * m * sizeof(T);
+    auto k = fft_rows_c2r_kernel<T, TM>;
+    if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
+    k<<<(nrows + rpc - 1) / rpc, 256, sm, s>>>(mid, out, nrows, rpc, to_stages(pxh), twxh, twx, scale);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  (void)px;
+  return cudaSuccess;
+}
+
+cudaError_t fft2d_r2c(const double2* in, double2* spec, int nfields, const FftPlan1D& px, const FftPlan1D& pxh,
+                      const FftPlan1D& py, int df, cudaStream_t s) {
+  if (df && px.twf && pxh.twf && py.twf)
+    return fft2d_r2c_impl<float4>(in, spec, nfields, px, pxh, py, px.twf, pxh.twf, py.twf, s);
+  return fft2d_r2c_impl<double2>(in, spec, nfields, px, pxh, py, px.tw, pxh.tw, py.tw, s);
+}
+
+cudaError_t fft2d_c2r(double2* spec, double2* out, int nfields, const FftPlan1D& px, const FftPlan1D& pxh,
+                      const FftPlan1D& py, double scale, int df, cudaStream_t s) {
+  if (df && px.twf && pxh.twf && py.twf)
+    return fft2d_c2r_impl<float4>(spec, out, nfields, px, pxh, py, px.twf, pxh.twf, py.twf, scale, s);
+  return fft2d_c2r_impl<double2>(spec, out, nfields, px, pxh, py, px.tw, pxh.tw, py.tw, scale, s);
 }
 
 cudaError_t fft2d(const double2* in, double2* out, int nfields, const FftPlan1D& px,

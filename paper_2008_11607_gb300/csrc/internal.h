@@ -52,6 +52,16 @@ cudaError_t fft2d_df(const double2* in, double2* out, int nfields, const FftPlan
                      const FftPlan1D& py, int sign, double scale, int zero_imag_in, int real_out,
                      cudaStream_t s);
 void split_twiddles(const double2* tw, int n, float4* out);  // host: FP64 table -> double-float
+// Real input (nx = 2 m even): forward transform of the real parts of `in`
+// into the half spectrum, ny x (m + 1) complex128 per field (field stride
+// ny (m + 1)), through an m-point transform per row (pxh: plan of length m);
+// inverse from the half spectrum (overwritten) to real fields (imaginary 0),
+// scaled.  df: double-float arithmetic when every plan carries double-float
+// twiddles.
+cudaError_t fft2d_r2c(const double2* in, double2* spec, int nfields, const FftPlan1D& px, const FftPlan1D& pxh,
+                      const FftPlan1D& py, int df, cudaStream_t s);
+cudaError_t fft2d_c2r(double2* spec, double2* out, int nfields, const FftPlan1D& px, const FftPlan1D& pxh,
+                      const FftPlan1D& py, double scale, int df, cudaStream_t s);
 
 // ---- Fourier-path pole kernels (pole_fft.cu) ------------------------------
 struct SymbolParams {
@@ -70,6 +80,30 @@ cudaError_t pole_fused_fp64(double2* spec, const SymbolParams& sp, const double*
                             const FusedScalars& fs, cudaStream_t s);
 cudaError_t pole_fused_mixed(double2* spec, const SymbolParams& sp, const float* table,
                              const FusedScalars& fs, double grid, cudaStream_t s);
+// Orbits of the wavenumber grid under the symmetries of omega(k): k -> -k
+// separately in x and y (|sin|, |cos| of the half angles are even), and
+// kx <-> ky when the grid is square with equal spacing.  One pole sum per
+// orbit, then a combine pass over every wavenumber with its own symbol.
+struct OrbitParams {
+  int ax, ay;  // nx/2 + 1, ny/2 + 1 (folded index ranges)
+  int sym;     // 1: swap-symmetric (representatives a <= b, triangular index)
+  int norb;    // number of orbits
+};
+OrbitParams orbit_params(const SymbolParams& sp);
+int orbit_slice_cap(int norb);  // most term slices a workspace holds partial sums for
+// Term slices for the orbit kernels: the count that minimises the modelled
+// run time (waves of resident blocks x terms per block), at most `cap`.
+int pole_orbit_slices(int form, int norb, int nterms, int cap);
+// part[s * norb + o] = sum of the table's terms in slice s at x = tau omega(rep(o)).
+cudaError_t pole_orbits_fp64(double2* part, int slices, const SymbolParams& sp, const OrbitParams& op,
+                             const double* table, const FusedScalars& fs, cudaStream_t s);
+cudaError_t pole_orbits_mixed(double2* part, int slices, const SymbolParams& sp, const OrbitParams& op,
+                              const float* table, const FusedScalars& fs, double grid, cudaStream_t s);
+// spec <- r(tau B) spec at every wavenumber, R+ = sum over slices of part.
+// row_len: nx (full spectrum, rows of nx values) or nx/2 + 1 (half spectrum
+// of real input, wavenumbers kx = 0..nx/2 only).
+cudaError_t pole_orbit_combine(double2* spec, const double2* part, int slices, const SymbolParams& sp,
+                               const OrbitParams& op, const FusedScalars& fs, int row_len, cudaStream_t s);
 struct PlainScalars {
   double tau;
   int nterms;   // terms in this chunk

@@ -125,6 +125,31 @@ __device__ __forceinline__ bool pair_of(int p, int nx, int ny, int& kx, int& ky,
   return true;
 }
 
+// Orbit of wavenumber (kx, ky): fold each index to a = min(k, n - k), then,
+// on a swap-symmetric grid, order the pair (a <= b).  Index: b (b + 1)/2 + a
+// (triangular) or b ax + a (rectangular).
+__device__ __forceinline__ int orbit_of(const OrbitParams& op, int nx, int ny, int kx, int ky) {
+  int a = min(kx, nx - kx), b = min(ky, ny - ky);
+  if (op.sym) {
+    if (a > b) { const int t = a; a = b; b = t; }
+    return b * (b + 1) / 2 + a;
+  }
+  return b * op.ax + a;
+}
+// Representative (a, b) of orbit o; a and b are themselves valid wavenumber
+// indices (a <= nx/2, b <= ny/2).
+__device__ __forceinline__ void orbit_rep(const OrbitParams& op, int o, int& a, int& b) {
+  if (op.sym) {
+    b = (int)((sqrtf(8.0f * (float)o + 1.0f) - 1.0f) * 0.5f);
+    while (b > 0 && b * (b + 1) / 2 > o) --b;
+    while ((b + 1) * (b + 2) / 2 <= o) ++b;
+    a = o - b * (b + 1) / 2;
+  } else {
+    b = o / op.ax;
+    a = o - b * op.ax;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // FP64 fused pole loop.
 // Table (per scalar term, 6 doubles): h n, A_re, A_im, B_re, B_im, 0 with

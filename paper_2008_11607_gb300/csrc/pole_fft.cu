@@ -26,6 +26,8 @@
 //    g1 = (alpha_n I + tau B)^{-1} f, g2 = (alpha_{-n} I - tau B)^{-1} g1,
 //    g3 = Gamma_n (C2 g1 + (C1 - C2 alpha_{-n}) g2) written to HBM for a chunk
 //    of terms, then a separate reduction pass over the chunk.
+#include <algorithm>
+
 #include "internal.h"
 #include "pole_common.cuh"
 
@@ -120,6 +122,176 @@ cudaError_t pole_fused_mixed(double2* spec, const SymbolParams& sp, const float*
   const float q_lo = (float)(fs.q - (double)q_hi);
   pole_fused_mixed_kernel<<<(np + tpb - 1) / tpb, tpb, 0, s>>>(
       spec, sp, reinterpret_cast<const float4*>(table), fs, grid, q_hi, q_lo, np);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Orbit form: one pole sum per orbit of omega's symmetry group (up to 8
+// wavenumbers on a square grid, 4 otherwise, against 2 for the pair form),
+// the terms split into `slices` ranges over blockIdx.y so that small grids
+// still fill the GPU; each (slice, orbit) writes its partial R+ in FP64 and
+// the combine pass sums the slices in a fixed order (deterministic).
+
+OrbitParams orbit_params(const SymbolParams& sp) {
+  OrbitParams op;
+  op.ax = sp.nx / 2 + 1;
+  op.ay = sp.ny / 2 + 1;
+  op.sym = (sp.nx == sp.ny && sp.inv_dx == sp.inv_dy) ? 1 : 0;
+  op.norb = op.sym ? op.ax * (op.ax + 1) / 2 : op.ax * op.ay;
+  return op;
+}
+
+int orbit_slice_cap(int norb) {
+  // partial sums of at most 64 MB, at least 8 slices, at most 64
+  const long long c = (64ll << 20) / (16ll * std::max(norb, 1));
+  return (int)std::min<long long>(64, std::max<long long>(8, c));
+}
+
+constexpr int kOrbitThreads = 128;
+
+__device__ __forceinline__ void slice_range(const FusedScalars& fs, int slices, int& t_begin, int& t_end) {
+  const int per = (fs.nterms + slices - 1) / slices;
+  t_begin = min(fs.nterms, (int)blockIdx.y * per);
+  t_end = min(fs.nterms, t_begin + per);
+}
+
+__global__ void __launch_bounds__(kOrbitThreads) pole_orbit_fp64_kernel(double2* __restrict__ part, SymbolParams sp,
+                                                                        OrbitParams op,
+                                                                        const double* __restrict__ table,
+                                                                        FusedScalars fs, int slices) {
+  __shared__ double2 st[kChunk * 3];
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  int a = 0, b = 0;
+  if (o < op.norb) orbit_rep(op, o, a, b);
+  const double x = fs.tau * symbol_at(sp, a, b).omega;
+  const double q = fs.q;
+  double accr = 0.0, acci = 0.0;
+  int t_begin, t_end;
+  slice_range(fs, slices, t_begin, t_end);
+  const double2* tb = reinterpret_cast<const double2*>(table);
+  for (int t0 = t_begin; t0 < t_end; t0 += kChunk) {
+    const int cnt = min(kChunk, t_end - t0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt * 3; i += blockDim.x) st[i] = tb[(size_t)t0 * 3 + i];
+    __syncthreads();
+#pragma unroll 4
+    for (int t = 0; t < cnt; ++t) fp64_term(st + 3 * t, x, q, accr, acci);
+  }
+  if (o < op.norb) part[(size_t)blockIdx.y * op.norb + o] = make_double2(accr, acci);
+}
+
+__global__ void __launch_bounds__(kOrbitThreads) pole_orbit_mixed_kernel(double2* __restrict__ part, SymbolParams sp,
+                                                                         OrbitParams op,
+                                                                         const float4* __restrict__ table,
+                                                                         FusedScalars fs, double grid, float q_hi,
+                                                                         float q_lo, int slices) {
+  __shared__ float4 st[kChunk * 3];
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  int a = 0, b = 0;
+  if (o < op.norb) orbit_rep(op, o, a, b);
+  const double x = fs.tau * symbol_at(sp, a, b).omega;
+  const double xg = rint(x / grid) * grid;
+  const float X_hi = (float)xg;
+  const float X_lo = (float)(x - xg);
+  const float X_lo2 = (float)((x - xg) - (double)X_lo);
+  float ar_h = 0.f, ar_l = 0.f, ai_h = 0.f, ai_l = 0.f;
+  int t_begin, t_end;
+  slice_range(fs, slices, t_begin, t_end);
+  for (int t0 = t_begin; t0 < t_end; t0 += kChunk) {
+    const int cnt = min(kChunk, t_end - t0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt * 3; i += blockDim.x) st[i] = table[(size_t)t0 * 3 + i];
+    __syncthreads();
+#pragma unroll 2
+    for (int t = 0; t < cnt; ++t) df_term(st + 3 * t, X_hi, X_lo, X_lo2, q_hi, q_lo, ar_h, ar_l, ai_h, ai_l);
+  }
+  if (o < op.norb)
+    part[(size_t)blockIdx.y * op.norb + o] =
+        make_double2((double)ar_h + (double)ar_l, (double)ai_h + (double)ai_l);
+}
+
+__global__ void __launch_bounds__(256) pole_orbit_combine_kernel(double2* spec, const double2* __restrict__ part,
+                                                                 int slices, SymbolParams sp, OrbitParams op,
+                                                                 double2 R0, int adjoint, int row_len) {
+  const size_t nk = (size_t)row_len * sp.ny;
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nk) return;
+  const int ky = (int)(k / row_len), kx = (int)(k - (size_t)ky * row_len);
+  const int o = orbit_of(op, sp.nx, sp.ny, kx, ky);
+  double2 Rp = part[o];
+  for (int s = 1; s < slices; ++s) {
+    const double2 v = part[(size_t)s * op.norb + o];
+    Rp.x += v.x;
+    Rp.y += v.y;
+  }
+  combine(spec, k, nk, symbol_at(sp, kx, ky), sp, false, adjoint != 0, R0, Rp);
+}
+
+namespace {
+struct OrbitOccupancy {
+  int sms = 0, fp64_blocks = 0, mixed_blocks = 0;
+};
+OrbitOccupancy orbit_occupancy() {
+  static OrbitOccupancy occ;  // per process: the library serves one device model
+  if (occ.sms == 0) {
+    int dev = 0, sms = 0, b64 = 0, bmx = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, pole_orbit_fp64_kernel, kOrbitThreads, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bmx, pole_orbit_mixed_kernel, kOrbitThreads, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return OrbitOccupancy{152, 8, 8};
+    }
+    occ.sms = sms;
+    occ.fp64_blocks = std::max(b64, 1);
+    occ.mixed_blocks = std::max(bmx, 1);
+  }
+  return occ;
+}
+}  // namespace
+
+int pole_orbit_slices(int form, int norb, int nterms, int cap) {
+  if (nterms <= 1) return 1;
+  const OrbitOccupancy occ = orbit_occupancy();
+  const long long resident = (long long)occ.sms * (form == REXI_FORM_MIXED ? occ.mixed_blocks : occ.fp64_blocks);
+  const long long bx = (norb + kOrbitThreads - 1) / kOrbitThreads;
+  // per block: its terms plus a fixed cost (symbol, FP64 setup, staging, the
+  // write) of about 48 terms; blocks run in waves of `resident`
+  double best = 0.0;
+  int best_s = 1;
+  for (int s = 1; s <= std::min(cap, nterms); ++s) {
+    const long long waves = (bx * s + resident - 1) / resident;
+    const double t = (double)waves * ((double)((nterms + s - 1) / s) + 48.0);
+    if (s == 1 || t < best * 0.98) {
+      best = t;
+      best_s = s;
+    }
+  }
+  return best_s;
+}
+
+cudaError_t pole_orbits_fp64(double2* part, int slices, const SymbolParams& sp, const OrbitParams& op,
+                             const double* table, const FusedScalars& fs, cudaStream_t s) {
+  dim3 grid((unsigned)((op.norb + kOrbitThreads - 1) / kOrbitThreads), (unsigned)slices);
+  pole_orbit_fp64_kernel<<<grid, kOrbitThreads, 0, s>>>(part, sp, op, table, fs, slices);
+  return cudaGetLastError();
+}
+
+cudaError_t pole_orbits_mixed(double2* part, int slices, const SymbolParams& sp, const OrbitParams& op,
+                              const float* table, const FusedScalars& fs, double grid_step, cudaStream_t s) {
+  const float q_hi = (float)fs.q;
+  const float q_lo = (float)(fs.q - (double)q_hi);
+  dim3 grid((unsigned)((op.norb + kOrbitThreads - 1) / kOrbitThreads), (unsigned)slices);
+  pole_orbit_mixed_kernel<<<grid, kOrbitThreads, 0, s>>>(part, sp, op, reinterpret_cast<const float4*>(table), fs,
+                                                         grid_step, q_hi, q_lo, slices);
+  return cudaGetLastError();
+}
+
+cudaError_t pole_orbit_combine(double2* spec, const double2* part, int slices, const SymbolParams& sp,
+                               const OrbitParams& op, const FusedScalars& fs, int row_len, cudaStream_t s) {
+  const size_t nk = (size_t)row_len * sp.ny;
+  pole_orbit_combine_kernel<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(
+      spec, part, slices, sp, op, make_double2(fs.R0re, fs.R0im), fs.adjoint, row_len);
   return cudaGetLastError();
 }
 

@@ -297,8 +297,9 @@ class Plan:
         _check(self._lib.rexi_plan_set_profiling(self._h, int(enable)), "rexi_plan_set_profiling")
 
     def read_profile(self):
-        """Returns (ms per phase [fwd, poles, inv, upload], calls, kernel launches) since the last read."""
-        ms = (ctypes.c_double * 4)()
+        """Returns (ms per phase [fwd, poles, inv, upload, combine part of poles], calls, kernel
+        launches) since the last read."""
+        ms = (ctypes.c_double * 5)()
         n = ctypes.c_int32()
         L = ctypes.c_int64()
         _check(self._lib.rexi_plan_read_profile(self._h, ms, ctypes.byref(n), ctypes.byref(L)),
@@ -418,5 +419,5 @@ class Batch:
     def info(self):
         vals = [ctypes.c_int32() for _ in range(4)] + [ctypes.c_int64(), ctypes.c_int64()]
         _check(self._lib.rexi_batch_info(self._h, *[ctypes.byref(v) for v in vals]), "rexi_batch_info")
-        keys = ["threads", "pairs_per_thread", "ctas", "n_items", "terms_pairs", "launches"]
+        keys = ["threads", "orbits_per_thread", "ctas", "n_items", "terms_orbits", "launches"]
         return {k: v.value for k, v in zip(keys, vals)}

@@ -12,6 +12,16 @@ from tests.gpu_util import TOL, oracle_step, rel_l2, to_dev, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
+# The single-instance step may split the terms into slices whose partial sums
+# are added in FP64, the persistent kernel sums all terms of an orbit in one
+# accumulator: the same terms (bit for bit) summed in another order.  An order
+# change moves the result by the accumulator's rounding: partial sums reach
+# sum |term| / 2 ~ 30 |result| at tau rho = 1000, FP64 rounds each add at
+# 2^-53 of that; the double-float accumulator adds its low words in plain
+# FP32 (2^-24 of a low word ~ 2^-48 of the partial sum), which over ~3000
+# terms gives up to ~1e-12 of the result.
+SAME_SUM = {"fp64": 1e-13, "mixed": 1e-11}
+
 
 def make_batch(torch, sizes, tau_rhos, form, seed0=0, real=True):
     from paper_2008_11607_gb300 import rexi
@@ -38,11 +48,12 @@ def test_small_batch_matches_single_instance(form, real):
     packed = b.pack(states)
     ws = b.workspace()
     refs = [p.step(s, dt, real_input=real) for p, s, dt in zip(plans, states, dts)]
+    same_sum = SAME_SUM[form]
     for mode in (rexi.REXI_BATCH_PERSISTENT, rexi.REXI_BATCH_PER_INSTANCE):
         out = b.step(packed, workspace=ws, real_input=real, mode=mode)
         torch.cuda.synchronize()
         for o, r in zip(b.unpack(out), refs):
-            assert rel_l2(o.cpu().numpy(), r.cpu().numpy()) < 1e-13
+            assert rel_l2(o.cpu().numpy(), r.cpu().numpy()) < same_sum
     assert b.M == [C.pole_count_M(tr, 0.5, 1e-10) for tr in trs]
     # one instance against the oracle
     st = states[1].cpu().numpy()
@@ -67,16 +78,16 @@ def test_graph_replay_and_autotune():
     b.step(packed, out, ws)
     torch.cuda.synchronize()
     for o, p, s, dt in zip(b.unpack(out), plans, states2, dts):
-        assert rel_l2(o.cpu().numpy(), p.step(s, dt).cpu().numpy()) < 1e-13
+        assert rel_l2(o.cpu().numpy(), p.step(s, dt).cpu().numpy()) < SAME_SUM["mixed"]
     t, ppt, ms = b.autotune(packed, out, ws)
     assert t in (64, 128, 256) and ppt in (1, 2) and ms > 0
     b.pack(states2, out=packed)
     b.step(packed, out, ws)
     torch.cuda.synchronize()
     info = b.info()
-    assert info["threads"] == t and info["pairs_per_thread"] == ppt and info["n_items"] > 0
+    assert info["threads"] == t and info["orbits_per_thread"] == ppt and info["n_items"] > 0
     for o, p, s, dt in zip(b.unpack(out), plans, states2, dts):
-        assert rel_l2(o.cpu().numpy(), p.step(s, dt).cpu().numpy()) < 1e-13
+        assert rel_l2(o.cpu().numpy(), p.step(s, dt).cpu().numpy()) < SAME_SUM["mixed"]
 
 
 def test_serving_mix_96_instances():
@@ -101,5 +112,5 @@ def test_serving_mix_96_instances():
     torch.cuda.synchronize()
     for o, o2, p, s, dt in zip(b.unpack(out), b.unpack(out2), plans, states, dts):
         r = p.step(s, dt).cpu().numpy()
-        assert rel_l2(o.cpu().numpy(), r) < 1e-12
+        assert rel_l2(o.cpu().numpy(), r) < SAME_SUM["mixed"]
         assert rel_l2(o2.cpu().numpy(), r) < 1e-12

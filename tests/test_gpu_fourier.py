@@ -33,7 +33,8 @@ def run(torch, state, dt, form, real_input=True, tol=1e-10, terms=(0, -1), **phy
 
 
 @pytest.mark.parametrize("form", FORMS)
-@pytest.mark.parametrize("case", ["16x16_real", "24x20_complex", "17x9_real", "12x10_phys"])
+@pytest.mark.parametrize("case", ["16x16_real", "24x20_complex", "17x9_real", "12x10_phys", "15x15_complex",
+                                  "16x16_aniso"])
 def test_small_grids_against_sparse_oracle(form, case):
     torch = torch_cuda()
     phys = {}
@@ -43,6 +44,13 @@ def test_small_grids_against_sparse_oracle(form, case):
         nx, ny, real, st = 24, 20, False, inputs.complex_random_state(24, 20, seed=1)
     elif case == "17x9_real":
         nx, ny, real, st = 17, 9, True, inputs.gaussian_bump(17, 9, width=0.15)
+    elif case == "15x15_complex":
+        # odd square grid: orbits of all eight symmetries, no Nyquist index
+        nx, ny, real, st = 15, 15, False, inputs.complex_random_state(15, 15, seed=3)
+    elif case == "16x16_aniso":
+        # square index grid with unequal spacing: omega is not symmetric in kx <-> ky
+        nx, ny, real, st = 16, 16, True, inputs.kminus3_field(16, 16, seed=4)
+        phys = dict(Lx=1.0, Ly=0.6)
     else:
         nx, ny, real, st = 12, 10, False, inputs.complex_random_state(12, 10, seed=2)
         phys = dict(Lx=1.3, Ly=0.7, g=2.0, f=0.6, H=0.8)
@@ -96,6 +104,37 @@ def test_adjoint_dot_product(form):
     M = C.pole_count_M(25.0, 0.5, 1e-10)
     ref = np.conj(R.rexii_apply_sparse(A.T.tocsr(), np.conj(y).ravel(), dt, 0.5, M, real_input=False))
     assert rel_l2(RHy.ravel(), ref) < TOL[form]
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+@pytest.mark.parametrize("nx,ny", [(20, 9), (18, 12), (4, 6), (30, 30)])
+def test_real_input_half_spectrum(form, nx, ny):
+    """Real input on a grid with even nx runs through real transforms along x
+    (half spectrum, kx = 0..nx/2).  It must equal the sparse oracle, the real
+    part of the complex-input step on the same state, and its transpose must
+    pass the dot-product test <y, S x> = <S^T y, x> on real vectors."""
+    torch = torch_cuda()
+    from paper_2008_11607_gb300 import rexi
+
+    st = inputs.kminus3_field(nx, ny, seed=nx + ny)
+    st[1] = 0.05 * inputs.kminus3_field(nx, ny, seed=nx + ny + 1)[0]  # nonzero u as well
+    plan = rexi.Plan(nx, ny, form=form, f=0.8)
+    dt = 35.0 / plan.rho
+    x = to_dev(torch, st)
+    out, info = plan.step(x, dt, want_info=True)
+    out = out.cpu().numpy()
+    assert np.all(out.imag == 0)
+    ref = oracle_step(st, dt, info.M, f=0.8)
+    assert rel_l2(out, ref) < TOL[form]
+    full = plan.step(x, dt, real_input=False).cpu().numpy().real
+    assert rel_l2(out, full) < {"fp64": 1e-13, "mixed": 1e-12}[form]
+    y = inputs.kminus3_field(nx, ny, seed=nx + ny + 2)
+    y[2] = 0.03 * y[0]
+    Sty = plan.step_adjoint(to_dev(torch, y), dt, real_input=True).cpu().numpy()
+    assert np.all(Sty.imag == 0)
+    lhs = np.vdot(y.real, out.real)
+    rhs = np.vdot(Sty.real, st.real)
+    assert abs(lhs - rhs) < 1e-11 * abs(lhs)
 
 
 @pytest.mark.parametrize("form", FORMS)
