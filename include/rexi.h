@@ -263,6 +263,18 @@ rexi_status rexi_step_host(rexi_plan_t plan, const void* in_host, void* out_host
 rexi_status rexi_workspace_size_host(rexi_plan_t plan, double dt, double tol, int32_t real_input,
                                      size_t* bytes);
 
+/* rexi_step_host without the final synchronisation: the copy in, the step
+ * and the copy out are enqueued on `stream` and the call returns.
+ * `out_host` holds the result, and `in_host` and the workspace may be reused,
+ * only once the stream has reached the end of this call's work (synchronise
+ * the stream or an event recorded on it).  With pinned host memory the
+ * copies run on the copy engines, so consecutive steps enqueued on two
+ * streams, each with its own workspace, overlap one step's copies with the
+ * other's kernels.  Steps on different streams may share the plan.  No
+ * per-call information is returned (use rexi_step_host for that). */
+rexi_status rexi_step_host_async(rexi_plan_t plan, const void* in_host, void* out_host, double dt, double tol,
+                                 int32_t real_input, void* workspace_dev, size_t workspace_bytes, void* stream);
+
 /* Device-side phase timing of rexi_step calls: with profiling enabled, each
  * call records CUDA events on its own stream around its phases.
  * rexi_plan_read_profile waits for the recorded events, fills ms5 (5

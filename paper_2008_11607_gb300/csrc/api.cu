@@ -64,6 +64,17 @@ struct rexi_plan_s {
   float4* twf_xh = nullptr;
   double2* half_x = nullptr;
   double2* half_y = nullptr;
+  // device coefficient tables of the FP64 and mixed Fourier forms, one per
+  // (form, M, term range, split grid); immutable once uploaded
+  struct CoefTable {
+    int M = 0, tb = 0, te = 0, nterms = 0;
+    double G = 0.0, R0re = 0.0, R0im = 0.0;
+    void* dev = nullptr;
+    cudaEvent_t ready = nullptr;
+    uint64_t last_use = 0;
+  };
+  std::vector<CoefTable> coef;
+  uint64_t coef_clock = 0;
   // coefficient staging (pinned host) guarded by an event
   void* staging = nullptr;
   size_t staging_bytes = 0;
@@ -209,6 +220,10 @@ void rexi_plan_destroy(rexi_plan_t p) {
   cudaFree(p->half_x);
   cudaFree(p->half_y);
   if (p->staging) cudaFreeHost(p->staging);
+  for (auto& c : p->coef) {
+    cudaFree(c.dev);
+    if (c.ready) cudaEventDestroy(c.ready);
+  }
   krylov_destroy(&p->kry);
   for (auto& set : p->prof_pool)
     for (auto e : set) cudaEventDestroy(e);
@@ -377,7 +392,7 @@ namespace {
 
 struct FourierLayout {
   int M, N, nterms_scalar, nterms_plain, slice_cap;
-  size_t table_off, table_bytes, spec_off, acc_off, chunk_off, chunk_terms, part_off, total;
+  size_t table_off, table_bytes, spec_off, acc_off, chunk_off, chunk_terms, part_off, fin_off, total;
 };
 
 SymbolParams symbol_params(const rexi_plan_s* p);
@@ -391,9 +406,8 @@ FourierLayout fourier_layout(const rexi_plan_s* p, int M, int real_input) {
   L.nterms_scalar = 2 * L.N + 1;
   L.nterms_plain = real_input ? L.N + 1 : 2 * L.N + 1;
   const size_t nk3 = 3 * (size_t)p->nx * p->ny;
-  size_t tb = 0;
+  size_t tb = 0;  // the FP64 and mixed forms keep their tables in the plan
   if (p->form == REXI_FORM_PLAIN) tb = (size_t)L.nterms_plain * 4 * sizeof(double2);
-  else tb = (size_t)L.nterms_scalar * 48;
   L.table_off = 0;
   L.table_bytes = tb;
   L.spec_off = align_up(tb, 256);
@@ -402,12 +416,16 @@ FourierLayout fourier_layout(const rexi_plan_s* p, int M, int real_input) {
   L.chunk_off = end;
   L.chunk_terms = 0;
   L.part_off = end;
+  L.fin_off = end;
   L.slice_cap = 0;
   if (p->form != REXI_FORM_PLAIN) {
-    // per-orbit partial sums of the pole loop, one row per term slice
+    // per-orbit partial sums of the pole loop, one row per term slice, then
+    // the per-orbit combine scalars
     const OrbitParams op = orbit_params(symbol_params(p));
     L.slice_cap = orbit_slice_cap(op.norb);
     end += align_up((size_t)L.slice_cap * op.norb * sizeof(double2), 256);
+    L.fin_off = end;
+    end += align_up(orbit_scalars_bytes(op.norb), 256);
   }
   if (p->form == REXI_FORM_PLAIN) {
     L.acc_off = end;
@@ -477,6 +495,107 @@ bool term_selected(int n, int tb, int te) {
   return a >= tb && a < te;
 }
 
+// The scalar-term table of the FP64 (G = 0) or mixed form for M and the
+// term range [tb, te): found in the plan's cache or built on the host and
+// uploaded on stream s.  A table is never rewritten, so calls on other streams
+// only wait for its upload.  At most kCoefTables are kept; evicting one waits
+// for the device to go idle (it may still be read).
+constexpr size_t kCoefTables = 8;
+
+rexi_status fused_table(rexi_plan_s* p, int M, int tb, int te, double G, cudaStream_t s,
+                        const rexi_plan_s::CoefTable** out) {
+  for (auto& c : p->coef) {
+    if (c.M == M && c.tb == tb && c.te == te && c.G == G) {
+      c.last_use = ++p->coef_clock;
+      if (cudaEventQuery(c.ready) == cudaErrorNotReady) CUDA_TRY(cudaStreamWaitEvent(s, c.ready, 0), "table wait");
+      *out = &c;
+      return REXI_OK;
+    }
+  }
+  TermSet ts;
+  rexii_terms(M, p->h, &ts);
+  const int N = ts.N;
+  const double h = p->h, hmu = h * ts.mu, q = hmu * hmu;
+  // scalar terms n = -N..N restricted to |n| in [tb, te)
+  std::vector<int> sel;
+  for (int n = -N; n <= N; ++n)
+    if (term_selected(n, tb, te)) sel.push_back(n);
+  rexi_plan_s::CoefTable c;
+  c.M = M;
+  c.tb = tb;
+  c.te = te;
+  c.G = G;
+  c.nterms = (int)sel.size();
+  for (int n : sel) {
+    const int i = n + N;
+    const double hn = h * n, d = q + hn * hn;
+    c.R0re += (ts.c1re[i] * hmu + ts.c2re[i] * hn) / d;
+    c.R0im += (ts.c1im[i] * hmu + ts.c2im[i] * hn) / d;
+  }
+  // 48 bytes per term in both forms
+  std::vector<double> tab(6 * std::max<size_t>(sel.size(), 1), 0.0);
+  if (G == 0.0) {  // FP64: h n, A_re, A_im, B_re, B_im, 0 with A = c1 h mu, B = c2
+    for (size_t t = 0; t < sel.size(); ++t) {
+      const int n = sel[t], i = n + N;
+      double* e = &tab[6 * t];
+      e[0] = h * n;
+      e[1] = ts.c1re[i] * hmu;
+      e[2] = ts.c1im[i] * hmu;
+      e[3] = ts.c2re[i];
+      e[4] = ts.c2im[i];
+      e[5] = 0.0;
+    }
+  } else {  // double-float: see pole_orbit_mixed_kernel
+    auto split = [](double v, float& hi, float& lo) {
+      hi = (float)v;
+      lo = (float)(v - (double)hi);
+    };
+    float* tf = reinterpret_cast<float*>(tab.data());
+    for (size_t t = 0; t < sel.size(); ++t) {
+      const int n = sel[t], i = n + N;
+      float* e = tf + 12 * t;
+      const double hn = h * n;
+      const double hn_g = rint(hn / G) * G;
+      float Arh, Arl, Aih, Ail, Brh, Brl, Bih, Bil;
+      split(ts.c1re[i] * hmu, Arh, Arl);
+      split(ts.c1im[i] * hmu, Aih, Ail);
+      split(ts.c2re[i], Brh, Brl);
+      split(ts.c2im[i], Bih, Bil);
+      e[0] = (float)hn_g; e[1] = Arh; e[2] = Aih; e[3] = Brh;
+      e[4] = Bih; e[5] = Arl; e[6] = Ail; e[7] = Brl;
+      e[8] = Bil; e[9] = (float)(hn - hn_g); e[10] = 0.f; e[11] = 0.f;
+    }
+  }
+  if (p->coef.size() >= kCoefTables) {
+    auto lru = std::min_element(p->coef.begin(), p->coef.end(),
+                                [](const rexi_plan_s::CoefTable& a, const rexi_plan_s::CoefTable& b) {
+                                  return a.last_use < b.last_use;
+                                });
+    CUDA_TRY(cudaDeviceSynchronize(), "table eviction");
+    cudaFree(lru->dev);
+    cudaEventDestroy(lru->ready);
+    p->coef.erase(lru);
+  }
+  const size_t bytes = tab.size() * sizeof(double);
+  if (cudaMalloc(&c.dev, bytes) != cudaSuccess) return fail(REXI_ENOMEM, "coefficient table allocation failed");
+  if (cudaEventCreateWithFlags(&c.ready, cudaEventDisableTiming) != cudaSuccess) {
+    cudaFree(c.dev);
+    return fail(REXI_ECUDA, "event creation failed");
+  }
+  rexi_status st = stage_upload(p, tab.data(), bytes, c.dev, s);
+  if (st == REXI_OK && cudaEventRecord(c.ready, s) != cudaSuccess) st = fail(REXI_ECUDA, "table event");
+  if (st != REXI_OK) {
+    cudaStreamSynchronize(s);
+    cudaFree(c.dev);
+    cudaEventDestroy(c.ready);
+    return st;
+  }
+  c.last_use = ++p->coef_clock;
+  p->coef.push_back(c);
+  *out = &p->coef.back();
+  return REXI_OK;
+}
+
 rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, int M, int real_input,
                          int tb, int te, void* ws, size_t ws_bytes, cudaStream_t s, bool adjoint) {
   const FourierLayout L = fourier_layout(p, M, real_input);
@@ -486,9 +605,7 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
   const int N = L.N;
   if (te < 0 || te > N + 1) te = N + 1;
   if (tb < 0 || tb > te) return fail(REXI_EINVAL, "bad term range [%d, %d)", tb, te);
-  TermSet ts;
-  rexii_terms(M, p->h, &ts);
-  const double h = p->h, hmu = h * ts.mu, q = hmu * hmu;
+  const double h = p->h, hmu = h * table_mu(), q = hmu * hmu;
   const double tau = dt;
   const SymbolParams sp = symbol_params(p);
   const size_t nk = (size_t)p->nx * p->ny;
@@ -514,23 +631,23 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
   };
 
   if (p->form == REXI_FORM_FP64 || p->form == REXI_FORM_MIXED) {
-    // scalar terms n = -N..N restricted to |n| in [tb, te)
-    std::vector<int> sel;
-    for (int n = -N; n <= N; ++n)
-      if (term_selected(n, tb, te)) sel.push_back(n);
-    double R0r = 0.0, R0i = 0.0;
-    for (int n : sel) {
-      const int i = n + N;
-      const double hn = h * n, d = q + hn * hn;
-      R0r += (ts.c1re[i] * hmu + ts.c2re[i] * hn) / d;
-      R0i += (ts.c1im[i] * hmu + ts.c2im[i] * hn) / d;
+    double G = 0.0;
+    if (p->form == REXI_FORM_MIXED) {
+      // grid G = 2^-g so that |x| + h N < 2^24 G: x <= tau rho
+      const double span = dt * p->rho + h * N + 4.0;
+      if (span > 4.0e6) return fail(REXI_EINVAL, "mixed form needs dt*rho + h*N < 4e6 (got %g)", span);
+      int gexp = 0;
+      while (ldexp(1.0, 23 - gexp) > span && gexp < 60) ++gexp;  // largest g with span < 2^(23-g)
+      G = ldexp(1.0, -(gexp - 1));
     }
+    const rexi_plan_s::CoefTable* ct = nullptr;
+    if ((st = fused_table(p, M, tb, te, G, s, &ct)) != REXI_OK) return st;
     FusedScalars fs;
     fs.tau = tau;
     fs.q = q;
-    fs.R0re = R0r;
-    fs.R0im = R0i;
-    fs.nterms = (int)sel.size();
+    fs.R0re = ct->R0re;
+    fs.R0im = ct->R0im;
+    fs.nterms = ct->nterms;
     fs.adjoint = adjoint ? 1 : 0;
     // With the real part of the step taken (real input), r(0) enters through
     // its real part: Re r(tau B) = Re(R0) I + Im(R+) Bt + (Re R0 - Re R+) Bt^2
@@ -540,61 +657,21 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
     const OrbitParams op = orbit_params(sp);
     const int slices = pole_orbit_slices(p->form, op.norb, fs.nterms, L.slice_cap);
     double2* part = reinterpret_cast<double2*>(base + L.part_off);
-    if (p->form == REXI_FORM_FP64) {
-      std::vector<double> tab(6 * std::max<size_t>(sel.size(), 1), 0.0);
-      for (size_t t = 0; t < sel.size(); ++t) {
-        const int n = sel[t], i = n + N;
-        double* e = &tab[6 * t];
-        e[0] = h * n;
-        e[1] = ts.c1re[i] * hmu;
-        e[2] = ts.c1im[i] * hmu;
-        e[3] = ts.c2re[i];
-        e[4] = ts.c2im[i];
-        e[5] = 0.0;
-      }
-      if ((st = stage_upload(p, tab.data(), tab.size() * sizeof(double), base + L.table_off, s)) != REXI_OK) return st;
-      if ((st = forward()) != REXI_OK) return st;
-      CUDA_TRY(pole_orbits_fp64(part, slices, sp, op, reinterpret_cast<const double*>(base + L.table_off), fs, s),
+    if ((st = forward()) != REXI_OK) return st;
+    if (p->form == REXI_FORM_FP64)
+      CUDA_TRY(pole_orbits_fp64(part, slices, sp, op, static_cast<const double*>(ct->dev), fs, s),
                "pole_orbits_fp64");
-      prof_mark(p, 5, s);
-      CUDA_TRY(pole_orbit_combine(spec, part, slices, sp, op, fs, row_len, s), "pole_orbit_combine");
-      p->launches += 2;
-    } else {
-      // grid G = 2^-g so that |x| + h N < 2^24 G: x <= tau rho
-      const double span = dt * p->rho + h * N + 4.0;
-      if (span > 4.0e6) return fail(REXI_EINVAL, "mixed form needs dt*rho + h*N < 4e6 (got %g)", span);
-      int gexp = 0;
-      while (ldexp(1.0, 23 - gexp) > span && gexp < 60) ++gexp;  // largest g with span < 2^(23-g)
-      const double G = ldexp(1.0, -(gexp - 1));
-      std::vector<float> tab(12 * std::max<size_t>(sel.size(), 1), 0.0f);
-      auto split = [](double v, float& hi, float& lo) {
-        hi = (float)v;
-        lo = (float)(v - (double)hi);
-      };
-      for (size_t t = 0; t < sel.size(); ++t) {
-        const int n = sel[t], i = n + N;
-        float* e = &tab[12 * t];
-        const double hn = h * n;
-        const double hn_g = rint(hn / G) * G;
-        float Arh, Arl, Aih, Ail, Brh, Brl, Bih, Bil;
-        split(ts.c1re[i] * hmu, Arh, Arl);
-        split(ts.c1im[i] * hmu, Aih, Ail);
-        split(ts.c2re[i], Brh, Brl);
-        split(ts.c2im[i], Bih, Bil);
-        e[0] = (float)hn_g; e[1] = Arh; e[2] = Aih; e[3] = Brh;
-        e[4] = Bih; e[5] = Arl; e[6] = Ail; e[7] = Brl;
-        e[8] = Bil; e[9] = (float)(hn - hn_g); e[10] = 0.f; e[11] = 0.f;
-      }
-      if ((st = stage_upload(p, tab.data(), tab.size() * sizeof(float), base + L.table_off, s)) != REXI_OK) return st;
-      if ((st = forward()) != REXI_OK) return st;
-      CUDA_TRY(pole_orbits_mixed(part, slices, sp, op, reinterpret_cast<const float*>(base + L.table_off), fs, G, s),
+    else
+      CUDA_TRY(pole_orbits_mixed(part, slices, sp, op, static_cast<const float*>(ct->dev), fs, G, s),
                "pole_orbits_mixed");
-      prof_mark(p, 5, s);
-      CUDA_TRY(pole_orbit_combine(spec, part, slices, sp, op, fs, row_len, s), "pole_orbit_combine");
-      p->launches += 2;
-    }
+    prof_mark(p, 5, s);
+    CUDA_TRY(pole_orbit_combine(spec, part, slices, base + L.fin_off, sp, op, fs, row_len, s),
+             "pole_orbit_combine");
+    p->launches += 3;
   } else {
     // plain form: terms n = 0..N (real) or -N..N (complex), |n| in [tb, te)
+    TermSet ts;
+    rexii_terms(M, p->h, &ts);
     std::vector<double2> tab;
     for (int n = real_input ? 0 : -N; n <= N; ++n) {
       if (!term_selected(n, tb, te)) continue;
@@ -735,9 +812,9 @@ rexi_status rexi_workspace_size_host(rexi_plan_t p, double dt, double tol, int32
   return REXI_OK;
 }
 
-rexi_status rexi_step_host(rexi_plan_t p, const void* in_host, void* out_host, double dt, double tol,
-                           int32_t real_input, void* ws, size_t ws_bytes, void* stream, rexi_step_info* info) {
-  g_err[0] = 0;
+namespace {
+rexi_status step_host_enqueue(rexi_plan_t p, const void* in_host, void* out_host, double dt, double tol,
+                              int32_t real_input, void* ws, size_t ws_bytes, void* stream, rexi_step_info* info) {
   if (!p || !in_host || !out_host || !ws) return fail(REXI_EINVAL, "NULL argument");
   if ((uintptr_t)ws & 255) return fail(REXI_EINVAL, "workspace must be 256-byte aligned");
   const size_t bytes = 3 * (size_t)p->nx * p->ny * sizeof(double2);
@@ -750,8 +827,23 @@ rexi_status rexi_step_host(rexi_plan_t p, const void* in_host, void* out_host, d
                              ws_bytes - 2 * state, stream, info);
   if (st != REXI_OK) return st;
   CUDA_TRY(cudaMemcpyAsync(out_host, base + state, bytes, cudaMemcpyDeviceToHost, s), "device-to-host copy");
-  CUDA_TRY(cudaStreamSynchronize(s), "stream synchronise");
   return REXI_OK;
+}
+}  // namespace
+
+rexi_status rexi_step_host(rexi_plan_t p, const void* in_host, void* out_host, double dt, double tol,
+                           int32_t real_input, void* ws, size_t ws_bytes, void* stream, rexi_step_info* info) {
+  g_err[0] = 0;
+  rexi_status st = step_host_enqueue(p, in_host, out_host, dt, tol, real_input, ws, ws_bytes, stream, info);
+  if (st != REXI_OK) return st;
+  CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "stream synchronise");
+  return REXI_OK;
+}
+
+rexi_status rexi_step_host_async(rexi_plan_t p, const void* in_host, void* out_host, double dt, double tol,
+                                 int32_t real_input, void* ws, size_t ws_bytes, void* stream) {
+  g_err[0] = 0;
+  return step_host_enqueue(p, in_host, out_host, dt, tol, real_input, ws, ws_bytes, stream, nullptr);
 }
 
 rexi_status rexi_plan_set_profiling(rexi_plan_t p, int32_t enable) {

@@ -31,7 +31,7 @@ namespace {
 
 struct InstDesc {
   long long spec_off;  // first element of this instance's spectrum (field 0)
-  long long orb_off;   // first entry of this instance's per-orbit R+ table
+  long long orb_off;   // first entry of this instance's per-orbit combine scalars
   int nx, ny, nterms, pad;
   int ax, ay, sym, norb;  // OrbitParams of the instance's grid
   double inv_dx, inv_dy, tau, q, R0re, R0im, grid;
@@ -94,7 +94,7 @@ namespace {
 // ---- persistent kernel ------------------------------------------------------
 
 template <int FORM, int PPT>
-__global__ void batch_pole_kernel(double2* orb, const InstDesc* __restrict__ desc,
+__global__ void batch_pole_kernel(OrbitScalars* orb, const InstDesc* __restrict__ desc,
                                   const WorkItem* __restrict__ items, int n_items, unsigned* counter,
                                   const void* __restrict__ tables, double g, double f, double H) {
   __shared__ float4 st[kChunk * 3];  // 48 bytes per term, both forms
@@ -124,13 +124,14 @@ __global__ void batch_pole_kernel(double2* orb, const InstDesc* __restrict__ des
     op.sym = D.sym;
     op.norb = D.norb;
     int o[PPT];
-    double x[PPT];
+    double x[PPT], om[PPT];
 #pragma unroll
     for (int u = 0; u < PPT; ++u) {
       o[u] = items[it].orbit_begin + u * blockDim.x + threadIdx.x;
       int a = 0, b = 0;
       if (o[u] < D.norb) orbit_rep(op, o[u], a, b);
-      x[u] = D.tau * symbol_at(sp, a, b).omega;
+      om[u] = symbol_at(sp, a, b).omega;
+      x[u] = D.tau * om[u];
     }
     double ar[PPT], ai[PPT];
     float arh[PPT], arl[PPT], aih[PPT], ail[PPT], Xh[PPT], Xl[PPT], Xl2[PPT];
@@ -166,16 +167,17 @@ __global__ void batch_pole_kernel(double2* orb, const InstDesc* __restrict__ des
 #pragma unroll
     for (int u = 0; u < PPT; ++u) {
       if (o[u] >= D.norb) continue;
-      orb[D.orb_off + o[u]] = FORM == REXI_FORM_FP64
-                                  ? make_double2(ar[u], ai[u])
-                                  : make_double2((double)arh[u] + (double)arl[u], (double)aih[u] + (double)ail[u]);
+      const double2 Rp = FORM == REXI_FORM_FP64
+                             ? make_double2(ar[u], ai[u])
+                             : make_double2((double)arh[u] + (double)arl[u], (double)aih[u] + (double)ail[u]);
+      orb[D.orb_off + o[u]] = orbit_scalars(om[u], make_double2(D.R0re, D.R0im), Rp);
     }
   }
 }
 
-// r(tau B) at every wavenumber of every instance from its orbit's R+.
+// r(tau B) at every wavenumber of every instance from its orbit's scalars.
 // Instance i owns combine blocks [blk[i], blk[i + 1]).
-__global__ void __launch_bounds__(256) batch_combine_kernel(double2* spec, const double2* __restrict__ orb,
+__global__ void __launch_bounds__(256) batch_combine_kernel(double2* spec, const OrbitScalars* __restrict__ orb,
                                                             const InstDesc* __restrict__ desc,
                                                             const int* __restrict__ blk, int n, double g, double f,
                                                             double H, int adjoint) {
@@ -205,13 +207,13 @@ __global__ void __launch_bounds__(256) batch_combine_kernel(double2* spec, const
   op.sym = D.sym;
   op.norb = D.norb;
   const int ky = k / D.nx, kx = k - ky * D.nx;
-  const double2 Rp = orb[D.orb_off + orbit_of(op, D.nx, D.ny, kx, ky)];
-  combine(spec + D.spec_off, (size_t)k, (size_t)nk, symbol_at(sp, kx, ky), sp, false, adjoint != 0,
-          make_double2(D.R0re, D.R0im), Rp);
+  const OrbitScalars o = orb[D.orb_off + orbit_of(op, D.nx, D.ny, kx, ky)];
+  combine_scaled(spec + D.spec_off, (size_t)k, (size_t)nk, symbol_entries(sp, kx, ky, adjoint != 0),
+                 make_double2(D.R0re, D.R0im), o, adjoint != 0);
 }
 
 template <int FORM, int PPT>
-cudaError_t launch_persistent(rexi_batch_s* b, double2* orb, unsigned* counter, int threads, cudaStream_t s) {
+cudaError_t launch_persistent(rexi_batch_s* b, OrbitScalars* orb, unsigned* counter, int threads, cudaStream_t s) {
   auto kern = batch_pole_kernel<FORM, PPT>;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
@@ -225,7 +227,7 @@ cudaError_t launch_persistent(rexi_batch_s* b, double2* orb, unsigned* counter, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_pole(rexi_batch_s* b, double2* orb, unsigned* counter, cudaStream_t s) {
+cudaError_t launch_pole(rexi_batch_s* b, OrbitScalars* orb, unsigned* counter, cudaStream_t s) {
   if (b->form == REXI_FORM_FP64)
     return b->ppt == 2 ? launch_persistent<REXI_FORM_FP64, 2>(b, orb, counter, b->threads, s)
                        : launch_persistent<REXI_FORM_FP64, 1>(b, orb, counter, b->threads, s);
@@ -233,7 +235,7 @@ cudaError_t launch_pole(rexi_batch_s* b, double2* orb, unsigned* counter, cudaSt
                      : launch_persistent<REXI_FORM_MIXED, 1>(b, orb, counter, b->threads, s);
 }
 
-cudaError_t launch_combine(rexi_batch_s* b, double2* spec, const double2* orb, cudaStream_t s) {
+cudaError_t launch_combine(rexi_batch_s* b, double2* spec, const OrbitScalars* orb, cudaStream_t s) {
   batch_combine_kernel<<<b->combine_blocks, 256, 0, s>>>(spec, orb, b->d_desc, b->d_blk, b->n, b->g, b->f, b->H, 0);
   return cudaGetLastError();
 }
@@ -242,16 +244,17 @@ size_t al256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Workspace: [counter (256 B)][packed spectrum][per-orbit R+ of every instance]
 size_t batch_spec_bytes(const rexi_batch_s* b) { return al256((size_t)b->offsets[b->n] * sizeof(double2)); }
-// The R+ region also serves the per-instance mode, one instance at a time,
-// with that instance's term slices.
-size_t batch_orb_entries(const rexi_batch_s* b) {
-  size_t m = (size_t)b->total_orbits;
-  for (const auto& D : b->h_desc) m = std::max(m, (size_t)orbit_slice_cap(D.norb) * D.norb);
+// The orbit region also serves the per-instance mode, one instance at a
+// time: its term slices' partial sums, then its combine scalars.
+size_t per_instance_part_bytes(const InstDesc& D) {
+  return al256((size_t)orbit_slice_cap(D.norb) * D.norb * sizeof(double2));
+}
+size_t batch_orb_bytes(const rexi_batch_s* b) {
+  size_t m = orbit_scalars_bytes((int)b->total_orbits);
+  for (const auto& D : b->h_desc) m = std::max(m, per_instance_part_bytes(D) + orbit_scalars_bytes(D.norb));
   return m;
 }
-size_t batch_ws_bytes(const rexi_batch_s* b) {
-  return 256 + batch_spec_bytes(b) + al256(batch_orb_entries(b) * sizeof(double2));
-}
+size_t batch_ws_bytes(const rexi_batch_s* b) { return 256 + batch_spec_bytes(b) + al256(batch_orb_bytes(b)); }
 
 // (Re)build the work items for the current item size, largest cost first.
 cudaError_t build_items(rexi_batch_s* b) {
@@ -294,7 +297,7 @@ cudaError_t enqueue_persistent(rexi_batch_s* b, const double2* in, double2* out,
                                cudaStream_t s) {
   unsigned* counter = reinterpret_cast<unsigned*>(ws);
   double2* spec = reinterpret_cast<double2*>(ws + 256);
-  double2* orb = reinterpret_cast<double2*>(ws + 256 + batch_spec_bytes(b));
+  OrbitScalars* orb = reinterpret_cast<OrbitScalars*>(ws + 256 + batch_spec_bytes(b));
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
   for (auto& G : b->groups) {
     if (e != cudaSuccess) return e;
@@ -573,7 +576,7 @@ rexi_status rexi_batch_step(rexi_batch_t b, const void* in, void* out, int32_t r
   cudaError_t e = cudaSuccess;
   if (mode == REXI_BATCH_PER_INSTANCE) {
     double2* spec = reinterpret_cast<double2*>(wsc + 256);
-    double2* orb = reinterpret_cast<double2*>(wsc + 256 + batch_spec_bytes(b));
+    char* orb = wsc + 256 + batch_spec_bytes(b);
     for (int i = 0; i < b->n && e == cudaSuccess; ++i) {
       const InstDesc& D = b->h_desc[i];
       FftPlan1D fx, fy;
@@ -595,14 +598,16 @@ rexi_status rexi_batch_step(rexi_batch_t b, const void* in, void* out, int32_t r
       OrbitParams op;
       op.ax = D.ax; op.ay = D.ay; op.sym = D.sym; op.norb = D.norb;
       const int slices = pole_orbit_slices(b->form, op.norb, D.nterms, orbit_slice_cap(op.norb));
+      double2* part = reinterpret_cast<double2*>(orb);
       if (e == cudaSuccess)
         e = b->form == REXI_FORM_FP64
-                ? pole_orbits_fp64(orb, slices, sp, op, reinterpret_cast<const double*>(tab), fs, s)
-                : pole_orbits_mixed(orb, slices, sp, op, tab, fs, D.grid, s);
-      if (e == cudaSuccess) e = pole_orbit_combine(sp_i, orb, slices, sp, op, fs, D.nx, s);
+                ? pole_orbits_fp64(part, slices, sp, op, reinterpret_cast<const double*>(tab), fs, s)
+                : pole_orbits_mixed(part, slices, sp, op, tab, fs, D.grid, s);
+      if (e == cudaSuccess)
+        e = pole_orbit_combine(sp_i, part, slices, orb + per_instance_part_bytes(D), sp, op, fs, D.nx, s);
       if (e == cudaSuccess)
         e = fft_any(b, sp_i, out2 + D.spec_off, 3, fx, fy, +1, 1.0 / ((double)D.nx * D.ny), 0, real_input, s);
-      b->launches += 6;
+      b->launches += 7;
     }
   } else if (mode == REXI_BATCH_PERSISTENT) {
     const bool same = b->exec && b->g_in == in && b->g_out == out && b->g_ws == ws && b->g_real == real_input &&

@@ -99,11 +99,14 @@ cudaError_t pole_orbits_fp64(double2* part, int slices, const SymbolParams& sp, 
                              const double* table, const FusedScalars& fs, cudaStream_t s);
 cudaError_t pole_orbits_mixed(double2* part, int slices, const SymbolParams& sp, const OrbitParams& op,
                               const float* table, const FusedScalars& fs, double grid, cudaStream_t s);
-// spec <- r(tau B) spec at every wavenumber, R+ = sum over slices of part.
-// row_len: nx (full spectrum, rows of nx values) or nx/2 + 1 (half spectrum
-// of real input, wavenumbers kx = 0..nx/2 only).
-cudaError_t pole_orbit_combine(double2* spec, const double2* part, int slices, const SymbolParams& sp,
+// spec <- r(tau B) spec at every wavenumber, R+ = sum over slices of part:
+// a per-orbit pass writes the combine scalars to `fin`
+// (orbit_scalars_bytes(norb) bytes, 32-byte aligned), then a pass over the
+// wavenumbers applies them.  row_len: nx (full spectrum, rows of nx values)
+// or nx/2 + 1 (half spectrum of real input, wavenumbers kx = 0..nx/2 only).
+cudaError_t pole_orbit_combine(double2* spec, const double2* part, int slices, void* fin, const SymbolParams& sp,
                                const OrbitParams& op, const FusedScalars& fs, int row_len, cudaStream_t s);
+size_t orbit_scalars_bytes(int norb);
 struct PlainScalars {
   double tau;
   int nterms;   // terms in this chunk

@@ -109,6 +109,88 @@ __device__ __forceinline__ void combine(double2* spec, size_t idx, size_t fs, co
   for (int c = 0; c < 3; ++c) spec[idx + c * fs] = out[c];
 }
 
+// Per-orbit scalars of the combine step: with y1 = B f and y2 = B^2 f
+// (unscaled), r(tau B) f = c0 f + s1 y1 + s2 y2, s1 = Im(R+)/omega,
+// s2 = (R0 - Re R+)/omega^2 (0 and 0 at omega = 0, where B = 0).
+struct OrbitScalars {
+  double s1, s2re, s2im, pad;
+};
+
+__device__ __forceinline__ OrbitScalars orbit_scalars(double omega, double2 R0, double2 Rp) {
+  OrbitScalars o;
+  o.pad = 0.0;
+  if (omega > 0.0) {
+    const double iw = 1.0 / omega, iw2 = iw * iw;
+    o.s1 = Rp.y * iw;
+    o.s2re = (R0.x - Rp.x) * iw2;
+    o.s2im = R0.y * iw2;
+  } else {
+    o.s1 = o.s2re = o.s2im = 0.0;
+  }
+  return o;
+}
+
+// The six nonzero entries of B(k) with g, H and f folded in (or of B^H for
+// the adjoint: (B^H)_ij = conj(B_ji)):
+//   y0 = e01 f1 + e02 f2,  y1 = e10 f0 + e12 f2,  y2 = e20 f0 + e21 f1.
+struct SymbolEntries {
+  double2 e01, e02, e10, e12, e20, e21;
+};
+
+__device__ __forceinline__ SymbolEntries symbol_entries(const SymbolParams& sp, int kx, int ky, bool adjoint) {
+  const Symbol S = symbol_at(sp, kx, ky);
+  SymbolEntries E;
+  E.e01 = cr(-sp.H, S.dxb);
+  E.e02 = cr(-sp.H, S.dyb);
+  E.e10 = cr(-sp.g, S.dxf);
+  E.e12 = cr(sp.f, S.P);
+  E.e20 = cr(-sp.g, S.dyf);
+  E.e21 = cr(-sp.f, cj(S.P));
+  if (adjoint) {
+    const SymbolEntries F = E;
+    E.e01 = cj(F.e10);
+    E.e02 = cj(F.e20);
+    E.e10 = cj(F.e01);
+    E.e12 = cj(F.e21);
+    E.e20 = cj(F.e02);
+    E.e21 = cj(F.e12);
+  }
+  return E;
+}
+
+// a b + c
+__device__ __forceinline__ double2 cma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+
+__device__ __forceinline__ void apply_entries(const SymbolEntries& E, const double2 f[3], double2 y[3]) {
+  y[0] = cma(E.e01, f[1], cm(E.e02, f[2]));
+  y[1] = cma(E.e10, f[0], cm(E.e12, f[2]));
+  y[2] = cma(E.e20, f[0], cm(E.e21, f[1]));
+}
+
+// out = c0 f + s1 B f + s2 B^2 f in place at wavenumber index idx (field
+// stride fs); for the adjoint c0 and s2 are conjugated and B is B^H.
+__device__ __forceinline__ void combine_scaled(double2* spec, size_t idx, size_t fs, const SymbolEntries& E,
+                                               double2 c0, OrbitScalars o, bool adjoint) {
+  double2 f[3], y1[3], y2[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) f[c] = spec[idx + c * fs];
+  double2 s2 = make_double2(o.s2re, o.s2im);
+  if (adjoint) {
+    c0 = cj(c0);
+    s2 = cj(s2);
+  }
+  apply_entries(E, f, y1);
+  apply_entries(E, y1, y2);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double2 t = cm(c0, f[c]);
+    const double2 u = make_double2(fma(o.s1, y1[c].x, t.x), fma(o.s1, y1[c].y, t.y));
+    spec[idx + c * fs] = cma(s2, y2[c], u);
+  }
+}
+
 // Map thread -> wavenumber pair.  Pairs (k, -k) with ky in [0, ny/2]; in the
 // self-conjugate rows (ky = 0, and ky = ny/2 for even ny) only kx <= nx/2.
 // omega(-k) = omega(k), so one pole loop serves both; the combine step takes

@@ -148,6 +148,10 @@ int orbit_slice_cap(int norb) {
 }
 
 constexpr int kOrbitThreads = 128;
+#ifndef REXI_ORBIT_PPT
+#define REXI_ORBIT_PPT 2
+#endif
+constexpr int kOrbitPPT = REXI_ORBIT_PPT;  // orbits per thread in the double-float pole sum
 
 __device__ __forceinline__ void slice_range(const FusedScalars& fs, int slices, int& t_begin, int& t_end) {
   const int per = (fs.nterms + slices - 1) / slices;
@@ -180,21 +184,28 @@ __global__ void __launch_bounds__(kOrbitThreads) pole_orbit_fp64_kernel(double2*
   if (o < op.norb) part[(size_t)blockIdx.y * op.norb + o] = make_double2(accr, acci);
 }
 
+// PPT orbits per thread share each staged term's shared-memory loads.
+template <int PPT>
 __global__ void __launch_bounds__(kOrbitThreads) pole_orbit_mixed_kernel(double2* __restrict__ part, SymbolParams sp,
                                                                          OrbitParams op,
                                                                          const float4* __restrict__ table,
                                                                          FusedScalars fs, double grid, float q_hi,
                                                                          float q_lo, int slices) {
   __shared__ float4 st[kChunk * 3];
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  int a = 0, b = 0;
-  if (o < op.norb) orbit_rep(op, o, a, b);
-  const double x = fs.tau * symbol_at(sp, a, b).omega;
-  const double xg = rint(x / grid) * grid;
-  const float X_hi = (float)xg;
-  const float X_lo = (float)(x - xg);
-  const float X_lo2 = (float)((x - xg) - (double)X_lo);
-  float ar_h = 0.f, ar_l = 0.f, ai_h = 0.f, ai_l = 0.f;
+  float X_hi[PPT], X_lo[PPT], X_lo2[PPT], ar_h[PPT], ar_l[PPT], ai_h[PPT], ai_l[PPT];
+  int o[PPT];
+#pragma unroll
+  for (int u = 0; u < PPT; ++u) {
+    o[u] = (blockIdx.x * PPT + u) * blockDim.x + threadIdx.x;
+    int a = 0, b = 0;
+    if (o[u] < op.norb) orbit_rep(op, o[u], a, b);
+    const double x = fs.tau * symbol_at(sp, a, b).omega;
+    const double xg = rint(x / grid) * grid;
+    X_hi[u] = (float)xg;
+    X_lo[u] = (float)(x - xg);
+    X_lo2[u] = (float)((x - xg) - (double)X_lo[u]);
+    ar_h[u] = ar_l[u] = ai_h[u] = ai_l[u] = 0.f;
+  }
   int t_begin, t_end;
   slice_range(fs, slices, t_begin, t_end);
   for (int t0 = t_begin; t0 < t_end; t0 += kChunk) {
@@ -203,28 +214,46 @@ __global__ void __launch_bounds__(kOrbitThreads) pole_orbit_mixed_kernel(double2
     for (int i = threadIdx.x; i < cnt * 3; i += blockDim.x) st[i] = table[(size_t)t0 * 3 + i];
     __syncthreads();
 #pragma unroll 2
-    for (int t = 0; t < cnt; ++t) df_term(st + 3 * t, X_hi, X_lo, X_lo2, q_hi, q_lo, ar_h, ar_l, ai_h, ai_l);
+    for (int t = 0; t < cnt; ++t)
+#pragma unroll
+      for (int u = 0; u < PPT; ++u)
+        df_term(st + 3 * t, X_hi[u], X_lo[u], X_lo2[u], q_hi, q_lo, ar_h[u], ar_l[u], ai_h[u], ai_l[u]);
   }
-  if (o < op.norb)
-    part[(size_t)blockIdx.y * op.norb + o] =
-        make_double2((double)ar_h + (double)ar_l, (double)ai_h + (double)ai_l);
+#pragma unroll
+  for (int u = 0; u < PPT; ++u)
+    if (o[u] < op.norb)
+      part[(size_t)blockIdx.y * op.norb + o[u]] =
+          make_double2((double)ar_h[u] + (double)ar_l[u], (double)ai_h[u] + (double)ai_l[u]);
 }
 
-__global__ void __launch_bounds__(256) pole_orbit_combine_kernel(double2* spec, const double2* __restrict__ part,
-                                                                 int slices, SymbolParams sp, OrbitParams op,
-                                                                 double2 R0, int adjoint, int row_len) {
-  const size_t nk = (size_t)row_len * sp.ny;
-  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nk) return;
-  const int ky = (int)(k / row_len), kx = (int)(k - (size_t)ky * row_len);
-  const int o = orbit_of(op, sp.nx, sp.ny, kx, ky);
+// Per orbit: R+ = sum of the slices' partial sums (fixed order), then the
+// combine scalars at the representative's omega.
+__global__ void __launch_bounds__(256) pole_orbit_finalize_kernel(const double2* __restrict__ part, int slices,
+                                                                  SymbolParams sp, OrbitParams op, double2 R0,
+                                                                  OrbitScalars* __restrict__ fin) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= op.norb) return;
   double2 Rp = part[o];
   for (int s = 1; s < slices; ++s) {
     const double2 v = part[(size_t)s * op.norb + o];
     Rp.x += v.x;
     Rp.y += v.y;
   }
-  combine(spec, k, nk, symbol_at(sp, kx, ky), sp, false, adjoint != 0, R0, Rp);
+  int a, b;
+  orbit_rep(op, o, a, b);
+  fin[o] = orbit_scalars(symbol_at(sp, a, b).omega, R0, Rp);
+}
+
+__global__ void __launch_bounds__(256) pole_orbit_combine_kernel(double2* spec,
+                                                                 const OrbitScalars* __restrict__ fin,
+                                                                 SymbolParams sp, OrbitParams op, double2 R0,
+                                                                 int adjoint, int row_len) {
+  const size_t nk = (size_t)row_len * sp.ny;
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nk) return;
+  const int ky = (int)(k / row_len), kx = (int)(k - (size_t)ky * row_len);
+  const OrbitScalars o = fin[orbit_of(op, sp.nx, sp.ny, kx, ky)];
+  combine_scaled(spec, k, nk, symbol_entries(sp, kx, ky, adjoint != 0), R0, o, adjoint != 0);
 }
 
 namespace {
@@ -238,7 +267,8 @@ OrbitOccupancy orbit_occupancy() {
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, pole_orbit_fp64_kernel, kOrbitThreads, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bmx, pole_orbit_mixed_kernel, kOrbitThreads, 0) != cudaSuccess) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bmx, pole_orbit_mixed_kernel<kOrbitPPT>, kOrbitThreads, 0) !=
+            cudaSuccess) {
       cudaGetLastError();
       return OrbitOccupancy{152, 8, 8};
     }
@@ -254,7 +284,8 @@ int pole_orbit_slices(int form, int norb, int nterms, int cap) {
   if (nterms <= 1) return 1;
   const OrbitOccupancy occ = orbit_occupancy();
   const long long resident = (long long)occ.sms * (form == REXI_FORM_MIXED ? occ.mixed_blocks : occ.fp64_blocks);
-  const long long bx = (norb + kOrbitThreads - 1) / kOrbitThreads;
+  const int per_block = kOrbitThreads * (form == REXI_FORM_MIXED ? kOrbitPPT : 1);
+  const long long bx = (norb + per_block - 1) / per_block;
   // per block: its terms plus a fixed cost (symbol, FP64 setup, staging, the
   // write) of about 48 terms; blocks run in waves of `resident`
   double best = 0.0;
@@ -281,19 +312,26 @@ cudaError_t pole_orbits_mixed(double2* part, int slices, const SymbolParams& sp,
                               const float* table, const FusedScalars& fs, double grid_step, cudaStream_t s) {
   const float q_hi = (float)fs.q;
   const float q_lo = (float)(fs.q - (double)q_hi);
-  dim3 grid((unsigned)((op.norb + kOrbitThreads - 1) / kOrbitThreads), (unsigned)slices);
-  pole_orbit_mixed_kernel<<<grid, kOrbitThreads, 0, s>>>(part, sp, op, reinterpret_cast<const float4*>(table), fs,
-                                                         grid_step, q_hi, q_lo, slices);
+  const int per_block = kOrbitThreads * kOrbitPPT;
+  dim3 grid((unsigned)((op.norb + per_block - 1) / per_block), (unsigned)slices);
+  pole_orbit_mixed_kernel<kOrbitPPT><<<grid, kOrbitThreads, 0, s>>>(
+      part, sp, op, reinterpret_cast<const float4*>(table), fs, grid_step, q_hi, q_lo, slices);
   return cudaGetLastError();
 }
 
-cudaError_t pole_orbit_combine(double2* spec, const double2* part, int slices, const SymbolParams& sp,
+cudaError_t pole_orbit_combine(double2* spec, const double2* part, int slices, void* fin, const SymbolParams& sp,
                                const OrbitParams& op, const FusedScalars& fs, int row_len, cudaStream_t s) {
+  const double2 R0 = make_double2(fs.R0re, fs.R0im);
+  OrbitScalars* F = static_cast<OrbitScalars*>(fin);
+  pole_orbit_finalize_kernel<<<(unsigned)((op.norb + 255) / 256), 256, 0, s>>>(part, slices, sp, op, R0, F);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   const size_t nk = (size_t)row_len * sp.ny;
-  pole_orbit_combine_kernel<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(
-      spec, part, slices, sp, op, make_double2(fs.R0re, fs.R0im), fs.adjoint, row_len);
+  pole_orbit_combine_kernel<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(spec, F, sp, op, R0, fs.adjoint, row_len);
   return cudaGetLastError();
 }
+
+size_t orbit_scalars_bytes(int norb) { return (size_t)norb * sizeof(OrbitScalars); }
 
 // ---------------------------------------------------------------------------
 // Plain form (paper-style): materialise g3 per (term, k), then reduce.

@@ -75,6 +75,7 @@ SIGNATURES = {
     "rexi_step_adjoint": (_c_int, [_vp, _vp, _vp, _c_dbl, _c_dbl, _c_int, _vp, ctypes.c_size_t, _vp]),
     "rexi_step_grad_depth": (_c_int, [_vp, _vp, _vp, _vp, _c_dbl, _c_dbl, _c_int, _vp, ctypes.c_size_t, _vp,
                                       ctypes.POINTER(rexi_step_info)]),
+    "rexi_step_host_async": (_c_int, [_vp, _vp, _vp, _c_dbl, _c_dbl, _c_int, _vp, ctypes.c_size_t, _vp]),
     "rexi_step_host": (_c_int, [_vp, _vp, _vp, _c_dbl, _c_dbl, _c_int, _vp, ctypes.c_size_t, _vp,
                                 ctypes.POINTER(rexi_step_info)]),
     "rexi_workspace_size_host": (_c_int, [_vp, _c_dbl, _c_dbl, _c_int, ctypes.POINTER(ctypes.c_size_t)]),
@@ -283,14 +284,23 @@ class Plan:
                "rexi_workspace_size_host")
         return torch.empty(max(b.value, 256), dtype=torch.uint8, device=device or "cuda")
 
-    def step_host(self, state_host, out_host, dt, tol=1e-10, real_input=True, workspace=None, stream=None):
-        """Host-buffer step: ``state_host``/``out_host`` are CPU tensors (pinned for full speed)."""
+    def step_host(self, state_host, out_host, dt, tol=1e-10, real_input=True, workspace=None, stream=None,
+                  blocking=True):
+        """Host-buffer step: ``state_host``/``out_host`` are CPU tensors (pinned for full speed).
+        With blocking=False the copies and the step are only enqueued on ``stream``
+        (rexi_step_host_async): ``out_host`` is ready once the stream gets there."""
         if workspace is None:
             workspace = self.workspace_host(dt, tol, real_input)
-        st = self._lib.rexi_step_host(self._h, ctypes.c_void_p(state_host.data_ptr()),
-                                      ctypes.c_void_p(out_host.data_ptr()), dt, tol, int(real_input),
-                                      _ptr(workspace), workspace.numel(), _stream_handle(stream), None)
-        _check(st, "rexi_step_host")
+        if blocking:
+            st = self._lib.rexi_step_host(self._h, ctypes.c_void_p(state_host.data_ptr()),
+                                          ctypes.c_void_p(out_host.data_ptr()), dt, tol, int(real_input),
+                                          _ptr(workspace), workspace.numel(), _stream_handle(stream), None)
+            _check(st, "rexi_step_host")
+        else:
+            st = self._lib.rexi_step_host_async(self._h, ctypes.c_void_p(state_host.data_ptr()),
+                                                ctypes.c_void_p(out_host.data_ptr()), dt, tol, int(real_input),
+                                                _ptr(workspace), workspace.numel(), _stream_handle(stream))
+            _check(st, "rexi_step_host_async")
         return out_host
 
     def set_profiling(self, enable=True):

@@ -137,6 +137,34 @@ def test_real_input_half_spectrum(form, nx, ny):
     assert abs(lhs - rhs) < 1e-11 * abs(lhs)
 
 
+def test_host_buffer_steps_blocking_and_overlapped():
+    """rexi_step_host equals rexi_step on the same state; rexi_step_host_async
+    on two streams with a workspace each (copies of one step overlapping the
+    kernels of the other) gives every step's result once its stream is
+    synchronised.  The plan is shared by both streams."""
+    torch = torch_cuda()
+    from paper_2008_11607_gb300 import rexi
+
+    nx, ny = 64, 48
+    plan = rexi.Plan(nx, ny, form="mixed")
+    dt = 60.0 / plan.rho
+    states = [inputs.kminus3_field(nx, ny, seed=40 + i) for i in range(5)]
+    refs = [plan.step(to_dev(torch, st), dt).cpu().numpy() for st in states]
+    pinned = [torch.from_numpy(st).pin_memory() for st in states]
+    out = torch.empty_like(pinned[0]).pin_memory()
+    plan.step_host(pinned[0], out, dt)
+    assert np.array_equal(out.numpy(), refs[0])
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    wss = [plan.workspace_host(dt), plan.workspace_host(dt)]
+    outs = [torch.empty_like(pinned[0]).pin_memory() for _ in states]
+    for i, st in enumerate(pinned):
+        plan.step_host(st, outs[i], dt, workspace=wss[i % 2], stream=streams[i % 2], blocking=False)
+    for sm in streams:
+        sm.synchronize()
+    for o, r in zip(outs, refs):
+        assert np.array_equal(o.numpy(), r)
+
+
 @pytest.mark.parametrize("form", FORMS)
 def test_term_slices_sum_to_full(form):
     torch = torch_cuda()
