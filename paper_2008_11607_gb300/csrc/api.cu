@@ -62,6 +62,10 @@ struct rexi_plan_s {
   bool r2c = false;
   double2* tw_xh = nullptr;
   float4* twf_xh = nullptr;
+  // half angles as double-float pairs (cos hi, cos lo, sin hi, sin lo) for
+  // the double-float combine pass
+  float4* halfdf_x = nullptr;
+  float4* halfdf_y = nullptr;
   double2* half_x = nullptr;
   double2* half_y = nullptr;
   // device coefficient tables of the FP64 and mixed Fourier forms, one per
@@ -217,6 +221,8 @@ void rexi_plan_destroy(rexi_plan_t p) {
   cudaFree(p->twf_y);
   cudaFree(p->tw_xh);
   cudaFree(p->twf_xh);
+  cudaFree(p->halfdf_x);
+  cudaFree(p->halfdf_y);
   cudaFree(p->half_x);
   cudaFree(p->half_y);
   if (p->staging) cudaFreeHost(p->staging);
@@ -295,6 +301,14 @@ rexi_status rexi_plan_create(rexi_plan_t* out, int32_t nx, int32_t ny, double Lx
       }
       p->fx.twf = p->twf_x;
       p->fy.twf = p->twf_y;
+      std::vector<double2> hx4(nx), hy4(ny);
+      split_twiddles(hx.data(), nx, reinterpret_cast<float4*>(hx4.data()));
+      split_twiddles(hy.data(), ny, reinterpret_cast<float4*>(hy4.data()));
+      if (!upload_table(hx4, reinterpret_cast<double2**>(&p->halfdf_x), &st) ||
+          !upload_table(hy4, reinterpret_cast<double2**>(&p->halfdf_y), &st)) {
+        rexi_plan_destroy(p);
+        return st;
+      }
     }
     if (nx % 2 == 0 && fft_factor(nx / 2, &p->fxh)) {  // real-input transforms along x
       const int m = nx / 2;
@@ -615,7 +629,10 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
   // transforms along x; the pole step there is the Hermitian part of the
   // full-spectrum step (the real part the full path takes at the end)
   const bool half = real_input && p->r2c && !p->spectral && p->form != REXI_FORM_PLAIN;
-  const int df = p->form == REXI_FORM_MIXED ? 1 : 0;
+  // mixed form on the half spectrum: the spectrum stays in double-float from
+  // the forward transform through the combine pass to the inverse transform
+  const bool df_spec = half && p->form == REXI_FORM_MIXED && fft_df_ready(p->fx, p->fxh, p->fy);
+  const int df = p->form == REXI_FORM_MIXED ? (df_spec ? 2 : 1) : 0;
   prof_mark(p, 0, s);
   const double2* in2 = static_cast<const double2*>(in);
   auto forward = [&]() -> rexi_status {
@@ -665,8 +682,13 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
       CUDA_TRY(pole_orbits_mixed(part, slices, sp, op, static_cast<const float*>(ct->dev), fs, G, s),
                "pole_orbits_mixed");
     prof_mark(p, 5, s);
-    CUDA_TRY(pole_orbit_combine(spec, part, slices, base + L.fin_off, sp, op, fs, row_len, s),
-             "pole_orbit_combine");
+    if (df_spec)
+      CUDA_TRY(pole_orbit_combine_df(spec, part, slices, base + L.fin_off, sp, p->halfdf_x, p->halfdf_y, op, fs,
+                                     row_len, s),
+               "pole_orbit_combine_df");
+    else
+      CUDA_TRY(pole_orbit_combine(spec, part, slices, base + L.fin_off, sp, op, fs, row_len, s),
+               "pole_orbit_combine");
     p->launches += 3;
   } else {
     // plain form: terms n = 0..N (real) or -N..N (complex), |n| in [tb, te)

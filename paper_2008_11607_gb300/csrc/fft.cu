@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace rexi {
@@ -41,34 +42,6 @@ __device__ __forceinline__ double2 mul_si(double2 a) {
   return SIGN < 0 ? make_double2(a.y, -a.x) : make_double2(-a.y, a.x);
 }
 
-// ---- double-float complex (float4: re_hi, re_lo, im_hi, im_lo) ----
-__device__ __forceinline__ float2 f_fast(float s, float e) {
-  const float h = s + e;
-  return make_float2(h, e - (h - s));
-}
-__device__ __forceinline__ float2 f_add(float a, float al, float b, float bl) {
-  const float s = a + b, bb = s - a;
-  return f_fast(s, ((a - (s - bb)) + (b - bb)) + (al + bl));
-}
-// x * y for double-floats x = (a, al), y = (b, bl), as an unnormalised pair
-__device__ __forceinline__ float2 f_mul(float a, float al, float b, float bl) {
-  const float p = a * b;
-  return make_float2(p, fmaf(a, bl, fmaf(al, b, fmaf(a, b, -p))));
-}
-__device__ __forceinline__ float4 cadd(float4 a, float4 b) {
-  const float2 r = f_add(a.x, a.y, b.x, b.y), i = f_add(a.z, a.w, b.z, b.w);
-  return make_float4(r.x, r.y, i.x, i.y);
-}
-__device__ __forceinline__ float4 csub(float4 a, float4 b) {
-  const float2 r = f_add(a.x, a.y, -b.x, -b.y), i = f_add(a.z, a.w, -b.z, -b.w);
-  return make_float4(r.x, r.y, i.x, i.y);
-}
-__device__ __forceinline__ float4 cmul(float4 a, float4 w) {
-  const float2 rr = f_mul(a.x, a.y, w.x, w.y), ii = f_mul(a.z, a.w, w.z, w.w);
-  const float2 ri = f_mul(a.x, a.y, w.z, w.w), ir = f_mul(a.z, a.w, w.x, w.y);
-  const float2 re = f_add(rr.x, rr.y, -ii.x, -ii.y), im = f_add(ri.x, ri.y, ir.x, ir.y);
-  return make_float4(re.x, re.y, im.x, im.y);
-}
 template <int SIGN>
 __device__ __forceinline__ float4 mul_si(float4 a) {
   return SIGN < 0 ? make_float4(a.z, a.w, -a.x, -a.y) : make_float4(-a.z, -a.w, a.x, a.y);
@@ -259,29 +232,32 @@ __device__ __forceinline__ void cvt(double2 v, int zero_imag, double2* o) {
   *o = v;
 }
 __device__ __forceinline__ void cvt(double2 v, int zero_imag, float4* o) {
-  const float rh = (float)v.x, ih = zero_imag ? 0.f : (float)v.y;
-  *o = make_float4(rh, (float)(v.x - (double)rh), ih, zero_imag ? 0.f : (float)(v.y - (double)ih));
+  const float2 re = df_from_double(v.x);
+  const float2 im = zero_imag ? make_float2(0.f, 0.f) : df_from_double(v.y);
+  *o = make_float4(re.x, re.y, im.x, im.y);
 }
 __device__ __forceinline__ void cvt(float4 v, int zero_imag, float4* o) {
   if (zero_imag) v.z = v.w = 0.f;
   *o = v;
 }
-__device__ __forceinline__ void out_cvt(double2 v, double scale, int real_out, double2* o) {
+// scale: FP64 (FP64 values) or the same as a double-float pair (double-float values)
+__device__ __forceinline__ void out_cvt(double2 v, double scale, float2, int real_out, double2* o) {
   *o = make_double2(v.x * scale, real_out ? 0.0 : v.y * scale);
 }
-__device__ __forceinline__ void out_cvt(float4 v, double scale, int real_out, double2* o) {
-  const double re = (double)v.x + (double)v.y, im = (double)v.z + (double)v.w;
-  *o = make_double2(re * scale, real_out ? 0.0 : im * scale);
+__device__ __forceinline__ void out_cvt(float4 v, double, float2 sdf, int real_out, double2* o) {
+  const double re = df_to_double(f_mulf(make_float2(v.x, v.y), sdf));
+  *o = make_double2(re, real_out ? 0.0 : df_to_double(f_mulf(make_float2(v.z, v.w), sdf)));
 }
 // between passes: scale 1, complex (the caller passes scale = 1, real_out = 0)
-__device__ __forceinline__ void out_cvt(float4 v, double, int, float4* o) { *o = v; }
+__device__ __forceinline__ void out_cvt(float4 v, double, float2, int, float4* o) { *o = v; }
 
 // Rows: `rpc` rows of length n per CTA.  `in` and `out` may alias (each CTA
 // reads all of its rows before writing them).  T: arithmetic type; TI, TO:
 // value types in HBM.
 template <int SIGN, typename T, typename TI, typename TO>
 __global__ void __launch_bounds__(256) fft_rows_kernel(const TI* in, TO* out, int nrows, int rpc, StageList st,
-                                                       const T* tw, double scale, int zero_imag_in, int real_out) {
+                                                       const T* tw, double scale, float2 sdf, int zero_imag_in,
+                                                       int real_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
   const int n = st.n;
@@ -298,13 +274,14 @@ __global__ void __launch_bounds__(256) fft_rows_kernel(const TI* in, TO* out, in
   __syncthreads();
   T* res = run_stages<SIGN>(b0, b1, st, rpc, n, 1, false, tw);
   TO* g_out = out + row0 * n;
-  for (int i = threadIdx.x; i < nr * n; i += blockDim.x) out_cvt(res[i], scale, real_out, g_out + i);
+  for (int i = threadIdx.x; i < nr * n; i += blockDim.x) out_cvt(res[i], scale, sdf, real_out, g_out + i);
 }
 
 // Columns: W adjacent columns of one field per CTA (blockIdx.y = field).
 template <int SIGN, typename T, typename TI, typename TO>
-__global__ void __launch_bounds__(256) fft_cols_kernel(const TI* in, TO* out, int nx, int W, StageList st,
-                                                       const T* tw, double scale, int zero_imag_in, int real_out) {
+__global__ void __launch_bounds__(512) fft_cols_kernel(const TI* in, TO* out, int nx, int W, StageList st,
+                                                       const T* tw, double scale, float2 sdf, int zero_imag_in,
+                                                       int real_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
   const int ny = st.n;
@@ -325,7 +302,7 @@ __global__ void __launch_bounds__(256) fft_cols_kernel(const TI* in, TO* out, in
   TO* g_out = out + field_off + x0;
   for (int i = threadIdx.x; i < ny * W; i += blockDim.x) {
     const int t = i / W, c = i - t * W;
-    if (c < w) out_cvt(res[i], scale, real_out, g_out + (size_t)t * nx + c);
+    if (c < w) out_cvt(res[i], scale, sdf, real_out, g_out + (size_t)t * nx + c);
   }
 }
 
@@ -350,9 +327,13 @@ __device__ __forceinline__ void real_pair(const double2* g, double2* v) { *v = m
 __device__ __forceinline__ void real_pair(const double2* g, float4* v) {
   cvt(make_double2(g[0].x, g[1].x), 0, v);
 }
-__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
-__device__ __forceinline__ double2 to_d2(float4 v) {
-  return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+// scaled real and imaginary parts as FP64
+__device__ __forceinline__ double2 to_d2(double2 v, double scale, float2) {
+  return make_double2(v.x * scale, v.y * scale);
+}
+__device__ __forceinline__ double2 to_d2(float4 v, double, float2 sdf) {
+  return make_double2(df_to_double(f_mulf(make_float2(v.x, v.y), sdf)),
+                      df_to_double(f_mulf(make_float2(v.z, v.w), sdf)));
 }
 
 // Forward, rows: `rpc` real rows of length 2m per CTA -> m + 1 spectrum values each.
@@ -383,7 +364,7 @@ __global__ void __launch_bounds__(256) fft_rows_r2c_kernel(const double2* in, TO
     const T e = half_of(cadd(zk, zc));
     const T o = half_of(mul_si<-1>(csub(zk, zc)));
     const T x = cadd(e, cmul(o, tw_load<-1>(tw_full, k)));
-    out_cvt(x, 1.0, 0, g_out + i);
+    out_cvt(x, 1.0, make_float2(1.f, 0.f), 0, g_out + i);
   }
 }
 
@@ -391,7 +372,7 @@ __global__ void __launch_bounds__(256) fft_rows_r2c_kernel(const double2* in, TO
 template <typename T, typename TI>
 __global__ void __launch_bounds__(256) fft_rows_c2r_kernel(const TI* in, double2* out, int nrows, int rpc,
                                                            StageList st, const T* tw_half, const T* tw_full,
-                                                           double scale) {
+                                                           double scale, float2 sdf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* smem = reinterpret_cast<T*>(smem_raw);
   const int m = st.n, n = 2 * m;
@@ -420,9 +401,9 @@ __global__ void __launch_bounds__(256) fft_rows_c2r_kernel(const TI* in, double2
   const T* res = run_stages<+1>(b0, b1, st, rpc, m, 1, false, tw_half);
   double2* g_out = out + row0 * n;
   for (int i = threadIdx.x; i < nr * m; i += blockDim.x) {
-    const double2 z = to_d2(res[i]);
-    g_out[2 * (size_t)i] = make_double2(z.x * scale, 0.0);
-    g_out[2 * (size_t)i + 1] = make_double2(z.y * scale, 0.0);
+    const double2 z = to_d2(res[i], scale, sdf);
+    g_out[2 * (size_t)i] = make_double2(z.x, 0.0);
+    g_out[2 * (size_t)i + 1] = make_double2(z.y, 0.0);
   }
 }
 
@@ -462,6 +443,11 @@ static StageList to_stages(const FftPlan1D& p) {
   return s;
 }
 
+static float2 split_scale(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
 static int rows_per_cta(int n) {
   int r = 1;
   while (r < 16 && r * n * 2 <= 1024) r *= 2;
@@ -472,6 +458,9 @@ static int cols_per_cta(int n) {
   while (w > 1 && 2 * (size_t)w * n * sizeof(double2) > 128 * 1024) w /= 2;
   return w;
 }
+// Threads of a column CTA: a large tile (one CTA per SM by its shared memory)
+// gets 512 threads, one radix-8 butterfly each per stage.
+static int cols_threads(int W, int n) { return (size_t)W * n >= 4096 ? 512 : 256; }
 
 template <typename K>
 static cudaError_t allow_smem(K kernel, size_t bytes) {
@@ -497,7 +486,7 @@ static cudaError_t fft2d_impl(const double2* in, double2* out, int nfields, cons
     auto k = fft_rows_kernel<SIGN, T, double2, TM>;
     if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
     dim3 grid((nrows + rpc - 1) / rpc);
-    k<<<grid, 256, sm, s>>>(in, mid, nrows, rpc, to_stages(px), twx, 1.0, zero_imag_in, 0);
+    k<<<grid, 256, sm, s>>>(in, mid, nrows, rpc, to_stages(px), twx, 1.0, split_scale(1.0), zero_imag_in, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
@@ -506,7 +495,8 @@ static cudaError_t fft2d_impl(const double2* in, double2* out, int nfields, cons
     auto k = fft_cols_kernel<SIGN, T, TM, double2>;
     if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
     dim3 grid((nx + W - 1) / W, nfields);
-    k<<<grid, 256, sm, s>>>(mid, out, nx, W, to_stages(py), twy, scale, 0, real_out);
+    k<<<grid, cols_threads(W, ny), sm, s>>>(mid, out, nx, W, to_stages(py), twy, scale, split_scale(scale), 0,
+                                            real_out);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -516,7 +506,7 @@ static cudaError_t fft2d_impl(const double2* in, double2* out, int nfields, cons
 // columns of the half spectrum; inverse columns, then rows (merge +
 // half-length complex).  T: arithmetic type, TM: value type of the
 // intermediate in HBM.
-template <typename T>
+template <typename T, typename TS>
 static cudaError_t fft2d_r2c_impl(const double2* in, double2* spec, int nfields, const FftPlan1D& px,
                                   const FftPlan1D& pxh, const FftPlan1D& py, const T* twx, const T* twxh,
                                   const T* twy, cudaStream_t s) {
@@ -537,17 +527,18 @@ static cudaError_t fft2d_r2c_impl(const double2* in, double2* spec, int nfields,
   {
     const int W = cols_per_cta(ny);
     const size_t sm = 2 * (size_t)W * ny * sizeof(T);
-    auto k = fft_cols_kernel<-1, T, TM, double2>;
+    auto k = fft_cols_kernel<-1, T, TM, TS>;
     if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
     dim3 grid((m + 1 + W - 1) / W, nfields);
-    k<<<grid, 256, sm, s>>>(mid, spec, m + 1, W, to_stages(py), twy, 1.0, 0, 0);
+    k<<<grid, cols_threads(W, ny), sm, s>>>(mid, reinterpret_cast<TS*>(spec), m + 1, W, to_stages(py), twy, 1.0,
+                                            split_scale(1.0), 0, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   (void)px;
   return cudaSuccess;
 }
 
-template <typename T>
+template <typename T, typename TS>
 static cudaError_t fft2d_c2r_impl(double2* spec, double2* out, int nfields, const FftPlan1D& px,
                                   const FftPlan1D& pxh, const FftPlan1D& py, const T* twx, const T* twxh,
                                   const T* twy, double scale, cudaStream_t s) {
@@ -559,10 +550,11 @@ static cudaError_t fft2d_c2r_impl(double2* spec, double2* out, int nfields, cons
   {
     const int W = cols_per_cta(ny);
     const size_t sm = 2 * (size_t)W * ny * sizeof(T);
-    auto k = fft_cols_kernel<+1, T, double2, TM>;
+    auto k = fft_cols_kernel<+1, T, TS, TM>;
     if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
     dim3 grid((m + 1 + W - 1) / W, nfields);
-    k<<<grid, 256, sm, s>>>(spec, mid, m + 1, W, to_stages(py), twy, 1.0, 0, 0);
+    k<<<grid, cols_threads(W, ny), sm, s>>>(reinterpret_cast<const TS*>(spec), mid, m + 1, W, to_stages(py), twy,
+                                            1.0, split_scale(1.0), 0, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
@@ -571,25 +563,34 @@ static cudaError_t fft2d_c2r_impl(double2* spec, double2* out, int nfields, cons
     const size_t sm = 2 * (size_t)rpc * m * sizeof(T);
     auto k = fft_rows_c2r_kernel<T, TM>;
     if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
-    k<<<(nrows + rpc - 1) / rpc, 256, sm, s>>>(mid, out, nrows, rpc, to_stages(pxh), twxh, twx, scale);
+    k<<<(nrows + rpc - 1) / rpc, 256, sm, s>>>(mid, out, nrows, rpc, to_stages(pxh), twxh, twx, scale,
+                                              split_scale(scale));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   (void)px;
   return cudaSuccess;
 }
 
+bool fft_df_ready(const FftPlan1D& px, const FftPlan1D& pxh, const FftPlan1D& py) {
+  return px.twf && pxh.twf && py.twf;
+}
+
 cudaError_t fft2d_r2c(const double2* in, double2* spec, int nfields, const FftPlan1D& px, const FftPlan1D& pxh,
                       const FftPlan1D& py, int df, cudaStream_t s) {
-  if (df && px.twf && pxh.twf && py.twf)
-    return fft2d_r2c_impl<float4>(in, spec, nfields, px, pxh, py, px.twf, pxh.twf, py.twf, s);
-  return fft2d_r2c_impl<double2>(in, spec, nfields, px, pxh, py, px.tw, pxh.tw, py.tw, s);
+  if (df == 2 && fft_df_ready(px, pxh, py))
+    return fft2d_r2c_impl<float4, float4>(in, spec, nfields, px, pxh, py, px.twf, pxh.twf, py.twf, s);
+  if (df && fft_df_ready(px, pxh, py))
+    return fft2d_r2c_impl<float4, double2>(in, spec, nfields, px, pxh, py, px.twf, pxh.twf, py.twf, s);
+  return fft2d_r2c_impl<double2, double2>(in, spec, nfields, px, pxh, py, px.tw, pxh.tw, py.tw, s);
 }
 
 cudaError_t fft2d_c2r(double2* spec, double2* out, int nfields, const FftPlan1D& px, const FftPlan1D& pxh,
                       const FftPlan1D& py, double scale, int df, cudaStream_t s) {
-  if (df && px.twf && pxh.twf && py.twf)
-    return fft2d_c2r_impl<float4>(spec, out, nfields, px, pxh, py, px.twf, pxh.twf, py.twf, scale, s);
-  return fft2d_c2r_impl<double2>(spec, out, nfields, px, pxh, py, px.tw, pxh.tw, py.tw, scale, s);
+  if (df == 2 && fft_df_ready(px, pxh, py))
+    return fft2d_c2r_impl<float4, float4>(spec, out, nfields, px, pxh, py, px.twf, pxh.twf, py.twf, scale, s);
+  if (df && fft_df_ready(px, pxh, py))
+    return fft2d_c2r_impl<float4, double2>(spec, out, nfields, px, pxh, py, px.twf, pxh.twf, py.twf, scale, s);
+  return fft2d_c2r_impl<double2, double2>(spec, out, nfields, px, pxh, py, px.tw, pxh.tw, py.tw, scale, s);
 }
 
 cudaError_t fft2d(const double2* in, double2* out, int nfields, const FftPlan1D& px,

@@ -56,8 +56,11 @@ void split_twiddles(const double2* tw, int n, float4* out);  // host: FP64 table
 // into the half spectrum, ny x (m + 1) complex128 per field (field stride
 // ny (m + 1)), through an m-point transform per row (pxh: plan of length m);
 // inverse from the half spectrum (overwritten) to real fields (imaginary 0),
-// scaled.  df: double-float arithmetic when every plan carries double-float
-// twiddles.
+// scaled.  df: 0 FP64; 1 double-float arithmetic (when every plan carries
+// double-float twiddles) with an FP64 half spectrum; 2 the same with the half
+// spectrum kept as double-float pairs (float4 per value, 16 bytes like FP64)
+// for a double-float combine pass.
+bool fft_df_ready(const FftPlan1D& px, const FftPlan1D& pxh, const FftPlan1D& py);
 cudaError_t fft2d_r2c(const double2* in, double2* spec, int nfields, const FftPlan1D& px, const FftPlan1D& pxh,
                       const FftPlan1D& py, int df, cudaStream_t s);
 cudaError_t fft2d_c2r(double2* spec, double2* out, int nfields, const FftPlan1D& px, const FftPlan1D& pxh,
@@ -107,6 +110,13 @@ cudaError_t pole_orbits_mixed(double2* part, int slices, const SymbolParams& sp,
 cudaError_t pole_orbit_combine(double2* spec, const double2* part, int slices, void* fin, const SymbolParams& sp,
                                const OrbitParams& op, const FusedScalars& fs, int row_len, cudaStream_t s);
 size_t orbit_scalars_bytes(int norb);
+// The same on a half spectrum kept as double-float pairs (float4 per value),
+// in double-float arithmetic; C-grid symbol and real R0 (real input) only,
+// cudaErrorInvalidValue otherwise.  half_x_df, half_y_df: (cos, sin) of
+// pi k / n as double-float pairs.
+cudaError_t pole_orbit_combine_df(void* spec_df, const double2* part, int slices, void* fin, const SymbolParams& sp,
+                                  const float4* half_x_df, const float4* half_y_df, const OrbitParams& op,
+                                  const FusedScalars& fs, int row_len, cudaStream_t s);
 struct PlainScalars {
   double tau;
   int nterms;   // terms in this chunk
