@@ -590,8 +590,11 @@ def run_ours(args):
     }
     phases = {"forward_fft_ms": ms_phase[0] / max(ncalls, 1), "pole_sum_ms": pole_ms, "combine_ms": combine_ms,
               "inverse_fft_ms": ms_phase[2] / max(ncalls, 1), "table_upload_ms": ms_phase[3] / max(ncalls, 1)}
-    # HBM roofline of the FFT passes (2 passes each way, each reads + writes 3 fields)
-    fft_bytes = 2 * 2 * 3 * D * D * 16
+    # HBM roofline of the forward transform of real input: the row pass reads
+    # the 3 fields (16 B per value) and writes the half spectrum, the column
+    # pass reads and writes the half spectrum (16 B per value)
+    half = D * (D // 2 + 1)
+    fft_bytes = 3 * D * D * 16 + 3 * 3 * half * 16
     fwd_gbs = fft_bytes / (phases["forward_fft_ms"] / 1e3) / 1e9
     mp = {}
     try:
@@ -599,15 +602,17 @@ def run_ours(args):
     except (OSError, ValueError):
         pass
     hbm_peak = mp.get("hbm_gbs", 6800.0)
-    roofline_fft = {"kernel": "fft_rows_kernel + fft_cols_kernel (forward)", "bound": "hbm",
+    roofline_fft = {"kernel": "fft_rows_r2c_kernel + fft_cols_kernel (forward)", "bound": "hbm",
                     "achieved": fwd_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": fwd_gbs / hbm_peak,
                     "traffic": None,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in mp else "fallback 6.8 TB/s"}
-    # combine pass: reads and writes the 3-field spectrum (96 B per wavenumber);
-    # the per-orbit sums it also reads are L2-resident and not counted
-    comb_bytes = 3 * D * D * 16 * 2
+    # combine pass: reads and writes the 3-field half spectrum (96 B per
+    # wavenumber); the per-orbit scalars it also reads are L2-resident and not
+    # counted
+    comb_bytes = 3 * half * 16 * 2
     comb_gbs = comb_bytes / (combine_ms / 1e3) / 1e9 if combine_ms > 0 else None
-    roofline_combine = {"kernel": "pole_orbit_combine_kernel", "bound": "hbm", "achieved": comb_gbs,
+    comb_kernel = "pole_orbit_combine_df_kernel" if args.form == "mixed" else "pole_orbit_combine_kernel"
+    roofline_combine = {"kernel": "pole_orbit_finalize_kernel + " + comb_kernel, "bound": "hbm", "achieved": comb_gbs,
                         "peak": hbm_peak, "unit": "GB/s", "frac": comb_gbs / hbm_peak if comb_gbs else None,
                         "traffic": NCU_COMBINE_TRAFFIC_BYTES, "algorithmic_bytes": comb_bytes}
 

@@ -56,14 +56,19 @@ __device__ __forceinline__ float4 cconj(float4 a) { return make_float4(a.x, a.y,
 // (truncated), lo the next 29 bits rounded to 24, both by integer operations;
 // |v - (hi + lo)| <= 2^-47 |v|.  Used for zero and |v| in [2^-74, 2^127);
 // other values take the FP64 route.
+// The FP64 routes are out-of-line calls so that the compiler does not
+// execute them under a predicate for every value.
+static __device__ __noinline__ float2 df_from_double_fp64(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+static __device__ __noinline__ double widen_float_fp64(float f) { return (double)f; }
+
 __device__ __forceinline__ float2 df_from_double(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   if ((b << 1) == 0ull) return make_float2(0.f, 0.f);
   const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
-  if (e < 949u || e > 1150u) {
-    const float h = (float)v;
-    return make_float2(h, (float)(v - (double)h));
-  }
+  if (e < 949u || e > 1150u) return df_from_double_fp64(v);
   const unsigned sign = (unsigned)(b >> 63) << 31;
   const unsigned long long m = b & 0xfffffffffffffull;
   const float hi = __uint_as_float(sign | ((e - 896u) << 23) | (unsigned)(m >> 29));
@@ -77,7 +82,7 @@ __device__ __forceinline__ double widen_float(float f) {
   const unsigned u = __float_as_uint(f);
   if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)(u >> 31) << 63));
   const unsigned ef = (u >> 23) & 0xffu;
-  if (ef == 0u || ef == 255u) return (double)f;
+  if (ef == 0u || ef == 255u) return widen_float_fp64(f);
   const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)(ef + 896u) << 52) |
                                   ((unsigned long long)(u & 0x7fffffu) << 29);
   return __longlong_as_double((long long)bits);

@@ -291,6 +291,7 @@ __global__ void __launch_bounds__(512) fft_cols_kernel(const TI* in, TO* out, in
   const int w = min(W, nx - x0);
   const size_t field_off = (size_t)blockIdx.y * nx * ny;
   const TI* g_in = in + field_off + x0;
+#pragma unroll 8
   for (int i = threadIdx.x; i < ny * W; i += blockDim.x) {
     const int t = i / W, c = i - t * W;
     T v = czero<T>();
@@ -348,6 +349,7 @@ __global__ void __launch_bounds__(256) fft_rows_r2c_kernel(const double2* in, TO
   const long long row0 = (long long)blockIdx.x * rpc;
   const int nr = (int)min((long long)rpc, nrows - row0);
   const double2* g_in = in + row0 * n;
+#pragma unroll 4
   for (int i = threadIdx.x; i < rpc * m; i += blockDim.x) {
     T v = czero<T>();
     if (i < nr * m) real_pair(g_in + 2 * (size_t)i, &v);
@@ -383,6 +385,7 @@ __global__ void __launch_bounds__(256) fft_rows_c2r_kernel(const TI* in, double2
   // each thread forms Z[k] from X[k] and X[m - k] (the second read of a row
   // hits the cache lines of the first)
   const TI* g_in = in + row0 * (m + 1);
+#pragma unroll 4
   for (int i = threadIdx.x; i < rpc * m; i += blockDim.x) {
     T v = czero<T>();
     if (i < nr * m) {
@@ -447,6 +450,9 @@ static float2 split_scale(double v) {
   const float h = (float)v;
   return make_float2(h, (float)(v - (double)h));
 }
+
+// Threads of a real-row CTA: one radix-8 butterfly per thread per stage.
+static int rows_threads(int rpc, int m) { return std::min(256, std::max(64, rpc * m / 8)); }
 
 static int rows_per_cta(int n) {
   int r = 1;
@@ -521,7 +527,7 @@ static cudaError_t fft2d_r2c_impl(const double2* in, double2* spec, int nfields,
     const size_t sm = 2 * (size_t)rpc * m * sizeof(T);
     auto k = fft_rows_r2c_kernel<T, TM>;
     if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
-    k<<<(nrows + rpc - 1) / rpc, 256, sm, s>>>(in, mid, nrows, rpc, to_stages(pxh), twxh, twx);
+    k<<<(nrows + rpc - 1) / rpc, rows_threads(rpc, m), sm, s>>>(in, mid, nrows, rpc, to_stages(pxh), twxh, twx);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
@@ -563,7 +569,7 @@ static cudaError_t fft2d_c2r_impl(double2* spec, double2* out, int nfields, cons
     const size_t sm = 2 * (size_t)rpc * m * sizeof(T);
     auto k = fft_rows_c2r_kernel<T, TM>;
     if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
-    k<<<(nrows + rpc - 1) / rpc, 256, sm, s>>>(mid, out, nrows, rpc, to_stages(pxh), twxh, twx, scale,
+    k<<<(nrows + rpc - 1) / rpc, rows_threads(rpc, m), sm, s>>>(mid, out, nrows, rpc, to_stages(pxh), twxh, twx, scale,
                                               split_scale(scale));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
