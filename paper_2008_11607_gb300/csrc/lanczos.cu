@@ -484,11 +484,27 @@ __global__ void __launch_bounds__(THREADS) lz_init_df(LGeom G, const double2* in
   }
 }
 
+// Programmatic dependent launch of consecutive Lanczos steps: a step's CTAs
+// may start while the previous step drains.  griddepcontrol.wait blocks until
+// the previous grid has completed and its writes are visible; a step lets the
+// next one start only after its own wait, so every grid that can run early
+// finds the step before its predecessor complete (W_{j-2} may be read early).
+// Resident CTAs per SM the double-float step is compiled for (48 registers at
+// 5: the step is bound by load latency, so occupancy pays).
+#ifndef REXI_LZ_DFSTEP_BLOCKS
+#define REXI_LZ_DFSTEP_BLOCKS 5
+#endif
+constexpr int kDfStepBlocks = REXI_LZ_DFSTEP_BLOCKS;
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // The real-form step (lz_wstep) in double-float.  The point-wise operands of
-// the thread's points are loaded before the tile, so that their latency
-// overlaps the halo loads.
+// the thread's points (W_{j-2}, H, g/H: complete before this grid may start)
+// are loaded before waiting for the previous step, so that their latency
+// overlaps its tail and the halo loads.
 template <int MODE>
-__global__ void __launch_bounds__(THREADS) lz_dfstep(LGeom G, const float2* __restrict__ Hdf,
+__global__ void __launch_bounds__(THREADS, kDfStepBlocks) lz_dfstep(LGeom G, const float2* __restrict__ Hdf,
                                                      const float2* __restrict__ wdf, int j,
                                                      const float2* __restrict__ wm1, const float2* __restrict__ wm2,
                                                      float2* __restrict__ wout, double* alpha, double* beta,
@@ -512,6 +528,8 @@ __global__ void __launch_bounds__(THREADS) lz_dfstep(LGeom G, const float2* __re
     pH[q] = live[q] ? Hdf[pid[q]] : z2;
     pw[q] = (live[q] && MODE == 0) ? wdf[pid[q]] : z2;
   }
+  pdl_wait();
+  pdl_release();
   const int i0 = blockIdx.x * TX - 1, j0 = blockIdx.y * TY - 1;
   for (int k = threadIdx.x; k < HX * HY; k += THREADS) {
     const int li = k % HX, lj = k / HX;
@@ -567,6 +585,23 @@ __global__ void __launch_bounds__(THREADS) lz_dfstep(LGeom G, const float2* __re
     invb[j + 1] = safe_inv(beta[j + 1]);
     df_coef_store(G, invb[j + 1], beta[j + 1] * invb[j], dfc + j + 1);
   }
+}
+
+// Launch of a Lanczos step that may overlap the previous step's tail (see
+// pdl_wait); a launch error is left for the caller's cudaGetLastError.
+template <typename... KArgs, typename... Args>
+void launch_step_pdl(void (*kern)(KArgs...), dim3 grid, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
 // Double-float: acc = sum_{b < nb} coef_b S_b (S_0 = f0, S_b = W_{b-1}).
@@ -1043,8 +1078,9 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   auto launch_chunk = [&](int c, int j0, int j1) -> cudaError_t {
     for (int j = j0; j < j1; ++j) {
       if constexpr (DF)
-        lz_dfstep<0><<<grid, THREADS, 0, s>>>(G_, k->Hdf, k->wdf, j, Wptr(j - 1), Wptr(j - 2), Wptr(j), alpha, beta,
-                                              invb, dfc, partials, counter, nullptr, nullptr);
+        launch_step_pdl(lz_dfstep<0>, grid, s, G_, k->Hdf, k->wdf, j, Wptr(j - 1), Wptr(j - 2), Wptr(j), alpha, beta,
+                        invb, dfc, partials, counter, static_cast<float2*>(nullptr),
+                        static_cast<const float2*>(nullptr));
       else if constexpr (REAL)
         lz_wstep<0><<<grid, THREADS, 0, s>>>(G_, j, Wptr(j - 1), Wptr(j - 2), Wptr(j), alpha, beta, invb, partials,
                                              counter, nullptr, nullptr);
@@ -1160,8 +1196,8 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   if (e == cudaSuccess && nb < kk) {
     for (int j = nb; j < kk; ++j) {
       if constexpr (DF)
-        lz_dfstep<1><<<grid, THREADS, 0, s>>>(G_, k->Hdf, k->wdf, j, Wptr(j - 1), Wptr(j - 2), Wptr(j), alpha, beta,
-                                              invb, dfc, partials, counter, acc, coef_df);
+        launch_step_pdl(lz_dfstep<1>, grid, s, G_, k->Hdf, k->wdf, j, Wptr(j - 1), Wptr(j - 2), Wptr(j), alpha, beta,
+                        invb, dfc, partials, counter, acc, coef_df);
       else if constexpr (REAL)
         lz_wstep<1><<<grid, THREADS, 0, s>>>(G_, j, Wptr(j - 1), Wptr(j - 2), Wptr(j), alpha, beta, invb, partials,
                                              counter, acc, coef);
