@@ -34,6 +34,10 @@ struct InstDesc {
   long long orb_off;   // first entry of this instance's per-orbit combine scalars
   int nx, ny, nterms, pad;
   int ax, ay, sym, norb;  // OrbitParams of the instance's grid
+  long long half_off;     // real input: first element of the instance's half spectrum (dense per size group)
+  int half_ok, pad2;      // 1: even nx, real transforms along x available
+  const float4* halfdf_x;  // half angles as double-float pairs
+  const float4* halfdf_y;
   double inv_dx, inv_dy, tau, q, R0re, R0im, grid;
   float q_hi, q_lo;
   long long table_off;  // first table entry (3 x 16 bytes per term)
@@ -48,7 +52,8 @@ struct WorkItem {
 struct SizeGroup {
   int nx, ny;
   std::vector<int> insts;  // packed consecutively
-  FftPlan1D fx, fy;
+  FftPlan1D fx, fy, fxh;   // fxh: half-length x plan (real input), if half_ok
+  bool half_ok = false;
   long long first_off;     // element offset of the group's first state
 };
 
@@ -64,6 +69,7 @@ struct rexi_batch_s {
   std::vector<rexi::SizeGroup> groups;
   std::map<int, std::pair<double2*, double2*>> axis_tables;  // n -> (twiddles, half angles), device
   std::map<int, float4*> axis_twf;                             // n -> double-float twiddles (mixed form)
+  std::map<int, float4*> axis_halfdf;                          // n -> half angles as double-float pairs
   // device data owned by the batch
   void* d_tables = nullptr;      // coefficient tables of all instances
   rexi::InstDesc* d_desc = nullptr;
@@ -176,11 +182,14 @@ __global__ void batch_pole_kernel(OrbitScalars* orb, const InstDesc* __restrict_
 }
 
 // r(tau B) at every wavenumber of every instance from its orbit's scalars.
-// Instance i owns combine blocks [blk[i], blk[i + 1]).
+// Instance i owns combine blocks [blk[i], blk[i + 1]) (enough for its full
+// spectrum).  Real input on an even-nx grid: the half spectrum at half_off
+// (double-float pairs for the mixed form, df = 1), r(0) through its real part.
 __global__ void __launch_bounds__(256) batch_combine_kernel(double2* spec, const OrbitScalars* __restrict__ orb,
                                                             const InstDesc* __restrict__ desc,
                                                             const int* __restrict__ blk, int n, double g, double f,
-                                                            double H, int adjoint) {
+                                                            double H, int adjoint, int real_input, int df,
+                                                            float2 g_df, float2 f_df, float2 H_df) {
   int lo = 0, hi = n - 1;  // last instance with blk[i] <= blockIdx.x
   while (lo < hi) {
     const int mid = (lo + hi + 1) / 2;
@@ -188,8 +197,10 @@ __global__ void __launch_bounds__(256) batch_combine_kernel(double2* spec, const
     else hi = mid - 1;
   }
   const InstDesc& D = desc[lo];
-  const int nk = D.nx * D.ny;
   const int k = ((int)blockIdx.x - blk[lo]) * blockDim.x + threadIdx.x;
+  const bool half = real_input && D.half_ok;
+  const int row_len = half ? D.nx / 2 + 1 : D.nx;
+  const int nk = row_len * D.ny;
   if (k >= nk) return;
   SymbolParams sp;
   sp.nx = D.nx;
@@ -206,10 +217,27 @@ __global__ void __launch_bounds__(256) batch_combine_kernel(double2* spec, const
   op.ay = D.ay;
   op.sym = D.sym;
   op.norb = D.norb;
-  const int ky = k / D.nx, kx = k - ky * D.nx;
-  const OrbitScalars o = orb[D.orb_off + orbit_of(op, D.nx, D.ny, kx, ky)];
-  combine_scaled(spec + D.spec_off, (size_t)k, (size_t)nk, symbol_entries(sp, kx, ky, adjoint != 0),
-                 make_double2(D.R0re, D.R0im), o, adjoint != 0);
+  const int ky = k / row_len, kx = k - ky * row_len;
+  OrbitScalars o = orb[D.orb_off + orbit_of(op, D.nx, D.ny, kx, ky)];
+  if (!half) {
+    combine_scaled(spec + D.spec_off, (size_t)k, (size_t)nk, symbol_entries(sp, kx, ky, adjoint != 0),
+                   make_double2(D.R0re, D.R0im), o, adjoint != 0);
+  } else if (df) {
+    SymbolDF sd;
+    sd.g = g_df;
+    sd.H = H_df;
+    sd.f = f_df;
+    sd.inv_dx = df_from_double(D.inv_dx);
+    sd.inv_dy = df_from_double(D.inv_dy);
+    sd.half_x = D.halfdf_x;
+    sd.half_y = D.halfdf_y;
+    combine_df_at(reinterpret_cast<float4*>(spec + D.half_off), (size_t)k, (size_t)nk, kx, ky, sd,
+                  df_from_double(D.R0re), df_from_double(o.s1), df_from_double(o.s2re), adjoint != 0);
+  } else {
+    o.s2im = 0.0;
+    combine_scaled(spec + D.half_off, (size_t)k, (size_t)nk, symbol_entries(sp, kx, ky, adjoint != 0),
+                   make_double2(D.R0re, 0.0), o, adjoint != 0);
+  }
 }
 
 template <int FORM, int PPT>
@@ -235,8 +263,15 @@ cudaError_t launch_pole(rexi_batch_s* b, OrbitScalars* orb, unsigned* counter, c
                      : launch_persistent<REXI_FORM_MIXED, 1>(b, orb, counter, b->threads, s);
 }
 
-cudaError_t launch_combine(rexi_batch_s* b, double2* spec, const OrbitScalars* orb, cudaStream_t s) {
-  batch_combine_kernel<<<b->combine_blocks, 256, 0, s>>>(spec, orb, b->d_desc, b->d_blk, b->n, b->g, b->f, b->H, 0);
+float2 split_host(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
+cudaError_t launch_combine(rexi_batch_s* b, double2* spec, const OrbitScalars* orb, int real_input, cudaStream_t s) {
+  batch_combine_kernel<<<b->combine_blocks, 256, 0, s>>>(spec, orb, b->d_desc, b->d_blk, b->n, b->g, b->f, b->H, 0,
+                                                         real_input, b->form == REXI_FORM_MIXED ? 1 : 0,
+                                                         split_host(b->g), split_host(b->f), split_host(b->H));
   return cudaGetLastError();
 }
 
@@ -299,19 +334,26 @@ cudaError_t enqueue_persistent(rexi_batch_s* b, const double2* in, double2* out,
   double2* spec = reinterpret_cast<double2*>(ws + 256);
   OrbitScalars* orb = reinterpret_cast<OrbitScalars*>(ws + 256 + batch_spec_bytes(b));
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+  const int df = b->form == REXI_FORM_MIXED ? 2 : 0;  // real transforms: double-float half spectrum
   for (auto& G : b->groups) {
     if (e != cudaSuccess) return e;
     const int nf = 3 * (int)G.insts.size();
-    e = fft_any(b, in + G.first_off, spec + G.first_off, nf, G.fx, G.fy, -1, 1.0, real_input, 0, s);
+    if (real_input && G.half_ok)
+      e = fft2d_r2c(in + G.first_off, spec + G.first_off, nf, G.fx, G.fxh, G.fy, df, s);
+    else
+      e = fft_any(b, in + G.first_off, spec + G.first_off, nf, G.fx, G.fy, -1, 1.0, real_input, 0, s);
   }
   if (e != cudaSuccess) return e;
   e = launch_pole(b, orb, counter, s);
-  if (e == cudaSuccess) e = launch_combine(b, spec, orb, s);
+  if (e == cudaSuccess) e = launch_combine(b, spec, orb, real_input, s);
   for (auto& G : b->groups) {
     if (e != cudaSuccess) return e;
     const int nf = 3 * (int)G.insts.size();
-    e = fft_any(b, spec + G.first_off, out + G.first_off, nf, G.fx, G.fy, +1, 1.0 / ((double)G.nx * G.ny), 0,
-                real_input, s);
+    const double scale = 1.0 / ((double)G.nx * G.ny);
+    if (real_input && G.half_ok)
+      e = fft2d_c2r(spec + G.first_off, out + G.first_off, nf, G.fx, G.fxh, G.fy, scale, df, s);
+    else
+      e = fft_any(b, spec + G.first_off, out + G.first_off, nf, G.fx, G.fy, +1, scale, 0, real_input, s);
   }
   return e;
 }
@@ -336,6 +378,7 @@ void rexi_batch_destroy(rexi_batch_t b) {
   if (b->ev_in) cudaEventDestroy(b->ev_in);
   if (b->ev_out) cudaEventDestroy(b->ev_out);
   for (auto& kv : b->axis_twf) cudaFree(kv.second);
+  for (auto& kv : b->axis_halfdf) cudaFree(kv.second);
   for (auto& kv : b->axis_tables) {
     cudaFree(kv.second.first);
     cudaFree(kv.second.second);
@@ -392,8 +435,8 @@ rexi_status rexi_batch_create(rexi_batch_t* out, int32_t n, const int32_t* nx, c
   }
   // axis tables per distinct length
   for (auto& G : b->groups) {
-    for (int len : {G.nx, G.ny}) {
-      if (b->axis_tables.count(len)) continue;
+    auto ensure_len = [&](int len) -> bool {
+      if (b->axis_tables.count(len)) return true;
       std::vector<double2> tw(len), half(len);
       for (int t = 0; t < len; ++t) {
         const double a = 2.0 * M_PI * t / len, c = M_PI * t / len;
@@ -404,18 +447,30 @@ rexi_status rexi_batch_create(rexi_batch_t* out, int32_t n, const int32_t* nx, c
       if (cudaMalloc(&dtw, len * sizeof(double2)) != cudaSuccess ||
           cudaMalloc(&dhalf, len * sizeof(double2)) != cudaSuccess) {
         cudaFree(dtw);
-        return bail(REXI_ENOMEM, "rexi_batch_create: table allocation failed");
+        return false;
       }
       b->axis_tables[len] = {dtw, dhalf};
       cudaMemcpy(dtw, tw.data(), len * sizeof(double2), cudaMemcpyHostToDevice);
       cudaMemcpy(dhalf, half.data(), len * sizeof(double2), cudaMemcpyHostToDevice);
-      std::vector<float4> twf(len);
+      std::vector<float4> twf(len), hdf(len);
       split_twiddles(tw.data(), len, twf.data());
-      float4* dtwf = nullptr;
-      if (cudaMalloc(&dtwf, len * sizeof(float4)) != cudaSuccess)
-        return bail(REXI_ENOMEM, "rexi_batch_create: table allocation failed");
+      split_twiddles(half.data(), len, hdf.data());
+      float4 *dtwf = nullptr, *dhdf = nullptr;
+      if (cudaMalloc(&dtwf, len * sizeof(float4)) != cudaSuccess) return false;
       b->axis_twf[len] = dtwf;
+      if (cudaMalloc(&dhdf, len * sizeof(float4)) != cudaSuccess) return false;
+      b->axis_halfdf[len] = dhdf;
       cudaMemcpy(dtwf, twf.data(), len * sizeof(float4), cudaMemcpyHostToDevice);
+      cudaMemcpy(dhdf, hdf.data(), len * sizeof(float4), cudaMemcpyHostToDevice);
+      return true;
+    };
+    if (!ensure_len(G.nx) || !ensure_len(G.ny))
+      return bail(REXI_ENOMEM, "rexi_batch_create: table allocation failed");
+    if (G.nx % 2 == 0 && fft_factor(G.nx / 2, &G.fxh)) {  // real transforms along x
+      if (!ensure_len(G.nx / 2)) return bail(REXI_ENOMEM, "rexi_batch_create: table allocation failed");
+      G.fxh.tw = b->axis_tables[G.nx / 2].first;
+      G.fxh.twf = b->axis_twf[G.nx / 2];
+      G.half_ok = true;
     }
     G.fx.tw = b->axis_tables[G.nx].first;
     G.fy.tw = b->axis_tables[G.ny].first;
@@ -524,6 +579,18 @@ rexi_status rexi_batch_create(rexi_batch_t* out, int32_t n, const int32_t* nx, c
     b->total_orbits += op.norb;
     b->total_terms_orbits += (long long)op.norb * nterms;
   }
+  // real input: the half spectra of a size group lie densely from the group's
+  // first element, field after field (the layout of the real transforms)
+  for (auto& G : b->groups) {
+    const long long field = (long long)G.ny * (G.nx / 2 + 1);
+    for (size_t q = 0; q < G.insts.size(); ++q) {
+      InstDesc& D = b->h_desc[G.insts[q]];
+      D.half_ok = G.half_ok ? 1 : 0;
+      D.half_off = G.first_off + 3 * (long long)q * field;
+      D.halfdf_x = b->axis_halfdf[G.nx];
+      D.halfdf_y = b->axis_halfdf[G.ny];
+    }
+  }
   std::vector<int> blk(n + 1, 0);
   for (int i = 0; i < n; ++i) blk[i + 1] = blk[i] + (b->nx[i] * b->ny[i] + 255) / 256;
   b->combine_blocks = blk[n];
@@ -587,12 +654,24 @@ rexi_status rexi_batch_step(rexi_batch_t b, const void* in, void* out, int32_t r
       fx.twf = b->axis_twf[D.nx];
       fy.twf = b->axis_twf[D.ny];
       double2* sp_i = spec + D.spec_off;
-      e = fft_any(b, in2 + D.spec_off, sp_i, 3, fx, fy, -1, 1.0, real_input, 0, s);
+      // real input: the instance's half spectrum in its own slot, as rexi_step lays it out
+      const bool half = real_input && D.half_ok;
+      const int df = b->form == REXI_FORM_MIXED ? 2 : 0;
+      FftPlan1D fxh;
+      if (half) {
+        fft_factor(D.nx / 2, &fxh);
+        fxh.tw = b->axis_tables[D.nx / 2].first;
+        fxh.twf = b->axis_twf[D.nx / 2];
+        e = fft2d_r2c(in2 + D.spec_off, sp_i, 3, fx, fxh, fy, df, s);
+      } else {
+        e = fft_any(b, in2 + D.spec_off, sp_i, 3, fx, fy, -1, 1.0, real_input, 0, s);
+      }
       SymbolParams sp;
       sp.nx = D.nx; sp.ny = D.ny; sp.inv_dx = D.inv_dx; sp.inv_dy = D.inv_dy;
       sp.g = b->g; sp.f = b->f; sp.H = b->H; sp.half_x = D.half_x; sp.half_y = D.half_y;
       FusedScalars fs;
-      fs.tau = D.tau; fs.q = D.q; fs.R0re = D.R0re; fs.R0im = D.R0im; fs.nterms = D.nterms; fs.adjoint = 0;
+      fs.tau = D.tau; fs.q = D.q; fs.R0re = D.R0re; fs.R0im = half ? 0.0 : D.R0im; fs.nterms = D.nterms;
+      fs.adjoint = 0;
       const float* tab = static_cast<const float*>(b->d_tables) + D.table_off * 12;
       // the single-instance kernels, term slices as rexi_step chooses them
       OrbitParams op;
@@ -603,10 +682,17 @@ rexi_status rexi_batch_step(rexi_batch_t b, const void* in, void* out, int32_t r
         e = b->form == REXI_FORM_FP64
                 ? pole_orbits_fp64(part, slices, sp, op, reinterpret_cast<const double*>(tab), fs, s)
                 : pole_orbits_mixed(part, slices, sp, op, tab, fs, D.grid, s);
+      void* fin = orb + per_instance_part_bytes(D);
+      const double scale = 1.0 / ((double)D.nx * D.ny);
+      if (e == cudaSuccess) {
+        if (half && df)
+          e = pole_orbit_combine_df(sp_i, part, slices, fin, sp, D.halfdf_x, D.halfdf_y, op, fs, D.nx / 2 + 1, s);
+        else
+          e = pole_orbit_combine(sp_i, part, slices, fin, sp, op, fs, half ? D.nx / 2 + 1 : D.nx, s);
+      }
       if (e == cudaSuccess)
-        e = pole_orbit_combine(sp_i, part, slices, orb + per_instance_part_bytes(D), sp, op, fs, D.nx, s);
-      if (e == cudaSuccess)
-        e = fft_any(b, sp_i, out2 + D.spec_off, 3, fx, fy, +1, 1.0 / ((double)D.nx * D.ny), 0, real_input, s);
+        e = half ? fft2d_c2r(sp_i, out2 + D.spec_off, 3, fx, fxh, fy, scale, df, s)
+                 : fft_any(b, sp_i, out2 + D.spec_off, 3, fx, fy, +1, scale, 0, real_input, s);
       b->launches += 7;
     }
   } else if (mode == REXI_BATCH_PERSISTENT) {

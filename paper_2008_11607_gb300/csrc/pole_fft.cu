@@ -264,68 +264,6 @@ __global__ void __launch_bounds__(256) pole_orbit_finalize_kernel(const double2*
   }
 }
 
-// Double-float combine on a double-float half spectrum (real input, C-grid):
-// out = c0 f + s1 B f + s2 B^2 f with real c0 = Re R0, s1, s2; the symbol from
-// double-float half-angle tables (cos, sin of pi k / n as float4 hi/lo pairs).
-struct SymbolDF {
-  float2 g, H, f, inv_dx, inv_dy;
-  const float4* half_x;
-  const float4* half_y;
-};
-
-__device__ __forceinline__ float4 c_of(float2 re, float2 im) { return make_float4(re.x, re.y, im.x, im.y); }
-__device__ __forceinline__ float2 f_neg(float2 a) { return make_float2(-a.x, -a.y); }
-
-__global__ void __launch_bounds__(256) pole_orbit_combine_df_kernel(float4* spec,
-                                                                    const OrbitScalarsDF* __restrict__ fin,
-                                                                    SymbolDF sd, int nx, int ny, OrbitParams op,
-                                                                    float2 c0, int adjoint, int row_len) {
-  const size_t nk = (size_t)row_len * ny;
-  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nk) return;
-  const int ky = (int)(k / row_len), kx = (int)(k - (size_t)ky * row_len);
-  const OrbitScalarsDF o = fin[orbit_of(op, nx, ny, kx, ky)];
-  const float4 hx = sd.half_x[kx], hy = sd.half_y[ky];
-  const float2 cx = make_float2(hx.x, hx.y), sx = make_float2(hx.z, hx.w);
-  const float2 cy = make_float2(hy.x, hy.y), sy = make_float2(hy.z, hy.w);
-  // a = 2 sin(theta/2) / dx; B entries with g, H, f folded in (see symbol_at)
-  const float2 ax = f_mulf(make_float2(2.f * sx.x, 2.f * sx.y), sd.inv_dx);
-  const float2 ay = f_mulf(make_float2(2.f * sy.x, 2.f * sy.y), sd.inv_dy);
-  const float2 Hax = f_neg(f_mulf(sd.H, ax)), Hay = f_neg(f_mulf(sd.H, ay));
-  const float2 gax = f_mulf(sd.g, ax), gay = f_mulf(sd.g, ay);
-  float4 e01 = c_of(f_mulf(Hax, sx), f_mulf(Hax, cx));        // -H dxb
-  float4 e02 = c_of(f_mulf(Hay, sy), f_mulf(Hay, cy));        // -H dyb
-  float4 e10 = c_of(f_mulf(gax, sx), f_neg(f_mulf(gax, cx)));  // -g dxf
-  float4 e20 = c_of(f_mulf(gay, sy), f_neg(f_mulf(gay, cy)));  // -g dyf
-  const float2 cxcy = f_mulf(cx, cy);
-  const float2 fcc = f_mulf(sd.f, cxcy);
-  const float2 pr = f_mulf(fcc, f_addf(cxcy, f_mulf(sx, sy)));
-  const float2 pi = f_mulf(fcc, f_subf(f_mulf(sx, cy), f_mulf(cx, sy)));
-  float4 e12 = c_of(pr, pi);          // f P
-  float4 e21 = c_of(f_neg(pr), pi);   // -f conj(P)
-  if (adjoint) {  // B^H: (B^H)_ij = conj(B_ji)
-    const float4 t01 = e01, t02 = e02, t10 = e10, t12 = e12, t20 = e20, t21 = e21;
-    e01 = cconj(t10);
-    e02 = cconj(t20);
-    e10 = cconj(t01);
-    e12 = cconj(t21);
-    e20 = cconj(t02);
-    e21 = cconj(t12);
-  }
-  float4 f[3], y1[3], y2[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) f[c] = spec[k + c * nk];
-  y1[0] = cadd(cmul(e01, f[1]), cmul(e02, f[2]));
-  y1[1] = cadd(cmul(e10, f[0]), cmul(e12, f[2]));
-  y1[2] = cadd(cmul(e20, f[0]), cmul(e21, f[1]));
-  y2[0] = cadd(cmul(e01, y1[1]), cmul(e02, y1[2]));
-  y2[1] = cadd(cmul(e10, y1[0]), cmul(e12, y1[2]));
-  y2[2] = cadd(cmul(e20, y1[0]), cmul(e21, y1[1]));
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-    spec[k + c * nk] = cadd(cadd(crmul(c0, f[c]), crmul(o.s1, y1[c])), crmul(o.s2, y2[c]));
-}
-
 __global__ void __launch_bounds__(256) pole_orbit_combine_kernel(double2* spec,
                                                                  const OrbitScalars* __restrict__ fin,
                                                                  SymbolParams sp, OrbitParams op, double2 R0,
@@ -336,6 +274,19 @@ __global__ void __launch_bounds__(256) pole_orbit_combine_kernel(double2* spec,
   const int ky = (int)(k / row_len), kx = (int)(k - (size_t)ky * row_len);
   const OrbitScalars o = fin[orbit_of(op, sp.nx, sp.ny, kx, ky)];
   combine_scaled(spec, k, nk, symbol_entries(sp, kx, ky, adjoint != 0), R0, o, adjoint != 0);
+}
+
+// Double-float combine on a double-float half spectrum (see combine_df_at).
+__global__ void __launch_bounds__(256) pole_orbit_combine_df_kernel(float4* spec,
+                                                                    const OrbitScalarsDF* __restrict__ fin,
+                                                                    SymbolDF sd, int nx, int ny, OrbitParams op,
+                                                                    float2 c0, int adjoint, int row_len) {
+  const size_t nk = (size_t)row_len * ny;
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nk) return;
+  const int ky = (int)(k / row_len), kx = (int)(k - (size_t)ky * row_len);
+  const OrbitScalarsDF o = fin[orbit_of(op, nx, ny, kx, ky)];
+  combine_df_at(spec, k, nk, kx, ky, sd, c0, o.s1, o.s2, adjoint != 0);
 }
 
 namespace {
