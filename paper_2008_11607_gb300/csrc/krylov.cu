@@ -972,7 +972,7 @@ rexi_status krylov_grad_depth(KrylovSettings* k, int form, double h, int M, cons
                               double* grad_depth, double dt, int real_input, void* ws, size_t ws_bytes,
                               cudaStream_t s, rexi_step_info* info, const KrylovHooks& hooks) {
   if (k->method == 1 && real_input)
-    return krylov_grad_depth_lanczos(k, h, M, f_in, g_out, grad_depth, dt, ws, ws_bytes, s, info, hooks);
+    return krylov_grad_depth_lanczos(k, form, h, M, f_in, g_out, grad_depth, dt, ws, ws_bytes, s, info, hooks);
   const size_t nk = (size_t)k->nx * k->ny, n3 = 3 * nk;
   KrylovRun run;
   rexi_status st = run.setup(k, form, h, M, dt, real_input, 0, -1, ws, ws_bytes, s, &hooks);

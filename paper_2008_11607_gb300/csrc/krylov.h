@@ -50,7 +50,8 @@ size_t lanczos_workspace_bytes(const KrylovSettings* k, int M, int real_input);
 rexi_status lanczos_tables(KrylovSettings* k);  // fills Hdf, wdf
 // Depth gradient from two kept Lanczos bases (real input; FP64).
 size_t lanczos_grad_workspace_bytes(const KrylovSettings* k, int M, double h);
-rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, double h, int M, const void* f_in, const void* g_out,
+rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, int form, double h, int M, const void* f_in,
+                                      const void* g_out,
                                       double* grad_depth, double dt, void* ws, size_t ws_bytes, cudaStream_t s,
                                       rexi_step_info* info, const KrylovHooks& hooks);
 rexi_status krylov_step_lanczos(KrylovSettings* k, int form, double h, int M, const void* in, void* out, double dt,

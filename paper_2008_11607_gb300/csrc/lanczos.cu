@@ -41,6 +41,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "internal.h"
 #include "krylov.h"
 
@@ -1351,6 +1352,60 @@ __global__ void __launch_bounds__(256) lz_grad_contract(int nx, int ny, double i
   if (live) grad[p] += w[p] * acc;
 }
 
+// The same contraction in double-float arithmetic (mixed form): the FP64
+// bases and R are split into (hi, lo) FP32 pairs on load (integer operations),
+// products and sums run on the FP32 pipes; the result is added in FP64.
+__global__ void __launch_bounds__(256) lz_grad_contract_df(int nx, int ny, double idx, double idy, const double* f0,
+                                                           const double* basA, const double* g0, const double* basB,
+                                                           size_t vstride, int kA, int kB, const double* R,
+                                                           const double* w, double* grad) {
+  __shared__ float2 Rs[kGA][kGB];
+  const size_t nk = (size_t)nx * ny;
+  const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = p < nk;
+  const int i = live ? (int)(p % nx) : 0, jrow = live ? (int)(p / nx) : 0;
+  const size_t pxm = (size_t)jrow * nx + (i == 0 ? nx - 1 : i - 1);
+  const size_t pym = (size_t)(jrow == 0 ? ny - 1 : jrow - 1) * nx + i;
+  const float2 idx_df = df_from_double(idx), idy_df = df_from_double(idy);
+  float2 acc = make_float2(0.f, 0.f);
+  for (int b0 = 0; b0 < kA; b0 += kGB) {
+    float2 z[kGB];
+#pragma unroll
+    for (int q = 0; q < kGB; ++q) z[q] = make_float2(0.f, 0.f);
+    for (int a0 = 0; a0 < kB; a0 += kGA) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < kGA * kGB; t += blockDim.x) {
+        const int a = a0 + t / kGB, b = b0 + t % kGB;
+        Rs[t / kGB][t % kGB] = (a < kB && b < kA) ? df_from_double(R[(size_t)a * kA + b]) : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      const int na = min(kGA, kB - a0);
+      for (int q = 0; q < na; ++q) {
+        const int a = a0 + q;
+        const float2 sv = df_from_double(live ? (a == 0 ? g0[p] : basB[(size_t)(a - 1) * vstride + p]) : 0.0);
+#pragma unroll
+        for (int bb = 0; bb < kGB; ++bb) {
+          const float2 t = f_mul(Rs[q][bb].x, Rs[q][bb].y, sv.x, sv.y);
+          z[bb] = f_add(z[bb].x, z[bb].y, t.x, t.y);
+        }
+      }
+    }
+    if (!live) continue;
+    const int nbb = min(kGB, kA - b0);
+#pragma unroll
+    for (int bb = 0; bb < kGB; ++bb) {
+      if (bb >= nbb) break;
+      const int b = b0 + bb;
+      const double* S = b == 0 ? f0 : basA + (size_t)(b - 1) * vstride;
+      const float2 ddx = f_subf(df_from_double(S[nk + p]), df_from_double(S[nk + pxm]));
+      const float2 ddy = f_subf(df_from_double(S[2 * nk + p]), df_from_double(S[2 * nk + pym]));
+      const float2 dv = f_addf(f_mulf(ddx, idx_df), f_mulf(ddy, idy_df));
+      acc = f_addf(acc, f_mulf(z[bb], dv));
+    }
+  }
+  if (live) grad[p] += w[p] * df_to_double(acc);
+}
+
 // Bytes of the gradient workspace; cap = kept Lanczos vectors per run.
 int grad_cap(const KrylovSettings* k, int M, double h) {
   return (int)std::min<double>(k->max_iters, std::ceil(3.0 * M * h) + 100.0);
@@ -1405,7 +1460,8 @@ GLayout grad_layout(const KrylovSettings* k, int M, double h) {
 
 size_t lanczos_grad_workspace_bytes(const KrylovSettings* k, int M, double h) { return grad_layout(k, M, h).total; }
 
-rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, double h, int M, const void* f_in, const void* g_out,
+rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, int form, double h, int M, const void* f_in,
+                                      const void* g_out,
                                       double* grad_depth, double dt, void* ws, size_t ws_bytes, cudaStream_t s,
                                       rexi_step_info* info, const KrylovHooks& hooks) {
   using cd = std::complex<double>;
@@ -1587,9 +1643,14 @@ rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, double h, int M, const 
                                                                      D(L.R));
     launches += 3;
     mark(3);
-    lz_grad_contract<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(
-        k->nx, k->ny, k->nx / k->Lx, k->ny / k->Ly, D(L.f0), D(L.basA), D(L.g0), D(L.basB), vstride, kA, kB,
-        D(L.R), k->w64, grad_depth);
+    if (form == REXI_FORM_MIXED)
+      lz_grad_contract_df<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(
+          k->nx, k->ny, k->nx / k->Lx, k->ny / k->Ly, D(L.f0), D(L.basA), D(L.g0), D(L.basB), vstride, kA, kB,
+          D(L.R), k->w64, grad_depth);
+    else
+      lz_grad_contract<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(
+          k->nx, k->ny, k->nx / k->Lx, k->ny / k->Ly, D(L.f0), D(L.basA), D(L.g0), D(L.basB), vstride, kA, kB,
+          D(L.R), k->w64, grad_depth);
     ++launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) {
