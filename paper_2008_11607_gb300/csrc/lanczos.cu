@@ -1076,7 +1076,12 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   const int G = bound_group(npc), groups = (npc + G - 1) / G;
   const int nslot_c = (nsamp - 1) / kCoarse + 1, nslot_f = nsamp;
   double* pin = k->pinned;
-  auto launch_chunk = [&](int c, int j0, int j1) -> cudaError_t {
+  // A Krylov polynomial of degree k resolves e^{ix} on [-Lh, Lh] only for k
+  // of the order of Lh, so no chunk ending below Lh / 2 can meet the bound:
+  // the bound is checked from there on (and at the step cap).
+  const int first_check = (int)std::floor(0.5 * Lh);
+  // par: pinned slot and event of a checked chunk (alternating over checked chunks)
+  auto launch_chunk = [&](int par, int j0, int j1, bool check) -> cudaError_t {
     for (int j = j0; j < j1; ++j) {
       if constexpr (DF)
         launch_step_pdl(lz_dfstep<0>, grid, s, G_, k->Hdf, k->wdf, j, Wptr(j - 1), Wptr(j - 2), Wptr(j), alpha, beta,
@@ -1090,6 +1095,10 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
                                                invb, partials, counter, nullptr, nullptr);
     }
     lz_poles_advance<<<(npc + 127) / 128, 128, 0, s>>>(npc, d_sc, d_wc, alpha, beta, j0, j1, d_dg, d_wy);
+    if (!check) {
+      launches += (j1 - j0) + 1;
+      return cudaGetLastError();
+    }
     cudaError_t err = cudaMemsetAsync(maxslots, 0, 2 * sizeof(unsigned long long), s);
     if (err != cudaSuccess) return err;
     const int sym = REAL ? (((j1 - 1) & 1) ? -1 : 1) : 0;  // (-1)^(k-1), k = j1 steps
@@ -1100,7 +1109,6 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
     lz_bound_part<<<gf, BT, 0, s>>>(npc, G, d_sc, d_wy, Lh, dl, nslot_f, 1, beta, j1, k->rtol, maxslots, d_part);
     lz_bound_max<<<gf.x, BT, 0, s>>>(groups, nslot_f, d_part, sym, beta, j1, k->rtol, maxslots, maxslots + 1);
     launches += (j1 - j0) + 5;
-    const int par = c & 1;
     err = cudaMemcpyAsync(pin + 3 * par, beta + j1, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (err == cudaSuccess)
       err = cudaMemcpyAsync(pin + 3 * par + 1, maxslots, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -1111,8 +1119,7 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   int kk = 0;
   bool converged = false, nonfinite = false;
   double bound = INFINITY;
-  auto evaluate = [&](int c, int j1) -> cudaError_t {
-    const int par = c & 1;
+  auto evaluate = [&](int par, int j1) -> cudaError_t {
     cudaError_t err = cudaEventSynchronize(k->ev[par]);
     if (err != cudaSuccess) return err;
     const double b = pin[3 * par], coarse = pin[3 * par + 1], fine = pin[3 * par + 2];
@@ -1127,19 +1134,24 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
     }
     return cudaSuccess;
   };
-  int pending = -1, pending_j1 = 0, steps_run = 0;
+  // the host evaluates a checked chunk while the next one runs
+  int pending = -1, pending_j1 = 0, steps_run = 0, nchecked = 0;
   for (int c = 0; e == cudaSuccess; ++c) {
     const int j0 = c * chunk;
     if (j0 >= k->max_iters) break;
     const int j1 = std::min(j0 + chunk, k->max_iters);
-    e = launch_chunk(c, j0, j1);
+    const bool check = j1 >= first_check || j1 >= k->max_iters;
+    const int par = nchecked & 1;
+    e = launch_chunk(par, j0, j1, check);
     steps_run = j1;
     if (e != cudaSuccess) break;
+    if (!check) continue;
+    ++nchecked;
     if (pending >= 0) {
       e = evaluate(pending, pending_j1);
       if (e != cudaSuccess || converged || nonfinite) break;
     }
-    pending = c;
+    pending = par;
     pending_j1 = j1;
   }
   if (e == cudaSuccess && !converged && !nonfinite && pending >= 0) e = evaluate(pending, pending_j1);
@@ -1559,8 +1571,7 @@ rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, int form, double h, int
     bool converged = false, nonfinite = false;
     int kk = 0, pending = -1, pending_j1 = 0;
     double bound = INFINITY;
-    auto evaluate = [&](int c, int j1) -> cudaError_t {
-      const int par = c & 1;
+    auto evaluate = [&](int par, int j1) -> cudaError_t {
       cudaError_t er = cudaEventSynchronize(k->ev[par]);
       if (er != cudaSuccess) return er;
       const double b = pin[3 * par], coarse = pin[3 * par + 1], fine = pin[3 * par + 2];
@@ -1575,6 +1586,9 @@ rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, int form, double h, int
       }
       return cudaSuccess;
     };
+    // checks from Lh / 2 on, as in the step's first pass
+    const int first_check = (int)std::floor(0.5 * Lh);
+    int nchecked = 0;
     for (int c = 0; err == cudaSuccess; ++c) {
       const int j0 = c * chunk;
       if (j0 >= L.cap) break;
@@ -1583,6 +1597,12 @@ rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, int form, double h, int
         lz_wstep<0><<<grid, THREADS, 0, s>>>(G, j, W(j - 1), W(j - 2), W(j), alpha, beta, invb, partials, counter,
                                              nullptr, nullptr);
       lz_poles_advance<<<(np + 127) / 128, 128, 0, s>>>(np, d_s, d_w, alpha, beta, j0, j1, D2(L.dg), D2(L.wy));
+      if (j1 < first_check && j1 < L.cap) {
+        launches += (j1 - j0) + 1;
+        err = cudaGetLastError();
+        continue;
+      }
+      const int par = nchecked++ & 1;
       err = cudaMemsetAsync(maxslots, 0, 2 * sizeof(unsigned long long), s);
       if (err != cudaSuccess) break;
       const int sym = ((j1 - 1) & 1) ? -1 : 1;
@@ -1595,7 +1615,6 @@ rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, int form, double h, int
       lz_bound_max<<<gf.x, BT, 0, s>>>(groups, nslot_f, D2(L.part), sym, beta, j1, k->rtol, maxslots,
                                        maxslots + 1);
       launches += (j1 - j0) + 5;
-      const int par = c & 1;
       err = cudaMemcpyAsync(pin + 3 * par, beta + j1, sizeof(double), cudaMemcpyDeviceToHost, s);
       if (err == cudaSuccess)
         err = cudaMemcpyAsync(pin + 3 * par + 1, maxslots, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -1606,7 +1625,7 @@ rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, int form, double h, int
         err = evaluate(pending, pending_j1);
         if (err != cudaSuccess || converged || nonfinite) break;
       }
-      pending = c;
+      pending = par;
       pending_j1 = j1;
     }
     if (err == cudaSuccess && !converged && !nonfinite && pending >= 0) err = evaluate(pending, pending_j1);
