@@ -60,8 +60,11 @@ typedef enum {
 
 /* Arithmetic form of the pole loop (plan creation). */
 enum {
-  REXI_FORM_FP64 = 0,  /* fused: all solves of a wavenumber in FP64 registers */
-  REXI_FORM_MIXED = 1, /* fused: solves in FP32 pairs (double-float), FP64 endpoints */
+  REXI_FORM_FP64 = 0,  /* fused: all solves of a wavenumber in FP64 registers (once per
+                          orbit of omega's symmetries), FP64 transforms and combine */
+  REXI_FORM_MIXED = 1, /* fused: solves in FP32 pairs (double-float); transforms and, for
+                          real input, the half spectrum and combine in double-float;
+                          FP64 at the state boundary */
   REXI_FORM_PLAIN = 2  /* paper-style: per-term solve pairs materialised, then a
                           separate reduction pass (Section 4.1, GPU algorithm) */
 };
