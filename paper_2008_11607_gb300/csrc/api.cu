@@ -521,7 +521,13 @@ rexi_status fused_table(rexi_plan_s* p, int M, int tb, int te, double G, cudaStr
   for (auto& c : p->coef) {
     if (c.M == M && c.tb == tb && c.te == te && c.G == G) {
       c.last_use = ++p->coef_clock;
-      if (cudaEventQuery(c.ready) == cudaErrorNotReady) CUDA_TRY(cudaStreamWaitEvent(s, c.ready, 0), "table wait");
+      // an upload still in flight (on another stream): order this stream after
+      // it; a finished one needs no wait (and none is recorded, so a step can be
+      // captured in a graph once its table exists)
+      if (cudaEventQuery(c.ready) == cudaErrorNotReady) {
+        if (cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();  // a status, not an error
+        CUDA_TRY(cudaStreamWaitEvent(s, c.ready, 0), "table wait");
+      }
       *out = &c;
       return REXI_OK;
     }
