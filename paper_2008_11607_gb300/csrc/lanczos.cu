@@ -1364,11 +1364,12 @@ __global__ void __launch_bounds__(256) lz_grad_contract(int nx, int ny, double i
   if (live) grad[p] += w[p] * acc;
 }
 
-// The same contraction in double-float arithmetic (mixed form): the FP64
-// bases and R are split into (hi, lo) FP32 pairs on load (integer operations),
-// products and sums run on the FP32 pipes; the result is added in FP64.
-__global__ void __launch_bounds__(256) lz_grad_contract_df(int nx, int ny, double idx, double idy, const double* f0,
-                                                           const double* basA, const double* g0, const double* basB,
+// The same contraction in double-float arithmetic (mixed form) on bases kept
+// as double-float pairs; R is split into (hi, lo) FP32 pairs on load (integer
+// operations), products and sums run on the FP32 pipes; the result is added
+// in FP64.
+__global__ void __launch_bounds__(256) lz_grad_contract_df(int nx, int ny, double idx, double idy, const float2* f0,
+                                                           const float2* basA, const float2* g0, const float2* basB,
                                                            size_t vstride, int kA, int kB, const double* R,
                                                            const double* w, double* grad) {
   __shared__ float2 Rs[kGA][kGB];
@@ -1394,7 +1395,7 @@ __global__ void __launch_bounds__(256) lz_grad_contract_df(int nx, int ny, doubl
       const int na = min(kGA, kB - a0);
       for (int q = 0; q < na; ++q) {
         const int a = a0 + q;
-        const float2 sv = df_from_double(live ? (a == 0 ? g0[p] : basB[(size_t)(a - 1) * vstride + p]) : 0.0);
+        const float2 sv = live ? (a == 0 ? g0[p] : basB[(size_t)(a - 1) * vstride + p]) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int bb = 0; bb < kGB; ++bb) {
           const float2 t = f_mul(Rs[q][bb].x, Rs[q][bb].y, sv.x, sv.y);
@@ -1408,9 +1409,9 @@ __global__ void __launch_bounds__(256) lz_grad_contract_df(int nx, int ny, doubl
     for (int bb = 0; bb < kGB; ++bb) {
       if (bb >= nbb) break;
       const int b = b0 + bb;
-      const double* S = b == 0 ? f0 : basA + (size_t)(b - 1) * vstride;
-      const float2 ddx = f_subf(df_from_double(S[nk + p]), df_from_double(S[nk + pxm]));
-      const float2 ddy = f_subf(df_from_double(S[2 * nk + p]), df_from_double(S[2 * nk + pym]));
+      const float2* S = b == 0 ? f0 : basA + (size_t)(b - 1) * vstride;
+      const float2 ddx = f_subf(S[nk + p], S[nk + pxm]);
+      const float2 ddy = f_subf(S[2 * nk + p], S[2 * nk + pym]);
       const float2 dv = f_addf(f_mulf(ddx, idx_df), f_mulf(ddy, idy_df));
       acc = f_addf(acc, f_mulf(z[bb], dv));
     }
@@ -1424,7 +1425,7 @@ int grad_cap(const KrylovSettings* k, int M, double h) {
 }
 struct GLayout {
   size_t vb, f0, g0, basA, basB, alA, beA, ibA, alB, beB, ibB, sA, wA, sB, wB, dg, wy, part, maxslots, partials,
-      counter, CA, DB, R, total;
+      counter, CA, DB, R, dfc, total;
   int cap;
 };
 GLayout grad_layout(const KrylovSettings* k, int M, double h) {
@@ -1464,6 +1465,7 @@ GLayout grad_layout(const KrylovSettings* k, int M, double h) {
   L.CA = take((size_t)L.cap * np * sizeof(double2));
   L.DB = take((size_t)L.cap * np * sizeof(double2));
   L.R = take((size_t)L.cap * L.cap * sizeof(double));
+  L.dfc = take(nmax * sizeof(DfCoef));
   L.total = o;
   return L;
 }
@@ -1524,6 +1526,8 @@ rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, int form, double h, int
   unsigned* counter = reinterpret_cast<unsigned*>(base + L.counter);
   unsigned long long* maxslots = reinterpret_cast<unsigned long long*>(base + L.maxslots);
   const size_t vstride = L.vb / sizeof(double);
+  // mixed form: Lanczos runs and the contraction in double-float
+  const bool df = form == REXI_FORM_MIXED;
 
   mark(0);
   cudaError_t e = cudaMemcpyAsync(D2(L.sA), sA.data(), np * sizeof(double2), cudaMemcpyHostToDevice, s);
@@ -1564,8 +1568,14 @@ rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, int form, double h, int
     G.H = k->depth;
     G.w = k->w64;
     const dim3 grid(G.tiles_x, G.tiles_y, 1);
+    // mixed form: the kept vectors are double-float pairs (8 bytes per value, as FP64)
     auto W = [&](int j) -> double* { return j < -1 ? nullptr : (j == -1 ? f0 : bas + (size_t)j * vstride); };
-    lz_init<double><<<grid, THREADS, 0, s>>>(G, src, adjoint, f0, beta, invb, partials, counter);
+    auto Wf = [&](int j) -> float2* { return reinterpret_cast<float2*>(W(j)); };
+    DfCoef* dfc = reinterpret_cast<DfCoef*>(base + L.dfc);
+    if (df)
+      lz_init_df<<<grid, THREADS, 0, s>>>(G, src, adjoint, Wf(-1), beta, invb, dfc, partials, counter);
+    else
+      lz_init<double><<<grid, THREADS, 0, s>>>(G, src, adjoint, f0, beta, invb, partials, counter);
     ++launches;
     cudaError_t err = cudaGetLastError();
     bool converged = false, nonfinite = false;
@@ -1593,9 +1603,15 @@ rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, int form, double h, int
       const int j0 = c * chunk;
       if (j0 >= L.cap) break;
       const int j1 = std::min(j0 + chunk, L.cap);
-      for (int j = j0; j < j1; ++j)
-        lz_wstep<0><<<grid, THREADS, 0, s>>>(G, j, W(j - 1), W(j - 2), W(j), alpha, beta, invb, partials, counter,
-                                             nullptr, nullptr);
+      for (int j = j0; j < j1; ++j) {
+        if (df)
+          launch_step_pdl(lz_dfstep<0>, grid, s, G, k->Hdf, k->wdf, j, Wf(j - 1), Wf(j - 2), Wf(j), alpha, beta,
+                          invb, dfc, partials, counter, static_cast<float2*>(nullptr),
+                          static_cast<const float2*>(nullptr));
+        else
+          lz_wstep<0><<<grid, THREADS, 0, s>>>(G, j, W(j - 1), W(j - 2), W(j), alpha, beta, invb, partials, counter,
+                                               nullptr, nullptr);
+      }
       lz_poles_advance<<<(np + 127) / 128, 128, 0, s>>>(np, d_s, d_w, alpha, beta, j0, j1, D2(L.dg), D2(L.wy));
       if (j1 < first_check && j1 < L.cap) {
         launches += (j1 - j0) + 1;
@@ -1662,9 +1678,10 @@ rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, int form, double h, int
                                                                      D(L.R));
     launches += 3;
     mark(3);
-    if (form == REXI_FORM_MIXED)
+    auto F = [&](size_t off) { return reinterpret_cast<const float2*>(base + off); };
+    if (df)
       lz_grad_contract_df<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(
-          k->nx, k->ny, k->nx / k->Lx, k->ny / k->Ly, D(L.f0), D(L.basA), D(L.g0), D(L.basB), vstride, kA, kB,
+          k->nx, k->ny, k->nx / k->Lx, k->ny / k->Ly, F(L.f0), F(L.basA), F(L.g0), F(L.basB), vstride, kA, kB,
           D(L.R), k->w64, grad_depth);
     else
       lz_grad_contract<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(

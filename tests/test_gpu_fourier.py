@@ -165,6 +165,28 @@ def test_host_buffer_steps_blocking_and_overlapped():
         assert np.array_equal(o.numpy(), r)
 
 
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_coefficient_table_cache_eviction(form):
+    """A plan keeps at most eight coefficient tables (one per pole count and
+    term range); steps with eleven different pole counts, then the first ones
+    again (evicted and rebuilt), equal the steps of fresh plans bit for bit."""
+    torch = torch_cuda()
+    from paper_2008_11607_gb300 import rexi
+
+    st = inputs.kminus3_field(16, 16, seed=21)
+    x = to_dev(torch, st)
+    plan = rexi.Plan(16, 16, form=form)
+    dts = [(4.0 + 3.0 * i) / plan.rho for i in range(11)]
+    Ms = set()
+    for dt in dts + dts[:3]:
+        out, info = plan.step(x, dt, want_info=True)
+        Ms.add(info.M)
+        ref = rexi.Plan(16, 16, form=form).step(x, dt)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    assert len(Ms) == 11
+
+
 @pytest.mark.parametrize("form", FORMS)
 def test_term_slices_sum_to_full(form):
     torch = torch_cuda()
