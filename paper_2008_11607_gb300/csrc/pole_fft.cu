@@ -6,21 +6,27 @@
 // (alpha I + tau B)^{-1} therefore reduces to scalar work on those
 // eigenvalues, and the sum over all REXII terms of eq. modifiedRexi,
 //   R+ = REXII(i x) = sum_n (c1_n h mu + c2_n (x + h n)) / ((h mu)^2 + (x + h n)^2),
-// x = tau omega(k), is accumulated in registers for one wavenumber pair
-// (k, -k) per thread (omega(-k) = omega(k)).  The conjugate symmetry of the
-// coefficients (remark before eq. modifiedRexiMatrixReducedSum) gives
+// x = tau omega(k), is accumulated in registers.  The conjugate symmetry of
+// the coefficients (remark before eq. modifiedRexiMatrixReducedSum) gives
 // REXII(-ix) = conj(R+), and with Bt = B / omega
 //   r(tau B) = R0 I + Im(R+) Bt + (R0 - Re R+) Bt^2,   R0 = REXII(0),
 // which is exact on all three eigenvalues (Bt^3 = -Bt).  No per-term field is
-// materialised.
+// materialised.  R+ depends on k only through omega(k), so it is summed once
+// per orbit of omega's symmetries (see OrbitParams) and a separate pass
+// applies r(tau B) at every wavenumber with its own symbol.
 //
 // Forms:
-//  * pole_fused_fp64  -- FP64 registers; 1/d by the rcp.approx seed plus one
-//    Newton-Raphson step in FP64 (relative error ~2^-44 per term).
-//  * pole_fused_mixed -- the same sum in double-float arithmetic (pairs of
-//    FP32 values with Dekker/Knuth error-free transformations: TwoSum,
-//    TwoProduct by FMA), FP64 only for the per-wavenumber setup and the
-//    final combine.  FP32 runs ~58x faster than FP64 on this GPU.
+//  * pole_orbit_fp64 / pole_fused_fp64 -- FP64 registers; 1/d by the
+//    rcp.approx seed plus a Newton-Raphson step with its next term in FP64.
+//  * pole_orbit_mixed / pole_fused_mixed -- the same sum in double-float
+//    arithmetic (pairs of FP32 values with Dekker/Knuth error-free
+//    transformations: TwoSum, TwoProduct by FMA), FP64 only for the
+//    per-orbit setup.  FP32 runs ~58x faster than FP64 on this GPU.
+//    (The pole_fused_* kernels are the earlier one-pair-per-thread form with
+//    the combine fused, kept for the allocation-free step.)
+//  * pole_orbit_combine (FP64) / pole_orbit_combine_df (double-float, real
+//    input, half spectrum) -- r(tau B) at every wavenumber from per-orbit
+//    scalars.
 //  * pole_plain_terms / pole_plain_reduce -- the paper's GPU structure
 //    (Section 4.1): per REXII term n the two shifted 3x3 solves
 //    g1 = (alpha_n I + tau B)^{-1} f, g2 = (alpha_{-n} I - tau B)^{-1} g1,
