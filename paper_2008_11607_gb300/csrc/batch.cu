@@ -263,15 +263,10 @@ cudaError_t launch_pole(rexi_batch_s* b, OrbitScalars* orb, unsigned* counter, c
                      : launch_persistent<REXI_FORM_MIXED, 1>(b, orb, counter, b->threads, s);
 }
 
-float2 split_host(double v) {
-  const float h = (float)v;
-  return make_float2(h, (float)(v - (double)h));
-}
-
 cudaError_t launch_combine(rexi_batch_s* b, double2* spec, const OrbitScalars* orb, int real_input, cudaStream_t s) {
   batch_combine_kernel<<<b->combine_blocks, 256, 0, s>>>(spec, orb, b->d_desc, b->d_blk, b->n, b->g, b->f, b->H, 0,
                                                          real_input, b->form == REXI_FORM_MIXED ? 1 : 0,
-                                                         split_host(b->g), split_host(b->f), split_host(b->H));
+                                                         df_split_host(b->g), df_split_host(b->f), df_split_host(b->H));
   return cudaGetLastError();
 }
 

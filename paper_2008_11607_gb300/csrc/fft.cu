@@ -446,11 +446,6 @@ static StageList to_stages(const FftPlan1D& p) {
   return s;
 }
 
-static float2 split_scale(double v) {
-  const float h = (float)v;
-  return make_float2(h, (float)(v - (double)h));
-}
-
 // Threads of a real-row CTA: one radix-8 butterfly per thread per stage.
 static int rows_threads(int rpc, int m) { return std::min(256, std::max(64, rpc * m / 8)); }
 
@@ -492,7 +487,7 @@ static cudaError_t fft2d_impl(const double2* in, double2* out, int nfields, cons
     auto k = fft_rows_kernel<SIGN, T, double2, TM>;
     if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
     dim3 grid((nrows + rpc - 1) / rpc);
-    k<<<grid, 256, sm, s>>>(in, mid, nrows, rpc, to_stages(px), twx, 1.0, split_scale(1.0), zero_imag_in, 0);
+    k<<<grid, 256, sm, s>>>(in, mid, nrows, rpc, to_stages(px), twx, 1.0, df_split_host(1.0), zero_imag_in, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
@@ -501,7 +496,7 @@ static cudaError_t fft2d_impl(const double2* in, double2* out, int nfields, cons
     auto k = fft_cols_kernel<SIGN, T, TM, double2>;
     if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
     dim3 grid((nx + W - 1) / W, nfields);
-    k<<<grid, cols_threads(W, ny), sm, s>>>(mid, out, nx, W, to_stages(py), twy, scale, split_scale(scale), 0,
+    k<<<grid, cols_threads(W, ny), sm, s>>>(mid, out, nx, W, to_stages(py), twy, scale, df_split_host(scale), 0,
                                             real_out);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -537,7 +532,7 @@ static cudaError_t fft2d_r2c_impl(const double2* in, double2* spec, int nfields,
     if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
     dim3 grid((m + 1 + W - 1) / W, nfields);
     k<<<grid, cols_threads(W, ny), sm, s>>>(mid, reinterpret_cast<TS*>(spec), m + 1, W, to_stages(py), twy, 1.0,
-                                            split_scale(1.0), 0, 0);
+                                            df_split_host(1.0), 0, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   (void)px;
@@ -560,7 +555,7 @@ static cudaError_t fft2d_c2r_impl(double2* spec, double2* out, int nfields, cons
     if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
     dim3 grid((m + 1 + W - 1) / W, nfields);
     k<<<grid, cols_threads(W, ny), sm, s>>>(reinterpret_cast<const TS*>(spec), mid, m + 1, W, to_stages(py), twy,
-                                            1.0, split_scale(1.0), 0, 0);
+                                            1.0, df_split_host(1.0), 0, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   {
@@ -570,7 +565,7 @@ static cudaError_t fft2d_c2r_impl(double2* spec, double2* out, int nfields, cons
     auto k = fft_rows_c2r_kernel<T, TM>;
     if ((e = allow_smem(k, sm)) != cudaSuccess) return e;
     k<<<(nrows + rpc - 1) / rpc, rows_threads(rpc, m), sm, s>>>(mid, out, nrows, rpc, to_stages(pxh), twxh, twx, scale,
-                                              split_scale(scale));
+                                              df_split_host(scale));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   (void)px;

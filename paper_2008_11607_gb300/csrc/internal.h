@@ -28,6 +28,12 @@ double table_mu();
 void table_a(double re[kL + 1], double im[kL + 1]);
 void rexii_terms(int M, double h, TermSet* ts);
 
+// Host: a double as a double-float pair (hi = nearest float, lo = the rest).
+inline float2 df_split_host(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
 // Records the text returned by rexi_last_error_message() (api.cu).
 void set_last_error(const char* msg);
 

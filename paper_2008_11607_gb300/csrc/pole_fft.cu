@@ -378,21 +378,17 @@ cudaError_t pole_orbit_combine_df(void* spec_df, const double2* part, int slices
   pole_orbit_finalize_kernel<true><<<(unsigned)((op.norb + 255) / 256), 256, 0, s>>>(part, slices, sp, op, R0, fin);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  auto split = [](double v) {
-    const float h = (float)v;
-    return make_float2(h, (float)(v - (double)h));
-  };
   SymbolDF sd;
-  sd.g = split(sp.g);
-  sd.H = split(sp.H);
-  sd.f = split(sp.f);
-  sd.inv_dx = split(sp.inv_dx);
-  sd.inv_dy = split(sp.inv_dy);
+  sd.g = df_split_host(sp.g);
+  sd.H = df_split_host(sp.H);
+  sd.f = df_split_host(sp.f);
+  sd.inv_dx = df_split_host(sp.inv_dx);
+  sd.inv_dy = df_split_host(sp.inv_dy);
   sd.half_x = half_x_df;
   sd.half_y = half_y_df;
   const size_t nk = (size_t)row_len * sp.ny;
   pole_orbit_combine_df_kernel<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(
-      static_cast<float4*>(spec_df), static_cast<const OrbitScalarsDF*>(fin), sd, sp.nx, sp.ny, op, split(fs.R0re),
+      static_cast<float4*>(spec_df), static_cast<const OrbitScalarsDF*>(fin), sd, sp.nx, sp.ny, op, df_split_host(fs.R0re),
       fs.adjoint, row_len);
   return cudaGetLastError();
 }
