@@ -26,8 +26,13 @@
  *   ((field * ny + j) * nx + i).  Device pointers unless stated otherwise;
  *   they must be 16-byte aligned.
  * - Memory ownership: the caller owns every buffer passed in.  The library
- *   never frees caller memory.  A plan owns only small tables (twiddles);
- *   rexi_plan_create allocates them and rexi_plan_destroy frees them.
+ *   never frees caller memory.  A plan owns only small tables (twiddles,
+ *   half angles, and up to eight coefficient tables of the FP64 and mixed
+ *   Fourier forms, one per pole count and term range, allocated by the first
+ *   step that needs one); rexi_plan_create allocates the fixed tables and
+ *   rexi_plan_destroy frees them all.
+ * - A plan is used by one host thread at a time; its steps may be enqueued on
+ *   different streams.
  *   rexi_step allocates nothing: its scratch is the caller's workspace.
  * - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
  *   default stream).  Calls are asynchronous on that stream; inputs must stay
