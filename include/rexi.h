@@ -278,8 +278,11 @@ rexi_status rexi_workspace_size_host(rexi_plan_t plan, double dt, double tol, in
  * the stream or an event recorded on it).  With pinned host memory the
  * copies run on the copy engines, so consecutive steps enqueued on two
  * streams, each with its own workspace, overlap one step's copies with the
- * other's kernels.  Steps on different streams may share the plan.  No
- * per-call information is returned (use rexi_step_host for that). */
+ * other's kernels.  Steps on different streams may share the plan; the
+ * kernels of a plan's host-buffer steps run in call order (each call's
+ * kernels wait, after its copy in, for those of the previous call), so that
+ * the GPU is never left waiting on copies of steps that finished together.
+ * No per-call information is returned (use rexi_step_host for that). */
 rexi_status rexi_step_host_async(rexi_plan_t plan, const void* in_host, void* out_host, double dt, double tol,
                                  int32_t real_input, void* workspace_dev, size_t workspace_bytes, void* stream);
 

@@ -79,6 +79,10 @@ struct rexi_plan_s {
   };
   std::vector<CoefTable> coef;
   uint64_t coef_clock = 0;
+  // host-buffer steps: kernels of consecutive calls run in call order (each
+  // waits for the previous call's kernels), their copies overlap
+  cudaEvent_t host_kernels_done = nullptr;
+  bool host_kernels_recorded = false;
   // coefficient staging (pinned host) guarded by an event
   void* staging = nullptr;
   size_t staging_bytes = 0;
@@ -230,6 +234,7 @@ void rexi_plan_destroy(rexi_plan_t p) {
     cudaFree(c.dev);
     if (c.ready) cudaEventDestroy(c.ready);
   }
+  if (p->host_kernels_done) cudaEventDestroy(p->host_kernels_done);
   krylov_destroy(&p->kry);
   for (auto& set : p->prof_pool)
     for (auto e : set) cudaEventDestroy(e);
@@ -850,10 +855,18 @@ rexi_status step_host_enqueue(rexi_plan_t p, const void* in_host, void* out_host
   if (ws_bytes < 2 * state) return fail(REXI_ENOMEM, "workspace too small for the host-buffer step");
   char* base = static_cast<char*>(ws);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!p->host_kernels_done)
+    CUDA_TRY(cudaEventCreateWithFlags(&p->host_kernels_done, cudaEventDisableTiming), "event creation");
   CUDA_TRY(cudaMemcpyAsync(base, in_host, bytes, cudaMemcpyHostToDevice, s), "host-to-device copy");
+  // the kernels of the previous host-buffer step of this plan (on any stream)
+  // first: concurrent steps would finish together and leave the copy engines
+  // and the SMs idle in turn
+  if (p->host_kernels_recorded) CUDA_TRY(cudaStreamWaitEvent(s, p->host_kernels_done, 0), "kernel order");
   rexi_status st = rexi_step(p, base, base + state, dt, tol, real_input, 0, -1, base + 2 * state,
                              ws_bytes - 2 * state, stream, info);
   if (st != REXI_OK) return st;
+  CUDA_TRY(cudaEventRecord(p->host_kernels_done, s), "kernel order");
+  p->host_kernels_recorded = true;
   CUDA_TRY(cudaMemcpyAsync(out_host, base + state, bytes, cudaMemcpyDeviceToHost, s), "device-to-host copy");
   return REXI_OK;
 }
