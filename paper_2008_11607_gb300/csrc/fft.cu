@@ -454,9 +454,15 @@ static int rows_per_cta(int n) {
   while (r < 16 && r * n * 2 <= 1024) r *= 2;
   return r;
 }
+// Columns per CTA: the two stage buffers of W columns fit in kColsSmemKB of
+// shared memory (64 KB: a 2048-point column per CTA, three CTAs per SM).
+#ifndef REXI_COLS_SMEM_KB
+#define REXI_COLS_SMEM_KB 64
+#endif
+constexpr size_t kColsSmemKB = REXI_COLS_SMEM_KB;
 static int cols_per_cta(int n) {
   int w = 16;
-  while (w > 1 && 2 * (size_t)w * n * sizeof(double2) > 128 * 1024) w /= 2;
+  while (w > 1 && 2 * (size_t)w * n * sizeof(double2) > kColsSmemKB * 1024) w /= 2;
   return w;
 }
 // Threads of a column CTA: a large tile (one CTA per SM by its shared memory)
