@@ -105,3 +105,21 @@ def test_plan_rejects_bad_grids_without_gpu(lib):
     assert lib.rexi_plan_create(ctypes.byref(h), 64, 64, 1.0, 1.0, 1.0, 1.0, -2.0, None, 0, 0.5) == rexi.REXI_EINVAL
     assert lib.rexi_plan_create(ctypes.byref(h), 2 * 131, 64, 1.0, 1.0, 1.0, 1.0, 1.0, None, 0, 0.5) == rexi.REXI_EINVAL
     assert lib.rexi_plan_create(ctypes.byref(h), 8192, 64, 1.0, 1.0, 1.0, 1.0, 1.0, None, 0, 0.5) == rexi.REXI_EINVAL
+
+
+def test_valid_plan_fails_loudly_without_a_gpu(lib):
+    """No CPU fallback: on a machine without a GPU a valid plan cannot be
+    created, through the C ABI or the binding, and the host-buffer entry
+    points reject a missing plan before touching the device."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    st = lib.rexi_plan_create(ctypes.byref(h), 64, 64, 1.0, 1.0, 1.0, 1.0, 1.0, None, 1, 0.5)
+    assert st in (rexi.REXI_ENOMEM, rexi.REXI_ECUDA)
+    assert lib.rexi_last_error_message()
+    with pytest.raises(rexi.RexiError):
+        rexi.Plan(64, 64, form="mixed")
+    buf = (ctypes.c_double * 8)()
+    assert lib.rexi_step_host_async(None, buf, buf, 0.1, 1e-10, 1, buf, 8, None) == rexi.REXI_EINVAL
