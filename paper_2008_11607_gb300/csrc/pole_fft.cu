@@ -149,7 +149,7 @@ OrbitParams orbit_params(const SymbolParams& sp) {
 }
 
 int orbit_slice_cap(int norb) {
-  // partial sums of at most 64 MB, at least 8 slices, at most 64
+  // as many slices as 64 MB of partial sums hold, at least 8 and at most 64
   const long long c = (64ll << 20) / (16ll * std::max(norb, 1));
   return (int)std::min<long long>(64, std::max<long long>(8, c));
 }
