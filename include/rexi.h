@@ -313,8 +313,12 @@ rexi_status rexi_plan_read_profile(rexi_plan_t plan, double* ms5, int32_t* n_cal
  * (dt * rho up to about 2030 at h = 0.5, tol = 1e-10); larger requests return
  * REXI_EINVAL with the reason in rexi_last_error_message().
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it: make that first call before any
- * stream capture.  All calls share the array: calls whose GPU work overlaps
+ * (cudaGetSymbolAddress) and caches it for the life of the process; the
+ * cache does not survive cudaDeviceReset, so make no call after one.  Each
+ * call copies its tables from static pageable host buffers, which the next
+ * call overwrites, so the entry point cannot be captured in a CUDA graph: a
+ * call on a capturing stream returns REXI_EINVAL before any copy or launch.
+ * All calls share the array: calls whose GPU work overlaps
  * (different streams, several host threads) race and give wrong results;
  * order them on one stream.  Every region is written before it is read, so
  * nothing needs clearing between calls. */

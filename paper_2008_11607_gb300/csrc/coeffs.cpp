@@ -53,19 +53,10 @@ int pole_count(double tau_rho, double h, double tol) {
 
 // c1_n = h sum_{k=L1(n)}^{L2(n)} Re(a_k) b_{n-k}, c2_n = h sum Im(a_k) b_{n-k},
 // b_m = e^{-i m h} e^{h^2}, L1 = max(-L, n-M), L2 = min(L, n+M), n = -N..N.
-void rexii_terms(int M, double h, TermSet* ts) {
+// bre/bim: 2M + 1 values of scratch (b_m at m + M); c*: 2N + 1 values each.
+void rexii_terms_into(int M, double h, double* bre, double* bim, double* c1re, double* c1im, double* c2re,
+                      double* c2im) {
   const int N = M + kL;
-  ts->M = M;
-  ts->N = N;
-  ts->h = h;
-  ts->mu = kMu;
-  const int nt = 2 * N + 1;
-  ts->c1re.assign(nt, 0.0);
-  ts->c1im.assign(nt, 0.0);
-  ts->c2re.assign(nt, 0.0);
-  ts->c2im.assign(nt, 0.0);
-  // b_m for m = -M..M
-  std::vector<double> bre(2 * M + 1), bim(2 * M + 1);
   const double eh2 = exp(h * h);
   for (int m = -M; m <= M; ++m) {
     const double ang = (double)m * h;
@@ -86,11 +77,27 @@ void rexii_terms(int M, double h, TermSet* ts) {
       s2r += aim * br;
       s2i += aim * bi;
     }
-    ts->c1re[n + N] = h * s1r;
-    ts->c1im[n + N] = h * s1i;
-    ts->c2re[n + N] = h * s2r;
-    ts->c2im[n + N] = h * s2i;
+    c1re[n + N] = h * s1r;
+    c1im[n + N] = h * s1i;
+    c2re[n + N] = h * s2r;
+    c2im[n + N] = h * s2i;
   }
+}
+
+void rexii_terms(int M, double h, TermSet* ts) {
+  const int N = M + kL;
+  ts->M = M;
+  ts->N = N;
+  ts->h = h;
+  ts->mu = kMu;
+  const int nt = 2 * N + 1;
+  ts->c1re.assign(nt, 0.0);
+  ts->c1im.assign(nt, 0.0);
+  ts->c2re.assign(nt, 0.0);
+  ts->c2im.assign(nt, 0.0);
+  std::vector<double> bre(2 * M + 1), bim(2 * M + 1);
+  rexii_terms_into(M, h, bre.data(), bim.data(), ts->c1re.data(), ts->c1im.data(), ts->c2re.data(),
+                   ts->c2im.data());
 }
 
 }  // namespace rexi

@@ -27,6 +27,10 @@ bool valid_tol(double tol);
 double table_mu();
 void table_a(double re[kL + 1], double im[kL + 1]);
 void rexii_terms(int M, double h, TermSet* ts);
+// The same sums into caller arrays (no allocation): bre/bim hold 2M + 1
+// values of scratch, c1re..c2im receive 2N + 1 values each (index n + N).
+void rexii_terms_into(int M, double h, double* bre, double* bim, double* c1re, double* c1im, double* c2re,
+                      double* c2im);
 
 // Host: a double as a double-float pair (hi = nearest float, lo = the rest).
 inline float2 df_split_host(double v) {

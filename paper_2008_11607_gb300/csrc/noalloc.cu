@@ -27,7 +27,18 @@
 //
 // Set-up: the first call on each device asks the runtime for the device
 // address of the array (cudaGetSymbolAddress, with that device current) and
-// caches it; make that first call before any stream capture.
+// caches it for the life of the process.  The cache does not survive
+// cudaDeviceReset (or any other teardown of the device's primary context):
+// after one, the cached address is stale, so do not call this entry point
+// again in that process.
+//
+// Tables: each call fills host-side static tables (twiddles, half angles, the
+// coefficient table) under a mutex and copies them into the device array with
+// cudaMemcpyAsync from that pageable memory; the driver stages such copies
+// before the call returns, so the next call may overwrite the host tables.
+// For the same reason the entry point cannot be captured in a CUDA graph (a
+// captured copy would read host tables that later calls overwrite): a call on
+// a capturing stream returns REXI_EINVAL before any copy or launch.
 #include <math.h>
 #include <stdint.h>
 
@@ -64,6 +75,7 @@ void* g_scratch_addr[kMaxDevices] = {};
 double2 h_tw_x[kMaxSide], h_tw_y[kMaxSide], h_half_x[kMaxSide], h_half_y[kMaxSide];
 double h_table[kMaxTerms * 6];
 double h_bre[2 * kMaxM + 1], h_bim[2 * kMaxM + 1];
+double h_c1re[kMaxTerms], h_c1im[kMaxTerms], h_c2re[kMaxTerms], h_c2im[kMaxTerms];
 
 // errors are reported through rexi_last_error_message()
 rexi_status fail(rexi_status st, const char* msg) {
@@ -120,6 +132,15 @@ extern "C" rexi_status rexi_step_noalloc(int32_t nx, int32_t ny, double Lx, doub
   if (nterms > kMaxTerms)
     return fail(REXI_EINVAL, "rexi_step_noalloc: more than 8193 REXII terms (dt*rho too large for the fixed scratch)");
 
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess)
+    return fail(REXI_ECUDA, "rexi_step_noalloc: cudaStreamIsCapturing failed");
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(REXI_EINVAL,
+                "rexi_step_noalloc: the stream is capturing a CUDA graph; this entry point copies from "
+                "host tables that later calls overwrite and cannot be captured");
+
   std::lock_guard<std::mutex> lock(g_mutex);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
@@ -131,31 +152,15 @@ extern "C" rexi_status rexi_step_noalloc(int32_t nx, int32_t ny, double Lx, doub
     g_scratch_addr[dev] = ptr;
   }
   char* base = static_cast<char*>(g_scratch_addr[dev]);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   // tables on the host, then copied into the static device array
   fill_axis(nx, h_tw_x, h_half_x);
   fill_axis(ny, h_tw_y, h_half_y);
-  double are[kL + 1], aim[kL + 1];
-  table_a(are, aim);
-  const double mu = table_mu(), hmu = h * mu, q = hmu * hmu, eh2 = exp(h * h);
-  for (int m = -M; m <= M; ++m) {
-    h_bre[m + M] = eh2 * cos((double)m * h);
-    h_bim[m + M] = -eh2 * sin((double)m * h);
-  }
+  rexii_terms_into(M, h, h_bre, h_bim, h_c1re, h_c1im, h_c2re, h_c2im);
+  const double mu = table_mu(), hmu = h * mu, q = hmu * hmu;
   double R0r = 0.0, R0i = 0.0;
   for (int n = -N; n <= N; ++n) {
-    // c1_n = h sum Re(a_k) b_{n-k}, c2_n = h sum Im(a_k) b_{n-k}, k in [max(-L, n-M), min(L, n+M)]
-    const int k0 = (n - M > -kL) ? n - M : -kL;
-    const int k1 = (n + M < kL) ? n + M : kL;
-    double c1r = 0, c1i = 0, c2r = 0, c2i = 0;
-    for (int k = k0; k <= k1; ++k) {
-      const int kk = k < 0 ? -k : k;
-      const double ar = are[kk], ai = k < 0 ? -aim[kk] : aim[kk];
-      const double br = h_bre[n - k + M], bi = h_bim[n - k + M];
-      c1r += ar * br; c1i += ar * bi; c2r += ai * br; c2i += ai * bi;
-    }
-    c1r *= h; c1i *= h; c2r *= h; c2i *= h;
+    const double c1r = h_c1re[n + N], c1i = h_c1im[n + N], c2r = h_c2re[n + N], c2i = h_c2im[n + N];
     double* e = &h_table[6 * (n + N)];
     e[0] = h * n;
     e[1] = c1r * hmu;

@@ -4,8 +4,10 @@ array inside the library).
 
 Checked through the C ABI against the ordinary entry point (rexi_step with a
 plan and a workspace, fused FP64 form) on two calls in a row, with the same
-tolerance as the other FP64 parity tests, and for the clear rejection of
-requests larger than the fixed scratch.  This file is collected last on
+tolerance as the other FP64 parity tests; that a call after the first one
+changes neither torch's allocator counters nor the device's free memory; that
+a call on a capturing stream is refused before it copies or launches anything;
+and for the clear rejection of requests larger than the fixed scratch.  This file is collected last on
 purpose; it passes alone in a fresh process and after the other tests.
 """
 import ctypes
@@ -64,3 +66,46 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
     rho = 2 * np.sqrt(2) * 64
     assert _noalloc(lib, torch, small, small, 3000.0 / rho, True, phys) == rexi.REXI_EINVAL
     assert b"8193" in lib.rexi_last_error_message()
+
+
+def test_noalloc_allocates_no_device_memory():
+    torch = torch_cuda()
+    from paper_2008_11607_gb300 import rexi
+
+    lib = rexi.load()
+    phys = dict(Lx=1.0, Ly=1.0, g=1.0, f=1.0, H=1.0)
+    x = to_dev(torch, inputs.kminus3_field(128, 96, seed=3))
+    out = torch.empty_like(x)
+    dt = 200.0 / (2 * np.sqrt(2) * 128)
+    # the warm-up call loads the module and looks up the static array
+    assert _noalloc(lib, torch, x, out, dt, True, phys) == rexi.REXI_OK, lib.rexi_last_error_message()
+    torch.cuda.synchronize()
+    before = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(), torch.cuda.mem_get_info()[0])
+    for _ in range(2):
+        assert _noalloc(lib, torch, x, out, dt, True, phys) == rexi.REXI_OK, lib.rexi_last_error_message()
+    torch.cuda.synchronize()
+    after = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(), torch.cuda.mem_get_info()[0])
+    assert after == before, (before, after)
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    torch = torch_cuda()
+    from paper_2008_11607_gb300 import rexi
+
+    lib = rexi.load()
+    phys = dict(Lx=1.0, Ly=1.0, g=1.0, f=1.0, H=1.0)
+    x = to_dev(torch, inputs.kminus3_field(32, 32, seed=4))
+    out = torch.zeros_like(x)
+    y = torch.empty_like(x)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        y.copy_(x)
+        st = _noalloc(lib, torch, x, out, 0.05, True, phys)
+    assert st == rexi.REXI_EINVAL
+    assert b"capturing" in lib.rexi_last_error_message()
+    torch.cuda.synchronize()
+    assert float(out.abs().max()) == 0.0
+    # the stream is usable afterwards and a plain call still works
+    assert _noalloc(lib, torch, x, out, 0.05, True, phys) == rexi.REXI_OK
+    torch.cuda.synchronize()
+    assert float(out.abs().max()) > 0.0
