@@ -152,6 +152,28 @@ def c_coeffs(h, M, mu=None, a=None):
     return ns, c1, c2
 
 
+def c_coeffs_sliced(h, M, mu=None, a=None):
+    """The same c_{1,n}, c_{2,n} as ``c_coeffs``, accumulated for all n at once:
+    for each k = -L..L in increasing order, Re(a_k) b_m and Im(a_k) b_m are
+    added to index n = m + k for every m = -M..M.  Every n therefore receives
+    the terms of its sum in the same order as in ``c_coeffs`` (k from L1(n)
+    to L2(n)), so the two agree to rounding of b_m (pinned in
+    tests/test_oracle_coeffs.py); this form is for large M (hundreds of
+    thousands of terms), where the loops of ``c_coeffs`` take minutes."""
+    if mu is None or a is None:
+        mu, a = table_a()
+    N = M + L
+    ns = np.arange(-N, N + 1)
+    b = b_coeff(np.arange(-M, M + 1), h)
+    c1 = np.zeros(2 * N + 1, dtype=np.complex128)
+    c2 = np.zeros(2 * N + 1, dtype=np.complex128)
+    for k in range(-L, L + 1):
+        lo = k + L  # index of n = -M + k
+        c1[lo:lo + 2 * M + 1] += a[L + k].real * b
+        c2[lo:lo + 2 * M + 1] += a[L + k].imag * b
+    return ns, h * c1, h * c2
+
+
 def alpha(n, h, mu):
     """alpha_n = h (mu + i n), Section 2.1 Step 3."""
     return h * (mu + 1j * np.asarray(n, dtype=np.float64))

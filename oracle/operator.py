@@ -126,3 +126,32 @@ def spectral_radius_bound(nx, ny, Lx=1.0, Ly=1.0, g=1.0, f=1.0, Hmax=1.0):
     dx = Lx / nx
     dy = Ly / ny
     return math.sqrt(g * Hmax * (4.0 / dx ** 2 + 4.0 / dy ** 2)) + abs(f)
+
+
+def symbol_grid(nx, ny, Lx=1.0, Ly=1.0, g=1.0, f=1.0, H=1.0):
+    """B(k) at every wavenumber at once: a (3, 3, ny, nx) complex array whose
+    [:, :, ky, kx] slice equals ``symbol(kx, ky, ...)``.  The same entries as
+    ``symbol`` (Section 4 operator on the C grid: forward/backward differences
+    and the four-point Coriolis average), written with numpy broadcasting so
+    that large grids can be checked field-wide."""
+    dx = Lx / nx
+    dy = Ly / ny
+    tx = 2.0 * np.pi * np.arange(nx) / nx
+    ty = 2.0 * np.pi * np.arange(ny) / ny
+    ex = np.exp(1j * tx)[None, :]
+    ey = np.exp(1j * ty)[:, None]
+    one = np.ones((ny, nx))
+    dxf = (ex - 1.0) / dx * one
+    dyf = (ey - 1.0) / dy * one
+    dxb = (1.0 - 1.0 / ex) / dx * one
+    dyb = (1.0 - 1.0 / ey) / dy * one
+    P = (1.0 + ex) * (1.0 + 1.0 / ey) / 4.0
+    Pu = (1.0 + 1.0 / ex) * (1.0 + ey) / 4.0
+    B = np.zeros((3, 3, ny, nx), dtype=np.complex128)
+    B[0, 1] = -H * dxb
+    B[0, 2] = -H * dyb
+    B[1, 0] = -g * dxf
+    B[1, 2] = f * P
+    B[2, 0] = -g * dyf
+    B[2, 1] = -f * Pu
+    return B

@@ -56,6 +56,15 @@ def complex_random_state(nx, ny, seed, scale=1.0):
     return scale * (rng.standard_normal((3, ny, nx)) + 1j * rng.standard_normal((3, ny, nx)))
 
 
+def white_real_state(nx, ny, seed):
+    """Real white-noise state: eta, u and v independent standard normal values
+    from default_rng(seed), stored as complex128.  Its spectrum has the same
+    expected amplitude at every wavenumber, so a per-wavenumber check of a
+    step weighs every wavenumber alike."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((3, ny, nx)).astype(np.complex128)
+
+
 def variable_depth(nx, ny, seed, n_bumps=8, sigma=0.05, amp=0.1, Lx=1.0, Ly=1.0):
     """H = 1 + 0.4 sin(2 pi x) cos(4 pi y) + n_bumps Gaussian bumps (amplitude
     ``amp``, width ``sigma``, centres uniform from default_rng(seed), periodic

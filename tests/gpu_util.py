@@ -35,3 +35,64 @@ def oracle_step(state, dt, M, real_input=True, Lx=1.0, Ly=1.0, g=1.0, f=1.0, H=1
 
 
 TOL = {"fp64": 1e-10, "plain": 1e-10, "mixed": 1e-8}
+
+
+# ---------------------------------------------------------------------------
+# Error model of the Fourier path (used for the tolerances of the full-size
+# and paper-reproduction tests).
+#
+# The step applies r(tau B(k)) per wavenumber, r(ix) = sum_n T_n(x) with the
+# REXII terms T_n(x) = (c1_n h mu + c2_n (x + h n)) / ((h mu)^2 + (x + h n)^2)
+# (eq. modifiedRexi).  B(k) is normal for H = g (skew-Hermitian), so by
+# Theorem 1 with cond = 1 the per-wavenumber error is at most
+#   eps_r + delta_pole  (relative to |fhat(k)|)  plus  delta_fft rms(fhat),
+# * eps_r = max_{|x| <= tau rho} |r(ix) - e^{ix}|: the approximation error,
+#   evaluated by the oracle on a 0.02-spaced grid (r varies on the scale of the
+#   pole distance h|mu| ~ 2.6), times 1.25;
+# * delta_pole: rounding of the term sum.  Each term carries a relative error
+#   of at most kt u and each accumulation step one of at most ks u of the
+#   running partial sum S_k.  Treating these as independent zero-mean errors
+#   (probabilistic rounding analysis, Higham and Mary 2019), the sum's error
+#   exceeds lam u (kt sqrt(sum |T_n|^2) + ks sqrt(sum |S_k|^2)) with
+#   probability at most 2 exp(-lam^2 / 2); lam = 8 (< 3e-14 per evaluation).
+#   FP64 form: u = 2^-53, kt = 4 (rcp seed, two-term correction, two fma),
+#   ks = 1.  Double-float form: u = 2^-48 (the pair's unit roundoff u32^2),
+#   kt = 8 (the FP32 reciprocal seed, 2^-23, squared by the one Newton step
+#   gives 4u; four dropped lo*lo products), ks = 4 (two FP32 roundings of the
+#   low word, each below u32 times a low word of at most u32 |S_k|).  The
+#   partial sums run over contiguous term ranges, so sqrt(sum |S_k|^2) is
+#   bounded by 2 sqrt(n) max_k |cumulative sum|.
+# * delta_fft: the forward and inverse transforms, lam kf u log2(nx ny) of the
+#   rms amplitude, kf = 2 (FP64) and 4 (double-float).
+# ---------------------------------------------------------------------------
+
+_FORM_ROUNDING = {"fp64": (2.0 ** -53, 4.0, 1.0, 2.0), "mixed": (2.0 ** -48, 8.0, 4.0, 4.0),
+                  "plain": (2.0 ** -53, 8.0, 1.0, 2.0)}
+_LAM = 8.0
+
+
+def scalar_error_max(tau_rho, h, M, step=0.02):
+    """max_{0 <= x <= tau_rho} |r(ix) - e^{ix}| on a grid of spacing `step`
+    (r(-ix) = conj r(ix), so the negative half adds nothing)."""
+    x = np.arange(0.0, tau_rho + step, step)
+    return float(np.max(np.abs(C.rexii_scalar(x, h, M) - np.exp(1j * x))))
+
+
+def pole_rounding_bound(form, tau_rho, h, M):
+    """delta_pole of the error model above, at the worse of x = 0 and x = tau_rho."""
+    u, kt, ks, _ = _FORM_ROUNDING[form]
+    mu, a = C.table_a()
+    ns, c1, c2 = C.c_coeffs_sliced(h, M, mu, a)
+    worst = 0.0
+    for x in (0.0, float(tau_rho)):
+        T = (c1 * h * mu + c2 * (x + h * ns)) / ((C.alpha(-ns, h, mu) - 1j * x) * (C.alpha(ns, h, mu) + 1j * x))
+        sT = math.sqrt(float(np.sum(np.abs(T) ** 2)))
+        sS = 2.0 * math.sqrt(len(T)) * float(np.max(np.abs(np.cumsum(T))))
+        worst = max(worst, _LAM * u * (kt * sT + ks * sS))
+    return worst
+
+
+def fft_rounding_bound(form, nx, ny):
+    """delta_fft of the error model above (relative to the rms amplitude)."""
+    u, _, _, kf = _FORM_ROUNDING[form]
+    return _LAM * kf * u * math.log2(nx * ny)

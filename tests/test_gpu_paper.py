@@ -13,7 +13,7 @@ from oracle import exact as E
 from oracle import rexi as R
 from oracle import spectral as S
 from paper_2008_11607_gb300 import inputs
-from tests.gpu_util import rel_l2, to_dev, torch_cuda
+from tests.gpu_util import pole_rounding_bound, rel_l2, to_dev, torch_cuda
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -64,14 +64,18 @@ def test_paper_scenarios_d128(form):
             refs[key] = E.exp_closed_form(st, tau, symbol_fn=S.symbol).real
         err = float(np.max(np.abs(out.cpu().numpy().real - refs[key])))
         bound_ok = (M - 11) * h >= tau * S.spectral_radius(46, 46) if scen == "ws2" else True
+        # rounding of the term sum (error model in tests/gpu_util.py), carried
+        # to the max norm: |e(x)| <= sum_k |delta r_k| |fhat(k)| / D^2, so the
+        # per-eigenvalue bound times the l1 norm of the input spectrum over D^2
+        a1 = float(np.sum(np.abs(np.fft.fft2(st, axes=(1, 2))))) / (D * D)
+        d_round = pole_rounding_bound(form, (M - 11) * h, h, M) * a1
         if printed > 0.1:
             assert err > 0.1, (scen, tau, h, M, err)        # below the accuracy bound: no approximation
         elif h == 1.0:
-            assert 1e-13 < err < 1e-11, (scen, tau, h, M, err)  # h = 1 error floor (Appendix B aliasing)
+            # h = 1 error floor (Appendix B aliasing, printed 6e-13 .. 4e-12)
+            assert 1e-13 < err < 1e-11 + d_round, (scen, tau, h, M, err)
         else:
-            # converged rows: the paper prints 6e-15 .. 7.7e-13.  FP64 form: within 3x of that
-            # scale.  Double-float form: ~44 bits per term, and the rounding of the 2N + 1
-            # terms accumulates (measured 6e-16 M at M = 2677, 1.7e-15 M at M = 56885), so
-            # max(1e-11, 4e-15 M), far inside its stated tolerance of 1e-8.
-            lim = max(1e-12, 3 * printed) if form == "fp64" else min(1e-8, max(1e-11, 4e-15 * M))
-            assert bound_ok and err < lim, (scen, tau, h, M, err)
+            # converged rows: the paper prints 6e-15 .. 9e-13; within 3x of that scale (at
+            # least 1e-12) plus the form's rounding bound for M terms
+            lim = max(1e-12, 3 * printed) + d_round
+            assert bound_ok and err < lim, (scen, tau, h, M, err, lim)

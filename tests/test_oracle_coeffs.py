@@ -170,3 +170,16 @@ def test_single_shift_poles_equal_term_form():
     pfr_m = np.sum(wr[None, :] / (-z - pr[None, :]), axis=1)
     # for a real matrix with eigenvalues +-ix the reduced sum gives Re over the pair
     assert np.max(np.abs(0.5 * (pfr + np.conj(pfr_m)) - C.rexii_scalar(x, h, M))) < 1e-12
+
+
+@pytest.mark.parametrize("h,M", [(0.5, 3), (0.5, 40), (1.0, 25), (0.1, 60), (0.3, 1)])
+def test_sliced_coefficients_equal_loop_form(h, M):
+    """c_coeffs_sliced adds the same terms in the same order as the explicit
+    loops of c_coeffs; only b_m is evaluated as an array, so the two agree to
+    a few ulps of the largest coefficient."""
+    ns, c1, c2 = C.c_coeffs(h, M)
+    ns2, d1, d2 = C.c_coeffs_sliced(h, M)
+    assert np.array_equal(ns, ns2)
+    scale = max(np.max(np.abs(c1)), np.max(np.abs(c2)))
+    assert np.max(np.abs(c1 - d1)) < 1e-14 * scale
+    assert np.max(np.abs(c2 - d2)) < 1e-14 * scale
