@@ -247,7 +247,9 @@ __global__ void __launch_bounds__(THREADS) cg_init(Geom<R> G, const VF* __restri
     S.beta = 0.0;
     S.a = 0.0;
     S.iters = 0;
-    S.status = (tot == 0.0) ? 1 : 0;  // zero right-hand side: x = 0 is exact
+    // zero right-hand side: x = 0 is exact; a non-finite one (NaN or Inf in
+    // the input) stops the term at once with status 3 (reported as ENOCONV)
+    S.status = !isfinite(tot) ? 3 : (tot == 0.0) ? 1 : 0;
   }
 }
 
@@ -378,7 +380,9 @@ __global__ void __launch_bounds__(THREADS) cg_update(Geom<R> G, const cplx<R>* t
     S.beta = S.gamma > 0.0 ? tot / S.gamma : 0.0;
     S.gamma = tot;
     S.iters += 1;
-    if (tot <= rtol * rtol * S.gamma0)
+    if (!isfinite(tot))
+      S.status = 3;  // a non-finite residual ends the term (reported as ENOCONV)
+    else if (tot <= rtol * rtol * S.gamma0)
       S.status = 1;
     else if (S.iters >= max_iters)
       S.status = 2;
@@ -432,7 +436,9 @@ __global__ void __launch_bounds__(THREADS) refine_residual(Geom<double> G, const
   if (last_block_total(s, partials + (size_t)term * ntiles, counters + term, ntiles, tile, &tot, red)) {
     S.gamma = tot;
     S.iters += 1;  // refinement steps
-    if (tot <= rtol * rtol * S.gamma0)
+    if (!isfinite(tot))
+      S.status = 3;
+    else if (tot <= rtol * rtol * S.gamma0)
       S.status = 1;
     else if (S.iters >= max_outer)
       S.status = 2;
@@ -726,7 +732,7 @@ struct KrylovRun {
   Geom<double> G{};
   Geom<float> G32{};
   std::vector<TermScalars> terms, hs, hs32;
-  int worst_iters = 0, unconverged = 0;
+  int worst_iters = 0, unconverged = 0, nonfinite = 0;
   int64_t term_iters = 0;
   double worst_res = 0.0;
   static constexpr int check_every = 16;
@@ -880,6 +886,7 @@ struct KrylovRun {
     for (int b = 0; b < nb; ++b) {
       worst_iters = std::max(worst_iters, mixed ? hs32[b].iters : hs[b].iters);
       if (hs[b].status != 1) ++unconverged;
+      if (hs[b].status == 3 || (mixed && hs32[b].status == 3)) ++nonfinite;
       if (hs[b].gamma0 > 0) worst_res = std::max(worst_res, sqrt(hs[b].gamma / hs[b].gamma0));
     }
     return cudaSuccess;
@@ -962,7 +969,8 @@ rexi_status krylov_step(KrylovSettings* k, int form, double h, int M, const void
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
   if (info) run.fill_info(info, M, real_input);
   if (run.unconverged > 0) {
-    set_last_error("variable-depth path: some terms reached the iteration cap");
+    set_last_error(run.nonfinite > 0 ? "variable-depth path: non-finite residual (NaN or Inf in the input?)"
+                                     : "variable-depth path: some terms reached the iteration cap");
     return REXI_ENOCONV;
   }
   return REXI_OK;

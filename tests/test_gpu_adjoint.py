@@ -122,18 +122,22 @@ def test_rollout_gradients_central_differences(method):
         assert abs(fd - an) <= 1e-6 * abs(an) + 1e-12, (fd, an)
 
 
-def test_rollout_against_oracle_adjoint():
+@pytest.mark.parametrize("n,steps,every", [(8, 4, 2), (32, 4, 2), (64, 2, 1)])
+def test_rollout_against_oracle_adjoint(n, steps, every):
+    """The checkpointed rollout's gradients against the oracle's adjoint
+    rollout (one sparse LU per pole for the forward states, the adjoint steps
+    and the depth gradients), at 8^2 and at the 32^2 - 64^2 sizes the oracle
+    handles in under a minute."""
     torch = torch_cuda()
     from paper_2008_11607_gb300.autograd import rexi_rollout
 
-    n, steps = 8, 4
     H, f0, target = _rollout_setup(torch, n, seed=3)
     plan, Hd = plan_for(torch, H)
     dt = 10.3 / plan.rho
     M = C.pole_count_M(10.3, 0.5, 1e-10)
     x = to_dev(torch, f0).requires_grad_(True)
     Hd.requires_grad_(True)
-    sT = rexi_rollout(x, plan, dt, steps, every=2, depth=Hd)
+    sT = rexi_rollout(x, plan, dt, steps, every=every, depth=Hd)
     loss = 0.5 * torch.sum((sT[0].real - torch.from_numpy(target).cuda()) ** 2)
     gx, gH = torch.autograd.grad(loss, [x, Hd])
     # oracle: forward states, then adjoint steps and depth gradients backwards
@@ -149,3 +153,55 @@ def test_rollout_against_oracle_adjoint():
         G = AD.rexii_adjoint_sparse(A, G, dt, 0.5, M)
     assert rel_l2(gx.cpu().numpy().ravel(), G) < 1e-9
     assert rel_l2(gH.cpu().numpy(), gH_ref) < 1e-9
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_config5_full_size_central_differences(form):
+    """The differentiation workload at its stated size: 512^2, depth
+    H = 1 + 0.4 sin(2 pi x) cos(4 pi y) + 8 bumps, |k|^-3 initial state,
+    8 REXII steps of tau rho = 200.3 (M = 410), checkpoints every 2 steps, loss
+    1/2 ||eta(T) - eta_target||^2 (|k|^-3 target, seed 1000), shared-Krylov
+    method with error bound 1e-12.  32 random state directions and 32 random
+    depth directions by central differences with step 1e-6, each within 1e-6
+    relative of the adjoint gradient."""
+    torch = torch_cuda()
+    from paper_2008_11607_gb300.autograd import rexi_rollout
+
+    n, steps, every = 512, 8, 2
+    H = inputs.variable_depth(n, n, seed=0)
+    f0 = inputs.kminus3_field(n, n, seed=0)
+    target = inputs.kminus3_field(n, n, seed=1000)[0].real
+    plan, Hd = plan_for(torch, H, form=form, rtol=1e-12, method="shared")
+    dt = 200.3 / plan.rho
+    tgt = torch.from_numpy(target).cuda()
+
+    def loss_of(plan_, x):
+        s = x
+        for _ in range(steps):
+            s = plan_.step(s, dt)
+        return 0.5 * float(torch.sum((s[0].real - tgt) ** 2))
+
+    x = to_dev(torch, f0).requires_grad_(True)
+    Hd.requires_grad_(True)
+    sT = rexi_rollout(x, plan, dt, steps, every=every, depth=Hd)
+    loss = 0.5 * torch.sum((sT[0].real - tgt) ** 2)
+    gx, gH = torch.autograd.grad(loss, [x, Hd])
+    rng = np.random.default_rng(512)
+    eps = 1e-6
+    base = to_dev(torch, f0)
+    worst = 0.0
+    for _ in range(32):
+        d = to_dev(torch, rng.standard_normal((3, n, n)))
+        fd = (loss_of(plan, base + eps * d) - loss_of(plan, base - eps * d)) / (2 * eps)
+        an = float(torch.sum(gx.real * d.real))
+        worst = max(worst, abs(fd - an) / abs(an))
+        assert abs(fd - an) <= 1e-6 * abs(an), ("state", fd, an)
+    for _ in range(32):
+        d = rng.standard_normal((n, n))
+        pp, _ = plan_for(torch, H + eps * d, form=form, rtol=1e-12, method="shared")
+        pm, _ = plan_for(torch, H - eps * d, form=form, rtol=1e-12, method="shared")
+        fd = (loss_of(pp, base) - loss_of(pm, base)) / (2 * eps)
+        an = float(torch.sum(gH * torch.from_numpy(d).cuda()))
+        worst = max(worst, abs(fd - an) / abs(an))
+        assert abs(fd - an) <= 1e-6 * abs(an), ("depth", fd, an)
+    print("config 5, %s: worst relative difference over 64 directions %.2e" % (form, worst))
