@@ -174,6 +174,62 @@ def c_coeffs_sliced(h, M, mu=None, a=None):
     return ns, h * c1, h * c2
 
 
+def beta_coeffs(h, M, mu=None, a=None):
+    """beta^{Re}_n, beta^{Im}_n for n = -N..N, Section 2.1 Step 3 (the
+    coefficients of the original REXI, eq. originalRexi):
+    beta^{Re}_n = h sum_{k=L1(n)}^{L2(n)} a_k Re(b_{n-k}),
+    beta^{Im}_n = h sum_{k=L1(n)}^{L2(n)} a_k Im(b_{n-k}),
+    L1(n) = max(-L, n - M), L2(n) = min(L, n + M).  Explicit loops.
+    Returns (n, beta_re, beta_im)."""
+    if mu is None or a is None:
+        mu, a = table_a()
+    N = M + L
+    ns = np.arange(-N, N + 1)
+    br = np.zeros(2 * N + 1, dtype=np.complex128)
+    bi = np.zeros(2 * N + 1, dtype=np.complex128)
+    for idx, n in enumerate(ns):
+        s1 = 0.0 + 0.0j
+        s2 = 0.0 + 0.0j
+        for k in range(max(-L, n - M), min(L, n + M) + 1):
+            bnk = complex(b_coeff(n - k, h))
+            s1 += a[L + k] * bnk.real
+            s2 += a[L + k] * bnk.imag
+        br[idx] = h * s1
+        bi[idx] = h * s2
+    return ns, br, bi
+
+
+def beta_coeffs_sliced(h, M, mu=None, a=None):
+    """``beta_coeffs`` accumulated for all n at once (k outer, in increasing
+    order, as ``c_coeffs_sliced``); pinned against the loop form."""
+    if mu is None or a is None:
+        mu, a = table_a()
+    N = M + L
+    ns = np.arange(-N, N + 1)
+    b = b_coeff(np.arange(-M, M + 1), h)
+    br = np.zeros(2 * N + 1, dtype=np.complex128)
+    bi = np.zeros(2 * N + 1, dtype=np.complex128)
+    for k in range(-L, L + 1):
+        lo = k + L
+        br[lo:lo + 2 * M + 1] += a[L + k] * b.real
+        bi[lo:lo + 2 * M + 1] += a[L + k] * b.imag
+    return ns, h * br, h * bi
+
+
+def rexi_original_scalar(x, h, M, mu=None, a=None):
+    """REXI(ix) = sum_{n=-N}^{N} Re(beta^{Re}_n / (ix + alpha_n))
+    + i Re(beta^{Im}_n / (ix + alpha_n)), eq. originalRexi (x real)."""
+    if mu is None or a is None:
+        mu, a = table_a()
+    x = np.asarray(x, dtype=np.float64)
+    ns, br, bi = beta_coeffs_sliced(h, M, mu, a)
+    acc = np.zeros(x.shape, dtype=np.complex128)
+    for idx, n in enumerate(ns):
+        den = 1j * x + alpha(n, h, mu)
+        acc += (br[idx] / den).real + 1j * (bi[idx] / den).real
+    return acc
+
+
 def alpha(n, h, mu):
     """alpha_n = h (mu + i n), Section 2.1 Step 3."""
     return h * (mu + 1j * np.asarray(n, dtype=np.float64))

@@ -155,3 +155,28 @@ def symbol_grid(nx, ny, Lx=1.0, Ly=1.0, g=1.0, f=1.0, H=1.0):
     B[2, 0] = -g * dyf
     B[2, 1] = -f * Pu
     return B
+
+
+def schrodinger_operator(nx, ny, Lx=1.0, Ly=1.0):
+    """A = i (d_xx + d_yy) by second-order centred differences with periodic
+    boundaries on an nx x ny grid (x fastest), as a complex scipy.sparse CSR
+    matrix of size nx ny.  With ny = 1 this is the paper's A_2 of Section 3.2
+    (the free Schroedinger operator; on [-1, 1] with step 1/35, nx = 70, its
+    eigenvalues lie in i[-4900, 0])."""
+    n = nx * ny
+    dx = Lx / nx
+    dy = Ly / ny
+    rows, cols, vals = [], [], []
+    for j in range(ny):
+        for i in range(nx):
+            r = j * nx + i
+            for di, dj, w in ((1, 0, 1.0 / dx ** 2), (-1, 0, 1.0 / dx ** 2), (0, 1, 1.0 / dy ** 2),
+                              (0, -1, 1.0 / dy ** 2), (0, 0, -2.0 / dx ** 2 - 2.0 / dy ** 2)):
+                if ny == 1 and dj != 0:
+                    continue
+                if ny == 1 and di == 0 and dj == 0:
+                    w = -2.0 / dx ** 2
+                rows.append(r)
+                cols.append(((j + dj) % ny) * nx + (i + di) % nx)
+                vals.append(1j * w)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, n), dtype=np.complex128)
