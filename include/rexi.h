@@ -122,6 +122,37 @@ rexi_status rexi_rexii_terms(int32_t M, double h, double* mu_out, int32_t* n_ter
 rexi_status rexi_coeffs(double tau_rho, double tol, double h, int32_t real_input, int32_t* M_out,
                         int32_t* n_poles, double* poles_re_im, double* weights_re_im, int32_t cap);
 
+/* The rational approximation of the Gaussian psi_1 (Section 2.1 Step 2),
+ * R(x) = Re sum_{l=-L}^{L} a_l / (ix + mu + il), L = 24, a_{-l} = conj(a_l).
+ * Coefficient arrays hold a_l for l = -L..L as interleaved (re, im) doubles
+ * (2 (2L + 1) = 98 values, a_l at index 2 (l + L)); host memory, caller-owned.
+ *
+ * rexi_gaussian_fit_table: Table tab:coef_al (Appendix A) and its mu.
+ *
+ * rexi_gaussian_refit: the least-squares fit of eq. minl2approx, written in
+ * the real form of eq. A(x,mu) (unknowns a_0, Re a_l, Im a_l), on K points
+ * chosen like Leja points: x_1 = 0, then each next point is the one of
+ * n_candidates equally spaced candidates in [0, xmax] that maximises the
+ * product of distances to the points chosen so far (R is even).  Solved by
+ * Householder QR of the column-scaled design matrix in FP64.  The paper leaves
+ * K, the interval and the choice of mu open; e.g. mu from the table, K = 200,
+ * xmax = 40, 20001 candidates reach max |psi_1 - R| ~ 5e-14 on [-60, 60]
+ * (the table: 8.1e-15).  max_err (nullable): max |psi_1 - R| on
+ * [-1.5 xmax, 1.5 xmax] at spacing 0.005.  EINVAL unless mu < 0,
+ * 2L + 1 <= K <= 100000, xmax > 0 and K <= n_candidates <= 1e7.
+ *
+ * rexi_plan_set_gaussian_fit: the plan's constant-depth steps use (mu, a)
+ * instead of the table in every REXII/REXI coefficient (a_re_im NULL restores
+ * the table).  EINVAL unless mu < 0, the values are finite and
+ * a_{-l} = conj(a_l) to 1e-14 of the largest |a|.  Frees the plan's cached
+ * coefficient tables (waiting for the device).  The variable-depth path
+ * keeps the table: its steps return REXI_EUNSUPPORTED while a custom fit is
+ * set. */
+rexi_status rexi_gaussian_fit_table(double* mu, double* a_re_im);
+rexi_status rexi_gaussian_refit(double mu, int32_t K, double xmax, int32_t n_candidates, double* a_re_im,
+                                double* max_err);
+rexi_status rexi_plan_set_gaussian_fit(rexi_plan_t plan, double mu, const double* a_re_im);
+
 /* ------------------------------------------------------------------------ */
 /* Plans.                                                                   */
 /* ------------------------------------------------------------------------ */
@@ -155,8 +186,49 @@ rexi_status rexi_spectral_radius(rexi_plan_t plan, double* rho_out);
  *   +n/2, no Coriolis averaging), the discretisation behind eq. lswRoh
  *   (rho = sqrt(2 pi^2 D^2 + 1) for D x D on the unit square, H = g = f = 1).
  * Recomputes rho.  Variable-depth plans accept only the C grid. */
-enum { REXI_SYMBOL_CGRID = 0, REXI_SYMBOL_SPECTRAL = 1 };
+/* REXI_SYMBOL_SCHRODINGER: the scalar operator A = i (d_xx + d_yy) by
+ *   second-order centred differences (periodic), applied to each of the three
+ *   fields independently (so a single wavefunction goes in field 0 with the
+ *   others zero).  Its eigenvalues are i lambda(k) with
+ *   lambda = -(4/dx^2) sin^2(pi kx/nx) - (4/dy^2) sin^2(pi ky/ny) in
+ *   [-(4/dx^2 + 4/dy^2), 0]; with ny = 2 and data constant in y it is the
+ *   one-dimensional free Schroedinger operator A_2 of Section 3.2.  Needs
+ *   complex input (real_input = 0) and the FP64 or mixed form; rho is the
+ *   largest |lambda - sigma| (sigma: rexi_plan_set_shift). */
+enum { REXI_SYMBOL_CGRID = 0, REXI_SYMBOL_SPECTRAL = 1, REXI_SYMBOL_SCHRODINGER = 2 };
 rexi_status rexi_plan_set_symbol(rexi_plan_t plan, int32_t symbol);
+
+/* Rational approximation used by the constant-depth path (Section 2):
+ * REXI_COEF_REXII (default): eq. modifiedRexi / REXI_Modified_matrix.
+ * REXI_COEF_REXI: the original REXI in its matrix form for real operators,
+ *   eq. originalREXImatrix, sum_n Re(beta^Re_n (tau A + alpha_n I)^{-1}) f,
+ *   with beta^Re of Section 2.1 Step 3 (shallow-water symbols only; for a real
+ *   operator and real data it is the rational function
+ *   sum_n gamma_n (tau A + alpha_n I)^{-1}, gamma_n = (beta^Re_n + conj(beta^Re_{-n}))/2,
+ *   which is what is applied to complex data too).  It is not the scalar REXI
+ *   applied to the eigenvalues, so Theorem 1 and the pole-count rule do not
+ *   hold for it: M is the rule's value for the plan's rho, or choose rho
+ *   (rexi_plan_set_rho) to reach the M wanted.
+ * REXI_COEF_REXIE: REXI Extended, eq. REXIE, for operators i B with B real
+ *   (the scalar symbol only).  Per eigenvalue it is the scalar eq. originalRexi,
+ *   which equals eq. modifiedRexi for real arguments (beta^Re = Re c1 + i Re c2,
+ *   beta^Im = Im c1 + i Im c2), so the Fourier path evaluates it with the same
+ *   term table as REXII.
+ * The variable-depth path and the plain form accept REXI_COEF_REXII only
+ * (REXI_EUNSUPPORTED at the step otherwise). */
+enum { REXI_COEF_REXII = 0, REXI_COEF_REXI = 1, REXI_COEF_REXIE = 2 };
+rexi_status rexi_plan_set_coefficients(rexi_plan_t plan, int32_t set);
+
+/* Spectral shift of the remark in Section 2.2: e^{tau A} = e^{tau nu} e^{tau (A - nu I)}
+ * with nu = i sigma, so that the pole count follows rho(A - nu I).
+ * REXI_SHIFT_NONE (default): sigma = 0; REXI_SHIFT_MIDPOINT: sigma = the midpoint
+ * of the operator's eigenvalue range (zeta_1 + zeta_2)/2; REXI_SHIFT_VALUE: the
+ * given sigma.  A non-zero sigma needs the scalar symbol (the shallow-water
+ * spectra are symmetric about 0, where the midpoint is 0): REXI_EUNSUPPORTED
+ * otherwise.  Recomputes rho; rexi_plan_get_shift returns the sigma in effect. */
+enum { REXI_SHIFT_NONE = 0, REXI_SHIFT_MIDPOINT = 1, REXI_SHIFT_VALUE = 2 };
+rexi_status rexi_plan_set_shift(rexi_plan_t plan, int32_t mode, double sigma);
+rexi_status rexi_plan_get_shift(rexi_plan_t plan, double* sigma);
 
 /* Override the spectral radius used by the pole-count rule (rho > 0), or
  * restore the plan's own value (rho = 0).  The paper's wave scenarios take
@@ -380,6 +452,20 @@ rexi_status rexi_batch_autotune(rexi_batch_t batch, const void* in_dev, void* ou
  * kernels launched so far. */
 rexi_status rexi_batch_info(rexi_batch_t batch, int32_t* threads, int32_t* orbits_per_thread, int32_t* ctas,
                             int32_t* n_items, int64_t* terms_orbits, int64_t* launches);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement utility.                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Fused multiply-add throughput probe (no counterpart in the paper; it
+ * measures the ALU rates that bound the pole-sum kernels).  kind 0: FP32,
+ * kind 1: FP64.  Launches `blocks` blocks of 256 threads; every thread does
+ * 128 * iters multiply-adds in 8 independent chains (2 flops each, so
+ * 256 * blocks * 128 * iters * 2 flops per call).  out_dev: device memory for
+ * blocks * 256 values of the kind's type, written only in an impossible
+ * sentinel case.  Asynchronous on `stream`; the caller times it.  EINVAL on
+ * a bad kind, blocks or iters < 1, or NULL out_dev. */
+rexi_status rexi_alu_probe(int32_t kind, int32_t blocks, int32_t iters, void* out_dev, void* stream);
 
 /* Human-readable name of a status code (static string). */
 const char* rexi_status_string(rexi_status status);

@@ -21,19 +21,20 @@ import scipy.sparse.linalg as spla
 from . import coeffs
 
 
-def rexii_apply_sparse(A, f0, tau, h, M, real_input=True, terms=None):
+def rexii_apply_sparse(A, f0, tau, h, M, real_input=True, terms=None, mu=None, a=None):
     """r(tau A) f0 with one sparse LU pair per term.
 
     ``A`` scipy.sparse (real), ``f0`` 1-D vector.  ``terms`` optionally
     restricts the sum to a subset of term indices n (for pole-partition
-    tests).  Returns a complex vector (real part taken when real_input).
+    tests).  ``mu``, ``a``: another fit of Step 2 than Table tab:coef_al.
+    Returns a complex vector (real part taken when real_input).
     """
     f0 = np.asarray(f0)
     n_unk = A.shape[0]
     Id = sp.identity(n_unk, dtype=np.complex128, format="csc")
     Ac = sp.csc_matrix(A, dtype=np.complex128)
     acc = np.zeros(n_unk, dtype=np.complex128)
-    for n, an, amn, C1, C2, gam in coeffs.matrix_term_weights(h, M, real_input):
+    for n, an, amn, C1, C2, gam in coeffs.matrix_term_weights(h, M, real_input, mu, a):
         if terms is not None and n not in terms:
             continue
         lu1 = spla.splu((an * Id + tau * Ac).tocsc())

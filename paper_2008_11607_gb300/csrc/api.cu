@@ -49,7 +49,14 @@ struct rexi_plan_s {
   int form = REXI_FORM_FP64;
   double rho = 0.0;
   double rho_natural = 0.0;  // rho of the discretisation (rho may be overridden)
-  int spectral = 0;
+  int spectral = 0;  // symbol: 0 C grid, 1 spectral LRSW, 2 scalar i (d_xx + d_yy)
+  int coef_set = REXI_COEF_REXII;
+  GaussFit fit = table_fit();  // rational fit of the Gaussian (Table tab:coef_al unless replaced)
+  bool fit_custom = false;
+  int fit_gen = 0;             // bumped when the fit changes (coefficient-table cache key)
+  int shift_mode = REXI_SHIFT_NONE;
+  double shift_value = 0.0;  // sigma requested with REXI_SHIFT_VALUE
+  double sigma = 0.0;        // sigma in effect (scalar operator only)
   double Hmax = 0.0, Hmean = 0.0;
   // Fourier path tables (device)
   FftPlan1D fx, fy;
@@ -71,7 +78,8 @@ struct rexi_plan_s {
   // device coefficient tables of the FP64 and mixed Fourier forms, one per
   // (form, M, term range, split grid); immutable once uploaded
   struct CoefTable {
-    int M = 0, tb = 0, te = 0, nterms = 0;
+    int M = 0, tb = 0, te = 0, nterms = 0, coef_set = 0, fit_gen = 0;
+    int exact_hn = 1;  // mixed form: every h n of the table on the split grid G
     double G = 0.0, R0re = 0.0, R0im = 0.0;
     void* dev = nullptr;
     cudaEvent_t ready = nullptr;
@@ -506,6 +514,7 @@ SymbolParams symbol_params(const rexi_plan_s* p) {
   sp.half_x = p->half_x;
   sp.half_y = p->half_y;
   sp.spectral = p->spectral;
+  sp.shift = p->sigma;
   return sp;
 }
 
@@ -524,7 +533,7 @@ constexpr size_t kCoefTables = 8;
 rexi_status fused_table(rexi_plan_s* p, int M, int tb, int te, double G, cudaStream_t s,
                         const rexi_plan_s::CoefTable** out) {
   for (auto& c : p->coef) {
-    if (c.M == M && c.tb == tb && c.te == te && c.G == G) {
+    if (c.M == M && c.tb == tb && c.te == te && c.G == G && c.coef_set == p->coef_set && c.fit_gen == p->fit_gen) {
       c.last_use = ++p->coef_clock;
       // an upload still in flight (on another stream): order this stream after
       // it; a finished one needs no wait (and none is recorded, so a step can be
@@ -538,7 +547,7 @@ rexi_status fused_table(rexi_plan_s* p, int M, int tb, int te, double G, cudaStr
     }
   }
   TermSet ts;
-  rexii_terms(M, p->h, &ts);
+  rexii_terms_fit(M, p->h, p->fit, &ts);
   const int N = ts.N;
   const double h = p->h, hmu = h * ts.mu, q = hmu * hmu;
   // scalar terms n = -N..N restricted to |n| in [tb, te)
@@ -550,12 +559,42 @@ rexi_status fused_table(rexi_plan_s* p, int M, int tb, int te, double G, cudaStr
   c.tb = tb;
   c.te = te;
   c.G = G;
+  c.coef_set = p->coef_set;
+  c.fit_gen = p->fit_gen;
   c.nterms = (int)sel.size();
+  // Every scalar term is (A_n + B_n y) / ((h mu)^2 + y^2), y = x + h n.
+  // REXII (eq. modifiedRexi): A = c1 h mu, B = c2.
+  // REXIE (eq. REXIE) on a scalar operator i B with B real: per eigenvalue it
+  //   is eq. originalRexi, Re(beta^Re / (ix + alpha_n)) + i Re(beta^Im / (ix + alpha_n)),
+  //   whose A = h mu (Re beta^Re + i Re beta^Im), B = Im beta^Re + i Im beta^Im;
+  //   with beta^Re = Re c1 + i Re c2 and beta^Im = Im c1 + i Im c2 (both are
+  //   h sum a_k b_{n-k} split by parts) these are again c1 h mu and c2.
+  // Original REXI, eq. originalREXImatrix, for a real operator and real data:
+  //   Re(beta (tau A + alpha_n)^{-1}) = (beta (tau A + alpha_n)^{-1}
+  //   + conj(beta) (tau A + alpha_{-n})^{-1}) / 2, so the scalar function is
+  //   sum_n gamma_n / (z + alpha_n), gamma_n = (beta^Re_n + conj(beta^Re_{-n})) / 2,
+  //   i.e. A = gamma h mu, B = -i gamma at z = ix.
+  std::vector<double> Are(2 * N + 1), Aim(2 * N + 1), Bre(2 * N + 1), Bim(2 * N + 1);
+  for (int n = -N; n <= N; ++n) {
+    const int i = n + N, j = -n + N;
+    if (p->coef_set == REXI_COEF_REXI) {
+      const double gr = 0.5 * (ts.c1re[i] + ts.c1re[j]), gi = 0.5 * (ts.c2re[i] - ts.c2re[j]);
+      Are[i] = gr * hmu;
+      Aim[i] = gi * hmu;
+      Bre[i] = gi;
+      Bim[i] = -gr;
+    } else {
+      Are[i] = ts.c1re[i] * hmu;
+      Aim[i] = ts.c1im[i] * hmu;
+      Bre[i] = ts.c2re[i];
+      Bim[i] = ts.c2im[i];
+    }
+  }
   for (int n : sel) {
     const int i = n + N;
     const double hn = h * n, d = q + hn * hn;
-    c.R0re += (ts.c1re[i] * hmu + ts.c2re[i] * hn) / d;
-    c.R0im += (ts.c1im[i] * hmu + ts.c2im[i] * hn) / d;
+    c.R0re += (Are[i] + Bre[i] * hn) / d;
+    c.R0im += (Aim[i] + Bim[i] * hn) / d;
   }
   // 48 bytes per term in both forms
   std::vector<double> tab(6 * std::max<size_t>(sel.size(), 1), 0.0);
@@ -564,10 +603,10 @@ rexi_status fused_table(rexi_plan_s* p, int M, int tb, int te, double G, cudaStr
       const int n = sel[t], i = n + N;
       double* e = &tab[6 * t];
       e[0] = h * n;
-      e[1] = ts.c1re[i] * hmu;
-      e[2] = ts.c1im[i] * hmu;
-      e[3] = ts.c2re[i];
-      e[4] = ts.c2im[i];
+      e[1] = Are[i];
+      e[2] = Aim[i];
+      e[3] = Bre[i];
+      e[4] = Bim[i];
       e[5] = 0.0;
     }
   } else {  // double-float: see pole_orbit_mixed_kernel
@@ -582,13 +621,14 @@ rexi_status fused_table(rexi_plan_s* p, int M, int tb, int te, double G, cudaStr
       const double hn = h * n;
       const double hn_g = rint(hn / G) * G;
       float Arh, Arl, Aih, Ail, Brh, Brl, Bih, Bil;
-      split(ts.c1re[i] * hmu, Arh, Arl);
-      split(ts.c1im[i] * hmu, Aih, Ail);
-      split(ts.c2re[i], Brh, Brl);
-      split(ts.c2im[i], Bih, Bil);
+      split(Are[i], Arh, Arl);
+      split(Aim[i], Aih, Ail);
+      split(Bre[i], Brh, Brl);
+      split(Bim[i], Bih, Bil);
       e[0] = (float)hn_g; e[1] = Arh; e[2] = Aih; e[3] = Brh;
       e[4] = Bih; e[5] = Arl; e[6] = Ail; e[7] = Brl;
-      e[8] = Bil; e[9] = (float)(hn - hn_g); e[10] = 0.f; e[11] = 0.f;
+      e[8] = Bil; e[9] = (float)(hn - hn_g); e[10] = (float)((hn - hn_g) - (double)e[9]); e[11] = 0.f;
+      if (hn != hn_g) c.exact_hn = 0;
     }
   }
   if (p->coef.size() >= kCoefTables) {
@@ -630,7 +670,18 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
   const int N = L.N;
   if (te < 0 || te > N + 1) te = N + 1;
   if (tb < 0 || tb > te) return fail(REXI_EINVAL, "bad term range [%d, %d)", tb, te);
-  const double h = p->h, hmu = h * table_mu(), q = hmu * hmu;
+  if (p->spectral == 2) {
+    if (real_input) return fail(REXI_EINVAL, "the scalar operator i(d_xx + d_yy) needs complex input (real_input = 0)");
+    if (p->form == REXI_FORM_PLAIN) return fail(REXI_EUNSUPPORTED, "plain form: shallow-water symbols only");
+    if (p->coef_set == REXI_COEF_REXI)
+      return fail(REXI_EUNSUPPORTED, "original REXI (eq. originalREXImatrix) needs a real operator");
+  } else {
+    if (p->coef_set == REXI_COEF_REXIE)
+      return fail(REXI_EUNSUPPORTED, "REXIE (eq. REXIE) needs an operator i B with B real (the scalar symbol)");
+    if (p->coef_set != REXI_COEF_REXII && p->form == REXI_FORM_PLAIN)
+      return fail(REXI_EUNSUPPORTED, "plain form: REXII coefficients only");
+  }
+  const double h = p->h, hmu = h * p->fit.mu, q = hmu * hmu;
   const double tau = dt;
   const SymbolParams sp = symbol_params(p);
   const size_t nk = (size_t)p->nx * p->ny;
@@ -661,8 +712,11 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
   if (p->form == REXI_FORM_FP64 || p->form == REXI_FORM_MIXED) {
     double G = 0.0;
     if (p->form == REXI_FORM_MIXED) {
-      // grid G = 2^-g so that |x| + h N < 2^24 G: x <= tau rho
-      const double span = dt * p->rho + h * N + 4.0;
+      // grid G = 2^-g so that |x| + h N < 2^24 G for every x the pole kernel
+      // evaluates: all wavenumbers of the grid, so x <= tau max(rho, rho of the
+      // discretisation) (an override of rho below the grid's own can only
+      // shrink the pole count, not the range of x)
+      const double span = dt * std::max(p->rho, p->rho_natural) + h * N + 4.0;
       if (span > 4.0e6) return fail(REXI_EINVAL, "mixed form needs dt*rho + h*N < 4e6 (got %g)", span);
       int gexp = 0;
       while (ldexp(1.0, 23 - gexp) > span && gexp < 60) ++gexp;  // largest g with span < 2^(23-g)
@@ -677,6 +731,7 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
     fs.R0im = ct->R0im;
     fs.nterms = ct->nterms;
     fs.adjoint = adjoint ? 1 : 0;
+    fs.exact_hn = ct->exact_hn;
     // With the real part of the step taken (real input), r(0) enters through
     // its real part: Re r(tau B) = Re(R0) I + Im(R+) Bt + (Re R0 - Re R+) Bt^2
     // on the C-grid, where B(-k) = conj B(k).
@@ -693,7 +748,18 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
       CUDA_TRY(pole_orbits_mixed(part, slices, sp, op, static_cast<const float*>(ct->dev), fs, G, s),
                "pole_orbits_mixed");
     prof_mark(p, 5, s);
-    if (df_spec)
+    if (p->spectral == 2) {
+      // e^{tau A} = e^{i tau sigma} e^{tau (A - i sigma I)}
+      const double2 phase = make_double2(cos(tau * p->sigma), sin(tau * p->sigma));
+      CUDA_TRY(pole_orbit_combine_scalar(spec, part, slices, sp, op, phase, adjoint ? 1 : 0, s),
+               "pole_orbit_combine_scalar");
+    } else if (p->form == REXI_FORM_MIXED && !half && !p->spectral) {
+      // complex input (or real input without the half-length transform): the
+      // combine in double-float arithmetic on the FP64 spectrum
+      CUDA_TRY(pole_orbit_combine_dfc(spec, part, slices, base + L.fin_off, sp, p->halfdf_x, p->halfdf_y, op, fs,
+                                      s),
+               "pole_orbit_combine_dfc");
+    } else if (df_spec)
       CUDA_TRY(pole_orbit_combine_df(spec, part, slices, base + L.fin_off, sp, p->halfdf_x, p->halfdf_y, op, fs,
                                      row_len, s),
                "pole_orbit_combine_df");
@@ -704,7 +770,7 @@ rexi_status fourier_step(rexi_plan_s* p, const void* in, void* out, double dt, i
   } else {
     // plain form: terms n = 0..N (real) or -N..N (complex), |n| in [tb, te)
     TermSet ts;
-    rexii_terms(M, p->h, &ts);
+    rexii_terms_fit(M, p->h, p->fit, &ts);
     std::vector<double2> tab;
     for (int n = real_input ? 0 : -N; n <= N; ++n) {
       if (!term_selected(n, tb, te)) continue;
@@ -804,6 +870,8 @@ rexi_status rexi_step(rexi_plan_t p, const void* in, void* out, double dt, doubl
   rexi_status st = check_step_args(p, in, out, dt, tol, ws, &M);
   if (st != REXI_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->depth && (p->coef_set != REXI_COEF_REXII || p->fit_custom))
+    return fail(REXI_EUNSUPPORTED, "the variable-depth path uses REXII with Table tab:coef_al only");
   if (p->depth) {
     KrylovHooks hooks;
     hooks.mark = [](void* ctx, int i, cudaStream_t st) { prof_mark(static_cast<rexi_plan_s*>(ctx), i, st); };
@@ -826,6 +894,8 @@ rexi_status rexi_step_adjoint(rexi_plan_t p, const void* gout, void* gin, double
   rexi_status st = check_step_args(p, gout, gin, dt, tol, ws, &M);
   if (st != REXI_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->depth && (p->coef_set != REXI_COEF_REXII || p->fit_custom))
+    return fail(REXI_EUNSUPPORTED, "the variable-depth path uses REXII with Table tab:coef_al only");
   if (p->depth)
     return krylov_step(&p->kry, p->form, p->h, M, gout, gin, dt, real_input, 0, -1, ws, ws_bytes, s, nullptr,
                        true, KrylovHooks());
@@ -942,16 +1012,22 @@ extern "C" rexi_status rexi_step_grad_depth(rexi_plan_t p, const void* in, const
   return st;
 }
 
-extern "C" rexi_status rexi_plan_set_symbol(rexi_plan_t p, int32_t symbol) {
-  g_err[0] = 0;
-  if (!p || (symbol != REXI_SYMBOL_CGRID && symbol != REXI_SYMBOL_SPECTRAL)) return fail(REXI_EINVAL, "bad symbol");
-  if (p->depth && symbol != REXI_SYMBOL_CGRID) return fail(REXI_EUNSUPPORTED, "spectral symbol needs constant depth");
-  p->spectral = symbol == REXI_SYMBOL_SPECTRAL;
-  if (p->depth) return REXI_OK;
-  // rho: the largest omega over the discrete wavenumbers of the chosen symbol
-  double best = 0.0;
+namespace {
+// rho of the constant-depth symbol in use: the largest |eigenvalue| over the
+// discrete wavenumbers (for the scalar operator, of the shifted operator
+// A - i sigma I, sigma from the plan's shift mode); resets any override.
+void update_rho(rexi_plan_s* p) {
+  double best = 0.0, lmin = 0.0, lmax = -1e300;
+  const double dx = p->Lx / p->nx, dy = p->Ly / p->ny;
   for (int ky = 0; ky < p->ny; ++ky) {
     for (int kx = 0; kx < p->nx; ++kx) {
+      if (p->spectral == 2) {
+        const double sx = sin(M_PI * kx / p->nx), sy = sin(M_PI * ky / p->ny);
+        const double lam = -(4.0 * sx * sx / (dx * dx) + 4.0 * sy * sy / (dy * dy));
+        lmin = std::min(lmin, lam);
+        lmax = std::max(lmax, lam);
+        continue;
+      }
       double w2;
       if (p->spectral) {
         const int sx = 2 * kx <= p->nx ? kx : kx - p->nx, sy = 2 * ky <= p->ny ? ky : ky - p->ny;
@@ -960,13 +1036,127 @@ extern "C" rexi_status rexi_plan_set_symbol(rexi_plan_t p, int32_t symbol) {
       } else {
         const double sx = sin(M_PI * kx / p->nx), cx = cos(M_PI * kx / p->nx);
         const double sy = sin(M_PI * ky / p->ny), cy = cos(M_PI * ky / p->ny);
-        const double dx = p->Lx / p->nx, dy = p->Ly / p->ny;
         w2 = p->g * p->H * (4 * sx * sx / (dx * dx) + 4 * sy * sy / (dy * dy)) + p->f * p->f * cx * cx * cy * cy;
       }
       best = std::max(best, w2);
     }
   }
-  p->rho = p->rho_natural = sqrt(best);
+  if (p->spectral == 2) {
+    p->sigma = p->shift_mode == REXI_SHIFT_MIDPOINT ? 0.5 * (lmin + lmax)
+               : p->shift_mode == REXI_SHIFT_VALUE  ? p->shift_value
+                                                    : 0.0;
+    p->rho = p->rho_natural = std::max(fabs(lmin - p->sigma), fabs(lmax - p->sigma));
+  } else {
+    p->sigma = 0.0;
+    p->rho = p->rho_natural = sqrt(best);
+  }
+}
+}  // namespace
+
+extern "C" rexi_status rexi_plan_set_symbol(rexi_plan_t p, int32_t symbol) {
+  g_err[0] = 0;
+  if (!p || (symbol != REXI_SYMBOL_CGRID && symbol != REXI_SYMBOL_SPECTRAL && symbol != REXI_SYMBOL_SCHRODINGER))
+    return fail(REXI_EINVAL, "bad symbol");
+  if (p->depth && symbol != REXI_SYMBOL_CGRID) return fail(REXI_EUNSUPPORTED, "this symbol needs constant depth");
+  p->spectral = symbol;
+  if (p->depth) return REXI_OK;
+  update_rho(p);
+  return REXI_OK;
+}
+
+extern "C" rexi_status rexi_plan_set_shift(rexi_plan_t p, int32_t mode, double sigma) {
+  g_err[0] = 0;
+  if (!p || mode < REXI_SHIFT_NONE || mode > REXI_SHIFT_VALUE || !isfinite(sigma))
+    return fail(REXI_EINVAL, "bad shift mode or value");
+  if (mode == REXI_SHIFT_VALUE && sigma != 0.0 && p->spectral != 2)
+    return fail(REXI_EUNSUPPORTED,
+                "a non-zero shift needs the scalar operator (the shallow-water spectrum is symmetric about 0)");
+  p->shift_mode = mode;
+  p->shift_value = sigma;
+  if (!p->depth) update_rho(p);
+  return REXI_OK;
+}
+
+extern "C" rexi_status rexi_plan_set_coefficients(rexi_plan_t p, int32_t set) {
+  g_err[0] = 0;
+  if (!p || set < REXI_COEF_REXII || set > REXI_COEF_REXIE) return fail(REXI_EINVAL, "bad coefficient set");
+  p->coef_set = set;
+  return REXI_OK;
+}
+
+namespace {
+void fit_to_array(const GaussFit& f, double* a) {
+  for (int l = -kL; l <= kL; ++l) {
+    const int k = l < 0 ? -l : l;
+    a[2 * (l + kL)] = f.are[k];
+    a[2 * (l + kL) + 1] = l < 0 ? -f.aim[k] : f.aim[k];
+  }
+}
+}  // namespace
+
+extern "C" rexi_status rexi_gaussian_fit_table(double* mu, double* a_re_im) {
+  g_err[0] = 0;
+  if (!mu || !a_re_im) return fail(REXI_EINVAL, "NULL argument");
+  const GaussFit f = table_fit();
+  *mu = f.mu;
+  fit_to_array(f, a_re_im);
+  return REXI_OK;
+}
+
+extern "C" rexi_status rexi_gaussian_refit(double mu, int32_t K, double xmax, int32_t n_candidates,
+                                           double* a_re_im, double* max_err) {
+  g_err[0] = 0;
+  if (!a_re_im) return fail(REXI_EINVAL, "NULL coefficient array");
+  GaussFit f;
+  if (!gauss_refit(mu, K, xmax, n_candidates, &f, max_err))
+    return fail(REXI_EINVAL, "refit needs mu < 0, 2L+1 <= K <= 100000, xmax > 0, K <= n_candidates <= 1e7");
+  fit_to_array(f, a_re_im);
+  return REXI_OK;
+}
+
+extern "C" rexi_status rexi_plan_set_gaussian_fit(rexi_plan_t p, double mu, const double* a_re_im) {
+  g_err[0] = 0;
+  if (!p) return fail(REXI_EINVAL, "plan NULL");
+  GaussFit f = table_fit();
+  bool custom = false;
+  if (a_re_im) {
+    if (!(mu < 0.0) || !isfinite(mu)) return fail(REXI_EINVAL, "mu must be finite and < 0");
+    double amax = 0.0;
+    for (int i = 0; i < 2 * (2 * kL + 1); ++i) {
+      if (!isfinite(a_re_im[i])) return fail(REXI_EINVAL, "non-finite coefficient");
+      amax = std::max(amax, fabs(a_re_im[i]));
+    }
+    // a_{-l} = conj(a_l) (the symmetric form of eq. A(x,mu)); a_0 real
+    for (int l = 0; l <= kL; ++l) {
+      const double* pl = a_re_im + 2 * (kL + l);
+      const double* ml = a_re_im + 2 * (kL - l);
+      if (fabs(pl[0] - ml[0]) > 1e-14 * amax || fabs(pl[1] + ml[1]) > 1e-14 * amax)
+        return fail(REXI_EINVAL, "coefficients must satisfy a_{-l} = conj(a_l)");
+      f.are[l] = pl[0];
+      f.aim[l] = l == 0 ? 0.0 : pl[1];
+    }
+    f.mu = mu;
+    custom = true;
+  }
+  // tables built from the old fit may still be read by queued work
+  if (!p->coef.empty()) {
+    CUDA_TRY(cudaDeviceSynchronize(), "fit change");
+    for (auto& c : p->coef) {
+      cudaFree(c.dev);
+      cudaEventDestroy(c.ready);
+    }
+    p->coef.clear();
+  }
+  p->fit = f;
+  p->fit_custom = custom;
+  ++p->fit_gen;
+  return REXI_OK;
+}
+
+extern "C" rexi_status rexi_plan_get_shift(rexi_plan_t p, double* sigma) {
+  g_err[0] = 0;
+  if (!p || !sigma) return fail(REXI_EINVAL, "NULL argument");
+  *sigma = p->sigma;
   return REXI_OK;
 }
 

@@ -40,6 +40,7 @@ struct InstDesc {
   const float4* halfdf_y;
   double inv_dx, inv_dy, tau, q, R0re, R0im, grid;
   float q_hi, q_lo;
+  int exact_hn;  // mixed table: every h n on the split grid
   long long table_off;  // first table entry (3 x 16 bytes per term)
   const double2* half_x;
   const double2* half_y;
@@ -162,12 +163,18 @@ __global__ void batch_pole_kernel(OrbitScalars* orb, const InstDesc* __restrict_
         for (int t = 0; t < cnt; ++t)
 #pragma unroll
           for (int u = 0; u < PPT; ++u) fp64_term(sd + 3 * t, x[u], D.q, ar[u], ai[u]);
+      } else if (D.exact_hn) {
+#pragma unroll 2
+        for (int t = 0; t < cnt; ++t)
+#pragma unroll
+          for (int u = 0; u < PPT; ++u)
+            df_term<true>(st + 3 * t, Xh[u], Xl[u], Xl2[u], D.q_hi, D.q_lo, arh[u], arl[u], aih[u], ail[u]);
       } else {
 #pragma unroll 2
         for (int t = 0; t < cnt; ++t)
 #pragma unroll
           for (int u = 0; u < PPT; ++u)
-            df_term(st + 3 * t, Xh[u], Xl[u], Xl2[u], D.q_hi, D.q_lo, arh[u], arl[u], aih[u], ail[u]);
+            df_term<false>(st + 3 * t, Xh[u], Xl[u], Xl2[u], D.q_hi, D.q_lo, arh[u], arl[u], aih[u], ail[u]);
       }
     }
 #pragma unroll
@@ -531,6 +538,7 @@ rexi_status rexi_batch_create(rexi_batch_t* out, int32_t n, const int32_t* nx, c
     int gexp = 0;
     while (ldexp(1.0, 23 - gexp) > span && gexp < 60) ++gexp;
     D.grid = ldexp(1.0, -(gexp - 1));
+    D.exact_hn = 1;
     double R0r = 0, R0i = 0;
     for (int nn = -N; nn <= N; ++nn) {
       const int k = nn + N;
@@ -553,7 +561,10 @@ rexi_status rexi_batch_create(rexi_batch_t* out, int32_t n, const int32_t* nx, c
         split(Ai, Aih, Ail);
         split(Br, Brh, Brl);
         split(Bi, Bih, Bil);
-        const float v[12] = {(float)hg, Arh, Aih, Brh, Bih, Arl, Ail, Brl, Bil, (float)(hn - hg), 0.f, 0.f};
+        const float hl = (float)(hn - hg);
+        const float v[12] = {(float)hg, Arh, Aih, Brh, Bih, Arl, Ail, Brl, Bil, hl, (float)((hn - hg) - (double)hl),
+                             0.f};
+        if (hn != hg) D.exact_hn = 0;
         memcpy(e, v, sizeof(v));
       }
       tab.insert(tab.end(), e, e + 12);

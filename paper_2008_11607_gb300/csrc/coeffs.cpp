@@ -29,6 +29,16 @@ static const double kAIm[kL + 1] = {
 
 double table_mu() { return kMu; }
 
+GaussFit table_fit() {
+  GaussFit g;
+  g.mu = kMu;
+  for (int l = 0; l <= kL; ++l) {
+    g.are[l] = kARe[l];
+    g.aim[l] = kAIm[l];
+  }
+  return g;
+}
+
 void table_a(double re[kL + 1], double im[kL + 1]) {
   for (int l = 0; l <= kL; ++l) {
     re[l] = kARe[l];
@@ -52,10 +62,11 @@ int pole_count(double tau_rho, double h, double tol) {
 }
 
 // c1_n = h sum_{k=L1(n)}^{L2(n)} Re(a_k) b_{n-k}, c2_n = h sum Im(a_k) b_{n-k},
-// b_m = e^{-i m h} e^{h^2}, L1 = max(-L, n-M), L2 = min(L, n+M), n = -N..N.
+// b_m = e^{-i m h} e^{h^2}, L1 = max(-L, n-M), L2 = min(L, n+M), n = -N..N,
+// for the fit (mu, a_l) of Step 2 (a_{-l} = conj(a_l)).
 // bre/bim: 2M + 1 values of scratch (b_m at m + M); c*: 2N + 1 values each.
-void rexii_terms_into(int M, double h, double* bre, double* bim, double* c1re, double* c1im, double* c2re,
-                      double* c2im) {
+void rexii_terms_into_fit(int M, double h, const GaussFit& fit, double* bre, double* bim, double* c1re,
+                          double* c1im, double* c2re, double* c2im) {
   const int N = M + kL;
   const double eh2 = exp(h * h);
   for (int m = -M; m <= M; ++m) {
@@ -69,8 +80,8 @@ void rexii_terms_into(int M, double h, double* bre, double* bim, double* c1re, d
     double s1r = 0.0, s1i = 0.0, s2r = 0.0, s2i = 0.0;
     for (int k = k0; k <= k1; ++k) {
       const int kk = k < 0 ? -k : k;
-      const double are = kARe[kk];
-      const double aim = k < 0 ? -kAIm[kk] : kAIm[kk];  // a_{-k} = conj(a_k)
+      const double are = fit.are[kk];
+      const double aim = k < 0 ? -fit.aim[kk] : fit.aim[kk];  // a_{-k} = conj(a_k)
       const double br = bre[n - k + M], bi = bim[n - k + M];
       s1r += are * br;
       s1i += are * bi;
@@ -84,20 +95,28 @@ void rexii_terms_into(int M, double h, double* bre, double* bim, double* c1re, d
   }
 }
 
-void rexii_terms(int M, double h, TermSet* ts) {
+void rexii_terms_into(int M, double h, double* bre, double* bim, double* c1re, double* c1im, double* c2re,
+                      double* c2im) {
+  static const GaussFit tab = table_fit();
+  rexii_terms_into_fit(M, h, tab, bre, bim, c1re, c1im, c2re, c2im);
+}
+
+void rexii_terms_fit(int M, double h, const GaussFit& fit, TermSet* ts) {
   const int N = M + kL;
   ts->M = M;
   ts->N = N;
   ts->h = h;
-  ts->mu = kMu;
+  ts->mu = fit.mu;
   const int nt = 2 * N + 1;
   ts->c1re.assign(nt, 0.0);
   ts->c1im.assign(nt, 0.0);
   ts->c2re.assign(nt, 0.0);
   ts->c2im.assign(nt, 0.0);
   std::vector<double> bre(2 * M + 1), bim(2 * M + 1);
-  rexii_terms_into(M, h, bre.data(), bim.data(), ts->c1re.data(), ts->c1im.data(), ts->c2re.data(),
-                   ts->c2im.data());
+  rexii_terms_into_fit(M, h, fit, bre.data(), bim.data(), ts->c1re.data(), ts->c1im.data(), ts->c2re.data(),
+                       ts->c2im.data());
 }
+
+void rexii_terms(int M, double h, TermSet* ts) { rexii_terms_fit(M, h, table_fit(), ts); }
 
 }  // namespace rexi

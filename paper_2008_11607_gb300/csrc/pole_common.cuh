@@ -21,6 +21,17 @@ struct Symbol {
 };
 
 __device__ __forceinline__ Symbol symbol_at(const SymbolParams& sp, int kx, int ky) {
+  if (sp.spectral == 2) {
+    // scalar operator i (d_xx + d_yy) (second-order centred differences):
+    // eigenvalue i lambda(k), lambda = -(4/dx^2) sin^2(pi kx/nx) - (4/dy^2) sin^2(pi ky/ny);
+    // omega carries the signed lambda - sigma of the shifted operator A - i sigma I
+    const double sx = sp.half_x[kx].y, sy = sp.half_y[ky].y;
+    const double ax = 2.0 * sx * sp.inv_dx, ay = 2.0 * sy * sp.inv_dy;
+    Symbol S;
+    S.dxf = S.dxb = S.dyf = S.dyb = S.P = make_double2(0.0, 0.0);
+    S.omega = -(ax * ax + ay * ay) - sp.shift;
+    return S;
+  }
   if (sp.spectral) {
     // spectral derivative i k' with the signed wavenumber (Nyquist taken as +n/2),
     // k' = 2 pi k_signed / L = 2 pi k_signed (1/dx) / n; no averaging (P = 1)
@@ -204,6 +215,63 @@ struct SymbolDF {
 __device__ __forceinline__ float4 c_of(float2 re, float2 im) { return make_float4(re.x, re.y, im.x, im.y); }
 __device__ __forceinline__ float2 f_neg(float2 a) { return make_float2(-a.x, -a.y); }
 
+// The six non-zero entries of the C-grid symbol at (kx, ky) in double-float
+// (B^H for the adjoint): e[0..5] = B01, B02, B10, B12, B20, B21.
+__device__ __forceinline__ void symbol_df(const SymbolDF& sd, int kx, int ky, bool adjoint, float4 e[6]) {
+  const float4 hx = sd.half_x[kx], hy = sd.half_y[ky];
+  const float2 cx = make_float2(hx.x, hx.y), sx = make_float2(hx.z, hx.w);
+  const float2 cy = make_float2(hy.x, hy.y), sy = make_float2(hy.z, hy.w);
+  const float2 ax = f_mulf(make_float2(2.f * sx.x, 2.f * sx.y), sd.inv_dx);
+  const float2 ay = f_mulf(make_float2(2.f * sy.x, 2.f * sy.y), sd.inv_dy);
+  const float2 Hax = f_neg(f_mulf(sd.H, ax)), Hay = f_neg(f_mulf(sd.H, ay));
+  const float2 gax = f_mulf(sd.g, ax), gay = f_mulf(sd.g, ay);
+  e[0] = c_of(f_mulf(Hax, sx), f_mulf(Hax, cx));        // -H dxb
+  e[1] = c_of(f_mulf(Hay, sy), f_mulf(Hay, cy));        // -H dyb
+  e[2] = c_of(f_mulf(gax, sx), f_neg(f_mulf(gax, cx)));  // -g dxf
+  e[4] = c_of(f_mulf(gay, sy), f_neg(f_mulf(gay, cy)));  // -g dyf
+  const float2 cxcy = f_mulf(cx, cy);
+  const float2 fcc = f_mulf(sd.f, cxcy);
+  const float2 pr = f_mulf(fcc, f_addf(cxcy, f_mulf(sx, sy)));
+  const float2 pim = f_mulf(fcc, f_subf(f_mulf(sx, cy), f_mulf(cx, sy)));
+  e[3] = c_of(pr, pim);          // f P
+  e[5] = c_of(f_neg(pr), pim);   // -f conj(P)
+  if (adjoint) {  // (B^H)_ij = conj(B_ji)
+    const float4 t01 = e[0], t02 = e[1], t10 = e[2], t12 = e[3], t20 = e[4], t21 = e[5];
+    e[0] = cconj(t10);
+    e[1] = cconj(t20);
+    e[2] = cconj(t01);
+    e[3] = cconj(t21);
+    e[4] = cconj(t02);
+    e[5] = cconj(t12);
+  }
+}
+
+// Complex input on an FP64 spectrum: values become double-float pairs on load
+// and FP64 again on store; out = c0 f + s1 B f + s2 B^2 f with c0 and s2
+// complex (r(0) enters whole), s1 real.
+__device__ __forceinline__ void combine_dfc_at(double2* spec, size_t k, size_t nk, int kx, int ky, const SymbolDF& sd,
+                                               float4 c0, float2 s1, float4 s2, bool adjoint) {
+  float4 e[6];
+  symbol_df(sd, kx, ky, adjoint, e);
+  float4 f[3], y1[3], y2[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double2 v = spec[k + c * nk];
+    f[c] = c_of(df_from_double(v.x), df_from_double(v.y));
+  }
+  y1[0] = cadd(cmul(e[0], f[1]), cmul(e[1], f[2]));
+  y1[1] = cadd(cmul(e[2], f[0]), cmul(e[3], f[2]));
+  y1[2] = cadd(cmul(e[4], f[0]), cmul(e[5], f[1]));
+  y2[0] = cadd(cmul(e[0], y1[1]), cmul(e[1], y1[2]));
+  y2[1] = cadd(cmul(e[2], y1[0]), cmul(e[3], y1[2]));
+  y2[2] = cadd(cmul(e[4], y1[0]), cmul(e[5], y1[1]));
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float4 o = cadd(cadd(cmul(c0, f[c]), crmul(s1, y1[c])), cmul(s2, y2[c]));
+    spec[k + c * nk] = make_double2(df_to_double(make_float2(o.x, o.y)), df_to_double(make_float2(o.z, o.w)));
+  }
+}
+
 // In place at index k of the three fields (field stride nk), wavenumber (kx, ky).
 __device__ __forceinline__ void combine_df_at(float4* spec, size_t k, size_t nk, int kx, int ky, const SymbolDF& sd,
                                               float2 c0, float2 s1, float2 s2, bool adjoint) {
@@ -342,15 +410,29 @@ __device__ __forceinline__ void fp64_term(const double2* e, double x, double q, 
 // One scalar REXII term in double-float arithmetic (see pole_fft.cu).
 // x is split as X_hi (a multiple of the table's grid G) + X_lo + X_lo2 (FP32).
 // acc += (A + B y) / (q + y^2) with every quantity an FP32 (hi, lo) pair.
-// Table entry (3 float4): [hn_hi, Ar_hi, Ai_hi, Br_hi], [Bi_hi, Ar_lo, Ai_lo, Br_lo], [Bi_lo, hn_lo, 0, 0].
+// Table entry (3 float4): [hn_hi, Ar_hi, Ai_hi, Br_hi], [Bi_hi, Ar_lo, Ai_lo, Br_lo], [Bi_lo, hn_lo, hn_lo2, 0]
+// (h n = hn_hi + hn_lo + hn_lo2, hn_hi on the grid G).
+// EXACT_HN: every h n of the table lies on the grid G (hn_lo = 0, e.g. h = 0.5
+// or 1), so only X_lo sits below the grid; otherwise hn_lo (up to G/2) joins
+// X_lo by an error-free TwoSum first, which keeps (y_h, y_l) a normalised pair
+// (a low word of order G would make the dropped y_l^2 and the FP32 rounding
+// of the low words visible at the 1e-7 level).
+template <bool EXACT_HN>
 __device__ __forceinline__ void df_term(const float4* ent, float X_hi, float X_lo, float X_lo2, float q_hi,
                                         float q_lo, float& ar_h, float& ar_l, float& ai_h, float& ai_l) {
   const float4 e0 = ent[0], e1 = ent[1], e2 = ent[2];
   // y = x + h n with x = X_hi + X_lo + X_lo2: the grid-aligned high parts add
   // exactly, X_lo joins by an error-free FastTwoSum, the rest is far below it
   float y_h, y_l;
-  fast_two_sum(__fadd_rn(X_hi, e0.x), X_lo, y_h, y_l);
-  y_l = __fadd_rn(y_l, __fadd_rn(X_lo2, e2.y));
+  if (EXACT_HN) {
+    fast_two_sum(__fadd_rn(X_hi, e0.x), X_lo, y_h, y_l);
+    y_l = __fadd_rn(y_l, __fadd_rn(X_lo2, e2.y));
+  } else {
+    float s_h, s_e;
+    two_sum(X_lo, e2.y, s_h, s_e);  // |s_h| <= G <= |X_hi + hn_hi| unless that is 0
+    fast_two_sum(__fadd_rn(X_hi, e0.x), s_h, y_h, y_l);
+    y_l = __fadd_rn(y_l, __fadd_rn(__fadd_rn(X_lo2, s_e), e2.z));  // e2.z: what hn_lo leaves of h n
+  }
   // d = q + y^2
   const float p_h = __fmul_rn(y_h, y_h);
   const float p_l = __fmaf_rn(y_h, y_h, -p_h);

@@ -18,12 +18,12 @@
 // Forms:
 //  * pole_orbit_fp64 / pole_fused_fp64 -- FP64 registers; 1/d by the
 //    rcp.approx seed plus a Newton-Raphson step with its next term in FP64.
-//  * pole_orbit_mixed / pole_fused_mixed -- the same sum in double-float
+//  * pole_orbit_mixed -- the same sum in double-float
 //    arithmetic (pairs of FP32 values with Dekker/Knuth error-free
 //    transformations: TwoSum, TwoProduct by FMA), FP64 only for the
 //    per-orbit setup.  FP32 runs ~58x faster than FP64 on this GPU.
-//    (The pole_fused_* kernels are the earlier one-pair-per-thread form with
-//    the combine fused, kept for the allocation-free step.)
+//    (pole_fused_fp64 is the earlier one-pair-per-thread form with the
+//    combine fused, kept for the allocation-free step.)
 //  * pole_orbit_combine (FP64) / pole_orbit_combine_df (double-float, real
 //    input, half spectrum) -- r(tau B) at every wavenumber from per-orbit
 //    scalars.
@@ -78,57 +78,6 @@ cudaError_t pole_fused_fp64(double2* spec, const SymbolParams& sp, const double*
   const int np = pairs_count(sp.nx, sp.ny);
   const int tpb = 128;
   pole_fused_fp64_kernel<<<(np + tpb - 1) / tpb, tpb, 0, s>>>(spec, sp, table, fs, np);
-  return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// Double-float fused pole loop (helpers in pole_common.cuh).
-
-// Table (per scalar term, 12 floats):
-//  [hn_hi, Ar_hi, Ai_hi, Br_hi], [Bi_hi, Ar_lo, Ai_lo, Br_lo], [Bi_lo, hn_lo, 0, 0]
-// hn_hi is h n rounded to the grid G = fs-supplied power of two, so that
-// X_hi + hn_hi is exact in FP32 (both multiples of G, magnitude < 2^24 G).
-__global__ void __launch_bounds__(128) pole_fused_mixed_kernel(double2* spec, SymbolParams sp,
-                                                               const float4* __restrict__ table,
-                                                               FusedScalars fs, double grid,
-                                                               float q_hi, float q_lo, int npairs) {
-  __shared__ float4 st[kChunk * 3];
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  int kx = 0, ky = 0, kx2 = 0, ky2 = 0;
-  const bool active = p < npairs && pair_of(p, sp.nx, sp.ny, kx, ky, kx2, ky2);
-  Symbol S = symbol_at(sp, active ? kx : 0, active ? ky : 0);
-  const double x = fs.tau * S.omega;
-  const double xg = rint(x / grid) * grid;
-  const float X_hi = (float)xg;
-  const float X_lo = (float)(x - xg);
-  const float X_lo2 = (float)((x - xg) - (double)X_lo);
-  float ar_h = 0.f, ar_l = 0.f, ai_h = 0.f, ai_l = 0.f;
-  for (int t0 = 0; t0 < fs.nterms; t0 += kChunk) {
-    const int cnt = min(kChunk, fs.nterms - t0);
-    __syncthreads();
-    for (int i = threadIdx.x; i < cnt * 3; i += blockDim.x) st[i] = table[(size_t)t0 * 3 + i];
-    __syncthreads();
-#pragma unroll 2
-    for (int t = 0; t < cnt; ++t) df_term(st + 3 * t, X_hi, X_lo, X_lo2, q_hi, q_lo, ar_h, ar_l, ai_h, ai_l);
-  }
-  if (!active) return;
-  const double2 R0 = make_double2(fs.R0re, fs.R0im);
-  const double2 Rp = make_double2((double)ar_h + (double)ar_l, (double)ai_h + (double)ai_l);
-  const size_t fstride = (size_t)sp.nx * sp.ny;
-  const bool adj = fs.adjoint != 0;
-  combine(spec, (size_t)ky * sp.nx + kx, fstride, S, sp, false, adj, R0, Rp);
-  if (kx2 != kx || ky2 != ky)
-    combine(spec, (size_t)ky2 * sp.nx + kx2, fstride, symbol_at(sp, kx2, ky2), sp, false, adj, R0, Rp);
-}
-
-cudaError_t pole_fused_mixed(double2* spec, const SymbolParams& sp, const float* table,
-                             const FusedScalars& fs, double grid, cudaStream_t s) {
-  const int np = pairs_count(sp.nx, sp.ny);
-  const int tpb = 128;
-  const float q_hi = (float)fs.q;
-  const float q_lo = (float)(fs.q - (double)q_hi);
-  pole_fused_mixed_kernel<<<(np + tpb - 1) / tpb, tpb, 0, s>>>(
-      spec, sp, reinterpret_cast<const float4*>(table), fs, grid, q_hi, q_lo, np);
   return cudaGetLastError();
 }
 
@@ -192,7 +141,7 @@ __global__ void __launch_bounds__(kOrbitThreads) pole_orbit_fp64_kernel(double2*
 }
 
 // PPT orbits per thread share each staged term's shared-memory loads.
-template <int PPT>
+template <int PPT, bool EXACT_HN>
 __global__ void __launch_bounds__(kOrbitThreads) pole_orbit_mixed_kernel(double2* __restrict__ part, SymbolParams sp,
                                                                          OrbitParams op,
                                                                          const float4* __restrict__ table,
@@ -224,7 +173,7 @@ __global__ void __launch_bounds__(kOrbitThreads) pole_orbit_mixed_kernel(double2
     for (int t = 0; t < cnt; ++t)
 #pragma unroll
       for (int u = 0; u < PPT; ++u)
-        df_term(st + 3 * t, X_hi[u], X_lo[u], X_lo2[u], q_hi, q_lo, ar_h[u], ar_l[u], ai_h[u], ai_l[u]);
+        df_term<EXACT_HN>(st + 3 * t, X_hi[u], X_lo[u], X_lo2[u], q_hi, q_lo, ar_h[u], ar_l[u], ai_h[u], ai_l[u]);
   }
 #pragma unroll
   for (int u = 0; u < PPT; ++u)
@@ -306,7 +255,7 @@ OrbitOccupancy orbit_occupancy() {
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b64, pole_orbit_fp64_kernel, kOrbitThreads, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bmx, pole_orbit_mixed_kernel<kOrbitPPT>, kOrbitThreads, 0) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bmx, pole_orbit_mixed_kernel<kOrbitPPT, true>, kOrbitThreads, 0) !=
             cudaSuccess) {
       cudaGetLastError();
       return OrbitOccupancy{152, 8, 8};
@@ -353,8 +302,12 @@ cudaError_t pole_orbits_mixed(double2* part, int slices, const SymbolParams& sp,
   const float q_lo = (float)(fs.q - (double)q_hi);
   const int per_block = kOrbitThreads * kOrbitPPT;
   dim3 grid((unsigned)((op.norb + per_block - 1) / per_block), (unsigned)slices);
-  pole_orbit_mixed_kernel<kOrbitPPT><<<grid, kOrbitThreads, 0, s>>>(
-      part, sp, op, reinterpret_cast<const float4*>(table), fs, grid_step, q_hi, q_lo, slices);
+  if (fs.exact_hn)
+    pole_orbit_mixed_kernel<kOrbitPPT, true><<<grid, kOrbitThreads, 0, s>>>(
+        part, sp, op, reinterpret_cast<const float4*>(table), fs, grid_step, q_hi, q_lo, slices);
+  else
+    pole_orbit_mixed_kernel<kOrbitPPT, false><<<grid, kOrbitThreads, 0, s>>>(
+        part, sp, op, reinterpret_cast<const float4*>(table), fs, grid_step, q_hi, q_lo, slices);
   return cudaGetLastError();
 }
 
@@ -367,6 +320,78 @@ cudaError_t pole_orbit_combine(double2* spec, const double2* part, int slices, v
   if (e != cudaSuccess) return e;
   const size_t nk = (size_t)row_len * sp.ny;
   pole_orbit_combine_kernel<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(spec, F, sp, op, R0, fs.adjoint, row_len);
+  return cudaGetLastError();
+}
+
+// Complex input, mixed form: the FP64 per-orbit scalars applied in
+// double-float arithmetic on the FP64 full spectrum (see combine_dfc_at).
+__global__ void __launch_bounds__(256) pole_orbit_combine_dfc_kernel(double2* spec,
+                                                                     const OrbitScalars* __restrict__ fin,
+                                                                     SymbolDF sd, int nx, int ny, OrbitParams op,
+                                                                     float4 c0, int adjoint) {
+  const size_t nk = (size_t)nx * ny;
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nk) return;
+  const int ky = (int)(k / nx), kx = (int)(k - (size_t)ky * nx);
+  const OrbitScalars o = fin[orbit_of(op, nx, ny, kx, ky)];
+  float4 s2 = c_of(df_from_double(o.s2re), df_from_double(o.s2im));
+  if (adjoint) s2 = cconj(s2);
+  combine_dfc_at(spec, k, nk, kx, ky, sd, c0, df_from_double(o.s1), s2, adjoint != 0);
+}
+
+cudaError_t pole_orbit_combine_dfc(double2* spec, const double2* part, int slices, void* fin, const SymbolParams& sp,
+                                   const float4* half_x_df, const float4* half_y_df, const OrbitParams& op,
+                                   const FusedScalars& fs, cudaStream_t s) {
+  if (sp.spectral) return cudaErrorInvalidValue;  // the C grid only
+  const double2 R0 = make_double2(fs.R0re, fs.R0im);
+  OrbitScalars* F = static_cast<OrbitScalars*>(fin);
+  pole_orbit_finalize_kernel<false><<<(unsigned)((op.norb + 255) / 256), 256, 0, s>>>(part, slices, sp, op, R0, F);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  SymbolDF sd;
+  sd.g = df_split_host(sp.g);
+  sd.H = df_split_host(sp.H);
+  sd.f = df_split_host(sp.f);
+  sd.inv_dx = df_split_host(sp.inv_dx);
+  sd.inv_dy = df_split_host(sp.inv_dy);
+  sd.half_x = half_x_df;
+  sd.half_y = half_y_df;
+  const float2 c0r = df_split_host(fs.R0re), c0i = df_split_host(fs.adjoint ? -fs.R0im : fs.R0im);
+  const float4 c0 = make_float4(c0r.x, c0r.y, c0i.x, c0i.y);
+  const size_t nk = (size_t)sp.nx * sp.ny;
+  pole_orbit_combine_dfc_kernel<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(spec, F, sd, sp.nx, sp.ny, op, c0,
+                                                                             fs.adjoint);
+  return cudaGetLastError();
+}
+
+// Scalar operator: every field at wavenumber k is multiplied by phase R(k).
+__global__ void __launch_bounds__(256) pole_orbit_combine_scalar_kernel(double2* spec,
+                                                                        const double2* __restrict__ part,
+                                                                        int slices, int nx, int ny, OrbitParams op,
+                                                                        double2 phase, int adjoint) {
+  const size_t nk = (size_t)nx * ny;
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nk) return;
+  const int ky = (int)(k / nx), kx = (int)(k - (size_t)ky * nx);
+  const int o = orbit_of(op, nx, ny, kx, ky);
+  double2 R = part[o];
+  for (int sl = 1; sl < slices; ++sl) {
+    const double2 v = part[(size_t)sl * op.norb + o];
+    R.x += v.x;
+    R.y += v.y;
+  }
+  double2 m = cm(phase, R);
+  if (adjoint) m = cj(m);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) spec[k + c * nk] = cm(m, spec[k + c * nk]);
+}
+
+cudaError_t pole_orbit_combine_scalar(double2* spec, const double2* part, int slices, const SymbolParams& sp,
+                                      const OrbitParams& op, double2 phase, int adjoint, cudaStream_t s) {
+  if (sp.spectral != 2) return cudaErrorInvalidValue;
+  const size_t nk = (size_t)sp.nx * sp.ny;
+  pole_orbit_combine_scalar_kernel<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(spec, part, slices, sp.nx, sp.ny,
+                                                                                op, phase, adjoint);
   return cudaGetLastError();
 }
 

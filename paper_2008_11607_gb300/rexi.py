@@ -24,6 +24,17 @@ REXI_BATCH_PER_INSTANCE = 1
 
 REXI_SYMBOL_CGRID = 0
 REXI_SYMBOL_SPECTRAL = 1
+REXI_SYMBOL_SCHRODINGER = 2
+SYMBOLS = {"cgrid": REXI_SYMBOL_CGRID, "spectral": REXI_SYMBOL_SPECTRAL, "schrodinger": REXI_SYMBOL_SCHRODINGER}
+
+REXI_COEF_REXII = 0
+REXI_COEF_REXI = 1
+REXI_COEF_REXIE = 2
+COEFFICIENT_SETS = {"rexii": REXI_COEF_REXII, "rexi": REXI_COEF_REXI, "rexie": REXI_COEF_REXIE}
+
+REXI_SHIFT_NONE = 0
+REXI_SHIFT_MIDPOINT = 1
+REXI_SHIFT_VALUE = 2
 
 REXI_FORM_FP64 = 0
 REXI_FORM_MIXED = 1
@@ -68,6 +79,12 @@ SIGNATURES = {
     "rexi_plan_set_krylov_method": (_c_int, [_vp, _c_int]),
     "rexi_plan_set_symbol": (_c_int, [_vp, _c_int]),
     "rexi_plan_set_rho": (_c_int, [_vp, _c_dbl]),
+    "rexi_plan_set_coefficients": (_c_int, [_vp, _c_int]),
+    "rexi_gaussian_fit_table": (_c_int, [_dp, _dp]),
+    "rexi_gaussian_refit": (_c_int, [_c_dbl, _c_int, _c_dbl, _c_int, _dp, _dp]),
+    "rexi_plan_set_gaussian_fit": (_c_int, [_vp, _c_dbl, _dp]),
+    "rexi_plan_set_shift": (_c_int, [_vp, _c_int, _c_dbl]),
+    "rexi_plan_get_shift": (_c_int, [_vp, _dp]),
     "rexi_workspace_size": (_c_int, [_vp, _c_dbl, _c_dbl, _c_int, ctypes.POINTER(ctypes.c_size_t)]),
     "rexi_workspace_size_grad_depth": (_c_int, [_vp, _c_dbl, _c_dbl, _c_int, ctypes.POINTER(ctypes.c_size_t)]),
     "rexi_step": (_c_int, [_vp, _vp, _vp, _c_dbl, _c_dbl, _c_int, _c_int, _c_int, _vp, ctypes.c_size_t, _vp,
@@ -91,6 +108,7 @@ SIGNATURES = {
     "rexi_batch_autotune": (_c_int, [_vp, _vp, _vp, _c_int, _vp, ctypes.c_size_t, _vp, _ip, _ip, _dp]),
     "rexi_batch_info": (_c_int, [_vp, _ip, _ip, _ip, _ip, ctypes.POINTER(ctypes.c_int64),
                                  ctypes.POINTER(ctypes.c_int64)]),
+    "rexi_alu_probe": (_c_int, [_c_int, _c_int, _c_int, _vp, _vp]),
     "rexi_status_string": (ctypes.c_char_p, [_c_int]),
     "rexi_version": (ctypes.c_char_p, []),
     "rexi_last_error_message": (ctypes.c_char_p, []),
@@ -167,6 +185,31 @@ def rexi_coeffs(tau_rho, tol=1e-10, h=0.5, real_input=True):
     return M.value, p[0::2] + 1j * p[1::2], w[0::2] + 1j * w[1::2]
 
 
+def gaussian_fit_table():
+    """(mu, a) of Table tab:coef_al, a[l + 24] = a_l for l = -24..24 (complex)."""
+    import numpy as np
+
+    mu = ctypes.c_double()
+    arr = (ctypes.c_double * 98)()
+    _check(load().rexi_gaussian_fit_table(ctypes.byref(mu), arr), "rexi_gaussian_fit_table")
+    v = np.frombuffer(arr, dtype=np.float64).copy()
+    return mu.value, v[0::2] + 1j * v[1::2]
+
+
+def gaussian_refit(mu=None, K=200, xmax=40.0, n_candidates=20001):
+    """Least-squares refit on Leja points (host FP64, in the library): returns (mu, a, max_err)."""
+    import numpy as np
+
+    if mu is None:
+        mu = gaussian_fit_table()[0]
+    arr = (ctypes.c_double * 98)()
+    err = ctypes.c_double()
+    _check(load().rexi_gaussian_refit(float(mu), int(K), float(xmax), int(n_candidates), arr, ctypes.byref(err)),
+           "rexi_gaussian_refit")
+    v = np.frombuffer(arr, dtype=np.float64).copy()
+    return mu, v[0::2] + 1j * v[1::2], err.value
+
+
 def term_partition(n_terms, world, rank):
     """Contiguous slice [begin, end) of the REXII term indices |n| = 0..n_terms-1
     for `rank` of `world` devices, balanced by count.  Each device passes it to
@@ -190,6 +233,14 @@ def _stream_handle(stream):
 
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def alu_probe(kind, blocks, iters, out, stream=None):
+    """Enqueue the multiply-add throughput probe (kind "fp32" or "fp64"); returns
+    the flops it performs (blocks * 256 threads * 128 * iters * 2)."""
+    k = {"fp32": 0, "fp64": 1}[kind]
+    _check(load().rexi_alu_probe(k, int(blocks), int(iters), _ptr(out), _stream_handle(stream)), "rexi_alu_probe")
+    return blocks * 256 * 128 * iters * 2
 
 
 class Plan:
@@ -227,9 +278,36 @@ class Plan:
         return r.value
 
     def set_symbol(self, symbol):
-        """"cgrid" or "spectral" (constant-depth plans)."""
-        code = {"cgrid": REXI_SYMBOL_CGRID, "spectral": REXI_SYMBOL_SPECTRAL}.get(symbol, symbol)
+        """"cgrid", "spectral" or "schrodinger" (constant-depth plans)."""
+        code = SYMBOLS.get(symbol, symbol)
         _check(self._lib.rexi_plan_set_symbol(self._h, int(code)), "rexi_plan_set_symbol")
+
+    def set_coefficients(self, name):
+        """"rexii" (default), "rexi" (original, eq. originalREXImatrix) or "rexie" (eq. REXIE)."""
+        _check(self._lib.rexi_plan_set_coefficients(self._h, int(COEFFICIENT_SETS.get(name, name))),
+               "rexi_plan_set_coefficients")
+
+    def set_gaussian_fit(self, mu=None, a=None):
+        """Use (mu, a) (a: 49 complex values a_-24..a_24) instead of the table; no arguments restore it."""
+        if a is None:
+            _check(self._lib.rexi_plan_set_gaussian_fit(self._h, 0.0, None), "rexi_plan_set_gaussian_fit")
+            return
+        import numpy as np
+
+        a = np.asarray(a, dtype=np.complex128)
+        arr = (ctypes.c_double * 98)(*np.column_stack([a.real, a.imag]).ravel().tolist())
+        _check(self._lib.rexi_plan_set_gaussian_fit(self._h, float(mu), arr), "rexi_plan_set_gaussian_fit")
+
+    def set_shift(self, mode="none", sigma=0.0):
+        """Spectral shift nu = i sigma: mode "none", "midpoint" or "value" (with sigma)."""
+        code = {"none": REXI_SHIFT_NONE, "midpoint": REXI_SHIFT_MIDPOINT, "value": REXI_SHIFT_VALUE}.get(mode, mode)
+        _check(self._lib.rexi_plan_set_shift(self._h, int(code), float(sigma)), "rexi_plan_set_shift")
+
+    @property
+    def shift(self):
+        v = ctypes.c_double()
+        _check(self._lib.rexi_plan_get_shift(self._h, ctypes.byref(v)), "rexi_plan_get_shift")
+        return v.value
 
     def set_rho(self, rho):
         """Override rho for the pole count (0 restores the plan's own value)."""

@@ -161,9 +161,12 @@ def test_config5_full_size_central_differences(form):
     H = 1 + 0.4 sin(2 pi x) cos(4 pi y) + 8 bumps, |k|^-3 initial state,
     8 REXII steps of tau rho = 200.3 (M = 410), checkpoints every 2 steps, loss
     1/2 ||eta(T) - eta_target||^2 (|k|^-3 target, seed 1000), shared-Krylov
-    method with error bound 1e-12.  32 random state directions and 32 random
+    method with error bound 1e-13.  32 random state directions and 32 random
     depth directions by central differences with step 1e-6, each within 1e-6
-    relative of the adjoint gradient."""
+    relative of the adjoint gradient.  The loss of a perturbed problem is only
+    as smooth as the Krylov stopping rule (its step count can change between
+    the + and - evaluations), which adds about rtol |L| / (2 eps) to a
+    difference quotient: the bound 1e-13 keeps that below 1e-7 of it."""
     torch = torch_cuda()
     from paper_2008_11607_gb300.autograd import rexi_rollout
 
@@ -171,7 +174,7 @@ def test_config5_full_size_central_differences(form):
     H = inputs.variable_depth(n, n, seed=0)
     f0 = inputs.kminus3_field(n, n, seed=0)
     target = inputs.kminus3_field(n, n, seed=1000)[0].real
-    plan, Hd = plan_for(torch, H, form=form, rtol=1e-12, method="shared")
+    plan, Hd = plan_for(torch, H, form=form, rtol=1e-13, method="shared")
     dt = 200.3 / plan.rho
     tgt = torch.from_numpy(target).cuda()
 
@@ -198,8 +201,8 @@ def test_config5_full_size_central_differences(form):
         assert abs(fd - an) <= 1e-6 * abs(an), ("state", fd, an)
     for _ in range(32):
         d = rng.standard_normal((n, n))
-        pp, _ = plan_for(torch, H + eps * d, form=form, rtol=1e-12, method="shared")
-        pm, _ = plan_for(torch, H - eps * d, form=form, rtol=1e-12, method="shared")
+        pp, _ = plan_for(torch, H + eps * d, form=form, rtol=1e-13, method="shared")
+        pm, _ = plan_for(torch, H - eps * d, form=form, rtol=1e-13, method="shared")
         fd = (loss_of(pp, base) - loss_of(pm, base)) / (2 * eps)
         an = float(torch.sum(gH * torch.from_numpy(d).cuda()))
         worst = max(worst, abs(fd - an) / abs(an))

@@ -13,8 +13,8 @@ spectrum's decay.
 Tolerances follow the error model in tests/gpu_util.py: the approximation
 error eps_r of the scalar REXII on [0, tau rho] (Theorem 1 with cond = 1: B(k)
 is skew-Hermitian for H = g), plus the form's rounding bound for the term sum
-(relative to |fhat(k)|) and for the transforms (relative to the rms
-amplitude).  The sampled per-mode check against the oracle's REXII solve chain
+(relative to |fhat(k)|) and for the transforms (relative to the largest
+wavenumber amplitude).  The sampled per-mode check against the oracle's REXII solve chain
 stays in tests/test_gpu_fourier.py.
 """
 import math
@@ -63,12 +63,13 @@ def test_config2_every_wavenumber_kminus3(form, eps_r):
     # whole field, relative l2 (Parseval: the same in physical and Fourier space)
     rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     assert rel < eps_r + d_pole + d_fft, (rel, eps_r, d_pole, d_fft)
+    print("2048^2 |k|^-3, %s: relative l2 %.2e (bound %.2e)" % (form, rel, eps_r + d_pole + d_fft))
     # every wavenumber
     amp = np.sqrt(np.sum(np.abs(fin) ** 2, axis=0))
-    rms = math.sqrt(float(np.mean(amp ** 2)))
     err = np.sqrt(np.sum(np.abs(got - ref) ** 2, axis=0))
-    lim = (eps_r + d_pole) * amp + d_fft * rms
+    lim = (eps_r + d_pole) * amp + d_fft * float(np.max(amp))
     bad = np.argwhere(err > lim)
+    print("2048^2 |k|^-3, %s: largest error / bound over wavenumbers %.3f" % (form, float(np.max(err / lim))))
     assert bad.size == 0, (form, bad[:5].tolist(), float(np.max(err / lim)))
 
 
@@ -82,10 +83,11 @@ def test_config2_every_wavenumber_white_noise(form, eps_r):
     d_pole = pole_rounding_bound(form, TAU_RHO, H_PARAM, M_EXPECTED)
     d_fft = fft_rounding_bound(form, D, D)
     amp = np.sqrt(np.sum(np.abs(fin) ** 2, axis=0))
-    rms = math.sqrt(float(np.mean(amp ** 2)))
     err = np.sqrt(np.sum(np.abs(got - ref) ** 2, axis=0))
-    lim = (eps_r + d_pole) * amp + d_fft * rms
+    lim = (eps_r + d_pole) * amp + d_fft * float(np.max(amp))
     bad = np.argwhere(err > lim)
+    print("2048^2 white noise, %s: largest error / bound %.3f, median error / amplitude %.2e"
+          % (form, float(np.max(err / lim)), float(np.median(err / amp))))
     assert bad.size == 0, (form, bad[:5].tolist(), float(np.max(err / lim)))
     # the bulk of the wavenumbers sits far below the bound: the median error is
     # at the level of the scalar approximation error, not of the bound
