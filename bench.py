@@ -1,17 +1,19 @@
 #!/usr/bin/env python
 """Benchmark of one REXII time step on the constant-depth (Fourier) path.
 
-Workload (one "step" = one whole REXII step over one batch of input):
-2048 x 2048 staggered grid, H = g = f = 1 on the unit square, eta from the
-seeded |k|^-3 recipe (seeds 0..9 cycled, u = v = 0, real input stored as
-complex128), dt with dt * rho(A) = 1000, pole-count tolerance 1e-10
+Workload (one bench "step" = one REXII step of each state of one batch):
+2048 x 2048 staggered grid, H = g = f = 1 on the unit square, a batch of ten
+eta fields from the seeded |k|^-3 recipe (seeds 0..9, u = v = 0, real input
+stored as complex128), dt with dt * rho(A) = 1000, pole-count tolerance 1e-10
 (M = 2009, N = 2033, J = 2(N + 1) = 4068 single-shift poles).
 
-Metric: grid points x poles solved per second = nx * ny * J / (time per step),
-summed over ranks.  Device time comes from CUDA events on the launching stream
-around exactly --steps steps after --warmup untimed steps (barrier and
-synchronise on both sides, max over ranks).  Each input state is 201 MB, larger
-than the 129 MB L2, and ten of them are cycled.
+Metric: grid points x poles solved per second = 10 * nx * ny * J / (time per
+bench step), summed over ranks.  Device time comes from CUDA events on the
+launching stream around exactly --steps bench steps after --warmup untimed
+ones (barrier and synchronise on both sides, max over ranks).  Each input
+state is 201 MB, larger than the 129 MB L2.  Clocks are sampled every 100 ms
+during the timed region; profiling events are off there (the per-kernel split
+comes from a repeat of the timed loop with them on).
 
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
 workload instead (rank 0 only).
@@ -81,16 +83,18 @@ def pole_count():
 def workload_config(form, M):
     N = M + 24
     return {
-        "workload": "LRSW constant-depth Fourier path, %dx%d C-grid, |k|^-3 eta seeds 0-%d, tau*rho=%g, "
-                    "tol=%g, h=%g, real input, form=%s" % (D, D, N_SEEDS - 1, TAU_RHO, TOL, H_PARAM, form),
+        "workload": "LRSW constant-depth Fourier path, %dx%d C-grid, |k|^-3 eta seeds 0-%d (one REXII step of each "
+                    "of the %d states per bench step), tau*rho=%g, tol=%g, h=%g, real input, form=%s"
+                    % (D, D, N_SEEDS - 1, N_SEEDS, TAU_RHO, TOL, H_PARAM, form),
         "grid": [D, D],
+        "states_per_step": N_SEEDS,
         "tau_rho": TAU_RHO,
         "tol": TOL,
         "h": H_PARAM,
         "M": M,
         "J": 2 * (N + 1),
         "form": form,
-        "l2": "inputs larger than L2 (201 MB state per step, %d states cycled)" % N_SEEDS,
+        "l2": "inputs larger than L2 (201 MB state per REXII step, %d states cycled)" % N_SEEDS,
     }
 
 
@@ -102,8 +106,9 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
               "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
 
-    def __init__(self, gpu_id):
+    def __init__(self, gpu_id, interval_ms=100):
         self.gpu_id = gpu_id
+        self.interval_ms = interval_ms
         self.proc = None
         self.path = None
 
@@ -112,7 +117,7 @@ class ClockSampler:
         os.close(fd)
         try:
             cmd = ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
-                   "-lms", "200"]
+                   "-lms", str(self.interval_ms)]
             if self.gpu_id is not None:
                 cmd += ["-i", str(self.gpu_id)]
             self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
@@ -191,42 +196,56 @@ def max_over_ranks(world, v):
 # oracle timing (cpu_baseline leg and the reference arm): per-mode FP64 solve
 # chain of the oracle on sampled wavenumbers of the same input
 
-def oracle_sample(n_modes, seed=0, fout=None):
-    """Runs the oracle's per-mode REXII chain on `n_modes` wavenumbers of the
-    2048^2 seed-`seed` input.  Returns (seconds, max relative error of `fout`
-    at those modes or None)."""
-    import numpy as np
+class OracleSample:
+    """The oracle's per-mode REXII chain on sampled wavenumbers of the 2048^2
+    seed-`seed` input.  The input field and its transform are built once in
+    the constructor, outside any timed region."""
 
-    from oracle import coeffs as C
-    from oracle import operator as O
-    from oracle import rexi as R
-    from paper_2008_11607_gb300 import inputs
+    def __init__(self, seed=0):
+        import numpy as np
 
-    st = inputs.kminus3_field(D, D, seed=seed)
-    fin = np.fft.fft2(st[0])  # u = v = 0
-    rho = 2.0 * math.sqrt(2.0) * D
-    dt = TAU_RHO / rho
-    M = C.pole_count_M(TAU_RHO, H_PARAM, TOL)
-    rng = np.random.default_rng(1234)
-    ks = [(int(a), int(b)) for a, b in rng.integers(0, D, size=(n_modes, 2))]
-    worst = 0.0
-    t0 = time.perf_counter()
-    tw = C.matrix_term_weights(H_PARAM, M, real_input=False)  # once per step, as on the GPU
-    refs = []
-    for kx, ky in ks:
-        B = O.symbol(kx, ky, D, D)
-        fh = np.array([fin[ky, kx], 0.0, 0.0], dtype=np.complex128)
-        refs.append(R.rexii_apply_dense_mode(B, fh, dt, H_PARAM, M, real_input=False, term_weights=tw))
-    secs = time.perf_counter() - t0
-    if fout is not None:
-        # error of each sampled mode against max(|ref(k)|, rms mode amplitude of
-        # the input): an upper estimate of the relative l2 error of the field
-        rms = math.sqrt(float(np.sum(np.abs(fin) ** 2)) / (D * D))
+        from oracle import coeffs as C
+        from paper_2008_11607_gb300 import inputs
+
+        st = inputs.kminus3_field(D, D, seed=seed)
+        self.fin = np.fft.fft2(st[0])  # u = v = 0
+        self.dt = TAU_RHO / (2.0 * math.sqrt(2.0) * D)
+        self.M = C.pole_count_M(TAU_RHO, H_PARAM, TOL)
+        self.rng = np.random.default_rng(1234)
+        # coefficients once per workload, as the library keeps its tables per plan
+        self.tw = C.matrix_term_weights(H_PARAM, self.M, real_input=False)
+
+    def modes(self, n):
+        return [(int(a), int(b)) for a, b in self.rng.integers(0, D, size=(n, 2))]
+
+    def run(self, ks):
+        """Per-mode chains for the wavenumbers `ks`."""
+        import numpy as np
+
+        from oracle import operator as O
+        from oracle import rexi as R
+
+        tw = self.tw
+        refs = []
+        for kx, ky in ks:
+            B = O.symbol(kx, ky, D, D)
+            fh = np.array([self.fin[ky, kx], 0.0, 0.0], dtype=np.complex128)
+            refs.append(R.rexii_apply_dense_mode(B, fh, self.dt, H_PARAM, self.M, real_input=False,
+                                                 term_weights=tw))
+        return refs
+
+    def max_rel_err(self, ks, refs, fout):
+        """Error of each sampled mode of `fout` against max(|ref(k)|, rms mode
+        amplitude of the input): an upper estimate of the field's relative l2
+        error."""
+        import numpy as np
+
+        rms = math.sqrt(float(np.sum(np.abs(self.fin) ** 2)) / (D * D))
+        worst = 0.0
         for (kx, ky), ref in zip(ks, refs):
             got = fout[:, ky, kx]
             worst = max(worst, float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), rms)))
-        return secs, worst
-    return secs, None
+        return worst
 
 
 def run_reference(args):
@@ -237,12 +256,14 @@ def run_reference(args):
 
     M = C.pole_count_M(TAU_RHO, H_PARAM, TOL)
     J = 2 * (M + 24 + 1)
-    modes = 1
+    modes = 16
+    orc = OracleSample(seed=0)  # input and its transform built before timing
     for _ in range(args.warmup):
-        oracle_sample(modes)
+        orc.run(orc.modes(modes))
+    batches = [orc.modes(modes) for _ in range(args.steps)]
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle_sample(modes)
+    for ks in batches:
+        orc.run(ks)
     secs = (time.perf_counter() - t0) / args.steps
     value = modes * J / secs
     cfg = workload_config("oracle", M)
@@ -251,8 +272,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d wavenumbers of the 2048^2 step per timed step, each through the "
-                                   "oracle's per-mode FP64 solve chain over all 2N+1 terms" % modes},
+                         "sample": "%d wavenumber(s) of the 2048^2 step per timed step, each through the "
+                                   "oracle's per-mode FP64 solve chain over all 2N+1 terms (input and its "
+                                   "transform built before the timed region)" % modes},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -260,13 +282,24 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------
 
-def time_form(torch, rexi, form, states, steps, warmup, world, profile=True):
-    plan = rexi.Plan(D, D, form=form, h=H_PARAM)
+def time_form(torch, rexi, form, states, steps, warmup, world, profile=False, nx=None, ny=None):
+    """Times `steps` bench steps after `warmup` untimed ones; one bench step is
+    one REXII step of every state in `states` (each to its own output buffer
+    of two, one workspace).  Returns (plan, dt, ms per bench step, profile
+    (phase sums, calls, launches) or None, last output)."""
+    nx = nx or D
+    ny = ny or D
+    plan = rexi.Plan(nx, ny, form=form, h=H_PARAM)
     dt = TAU_RHO / plan.rho
     ws = plan.workspace(dt, TOL)
-    out = torch.empty_like(states[0])
-    for i in range(warmup):
-        plan.step(states[i % len(states)], dt, tol=TOL, out=out, workspace=ws)
+    outs = [torch.empty_like(states[0]) for _ in range(2)]
+
+    def one_step():
+        for i, st in enumerate(states):
+            plan.step(st, dt, tol=TOL, out=outs[i % 2], workspace=ws)
+
+    for _ in range(warmup):
+        one_step()
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
@@ -275,14 +308,42 @@ def time_form(torch, rexi, form, states, steps, warmup, world, profile=True):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for i in range(steps):
-        plan.step(states[i % len(states)], dt, tol=TOL, out=out, workspace=ws)
+    for _ in range(steps):
+        one_step()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
     ms = e0.elapsed_time(e1) / steps
     prof = plan.read_profile() if profile else None
-    return plan, dt, ms, prof, out
+    plan.set_profiling(False)
+    return plan, dt, ms, prof, outs[(len(states) - 1) % 2]
+
+
+def alu_peaks(torch, rexi, sampler_gpu):
+    """Measured multiply-add throughput of this GPU (rexi_alu_probe): 1216
+    blocks of 256 threads (8 per SM), 3 untimed and 10 timed launches per
+    kind, CUDA events, clocks sampled during the timed launches."""
+    res = {}
+    out = torch.empty(1216 * 256, dtype=torch.float64, device="cuda")
+    for kind, iters in (("fp32", 16000), ("fp64", 300)):
+        for _ in range(3):
+            rexi.alu_probe(kind, 1216, iters, out)
+        torch.cuda.synchronize()
+        smp = ClockSampler(sampler_gpu, interval_ms=50)
+        smp.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        flops = 0
+        for _ in range(10):
+            flops += rexi.alu_probe(kind, 1216, iters, out)
+        e1.record()
+        torch.cuda.synchronize()
+        clk = smp.stop()
+        secs = e0.elapsed_time(e1) / 1e3
+        res[kind] = {"tflops": flops / secs / 1e12, "lane_ops_per_s": flops / 2 / secs, "seconds": secs,
+                     "clocks": clk}
+    return res
 
 
 KRYLOV_D = 1024
@@ -527,6 +588,43 @@ def adjoint_measure(torch, rexi, inputs, form="mixed", n=512, steps=8, tau_rho=2
     }
 
 
+def pole_roofline(form, pole_ms, orbits, nterms, peaks):
+    """Roofline of the pole-sum kernel: executed orbit-terms per launch x
+    operations per term over its launch time, against the measured
+    multiply-add rate (and, beside it, the lane rate derived from unit counts
+    at the maximum clock)."""
+    terms = orbits * nterms
+    t_pole = pole_ms / 1e3
+    if form == "mixed":
+        # every FP32 arithmetic operation counted once (61 of the 73 operations
+        # per term are single-flop FADD/FMUL), against FP32 lane operations per
+        # second: the measured FFMA rate in lane operations (flops / 2)
+        ops = terms * FP32_INSTR_PER_TERM
+        peak_meas = peaks["fp32"]["lane_ops_per_s"] / 1e12 if peaks else None
+        peak_derived = SMS * 128 * SM_MAX_GHZ / 1e3
+        conv = "FP32 operations per launch (FADD/FMUL/FFMA each 1; 73 per term) per second, vs the measured FFMA " \
+               "lane-operation rate (rexi_alu_probe)"
+    else:
+        ops = terms * FP64_INSTR_PER_TERM
+        peak_meas = peaks["fp64"]["lane_ops_per_s"] / 1e12 if peaks else None
+        peak_derived = PEAK_FP64_TFLOPS / 2
+        conv = "FP64 operations per launch (DADD/DFMA each 1; 9 per term) per second, vs the measured DFMA " \
+               "lane-operation rate (rexi_alu_probe)"
+    achieved = ops / t_pole / 1e12
+    peak = peak_meas if peak_meas else peak_derived
+    return {
+        "kernel": "pole_orbit_%s_kernel" % form,
+        "bound": "alu", "achieved": achieved, "peak": peak, "unit": "T op/s", "frac": achieved / peak,
+        "traffic": NCU_POLE_TRAFFIC_BYTES.get(form),
+        "flop_convention": conv,
+        "peak_source": "measured (rexi_alu_probe, this run)" if peak_meas else "derived from unit counts",
+        "peak_derived_lane_rate": peak_derived, "frac_of_derived": achieved / peak_derived,
+        "fma2_tflops": terms * FLOPS_PER_TERM[form] / t_pole / 1e12,
+        "pole_ms_per_launch": pole_ms, "orbits": orbits, "terms_per_launch": terms,
+        "orbit_terms_per_s": terms / t_pole,
+    }
+
+
 def run_ours(args):
     import torch
 
@@ -543,7 +641,7 @@ def run_ours(args):
     states = [h.to(dev) for h in host_states]
     M = pole_count()
     J = 2 * (M + 24 + 1)
-    units = D * D * J
+    units = len(states) * D * D * J  # one bench step: one REXII step of each seeded state
 
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -551,45 +649,30 @@ def run_ours(args):
         gpu_id = None
     sampler = ClockSampler(gpu_id)
 
-    # headline form, with clocks sampled during the timed region
+    # headline: no profiling events inside the timed region; clocks sampled
     sampler.start()
-    plan, dt, ms, prof, out = time_form(torch, rexi, args.form, states, args.steps, args.warmup, world)
+    plan, dt, ms, _, out = time_form(torch, rexi, args.form, states, args.steps, args.warmup, world)
     clocks = sampler.stop()
     ms_max = max_over_ranks(world, ms)
     value = world * units / (ms_max / 1e3)
+    # the same timed loop again with the library's phase events, for the
+    # per-kernel split and the roofline of the dominant kernel
+    _, _, ms_prof, prof, _ = time_form(torch, rexi, args.form, states, max(2, args.steps // 4), 1, world,
+                                       profile=True)
     ms_phase, ncalls, nlaunch = prof
+    launches_per_step = nlaunch / max(1, max(2, args.steps // 4))
     combine_ms = ms_phase[4] / max(ncalls, 1)
     pole_ms = ms_phase[1] / max(ncalls, 1) - combine_ms  # the pole-sum kernel alone
     orbits = orbit_count(D)
     nterms = 2 * (M + 24) + 1
-    terms = orbits * nterms
-    t_pole = pole_ms / 1e3
-    if args.form == "mixed":
-        # every FP32 arithmetic operation counted once (the kernel is FADD-heavy:
-        # 61 of its 73 operations per term are single-flop), against the FP32
-        # lane rate 152 SMs x 128 lanes x 2.07 GHz
-        ops = terms * FP32_INSTR_PER_TERM
-        peak = SMS * 128 * SM_MAX_GHZ / 1e3
-        conv = "FP32 operations per launch (FADD/FMUL/FFMA each 1; 73 per term) vs 152 SMs x 128 lanes x 2.07 GHz"
-    else:
-        ops = terms * FP64_INSTR_PER_TERM
-        peak = PEAK_FP64_TFLOPS / 2
-        conv = "FP64 operations per launch (DADD/DFMA each 1; 9 per term) vs nominal 1.25 TFLOP/s / 2"
-    achieved = ops / t_pole / 1e12
-    roofline = {
-        "kernel": "pole_orbit_%s_kernel" % args.form,
-        "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-        "traffic": NCU_POLE_TRAFFIC_BYTES.get(args.form),
-        "flop_convention": conv,
-        "fma2_tflops": terms * FLOPS_PER_TERM[args.form] / t_pole / 1e12,
-        "fma2_peak": PEAK_FP32_TFLOPS if args.form == "mixed" else PEAK_FP64_TFLOPS,
-        "pole_ms_per_launch": pole_ms,
-        "orbits": orbits,
-        "terms_per_launch": terms,
-        "peak_source": "derived from unit counts and the maximum SM clock (no measured ALU peak on file)",
-    }
+
+    peaks = None
+    if not args.skip_peaks:
+        peaks = alu_peaks(torch, rexi, gpu_id)
+    roofline = pole_roofline(args.form, pole_ms, orbits, nterms, peaks)
     phases = {"forward_fft_ms": ms_phase[0] / max(ncalls, 1), "pole_sum_ms": pole_ms, "combine_ms": combine_ms,
-              "inverse_fft_ms": ms_phase[2] / max(ncalls, 1), "table_upload_ms": ms_phase[3] / max(ncalls, 1)}
+              "inverse_fft_ms": ms_phase[2] / max(ncalls, 1), "table_upload_ms": ms_phase[3] / max(ncalls, 1),
+              "profiled_ms_per_rexii_step": ms_prof / len(states)}
     # HBM roofline of the forward transform of real input: the row pass reads
     # the 3 fields (16 B per value) and writes the half spectrum, the column
     # pass reads and writes the half spectrum (16 B per value)
@@ -617,59 +700,124 @@ def run_ours(args):
                         "traffic": NCU_COMBINE_TRAFFIC_BYTES, "algorithmic_bytes": comb_bytes}
 
     # end-to-end through the host-buffer C-ABI calls (pinned host memory):
-    # every step copies its input state in and its result out.  Headline:
+    # every REXII step copies its input state in and its result out.  Headline:
     # rexi_step_host_async on two streams, a workspace and an output buffer
-    # each, so one step's copies overlap the other's kernels; the timed region
+    # each, so one call's copies overlap the other's kernels; the timed region
     # ends when both streams are done.  Beside it: rexi_step_host, one
     # blocking call after another.
     e2e = None
     if not args.skip_e2e:
-        plan.set_profiling(False)
         pinned = [h.pin_memory() for h in host_states]
         outs = [torch.empty_like(pinned[0]).pin_memory() for _ in range(2)]
         wss = [plan.workspace_host(dt, TOL) for _ in range(2)]
         streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-        k_e2e = max(3, min(args.steps, 20))
+        k_e2e = max(2, min(args.steps, 10))
 
         def overlapped(k):
-            for i in range(k):
-                plan.step_host(pinned[i % N_SEEDS], outs[i % 2], dt, tol=TOL, workspace=wss[i % 2],
-                               stream=streams[i % 2], blocking=False)
+            c = 0
+            for _ in range(k):
+                for st in pinned:
+                    plan.step_host(st, outs[c % 2], dt, tol=TOL, workspace=wss[c % 2], stream=streams[c % 2],
+                                   blocking=False)
+                    c += 1
             for sm in streams:
                 sm.synchronize()
 
-        overlapped(max(2, min(4, args.warmup)))
+        overlapped(1)
         barrier(world)
         t0 = time.perf_counter()
         overlapped(k_e2e)
         secs = (time.perf_counter() - t0) / k_e2e
         secs = max_over_ranks(world, secs)
-        for i in range(min(2, args.warmup)):
-            plan.step_host(pinned[i], outs[0], dt, tol=TOL, workspace=wss[0])
+        for st in pinned[:2]:
+            plan.step_host(st, outs[0], dt, tol=TOL, workspace=wss[0])
         barrier(world)
         t0 = time.perf_counter()
-        for i in range(k_e2e):
-            plan.step_host(pinned[i % N_SEEDS], outs[0], dt, tol=TOL, workspace=wss[0])
-        secs_b = (time.perf_counter() - t0) / k_e2e
+        for _ in range(max(1, k_e2e // 2)):
+            for st in pinned:
+                plan.step_host(st, outs[0], dt, tol=TOL, workspace=wss[0])
+        secs_b = (time.perf_counter() - t0) / max(1, k_e2e // 2)
         secs_b = max_over_ranks(world, secs_b)
-        nbytes = 3 * D * D * 16
+        nbytes = len(pinned) * 3 * D * D * 16
         e2e = {"value": world * units / secs, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "ms_per_step": secs * 1e3, "steps": k_e2e,
-               "mode": "rexi_step_host_async, two streams with a workspace each (copies overlap kernels)",
+               "mode": "rexi_step_host_async, two streams with a workspace each (copies overlap kernels), "
+                       "10 states per step",
                "blocking": {"value": world * units / secs_b, "ms_per_step": secs_b * 1e3,
                             "mode": "rexi_step_host, one call at a time"}}
         del wss
 
-    # other forms on the same GPU and workload (fewer steps)
+    # other forms on the same GPU and workload (fewer steps; the plain form on one state)
     forms = {}
     if not args.skip_forms:
-        for form, k in (("fp64", 3), ("plain", 1)):
+        for form, k, nst in (("fp64", 2, len(states)), ("plain", 1, 1)):
             if form == args.form:
                 continue
-            _, _, fms, fprof, _ = time_form(torch, rexi, form, states, k, 1, world)
+            _, _, fms, _, _ = time_form(torch, rexi, form, states[:nst], k, 1, world)
             fms = max_over_ranks(world, fms)
-            forms[form] = {"value": world * units / (fms / 1e3), "ms_per_step": fms, "steps": k,
-                           "pole_ms": fprof[0][1] / max(fprof[1], 1)}
+            u = nst * D * D * J
+            forms[form] = {"value": world * u / (fms / 1e3), "ms_per_rexii_step": fms / nst, "steps": k,
+                           "states_per_step": nst}
+        # the fp64 form's pole kernel, for its own roofline
+        if args.form != "fp64":
+            _, _, _, fp, _ = time_form(torch, rexi, "fp64", states[:2], 1, 1, world, profile=True)
+            f_pole = fp[0][1] / max(fp[1], 1) - fp[0][4] / max(fp[1], 1)
+            forms["fp64"]["roofline"] = pole_roofline("fp64", f_pole, orbits, nterms, peaks)
+
+    # complex input (the full two-sided sum, J = 2(2N + 1) poles): the mixed
+    # form's complex transforms and its double-float combine on the full spectrum
+    cplx = None
+    if not args.skip_forms:
+        cst = []
+        for sd in seeds[:4]:
+            a = inputs.kminus3_field(D, D, seed=sd)
+            a[0] = a[0] + 1j * inputs.kminus3_field(D, D, seed=sd + 500)[0].real
+            cst.append(torch.from_numpy(a).to(dev))
+        cplan = rexi.Plan(D, D, form=args.form, h=H_PARAM)
+        cdt = TAU_RHO / cplan.rho
+        cws = cplan.workspace(cdt, TOL, real_input=False)
+        cout = torch.empty_like(cst[0])
+        for st_ in cst[:2]:
+            cplan.step(st_, cdt, tol=TOL, real_input=False, out=cout, workspace=cws)
+        torch.cuda.synchronize()
+        cplan.set_profiling(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        kc = max(2, args.steps // 4)
+        e0.record()
+        for i in range(kc):
+            cplan.step(cst[i % len(cst)], cdt, tol=TOL, real_input=False, out=cout, workspace=cws)
+        e1.record()
+        torch.cuda.synchronize()
+        cms = e0.elapsed_time(e1) / kc
+        cph, cn, _ = cplan.read_profile()
+        cplan.set_profiling(False)
+        Jc = 2 * (2 * (M + 24) + 1)
+        cplx = {"workload": "2048^2 C-grid, complex eta (|k|^-3 real and imaginary parts, seeds 0-3 and 500-503), "
+                            "tau*rho=%g, real_input=0, form=%s" % (TAU_RHO, args.form),
+                "J": Jc, "value": world * D * D * Jc / (cms / 1e3), "unit": UNIT, "ms_per_rexii_step": cms,
+                "phases_ms": {"forward_fft_ms": cph[0] / max(cn, 1), "pole_sum_ms": (cph[1] - cph[4]) / max(cn, 1),
+                              "combine_ms": cph[4] / max(cn, 1), "inverse_fft_ms": cph[2] / max(cn, 1)}}
+        del cws
+
+    # rectangular grid: the kx <-> ky fold is not available, so one pole sum
+    # serves four wavenumbers instead of eight
+    rect = None
+    if not args.skip_rect:
+        RX, RY = D, (3 * D) // 4
+        rstates = [torch.from_numpy(inputs.kminus3_field(RX, RY, seed=s)).to(dev) for s in seeds[:4]]
+        rplan, rdt, rms, rprof, _ = time_form(torch, rexi, args.form, rstates, max(4, args.steps // 4), 2, world,
+                                              nx=RX, ny=RY)
+        Mr = rexi.rexi_pole_count(TAU_RHO, H_PARAM, TOL)
+        Jr = 2 * (Mr + 24 + 1)
+        _, _, _, rp, _ = time_form(torch, rexi, args.form, rstates, 2, 1, world, nx=RX, ny=RY, profile=True)
+        r_pole = rp[0][1] / max(rp[1], 1) - rp[0][4] / max(rp[1], 1)
+        r_orbits = (RX // 2 + 1) * (RY // 2 + 1)
+        rect = {"workload": "%dx%d C-grid (dx = 1/%d, dy = 1/%d), |k|^-3 eta seeds 0-3, tau*rho=%g, form=%s"
+                            % (RX, RY, RX, RY, TAU_RHO, args.form),
+                "value": len(rstates) * RX * RY * Jr / (rms / 1e3), "unit": UNIT,
+                "ms_per_rexii_step": rms / len(rstates), "rho": rplan.rho,
+                "roofline": pole_roofline(args.form, r_pole, r_orbits, 2 * (Mr + 24) + 1, peaks)}
 
     batched = None
     if not args.skip_batch:
@@ -695,18 +843,36 @@ def run_ours(args):
     if not args.skip_adjoint:
         differentiation = adjoint_measure(torch, rexi, inputs, n=args.adjoint_grid)
 
-    # CPU oracle on a bounded sample (rank 0, N = 1 only), also the accuracy check
+    # CPU baselines on bounded samples (rank 0, N = 1 only): the oracle's
+    # per-mode chain (1 core; also the accuracy check of the GPU output), and
+    # Algorithm 1 on all host cores
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         import numpy as np
 
-        plan0, dt0, _, _, o0 = time_form(torch, rexi, args.form, states[:1], 1, 0, 1, profile=False)
+        from baseline import alg1_cpu as A1
+
+        _, _, _, _, o0 = time_form(torch, rexi, args.form, states[:1], 1, 0, 1)
         fout = np.fft.fft2(o0.cpu().numpy(), axes=(1, 2))
-        secs, err = oracle_sample(args.cpu_modes, seed=seeds[0], fout=fout)
+        orc = OracleSample(seed=seeds[0])
+        ks = orc.modes(args.cpu_modes)
+        t0 = time.perf_counter()
+        refs = orc.run(ks)
+        secs = time.perf_counter() - t0
+        err = orc.max_rel_err(ks, refs, fout)
         cpu = {"value": args.cpu_modes * J / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "%d random wavenumbers of the seed-0 2048^2 step through the oracle's per-mode FP64 "
                          "solve chain (all 2N+1 terms, 2 dense 3x3 solves each), %.1f s" % (args.cpu_modes, secs),
                "max_rel_err_vs_oracle": err}
+        st0 = host_states[0].numpy()
+        est, det = A1.time_sample(D, D, dt, H_PARAM, M, st0, args.alg1_terms)
+        cpu["alg1_all_cores"] = {
+            "value": D * D * J / est, "unit": UNIT, "cores": det["threads"], "kind": "Algorithm 1 (Section 4.1)",
+            "cpu_model": A1.cpu_model(), "nproc": os.cpu_count(), "seconds_per_step_estimated": est,
+            "sample": "2048^2 seed-0 step: transforms, coefficients and %d of the %d REXII terms (evenly spaced) "
+                      "over the whole spectrum with NumPy on %d threads; the step time extrapolates the sampled "
+                      "terms to all terms" % (det["terms_sampled"], det["terms_total"], det["threads"]),
+            "detail": det}
 
     if rank == 0:
         cfg = workload_config(args.form, M)
@@ -714,8 +880,14 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32x2+f64" if args.form == "mixed" else "f64", "data": "synthetic",
-            "config": cfg, "clocks": clocks, "e2e": e2e, "gpu_launches": nlaunch, "roofline": roofline,
-            "roofline_fft": roofline_fft, "roofline_combine": roofline_combine, "phases_ms": phases, "forms": forms, "batched": batched, "krylov": krylov,
+            "config": cfg, "clocks": clocks, "e2e": e2e, "gpu_launches": int(round(launches_per_step * args.steps)),
+            "roofline": roofline, "alu_peaks": peaks,
+            "executed": {"orbit_terms_per_s": world * len(states) * orbits * nterms / (ms_max / 1e3),
+                         "note": "one pole sum per orbit of omega's symmetries (8 wavenumbers on this square grid); "
+                                 "value counts every grid point and every pole"},
+            "rectangular": rect, "complex_input": cplx,
+            "roofline_fft": roofline_fft, "roofline_combine": roofline_combine, "phases_ms": phases, "forms": forms,
+            "batched": batched, "krylov": krylov,
             "differentiation": differentiation,
             "cpu_baseline": cpu,
             "accuracy": {"tolerance": 1e-8 if args.form == "mixed" else 1e-10,
@@ -739,6 +911,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-krylov", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-peaks", action="store_true")
+    ap.add_argument("--skip-rect", action="store_true")
+    ap.add_argument("--alg1-terms", type=int, default=64, help="REXII terms sampled by the Algorithm 1 CPU baseline")
     ap.add_argument("--adjoint-only", action="store_true",
                     help="run only the differentiation workload (minutes at 512^2)")
     ap.add_argument("--adjoint-grid", type=int, default=512)
