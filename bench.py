@@ -325,7 +325,7 @@ def alu_peaks(torch, rexi, sampler_gpu):
     kind, CUDA events, clocks sampled during the timed launches."""
     res = {}
     out = torch.empty(1216 * 256, dtype=torch.float64, device="cuda")
-    for kind, iters in (("fp32", 16000), ("fp64", 300)):
+    for kind, iters in (("fp32", 8000), ("fp64", 150)):
         for _ in range(3):
             rexi.alu_probe(kind, 1216, iters, out)
         torch.cuda.synchronize()

@@ -2,7 +2,7 @@
 // FP64 fused multiply-add rates that bound the pole-sum kernels (a
 // measurement utility; the paper has no counterpart).
 //
-// Every thread runs kChains independent multiply-add recurrences
+// Every thread runs kChains (16) independent multiply-add recurrences
 // acc = acc * m + c (m slightly below 1, so the values settle at c / (1 - m)
 // and never become subnormal or overflow) for `iters` rounds, so the pipes see
 // kChains independent operations per round and per thread.  One value per
@@ -14,7 +14,7 @@
 
 namespace {
 
-constexpr int kChains = 8;
+constexpr int kChains = 16;  // enough independent work to cover the FP64 pipe's latency too
 constexpr int kThreads = 256;
 
 template <typename T>
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kThreads) alu_probe_kernel(int iters, T m, T c
 }  // namespace
 
 // kind 0: FP32 (fmaf), kind 1: FP64 (fma).  blocks x 256 threads, each
-// thread 16 * 8 * iters multiply-adds (2 flops each).  out_dev: at least
+// thread 16 * 16 * iters multiply-adds (2 flops each).  out_dev: at least
 // blocks * 256 values of the kind's type (written only in the impossible
 // sentinel case).  Asynchronous on `stream`; the caller times it.
 extern "C" rexi_status rexi_alu_probe(int32_t kind, int32_t blocks, int32_t iters, void* out_dev, void* stream) {

@@ -237,10 +237,10 @@ def _stream_handle(stream):
 
 def alu_probe(kind, blocks, iters, out, stream=None):
     """Enqueue the multiply-add throughput probe (kind "fp32" or "fp64"); returns
-    the flops it performs (blocks * 256 threads * 128 * iters * 2)."""
+    the flops it performs (blocks * 256 threads * 256 * iters * 2)."""
     k = {"fp32": 0, "fp64": 1}[kind]
     _check(load().rexi_alu_probe(k, int(blocks), int(iters), _ptr(out), _stream_handle(stream)), "rexi_alu_probe")
-    return blocks * 256 * 128 * iters * 2
+    return blocks * 256 * 256 * iters * 2
 
 
 class Plan:

@@ -191,3 +191,89 @@ def test_mutation_chain(monkeypatch, which):
 
     monkeypatch.setattr(C, "matrix_term_weights", bad)
     assert expm_pin() > 1e-3
+
+
+# ---------------------------------------------------------------------------
+# The original REXI, REXIE, the shift and the field-wide exponential.
+
+def rexi_row_pin():
+    """WS1, tau = 1, h = 0.2, M = 150 at D = 128: the printed 6.98e-2 (Table tab:w11)."""
+    from oracle import spectral as S
+
+    st = inputs.paper_scenario("ws1", 128, 128)
+    ref = E.exp_closed_form(st, 1.0, symbol_fn=S.symbol).real
+    out = R.rexi_original_apply_modes(st, 1.0, 0.2, 150, S.symbol).real
+    return abs(float(np.max(np.abs(out - ref))) - 6.98e-2) / 6.98e-2
+
+
+def a2_pin():
+    """A_2 with the shift nu = -2450 i against dense expm (Section 3.2)."""
+    A2 = O.schrodinger_operator(70, 1, Lx=2.0)
+    x = -1.0 + np.arange(70) * (2.0 / 70)
+    f0 = 1.0 / (2.0 + np.cos(2 * math.pi * x))
+    ref = E.expm_dense(A2, f0, 1.0)
+    got = R.rexie_apply(A2, f0, 1.0, 0.5, C.pole_count_M(2450.0, 0.5, 1e-16), sigma=-2450.0)
+    return np.linalg.norm(got - ref) / np.linalg.norm(ref)
+
+
+def grid_exp_pin():
+    st = inputs.complex_random_state(6, 5, seed=2)
+    A = O.cgrid_operator(6, 5, 1.1, 0.9, 1.5, 0.6, 2.0)
+    ref = E.expm_dense(A, st.ravel(), 0.7).reshape(st.shape)
+    got = E.exp_closed_form_grid(st, 0.7, 1.1, 0.9, 1.5, 0.6, 2.0)
+    return np.linalg.norm(got - ref) / np.linalg.norm(ref)
+
+
+def test_new_pins_pass_unmodified():
+    assert rexi_row_pin() < 0.02
+    assert a2_pin() < 1e-12
+    assert grid_exp_pin() < 1e-12
+
+
+def test_mutation_beta_uses_the_wrong_part_of_b(monkeypatch):
+    """beta^Re built from Im(b_m) instead of Re(b_m): the REXI row no longer
+    reproduces the printed error."""
+    orig = C.beta_coeffs_sliced
+
+    def bad(h, M, mu=None, a=None):
+        ns, br, bi = orig(h, M, mu, a)
+        return ns, bi, br
+
+    monkeypatch.setattr(C, "beta_coeffs_sliced", bad)
+    assert rexi_row_pin() > 0.5
+
+
+def test_mutation_rexie_shift_phase_sign(monkeypatch):
+    """e^{-i tau sigma} instead of e^{+i tau sigma} when undoing the shift."""
+    orig = R.rexie_apply
+
+    def bad(A, f0, tau, h, M, sigma=0.0):
+        return orig(A, f0, tau, h, M, sigma) * np.exp(-2j * tau * sigma)
+
+    monkeypatch.setattr(R, "rexie_apply", bad)
+    assert a2_pin() > 1e-3
+
+
+def test_mutation_rexie_drops_the_imaginary_part(monkeypatch):
+    """REXIE without its i Re(beta^Im ...) half is the original REXI, which
+    approximates only cos on an operator i B."""
+    monkeypatch.setattr(C, "beta_coeffs", lambda h, M, mu=None, a=None: (
+        C.beta_coeffs_sliced(h, M, mu, a)[0], C.beta_coeffs_sliced(h, M, mu, a)[1],
+        np.zeros_like(C.beta_coeffs_sliced(h, M, mu, a)[2])))
+    assert a2_pin() > 1e-3
+
+
+@pytest.mark.parametrize("which", ["sin_sign", "missing_B2"])
+def test_mutation_grid_exponential(monkeypatch, which):
+    orig = O.symbol_grid
+
+    def bad(*args, **kw):
+        B = orig(*args, **kw)
+        if which == "sin_sign":
+            return -B  # e^{-tau B}: the sin term changes sign, the B^2 term does not
+        B2 = B.copy()
+        B2[1, 0] = B2[2, 0] = 0.0  # a dropped gradient column
+        return B2
+
+    monkeypatch.setattr(O, "symbol_grid", bad)
+    assert grid_exp_pin() > 1e-3
