@@ -58,7 +58,7 @@ PEAK_FP64_TFLOPS = 1.25
 # DRAM traffic per launch of the pole-sum kernel and of the combine pass from
 # ncu captures on the 2048^2 grid (the traffic does not depend on the term
 # count); None where no capture of the current kernel exists.
-NCU_POLE_TRAFFIC_BYTES = {"mixed": 283.90e3 + 4.61e3, "fp64": None}  # 2048^2, tau rho = 1000 (one-pass capture)
+NCU_POLE_TRAFFIC_BYTES = {"mixed": 285440 + 5632, "fp64": None}  # 2048^2, tau rho = 1000 (one-pass capture)
 NCU_COMBINE_TRAFFIC_BYTES = None
 
 

@@ -114,3 +114,27 @@ def test_serving_mix_96_instances():
         r = p.step(s, dt).cpu().numpy()
         assert rel_l2(o.cpu().numpy(), r) < SAME_SUM["mixed"]
         assert rel_l2(o2.cpu().numpy(), r) < 1e-12
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_batch_with_h_off_the_split_grid(form):
+    """h = 0.3: h n is not a binary fraction, so the double-float tables carry
+    a low part of h n (the kernels' inexact branch).  Both launch modes against
+    the oracle's sparse REXII chain."""
+    torch = torch_cuda()
+    from paper_2008_11607_gb300 import rexi
+
+    sizes = [(16, 16), (12, 18), (20, 14)]
+    trs = [25.0, 60.0, 15.0]
+    plans = [rexi.Plan(nx, ny, form=form, h=0.3) for nx, ny in sizes]
+    dts = [tr / p.rho for tr, p in zip(trs, plans)]
+    b = rexi.Batch(sizes, dts, form=form, h=0.3)
+    states = [to_dev(torch, inputs.kminus3_field(nx, ny, seed=40 + i)) for i, (nx, ny) in enumerate(sizes)]
+    packed = b.pack(states)
+    ws = b.workspace()
+    for mode in (rexi.REXI_BATCH_PERSISTENT, rexi.REXI_BATCH_PER_INSTANCE):
+        outs = b.unpack(b.step(packed, workspace=ws, mode=mode))
+        torch.cuda.synchronize()
+        for o, st, dt, M in zip(outs, states, dts, b.M):
+            ref = oracle_step(st.cpu().numpy(), dt, M, h=0.3)
+            assert rel_l2(o.cpu().numpy(), ref) < TOL[form]
