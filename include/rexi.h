@@ -459,9 +459,11 @@ rexi_status rexi_batch_info(rexi_batch_t batch, int32_t* threads, int32_t* orbit
 
 /* Fused multiply-add throughput probe (no counterpart in the paper; it
  * measures the ALU rates that bound the pole-sum kernels).  kind 0: FP32,
- * kind 1: FP64.  Launches `blocks` blocks of 256 threads; every thread does
- * 256 * iters multiply-adds in 16 independent chains (2 flops each, so
- * 256 * blocks * 256 * iters * 2 flops per call).  out_dev: device memory for
+ * kind 1: FP64, kind 2: packed FP32 (fma.rn.f32x2, two multiply-adds per
+ * instruction).  Launches `blocks` blocks of 256 threads; every thread does
+ * 256 * iters multiply-add instructions in 16 independent chains (2 flops per
+ * instruction for kinds 0 and 1, 4 for kind 2, so 256 * blocks * 256 * iters
+ * * 2 flops per call, twice that for kind 2).  out_dev: device memory for
  * blocks * 256 values of the kind's type, written only in an impossible
  * sentinel case.  Asynchronous on `stream`; the caller times it.  EINVAL on
  * a bad kind, blocks or iters < 1, or NULL out_dev. */

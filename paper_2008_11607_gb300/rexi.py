@@ -236,11 +236,12 @@ def _stream_handle(stream):
 
 
 def alu_probe(kind, blocks, iters, out, stream=None):
-    """Enqueue the multiply-add throughput probe (kind "fp32" or "fp64"); returns
-    the flops it performs (blocks * 256 threads * 256 * iters * 2)."""
-    k = {"fp32": 0, "fp64": 1}[kind]
+    """Enqueue the multiply-add throughput probe (kind "fp32", "fp64" or
+    "fp32x2"); returns the flops it performs (blocks * 256 threads * 256 * iters
+    * 2, twice that for the packed kind)."""
+    k = {"fp32": 0, "fp64": 1, "fp32x2": 2}[kind]
     _check(load().rexi_alu_probe(k, int(blocks), int(iters), _ptr(out), _stream_handle(stream)), "rexi_alu_probe")
-    return blocks * 256 * 256 * iters * 2
+    return blocks * 256 * 256 * iters * 2 * (2 if k == 2 else 1)
 
 
 class Plan:
