@@ -160,3 +160,12 @@ def test_library_refit_rejects_bad_arguments(lib):
     assert lib.rexi_gaussian_refit(-5.0, 10, 40.0, 20001, arr, ctypes.byref(err)) == rexi.REXI_EINVAL
     assert lib.rexi_gaussian_refit(-5.0, 200, 40.0, 100, arr, ctypes.byref(err)) == rexi.REXI_EINVAL
     assert lib.rexi_gaussian_refit(-5.0, 200, 40.0, 20001, None, ctypes.byref(err)) == rexi.REXI_EINVAL
+
+
+def test_alu_probe_rejects_bad_arguments(lib):
+    """Argument checks happen before any launch (no GPU needed)."""
+    buf = ctypes.c_void_p(16)
+    assert lib.rexi_alu_probe(3, 1, 1, buf, None) == rexi.REXI_EINVAL
+    assert lib.rexi_alu_probe(0, 0, 1, buf, None) == rexi.REXI_EINVAL
+    assert lib.rexi_alu_probe(1, 1, 0, buf, None) == rexi.REXI_EINVAL
+    assert lib.rexi_alu_probe(2, 1, 1, None, None) == rexi.REXI_EINVAL
