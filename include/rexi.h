@@ -139,7 +139,8 @@ rexi_status rexi_coeffs(double tau_rho, double tol, double h, int32_t real_input
  * xmax = 40, 20001 candidates reach max |psi_1 - R| ~ 5e-14 on [-60, 60]
  * (the table: 8.1e-15).  max_err (nullable): max |psi_1 - R| on
  * [-1.5 xmax, 1.5 xmax] at spacing 0.005.  EINVAL unless mu < 0,
- * 2L + 1 <= K <= 100000, xmax > 0 and K <= n_candidates <= 1e7.
+ * 2L + 1 <= K <= 20000, xmax > 0, K <= n_candidates <= 1e6 and
+ * K n_candidates <= 5e8 (the point selection costs K n_candidates steps).
  *
  * rexi_plan_set_gaussian_fit: the plan's constant-depth steps use (mu, a)
  * instead of the table in every REXII/REXI coefficient (a_re_im NULL restores

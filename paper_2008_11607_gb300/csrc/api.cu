@@ -1109,7 +1109,8 @@ extern "C" rexi_status rexi_gaussian_refit(double mu, int32_t K, double xmax, in
   if (!a_re_im) return fail(REXI_EINVAL, "NULL coefficient array");
   GaussFit f;
   if (!gauss_refit(mu, K, xmax, n_candidates, &f, max_err))
-    return fail(REXI_EINVAL, "refit needs mu < 0, 2L+1 <= K <= 100000, xmax > 0, K <= n_candidates <= 1e7");
+    return fail(REXI_EINVAL,
+                "refit needs mu < 0, 2L+1 <= K <= 20000, xmax > 0, K <= n_candidates <= 1e6, K n_candidates <= 5e8");
   fit_to_array(f, a_re_im);
   return REXI_OK;
 }

@@ -148,8 +148,9 @@ bool lstsq_qr(int m, int n, const std::vector<double>& A0, const std::vector<dou
 }  // namespace
 
 bool gauss_refit(double mu, int K, double xmax, int n_candidates, GaussFit* out, double* max_err) {
-  if (!(mu < 0.0) || !isfinite(mu) || K < kCols || K > 100000 || !(xmax > 0.0) || !isfinite(xmax) ||
-      n_candidates < K || n_candidates > 10000000)
+  // the Leja selection costs K x n_candidates logarithms: keep a call to seconds
+  if (!(mu < 0.0) || !isfinite(mu) || K < kCols || K > 20000 || !(xmax > 0.0) || !isfinite(xmax) ||
+      n_candidates < K || n_candidates > 1000000 || (double)K * (double)n_candidates > 5e8)
     return false;
   const std::vector<double> x = leja(K, xmax, n_candidates);
   std::vector<double> a((size_t)K * kCols), b(K), scale(kCols, 0.0), y;

@@ -160,6 +160,7 @@ def test_library_refit_rejects_bad_arguments(lib):
     assert lib.rexi_gaussian_refit(-5.0, 10, 40.0, 20001, arr, ctypes.byref(err)) == rexi.REXI_EINVAL
     assert lib.rexi_gaussian_refit(-5.0, 200, 40.0, 100, arr, ctypes.byref(err)) == rexi.REXI_EINVAL
     assert lib.rexi_gaussian_refit(-5.0, 200, 40.0, 20001, None, ctypes.byref(err)) == rexi.REXI_EINVAL
+    assert lib.rexi_gaussian_refit(-5.0, 20000, 40.0, 1000000, arr, ctypes.byref(err)) == rexi.REXI_EINVAL
 
 
 def test_alu_probe_rejects_bad_arguments(lib):
