@@ -43,12 +43,14 @@ METRIC = "grid-points×poles solved/sec and HBM GB/s vs roofline at stated error
 UNIT = "grid-points*poles/s"
 
 # Per-term work of the pole-sum loops, counted from the kernel source
-# (csrc/pole_common.cuh).  mixed: 73 FP32 arithmetic instructions per term, 12
-# of them FFMA -> 85 flops; fp64: 8 DFMA + 1 DADD -> 17 flops.  One MUFU
-# reciprocal seed per term in both.  The sum runs once per orbit of omega's
-# symmetries ((+-kx, +-ky) and kx <-> ky on the square grid).
-FLOPS_PER_TERM = {"mixed": 85, "fp64": 17}
-FP32_INSTR_PER_TERM = 73
+# (csrc/pole_common.cuh).  mixed: 63 FP32 arithmetic instructions per term (14
+# of them FFMA) plus the renormalisation of both accumulators every 16 terms
+# (6 / 16) -> 63.375 operations, 77.375 flops; besides these, one FMNMX pair
+# and the MUFU reciprocal seed.  fp64: 8 DFMA + 1 DADD -> 17 flops, one MUFU
+# seed.  The sum runs once per orbit of omega's symmetries ((+-kx, +-ky) and
+# kx <-> ky on the square grid).
+FLOPS_PER_TERM = {"mixed": 77.375, "fp64": 17}
+FP32_INSTR_PER_TERM = 63.375
 FP64_INSTR_PER_TERM = 9
 # Peaks for ALU-bound kernels, derived from unit counts and the maximum clock:
 # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz; FP64 from the nominal
@@ -60,7 +62,7 @@ PEAK_FP64_TFLOPS = 1.25
 # DRAM traffic per launch of the pole-sum kernel and of the combine pass from
 # ncu captures on the 2048^2 grid (the traffic does not depend on the term
 # count); None where no capture of the current kernel exists.
-NCU_POLE_TRAFFIC_BYTES = {"mixed": 285440 + 5632, "fp64": None}  # 2048^2, tau rho = 1000 (one-pass capture)
+NCU_POLE_TRAFFIC_BYTES = {"mixed": None, "fp64": None}  # 2048^2, tau rho = 1000 (one-pass capture)
 NCU_COMBINE_TRAFFIC_BYTES = None
 
 
@@ -616,13 +618,13 @@ def pole_roofline(form, pole_ms, orbits, nterms, peaks):
     terms = orbits * nterms
     t_pole = pole_ms / 1e3
     if form == "mixed":
-        # every FP32 arithmetic operation counted once (61 of the 73 operations
-        # per term are single-flop FADD/FMUL), against FP32 lane operations per
-        # second: the measured FFMA rate in lane operations (flops / 2)
+        # every FP32 arithmetic operation counted once (49 of the 63 per term
+        # are single-flop FADD/FMUL), against FP32 lane operations per second:
+        # the measured FFMA rate in lane operations (flops / 2)
         ops = terms * FP32_INSTR_PER_TERM
         peak_meas = peaks["fp32"]["lane_ops_per_s"] / 1e12 if peaks else None
         peak_derived = SMS * 128 * SM_MAX_GHZ / 1e3
-        conv = "FP32 operations per launch (FADD/FMUL/FFMA each 1; 73 per term) per second, vs the measured FFMA " \
+        conv = "FP32 operations per launch (FADD/FMUL/FFMA each 1; 63.375 per term) per second, vs the measured FFMA " \
                "lane-operation rate (rexi_alu_probe)"
     else:
         ops = terms * FP64_INSTR_PER_TERM

@@ -38,7 +38,7 @@ struct InstDesc {
   int half_ok, pad2;      // 1: even nx, real transforms along x available
   const float4* halfdf_x;  // half angles as double-float pairs
   const float4* halfdf_y;
-  double inv_dx, inv_dy, tau, q, R0re, R0im, grid;
+  double inv_dx, inv_dy, tau, q, R0re, R0im, grid, inv_grid;  // grid: a power of 2 (inv_grid exact)
   float q_hi, q_lo;
   int exact_hn;  // mixed table: every h n on the split grid
   long long table_off;  // first table entry (3 x 16 bytes per term)
@@ -146,7 +146,7 @@ __global__ void batch_pole_kernel(OrbitScalars* orb, const InstDesc* __restrict_
     for (int u = 0; u < PPT; ++u) {
       ar[u] = ai[u] = 0.0;
       arh[u] = arl[u] = aih[u] = ail[u] = 0.f;
-      const double xg = rint(x[u] / D.grid) * D.grid;
+      const double xg = rint(x[u] * D.inv_grid) * D.grid;
       Xh[u] = (float)xg;
       Xl[u] = (float)(x[u] - xg);
       Xl2[u] = (float)((x[u] - xg) - (double)Xl[u]);
@@ -164,17 +164,9 @@ __global__ void batch_pole_kernel(OrbitScalars* orb, const InstDesc* __restrict_
 #pragma unroll
           for (int u = 0; u < PPT; ++u) fp64_term(sd + 3 * t, x[u], D.q, ar[u], ai[u]);
       } else if (D.exact_hn) {
-#pragma unroll 2
-        for (int t = 0; t < cnt; ++t)
-#pragma unroll
-          for (int u = 0; u < PPT; ++u)
-            df_term<true>(st + 3 * t, Xh[u], Xl[u], Xl2[u], D.q_hi, D.q_lo, arh[u], arl[u], aih[u], ail[u]);
+        df_terms<true, PPT>(st, cnt, Xh, Xl, Xl2, D.q_hi, D.q_lo, arh, arl, aih, ail);
       } else {
-#pragma unroll 2
-        for (int t = 0; t < cnt; ++t)
-#pragma unroll
-          for (int u = 0; u < PPT; ++u)
-            df_term<false>(st + 3 * t, Xh[u], Xl[u], Xl2[u], D.q_hi, D.q_lo, arh[u], arl[u], aih[u], ail[u]);
+        df_terms<false, PPT>(st, cnt, Xh, Xl, Xl2, D.q_hi, D.q_lo, arh, arl, aih, ail);
       }
     }
 #pragma unroll
@@ -538,6 +530,7 @@ rexi_status rexi_batch_create(rexi_batch_t* out, int32_t n, const int32_t* nx, c
     int gexp = 0;
     while (ldexp(1.0, 23 - gexp) > span && gexp < 60) ++gexp;
     D.grid = ldexp(1.0, -(gexp - 1));
+    D.inv_grid = ldexp(1.0, gexp - 1);
     D.exact_hn = 1;
     double R0r = 0, R0i = 0;
     for (int nn = -N; nn <= N; ++nn) {

@@ -44,6 +44,7 @@
 
 #include "internal.h"
 #include "krylov.h"
+#include "partials.cuh"
 
 namespace rexi {
 
@@ -142,9 +143,7 @@ __device__ __forceinline__ bool last_block_total(double mine, double* partials, 
   __syncthreads();
   if (!is_last) return false;  // uniform across the block
   __threadfence();
-  const volatile double* vp = partials;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < ntiles; i += THREADS) s += vp[i];
+  double s = strided_partial_sum(partials, ntiles, threadIdx.x, THREADS, 0.0, [](double a, double b) { return a + b; });
   s = block_sum(s, red);
   if (threadIdx.x == 0) {
     *total = s;

@@ -44,6 +44,7 @@
 #include "dfloat.cuh"
 #include "internal.h"
 #include "krylov.h"
+#include "partials.cuh"
 
 namespace rexi {
 namespace {
@@ -100,12 +101,8 @@ __device__ __forceinline__ bool llast_block2(double2 mine, double2* partials, un
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
-  const volatile double2* vp = partials;
-  double2 s = make_double2(0.0, 0.0);
-  for (int i = threadIdx.x; i < ntiles; i += THREADS) {
-    s.x += vp[i].x;
-    s.y += vp[i].y;
-  }
+  double2 s = strided_partial_sum(partials, ntiles, threadIdx.x, THREADS, make_double2(0.0, 0.0),
+                                  [](double2 a, double2 b) { return ladd(a, b); });
   s = lblock_sum2(s, red);
   if (threadIdx.x == 0) {
     *total = s;
@@ -422,9 +419,8 @@ __device__ __forceinline__ bool llast_block_df(float2 mine, float2* partials, un
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
-  const volatile float2* vp = partials;
-  float2 s = make_float2(0.f, 0.f);
-  for (int i = threadIdx.x; i < ntiles; i += THREADS) s = df_add(s, make_float2(vp[i].x, vp[i].y));
+  float2 s = strided_partial_sum(partials, ntiles, threadIdx.x, THREADS, make_float2(0.f, 0.f),
+                                 [](float2 a, float2 b) { return df_add(a, b); });
   s = df_block_reduce(s, red);
   if (threadIdx.x == 0) {
     *total = df_to(s);

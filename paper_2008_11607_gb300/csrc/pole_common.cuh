@@ -407,6 +407,36 @@ __device__ __forceinline__ void fp64_term(const double2* e, double x, double q, 
   acci = fma(fma(e2.x, y, e1.x), r, acci);
 }
 
+// acc += (a + b y) / d for one real component of a term, every quantity an
+// FP32 (hi, lo) pair: a = (a_h, a_l), b = (b_h, b_l), y = (y_h, y_l),
+// d = (d_h, d_l); r0 is an FP32 approximation of 1 / d_h (within one unit in
+// the last place).  The quotient's high word is T_h = n_h r0 and its low word
+// the remainder (n - T_h d) r0: n_h - T_h d_h is of order 2^-23 n_h and the
+// FMA forms it to FP32 precision, so the low word is correct to about 2^-46
+// of the quotient without a refined reciprocal.  The low word goes straight
+// into the accumulator's low word (two roundings there per term).
+__device__ __forceinline__ void df_quot_acc(float b_h, float b_l, float a_h, float a_l, float y_h, float y_l,
+                                            float d_h, float d_l, float r0, float& acc_h, float& acc_l) {
+  const float t_h = __fmul_rn(b_h, y_h);
+  const float t_l = __fmaf_rn(b_h, y_h, -t_h);
+  float n_h, n_e;
+  two_sum(a_h, t_h, n_h, n_e);
+  const float n_l = __fadd_rn(__fadd_rn(n_e, t_l), __fmaf_rn(b_h, y_l, __fmaf_rn(b_l, y_h, a_l)));
+  const float T_h = __fmul_rn(n_h, r0);
+  const float rem = __fmaf_rn(-T_h, d_l, __fadd_rn(__fmaf_rn(-T_h, d_h, n_h), n_l));
+  float s, e;
+  two_sum(acc_h, T_h, s, e);
+  acc_h = s;
+  acc_l = __fmaf_rn(rem, r0, __fadd_rn(acc_l, e));
+}
+
+// The accumulators' low words take two FP32 roundings per term and are not
+// renormalised by the term itself; every kRenorm terms a FastTwoSum folds
+// them back below half a unit of the high word, so that a low word never
+// exceeds about kRenorm units of the partial sum's last place.
+constexpr int kRenorm = 16;
+__device__ __forceinline__ void df_renorm(float& h, float& l) { fast_two_sum(h, l, h, l); }
+
 // One scalar REXII term in double-float arithmetic (see pole_fft.cu).
 // x is split as X_hi (a multiple of the table's grid G) + X_lo + X_lo2 (FP32).
 // acc += (A + B y) / (q + y^2) with every quantity an FP32 (hi, lo) pair.
@@ -433,46 +463,50 @@ __device__ __forceinline__ void df_term(const float4* ent, float X_hi, float X_l
     fast_two_sum(__fadd_rn(X_hi, e0.x), s_h, y_h, y_l);
     y_l = __fadd_rn(y_l, __fadd_rn(__fadd_rn(X_lo2, s_e), e2.z));  // e2.z: what hn_lo leaves of h n
   }
-  // d = q + y^2
+  // d = q + y^2: both parts are >= 0, so ordering them by size makes the
+  // (error-free) FastTwoSum apply
   const float p_h = __fmul_rn(y_h, y_h);
   const float p_l = __fmaf_rn(y_h, y_h, -p_h);
   float d_h, d_e;
-  two_sum(q_hi, p_h, d_h, d_e);
+  fast_two_sum(fmaxf(q_hi, p_h), fminf(q_hi, p_h), d_h, d_e);
   const float d_l = __fadd_rn(__fadd_rn(d_e, p_l), __fmaf_rn(2.0f * y_h, y_l, q_lo));
-  // r = 1/d: FP32 seed, one Newton-Raphson correction carried in the low part
   const float r0 = rcp_approx_f32(d_h);
-  float tcorr = __fmaf_rn(-d_h, r0, 1.0f);
-  tcorr = __fmaf_rn(-d_l, r0, tcorr);
-  const float r_l = __fmul_rn(r0, tcorr);
-  // N = A + B y (real and imaginary parts), then T = N r, acc += T
-  {
-    const float t_h = __fmul_rn(e0.w, y_h);
-    const float t_l = __fmaf_rn(e0.w, y_h, -t_h);
-    const float cross = __fmaf_rn(e0.w, y_l, __fmul_rn(e1.w, y_h));
-    float n_h, n_e;
-    two_sum(e0.y, t_h, n_h, n_e);
-    const float n_l = __fadd_rn(__fadd_rn(n_e, t_l), __fadd_rn(cross, e1.y));
-    const float T_h = __fmul_rn(n_h, r0);
-    const float T_l = __fadd_rn(__fmaf_rn(n_h, r0, -T_h), __fmaf_rn(n_h, r_l, __fmul_rn(n_l, r0)));
-    float s, e;
-    two_sum(ar_h, T_h, s, e);
-    ar_h = s;
-    ar_l = __fadd_rn(ar_l, __fadd_rn(e, T_l));
+  // real and imaginary parts: A = (Ar, Ai), B = (Br, Bi)
+  df_quot_acc(e0.w, e1.w, e0.y, e1.y, y_h, y_l, d_h, d_l, r0, ar_h, ar_l);
+  df_quot_acc(e1.x, e2.x, e0.z, e1.z, y_h, y_l, d_h, d_l, r0, ai_h, ai_l);
+}
+
+// acc += terms [0, cnt) of a staged table chunk for PPT values of x, with the
+// accumulators renormalised every kRenorm terms and at the end.
+template <bool EXACT_HN, int PPT>
+__device__ __forceinline__ void df_terms(const float4* st, int cnt, const float (&X_hi)[PPT],
+                                         const float (&X_lo)[PPT], const float (&X_lo2)[PPT], float q_hi,
+                                         float q_lo, float (&ar_h)[PPT], float (&ar_l)[PPT], float (&ai_h)[PPT],
+                                         float (&ai_l)[PPT]) {
+  int t = 0;
+  for (; t + kRenorm <= cnt; t += kRenorm) {
+#pragma unroll 4
+    for (int k = 0; k < kRenorm; ++k)
+#pragma unroll
+      for (int u = 0; u < PPT; ++u)
+        df_term<EXACT_HN>(st + 3 * (t + k), X_hi[u], X_lo[u], X_lo2[u], q_hi, q_lo, ar_h[u], ar_l[u], ai_h[u],
+                          ai_l[u]);
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) {
+      df_renorm(ar_h[u], ar_l[u]);
+      df_renorm(ai_h[u], ai_l[u]);
+    }
   }
-  {
-    const float t_h = __fmul_rn(e1.x, y_h);
-    const float t_l = __fmaf_rn(e1.x, y_h, -t_h);
-    const float cross = __fmaf_rn(e1.x, y_l, __fmul_rn(e2.x, y_h));
-    float n_h, n_e;
-    two_sum(e0.z, t_h, n_h, n_e);
-    const float n_l = __fadd_rn(__fadd_rn(n_e, t_l), __fadd_rn(cross, e1.z));
-    const float T_h = __fmul_rn(n_h, r0);
-    const float T_l = __fadd_rn(__fmaf_rn(n_h, r0, -T_h), __fmaf_rn(n_h, r_l, __fmul_rn(n_l, r0)));
-    float s, e;
-    two_sum(ai_h, T_h, s, e);
-    ai_h = s;
-    ai_l = __fadd_rn(ai_l, __fadd_rn(e, T_l));
+  for (; t < cnt; ++t)
+#pragma unroll
+    for (int u = 0; u < PPT; ++u)
+      df_term<EXACT_HN>(st + 3 * t, X_hi[u], X_lo[u], X_lo2[u], q_hi, q_lo, ar_h[u], ar_l[u], ai_h[u], ai_l[u]);
+#pragma unroll
+  for (int u = 0; u < PPT; ++u) {
+    df_renorm(ar_h[u], ar_l[u]);
+    df_renorm(ai_h[u], ai_l[u]);
   }
 }
+
 
 }  // namespace rexi

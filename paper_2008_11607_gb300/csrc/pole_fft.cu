@@ -145,8 +145,9 @@ template <int PPT, bool EXACT_HN>
 __global__ void __launch_bounds__(kOrbitThreads) pole_orbit_mixed_kernel(double2* __restrict__ part, SymbolParams sp,
                                                                          OrbitParams op,
                                                                          const float4* __restrict__ table,
-                                                                         FusedScalars fs, double grid, float q_hi,
-                                                                         float q_lo, int slices) {
+                                                                         FusedScalars fs, double grid,
+                                                                         double inv_grid, float q_hi, float q_lo,
+                                                                         int slices) {
   __shared__ float4 st[kChunk * 3];
   float X_hi[PPT], X_lo[PPT], X_lo2[PPT], ar_h[PPT], ar_l[PPT], ai_h[PPT], ai_l[PPT];
   int o[PPT];
@@ -156,7 +157,7 @@ __global__ void __launch_bounds__(kOrbitThreads) pole_orbit_mixed_kernel(double2
     int a = 0, b = 0;
     if (o[u] < op.norb) orbit_rep(op, o[u], a, b);
     const double x = fs.tau * symbol_at(sp, a, b).omega;
-    const double xg = rint(x / grid) * grid;
+    const double xg = rint(x * inv_grid) * grid;  // grid a power of 2: x * (1/grid) is exact
     X_hi[u] = (float)xg;
     X_lo[u] = (float)(x - xg);
     X_lo2[u] = (float)((x - xg) - (double)X_lo[u]);
@@ -169,11 +170,7 @@ __global__ void __launch_bounds__(kOrbitThreads) pole_orbit_mixed_kernel(double2
     __syncthreads();
     for (int i = threadIdx.x; i < cnt * 3; i += blockDim.x) st[i] = table[(size_t)t0 * 3 + i];
     __syncthreads();
-#pragma unroll 2
-    for (int t = 0; t < cnt; ++t)
-#pragma unroll
-      for (int u = 0; u < PPT; ++u)
-        df_term<EXACT_HN>(st + 3 * t, X_hi[u], X_lo[u], X_lo2[u], q_hi, q_lo, ar_h[u], ar_l[u], ai_h[u], ai_l[u]);
+    df_terms<EXACT_HN, PPT>(st, cnt, X_hi, X_lo, X_lo2, q_hi, q_lo, ar_h, ar_l, ai_h, ai_l);
   }
 #pragma unroll
   for (int u = 0; u < PPT; ++u)
@@ -300,14 +297,15 @@ cudaError_t pole_orbits_mixed(double2* part, int slices, const SymbolParams& sp,
                               const float* table, const FusedScalars& fs, double grid_step, cudaStream_t s) {
   const float q_hi = (float)fs.q;
   const float q_lo = (float)(fs.q - (double)q_hi);
+  const double inv_step = 1.0 / grid_step;  // exact: the split grid is a power of 2
   const int per_block = kOrbitThreads * kOrbitPPT;
   dim3 grid((unsigned)((op.norb + per_block - 1) / per_block), (unsigned)slices);
   if (fs.exact_hn)
     pole_orbit_mixed_kernel<kOrbitPPT, true><<<grid, kOrbitThreads, 0, s>>>(
-        part, sp, op, reinterpret_cast<const float4*>(table), fs, grid_step, q_hi, q_lo, slices);
+        part, sp, op, reinterpret_cast<const float4*>(table), fs, grid_step, inv_step, q_hi, q_lo, slices);
   else
     pole_orbit_mixed_kernel<kOrbitPPT, false><<<grid, kOrbitThreads, 0, s>>>(
-        part, sp, op, reinterpret_cast<const float4*>(table), fs, grid_step, q_hi, q_lo, slices);
+        part, sp, op, reinterpret_cast<const float4*>(table), fs, grid_step, inv_step, q_hi, q_lo, slices);
   return cudaGetLastError();
 }
 

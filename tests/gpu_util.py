@@ -45,7 +45,7 @@ TOL = {"fp64": 1e-10, "plain": 1e-10, "mixed": 1e-8}
 # REXII terms T_n(x) = (c1_n h mu + c2_n (x + h n)) / ((h mu)^2 + (x + h n)^2)
 # (eq. modifiedRexi).  B(k) is normal for H = g (skew-Hermitian), so by
 # Theorem 1 with cond = 1 the per-wavenumber error is at most
-#   eps_r + delta_pole  (relative to |fhat(k)|)  plus  delta_fft rms(fhat),
+#   eps_r + delta_pole  (relative to |fhat(k)|)  plus  delta_fft max_k |fhat(k)|,
 # * eps_r = max_{|x| <= tau rho} |r(ix) - e^{ix}|: the approximation error,
 #   evaluated by the oracle on a 0.02-spaced grid (r varies on the scale of the
 #   pole distance h|mu| ~ 2.6), times 1.25;
@@ -57,11 +57,16 @@ TOL = {"fp64": 1e-10, "plain": 1e-10, "mixed": 1e-8}
 #   probability at most 2 exp(-lam^2 / 2); lam = 8 (< 3e-14 per evaluation).
 #   FP64 form: u = 2^-53, kt = 4 (rcp seed, two-term correction, two fma),
 #   ks = 1.  Double-float form: u = 2^-48 (the pair's unit roundoff u32^2),
-#   kt = 8 (the FP32 reciprocal seed, 2^-23, squared by the one Newton step
-#   gives 4u; four dropped lo*lo products), ks = 4 (two FP32 roundings of the
-#   low word, each below u32 times a low word of at most u32 |S_k|).  The
-#   partial sums run over contiguous term ranges, so sqrt(sum |S_k|^2) is
-#   bounded by 2 sqrt(n) max_k |cumulative sum|.
+#   kt = 20: the quotient's low word is the remainder (n - T_h d) times the
+#   FP32 reciprocal seed r0, so r0's error (<= 2 u32) times the remainder
+#   (<= 1.5 u32 |T|) gives 6u, the remainder's three FP32 roundings 9u, and
+#   the low words of numerator and denominator about 4u; ks = 20: the
+#   accumulator's low word takes two FP32 roundings per term and grows by at
+#   most u32 max|S| per term between renormalisations (every 16 terms), so the
+#   k-th term after one adds at most (2k + 1) u max|S|, whose root mean square
+#   over a block of 16 is 18.5.  The partial sums run over contiguous term
+#   ranges, so sqrt(sum |S_k|^2) is bounded by 2 sqrt(n) max_k |cumulative
+#   sum|.
 # * delta_fft: the forward and inverse transforms (the library's and the
 #   check's), lam kf u log2(nx ny) of the LARGEST wavenumber amplitude, kf = 8:
 #   the butterflies spread the rounding of the large modes over every output,
@@ -70,7 +75,7 @@ TOL = {"fp64": 1e-10, "plain": 1e-10, "mixed": 1e-8}
 #   is Hermitian only to 1.2e-13 of the rms, 1.3e-16 of the largest mode).
 # ---------------------------------------------------------------------------
 
-_FORM_ROUNDING = {"fp64": (2.0 ** -53, 4.0, 1.0, 8.0), "mixed": (2.0 ** -48, 8.0, 4.0, 8.0),
+_FORM_ROUNDING = {"fp64": (2.0 ** -53, 4.0, 1.0, 8.0), "mixed": (2.0 ** -48, 20.0, 20.0, 8.0),
                   "plain": (2.0 ** -53, 8.0, 1.0, 8.0)}
 _LAM = 8.0
 
