@@ -62,8 +62,12 @@ PEAK_FP64_TFLOPS = 1.25
 # DRAM traffic per launch of the pole-sum kernel and of the combine pass from
 # ncu captures on the 2048^2 grid (the traffic does not depend on the term
 # count); None where no capture of the current kernel exists.
-NCU_POLE_TRAFFIC_BYTES = {"mixed": None, "fp64": None}  # 2048^2, tau rho = 1000 (one-pass capture)
+NCU_POLE_TRAFFIC_BYTES = {"mixed": 284416 + 32000, "fp64": None}  # 2048^2, tau rho = 1000 (one-pass capture)
 NCU_COMBINE_TRAFFIC_BYTES = None
+# the forward double-float transform of real input at 2048^2 (fft_rows_r2c_kernel
+# + fft_cols_kernel, one launch each; --set full capture of the current
+# kernels): DRAM bytes read + written by the two launches
+NCU_FFT_FWD_TRAFFIC_BYTES = (201429760 + 67403520) + (100838144 + 46498560)
 
 
 def orbit_count(n):
@@ -610,7 +614,7 @@ def adjoint_measure(torch, rexi, inputs, form="mixed", n=512, steps=8, tau_rho=2
     }
 
 
-def pole_roofline(form, pole_ms, orbits, nterms, peaks):
+def pole_roofline(form, pole_ms, orbits, nterms, peaks, traffic=None):
     """Roofline of the pole-sum kernel: executed orbit-terms per launch x
     operations per term over its launch time, against the measured
     multiply-add rate (and, beside it, the lane rate derived from unit counts
@@ -646,7 +650,7 @@ def pole_roofline(form, pole_ms, orbits, nterms, peaks):
     return {
         "kernel": "pole_orbit_%s_kernel" % form,
         "bound": "alu", "achieved": achieved, "peak": peak, "unit": "T op/s", "frac": achieved / peak,
-        "traffic": NCU_POLE_TRAFFIC_BYTES.get(form),
+        "traffic": traffic,
         "flop_convention": conv,
         "peak_source": source,
         "peak_derived_lane_rate": peak_derived, "frac_of_derived": achieved / peak_derived,
@@ -701,7 +705,8 @@ def run_ours(args):
     peaks = None
     if not args.skip_peaks:
         peaks = alu_peaks(torch, rexi, gpu_id)
-    roofline = pole_roofline(args.form, pole_ms, orbits, nterms, peaks)
+    roofline = pole_roofline(args.form, pole_ms, orbits, nterms, peaks,
+                             traffic=NCU_POLE_TRAFFIC_BYTES.get(args.form) if D == 2048 else None)
     phases = {"forward_fft_ms": ms_phase[0] / max(ncalls, 1), "pole_sum_ms": pole_ms, "combine_ms": combine_ms,
               "inverse_fft_ms": ms_phase[2] / max(ncalls, 1), "table_upload_ms": ms_phase[3] / max(ncalls, 1),
               "profiled_ms_per_rexii_step": ms_prof / len(states)}
@@ -719,7 +724,8 @@ def run_ours(args):
     hbm_peak = mp.get("hbm_gbs", 6800.0)
     roofline_fft = {"kernel": "fft_rows_r2c_kernel + fft_cols_kernel (forward)", "bound": "hbm",
                     "achieved": fwd_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": fwd_gbs / hbm_peak,
-                    "traffic": None,
+                    "traffic": NCU_FFT_FWD_TRAFFIC_BYTES if (D == 2048 and args.form == "mixed") else None,
+                    "algorithmic_bytes": fft_bytes,
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in mp else "fallback 6.8 TB/s"}
     # combine pass: reads and writes the 3-field half spectrum (96 B per
     # wavenumber); the per-orbit scalars it also reads are L2-resident and not
