@@ -43,14 +43,15 @@ METRIC = "grid-points×poles solved/sec and HBM GB/s vs roofline at stated error
 UNIT = "grid-points*poles/s"
 
 # Per-term work of the pole-sum loops, counted from the kernel source
-# (csrc/pole_common.cuh).  mixed: 63 FP32 arithmetic instructions per term (14
-# of them FFMA) plus the renormalisation of both accumulators every 16 terms
-# (6 / 16) -> 63.375 operations, 77.375 flops; besides these, one FMNMX pair
-# and the MUFU reciprocal seed.  fp64: 8 DFMA + 1 DADD -> 17 flops, one MUFU
+# (csrc/pole_common.cuh).  mixed (h n on the split grid, as at h = 0.5): 62
+# FP32 arithmetic instructions per term (14 of them FFMA) plus the
+# renormalisation of both accumulators every 16 terms (6 / 16) -> 62.375
+# operations, 76.375 flops; besides these, one FMNMX pair and the MUFU
+# reciprocal seed.  fp64: 8 DFMA + 1 DADD -> 17 flops, one MUFU
 # seed.  The sum runs once per orbit of omega's symmetries ((+-kx, +-ky) and
 # kx <-> ky on the square grid).
-FLOPS_PER_TERM = {"mixed": 77.375, "fp64": 17}
-FP32_INSTR_PER_TERM = 63.375
+FLOPS_PER_TERM = {"mixed": 76.375, "fp64": 17}
+FP32_INSTR_PER_TERM = 62.375
 FP64_INSTR_PER_TERM = 9
 # Peaks for ALU-bound kernels, derived from unit counts and the maximum clock:
 # 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz; FP64 from the nominal
@@ -622,13 +623,13 @@ def pole_roofline(form, pole_ms, orbits, nterms, peaks, traffic=None):
     terms = orbits * nterms
     t_pole = pole_ms / 1e3
     if form == "mixed":
-        # every FP32 arithmetic operation counted once (49 of the 63 per term
+        # every FP32 arithmetic operation counted once (48 of the 62 per term
         # are single-flop FADD/FMUL), against FP32 lane operations per second:
         # the measured FFMA rate in lane operations (flops / 2)
         ops = terms * FP32_INSTR_PER_TERM
         peak_meas = peaks["fp32"]["lane_ops_per_s"] / 1e12 if peaks else None
         peak_derived = SMS * 128 * SM_MAX_GHZ / 1e3
-        conv = "FP32 operations per launch (FADD/FMUL/FFMA each 1; 63.375 per term) per second, vs the measured FFMA " \
+        conv = "FP32 operations per launch (FADD/FMUL/FFMA each 1; 62.375 per term) per second, vs the measured FFMA " \
                "lane-operation rate (rexi_alu_probe)"
     else:
         ops = terms * FP64_INSTR_PER_TERM

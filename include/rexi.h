@@ -83,10 +83,14 @@ typedef struct {
   int32_t n_poles;    /* single-shift poles J: 2(N + 1) or 2(2N + 1) */
   double tau_rho;     /* dt * rho(A) */
   double rho;         /* spectral radius used */
-  int32_t krylov_iters;        /* Krylov path: largest iteration count over terms */
+  int32_t krylov_iters;        /* Krylov path: largest iteration count over terms
+                                  (shared method: Lanczos steps of the basis) */
   int32_t krylov_unconverged;  /* Krylov path: terms that hit the iteration cap */
-  double krylov_max_rel_res;   /* Krylov path: largest final relative residual */
-  int64_t krylov_term_iters;   /* Krylov path: CG iterations summed over all terms */
+  double krylov_max_rel_res;   /* Krylov path: largest final relative residual
+                                  (shared method: the step's error bound) */
+  int64_t krylov_term_iters;   /* Krylov path: CG iterations summed over all terms
+                                  (shared method: Lanczos steps run in the first
+                                  pass, a multiple of the check interval) */
 } rexi_step_info;
 
 /* ------------------------------------------------------------------------ */

@@ -671,6 +671,7 @@ rexi_status rexi_batch_step(rexi_batch_t b, const void* in, void* out, int32_t r
       FusedScalars fs;
       fs.tau = D.tau; fs.q = D.q; fs.R0re = D.R0re; fs.R0im = half ? 0.0 : D.R0im; fs.nterms = D.nterms;
       fs.adjoint = 0;
+      fs.exact_hn = D.exact_hn;  // the instance's table: whether every h n lies on its split grid
       const float* tab = static_cast<const float*>(b->d_tables) + D.table_off * 12;
       // the single-instance kernels, term slices as rexi_step chooses them
       OrbitParams op;

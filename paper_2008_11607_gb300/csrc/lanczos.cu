@@ -53,6 +53,10 @@ constexpr int TX = 32, TY = 16, THREADS = 256, HX = TX + 2, HY = TY + 2;
 constexpr int kChunk = 16;         // Lanczos steps between convergence checks
 constexpr int kCoarse = 8;         // coarse check: every 8th sample of the fine grid
 constexpr int kMinScratchPoles = 32;
+// Threads per block of the per-pole recurrences (one thread per pole, a
+// chain of dependent FP64 operations each): one warp per block spreads the
+// poles over as many SMs, and so FP64 pipes, as there are warps.
+constexpr int kPoleThreads = 32;
 
 struct LGeom {
   int nx, ny, tiles_x, tiles_y;
@@ -224,10 +228,11 @@ __global__ void __launch_bounds__(THREADS) lz_step(LGeom G, int j, const T* __re
                                                    const T* __restrict__ vprev, T* __restrict__ vout,
                                                    T* __restrict__ wout, double* alpha,
                                                    double* beta, double* invb, double2* partials, unsigned* counter,
-                                                   T* acc, const double2* cvec) {
+                                                   T* acc, const double2* cvec, const unsigned* stop) {
   constexpr bool CPLX = sizeof(T) == sizeof(double2);
   __shared__ T E[HY][HX], U[HY][HX], V[HY][HX];
   __shared__ double2 red[THREADS / 32];
+  if (MODE == 0 && stop && *stop) return;  // the recurrence already met its bound
   const double bj = beta[j];
   const double sc = invb[j];
   const double am = (CPLX && j > 0) ? alpha[j - 1] : 0.0;
@@ -302,11 +307,13 @@ template <int MODE>
 __global__ void __launch_bounds__(THREADS) lz_wstep(LGeom G, int j, const double* __restrict__ wm1,
                                                     const double* __restrict__ wm2, double* __restrict__ wout,
                                                     double* alpha, double* beta, double* invb, double2* partials,
-                                                    unsigned* counter, double* acc, const double* coef) {
+                                                    unsigned* counter, double* acc, const double* coef,
+                                                    const unsigned* stop) {
   __shared__ double E[HY][HX], U[HY][HX], V[HY][HX];
   __shared__ double2 red[THREADS / 32];
   __shared__ StencilCoef cfs;
   __shared__ double r2s;
+  if (MODE == 0 && stop && *stop) return;  // the recurrence already met its bound
   if (threadIdx.x == 0) {  // step scalars, once per block
     const double sc = invb[j];
     cfs.cdx = -sc * G.tdx;
@@ -407,9 +414,9 @@ __device__ __forceinline__ float2 df_block_reduce(float2 v, float2* red) {
 }
 
 // Deterministic cross-block double-float sum (fixed order) finished by the
-// last block; returns true in that block's thread 0 with *total (FP64).
+// last block; returns true in that block's thread 0 with *total.
 __device__ __forceinline__ bool llast_block_df(float2 mine, float2* partials, unsigned* counter, int ntiles, int tile,
-                                               double* total, float2* red) {
+                                               float2* total, float2* red) {
   __shared__ bool is_last;
   if (threadIdx.x == 0) {
     partials[tile] = mine;
@@ -423,19 +430,21 @@ __device__ __forceinline__ bool llast_block_df(float2 mine, float2* partials, un
                                  [](float2 a, float2 b) { return df_add(a, b); });
   s = df_block_reduce(s, red);
   if (threadIdx.x == 0) {
-    *total = df_to(s);
+    *total = s;
     *counter = 0u;
   }
   return threadIdx.x == 0;
 }
 
 // Double-float coefficients of step j (computed once, by the reduction that
-// produces b_j): the stencil coefficients times -1 / b_j and r2 = b_j / b_{j-1}.
+// produces b_j): the stencil coefficients times -1 / b_j, r2 = b_j / b_{j-1}
+// and 1 / b_j itself.
 struct DfCoef {
-  float2 cdx, cdy, cgdx, cgdy, cf4, r2;
+  float2 cdx, cdy, cgdx, cgdy, cf4, r2, ib;
 };
 __device__ __forceinline__ void df_coef_store(const LGeom& G, double ib, double r2, DfCoef* dst) {
   DfCoef c;
+  c.ib = df_from(ib);
   c.cdx = df_from(-ib * G.tdx);
   c.cdy = df_from(-ib * G.tdy);
   c.cgdx = df_from(-ib * G.tgdx);
@@ -443,6 +452,26 @@ __device__ __forceinline__ void df_coef_store(const LGeom& G, double ib, double 
   c.cf4 = df_from(-ib * G.tf4);
   c.r2 = df_from(r2);
   *dst = c;
+}
+
+// sqrt(s) and 1 / b for non-negative double-float values on the FP32 pipes:
+// a correctly rounded FP32 root (reciprocal) and one correction from the
+// exact FMA residual (Markstein), within about 2^-48 of the result.  Zero
+// gives zero (1 / 0 too: b = 0 ends the recurrence); a NaN or an infinity in
+// s comes out non-finite.  On this GPU a dependent FP64 operation waits about
+// a hundred cycles, so the scalars at the end of each step stay off the FP64
+// pipe.
+__device__ __forceinline__ float2 df_sqrt(float2 s) {
+  if (s.x == 0.f) return make_float2(0.f, 0.f);
+  const float h = __fsqrt_rn(s.x);
+  const float e = __fadd_rn(__fmaf_rn(-h, h, s.x), s.y);  // s - h^2
+  return df_fast(h, __fdiv_rn(e, 2.f * h));
+}
+__device__ __forceinline__ float2 df_recip(float2 b) {
+  if (b.x == 0.f) return make_float2(0.f, 0.f);
+  const float r = __frcp_rn(b.x);
+  const float e = __fmaf_rn(-b.y, r, __fmaf_rn(-b.x, r, 1.f));  // 1 - b r
+  return df_fast(r, __fmul_rn(e, r));
 }
 
 __global__ void lz_df_tables(const double* H, const double* w, size_t nk, float2* Hdf, float2* wdf) {
@@ -514,7 +543,8 @@ __global__ void __launch_bounds__(THREADS, kDfStepBlocks) lz_dfstep(LGeom G, con
                                                      const float2* __restrict__ wm1, const float2* __restrict__ wm2,
                                                      float2* __restrict__ wout, double* alpha, double* beta,
                                                      double* invb, DfCoef* dfc, double2* partials,
-                                                     unsigned* counter, float2* acc, const float2* coef_df) {
+                                                     unsigned* counter, float2* acc, const float2* coef_df,
+                                                     const unsigned* stop) {
   constexpr int PPT = TX * TY / THREADS;  // interior points per thread
   __shared__ float2 E[HY][HX], U[HY][HX], V[HY][HX];
   __shared__ float2 red[THREADS / 32];
@@ -550,8 +580,12 @@ __global__ void __launch_bounds__(THREADS, kDfStepBlocks) lz_dfstep(LGeom G, con
       cp_async8(&V[lj][li], wm1 + id + 2 * G.fstride);
     }
   }
+  // read while the halo copies are in flight; a block leaves only after its
+  // copies have landed
+  const unsigned stopped = (MODE == 0 && stop) ? *stop : 0u;
   cp_async_wait_all();
   __syncthreads();
+  if (stopped) return;  // the recurrence already met its bound
   const DfCoef cf = dfc[j];
   const float2 cu = MODE == 1 ? coef_df[j] : z2;
   float2 nrm = z2;
@@ -590,13 +624,24 @@ __global__ void __launch_bounds__(THREADS, kDfStepBlocks) lz_dfstep(LGeom G, con
   }
   if (MODE != 0) return;
   const float2 bs = df_block_reduce(nrm, red);
-  double tot;
+  float2 tot;
   if (llast_block_df(bs, reinterpret_cast<float2*>(partials), counter, G.tiles_x * G.tiles_y,
                      blockIdx.y * G.tiles_x + blockIdx.x, &tot, red)) {
+    // b_{j+1} = ||W_j||_W and the next step's coefficients in double-float
+    // (the FP64 copies of b and 1 / b for the tridiagonal solves after them)
+    const float2 b = df_sqrt(tot), ib = df_recip(b), nib = df_neg(ib);
+    DfCoef c;
+    c.cdx = df_mul(nib, df_from_double(G.tdx));
+    c.cdy = df_mul(nib, df_from_double(G.tdy));
+    c.cgdx = df_mul(nib, df_from_double(G.tgdx));
+    c.cgdy = df_mul(nib, df_from_double(G.tgdy));
+    c.cf4 = df_mul(nib, df_from_double(G.tf4));
+    c.r2 = df_mul(b, cf.ib);
+    c.ib = ib;
+    dfc[j + 1] = c;
     alpha[j] = 0.0;
-    beta[j + 1] = sqrt(tot);
-    invb[j + 1] = safe_inv(beta[j + 1]);
-    df_coef_store(G, invb[j + 1], beta[j + 1] * invb[j], dfc + j + 1);
+    beta[j + 1] = df_to_double(b);
+    invb[j + 1] = df_to_double(ib);
   }
 }
 
@@ -701,17 +746,41 @@ __global__ void lz_finish(const T* acc, double2* out, const double* w, size_t nk
   out[i] = v;
 }
 
-__device__ __forceinline__ double2 cdivd(double2 a, double2 b) {
-  const double q = 1.0 / fma(b.x, b.x, b.y * b.y);
-  return make_double2(fma(a.x, b.x, a.y * b.y) * q, fma(a.y, b.x, -a.x * b.y) * q);
+// 1 / x for normal FP64 x: the hardware's approximate FP64 reciprocal r0 as
+// the seed, then r0 (1 + e + e^2) with e = 1 - x r0 (1 / x = r0 / (1 - e)),
+// which leaves a relative error of order e^3, below FP64 rounding: four
+// dependent operations, where a dependent FP64 operation on this GPU waits
+// about a hundred cycles.
+__device__ __forceinline__ double lrcp(double x) {
+  double r0;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r0) : "d"(x));
+  const double e = fma(-x, r0, 1.0);
+  return fma(r0, fma(e, e, e), r0);
 }
+// 1 / z for the pivots of the shifted tridiagonal systems (T_k + s_p): every
+// shift lies h |mu| from the line that holds the spectrum of T_k, and each
+// pivot d_j = a_j + s_p - b_j^2 / d_{j-1} keeps at least that distance (the
+// term -b_j^2 / d_{j-1} moves it away from the line, never towards it), so
+// |z|^2 is a normal number for lrcp.  The hardware seed and three FMAs
+// instead of an FP64 division, the longest step of the per-pole recurrences.
+__device__ __forceinline__ double2 crcp(double2 z) {
+  const double r = lrcp(fma(z.x, z.x, z.y * z.y));
+  return make_double2(z.x * r, -z.y * r);
+}
+__device__ __forceinline__ double2 cmuld(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
 
 // Per pole p: forward elimination of (T + s_p) over the new steps [j0, j1);
 // wy_p = weight_p * e_{j1-1}^T (T_{j1} + s_p)^{-1} e_0 = weight_p g / d.
+// `clear` (nullable): the two maxima of the check that follows, zeroed here.
 __global__ void lz_poles_advance(int np, const double2* s, const double2* wgt, const double* alpha,
-                                 const double* beta, int j0, int j1, double2* dg, double2* wy) {
+                                 const double* beta, int j0, int j1, double2* dg, double2* wy, const unsigned* stop,
+                                 unsigned long long* clear) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= np) return;
+  if (clear && p == 0) clear[0] = clear[1] = 0ull;
+  if (p >= np || *stop) return;
   double2 d = dg[2 * p], g = dg[2 * p + 1];
   const double2 sp = s[p];
   for (int j = j0; j < j1; ++j) {
@@ -719,26 +788,20 @@ __global__ void lz_poles_advance(int np, const double2* s, const double2* wgt, c
       d = make_double2(alpha[0] + sp.x, sp.y);
       g = make_double2(1.0, 0.0);
     } else {
+      // m = b / d; d <- a + s - m b, g <- -m g
       const double b = beta[j];
-      const double2 m = cdivd(make_double2(b, 0.0), d);
-      d = make_double2(alpha[j] + sp.x - m.x * b, sp.y - m.y * b);
-      g = make_double2(-(m.x * g.x - m.y * g.y), -(m.x * g.y + m.y * g.x));
+      const double2 id = crcp(d);
+      const double2 mg = cmuld(id, g);
+      d = make_double2(fma(-b * b, id.x, alpha[j] + sp.x), fma(-b * b, id.y, sp.y));
+      g = make_double2(-b * mg.x, -b * mg.y);
     }
   }
   dg[2 * p] = d;
   dg[2 * p + 1] = g;
-  const double2 y = cdivd(g, d), wp = wgt[p];
+  const double2 y = cmuld(g, crcp(d)), wp = wgt[p];
   wy[p] = make_double2(wp.x * y.x - wp.y * y.y, wp.x * y.y + wp.y * y.x);
 }
 
-// 1 / x for x >= 1e-30 and below 1e30: FP32 hardware reciprocal as the seed,
-// two Newton-Raphson steps r <- r (2 - x r) in FP64 (relative error ~1e-16;
-// the bound needs a few digits after the cancellation inside phi).
-__device__ __forceinline__ double lrcp(double x) {
-  double r = (double)__frcp_rn((float)x);
-  r = fma(r, fma(-x, r, 1.0), r);
-  return fma(r, fma(-x, r, 1.0), r);
-}
 
 constexpr int BT = 64;  // threads per block of the error-bound kernels
 
@@ -748,8 +811,9 @@ constexpr int BT = 64;  // threads per block of the error-bound kernels
 // beta[jk] * (max of the gate pass) <= rtol.
 __global__ void __launch_bounds__(BT) lz_bound_part(int np, int G, const double2* s, const double2* wy, double L,
                                                     double dl, int nslot, int stride, const double* beta, int jk,
-                                                    double rtol, const unsigned long long* gate, double2* part) {
-  if (gate && beta[jk] * __longlong_as_double((long long)*gate) > rtol) return;
+                                                    double rtol, const unsigned long long* gate, double2* part,
+                                                    const unsigned* stop) {
+  if (*stop || (gate && beta[jk] * __longlong_as_double((long long)*gate) > rtol)) return;
   __shared__ double2 ss[BT], sw[BT];
   const int slot = blockIdx.x * BT + threadIdx.x;
   const double lam = -L + (double)slot * stride * dl;
@@ -780,8 +844,9 @@ __global__ void __launch_bounds__(BT) lz_bound_part(int np, int G, const double2
 // symmetric (slot nslot - 1 - m sits at -l_m).
 __global__ void __launch_bounds__(BT) lz_bound_max(int groups, int nslot, const double2* part, int sym,
                                                    const double* beta, int jk, double rtol,
-                                                   const unsigned long long* gate, unsigned long long* out) {
-  if (gate && beta[jk] * __longlong_as_double((long long)*gate) > rtol) return;
+                                                   const unsigned long long* gate, unsigned long long* out,
+                                                   const unsigned* stop) {
+  if (*stop || (gate && beta[jk] * __longlong_as_double((long long)*gate) > rtol)) return;
   __shared__ double red[BT / 32];
   const int slot = blockIdx.x * BT + threadIdx.x;
   double v = 0.0;
@@ -815,6 +880,30 @@ __global__ void __launch_bounds__(BT) lz_bound_max(int groups, int nslot, const 
   }
 }
 
+// The host's convergence test of a checked chunk, repeated on the device so
+// that the chunk enqueued behind it (the host tests one chunk while the next
+// runs) stops at once: *stop = 1 once beta[jk] times the sampled maximum of
+// |phi| meets rtol (the fine maximum when the coarse one passed), or when
+// either is not finite (the host then reports the non-finite scalars).
+// Every later kernel of the first pass returns on *stop.  `report` receives
+// (b, coarse, fine) for the host's copy.
+__global__ void lz_gate(const double* beta, int jk, const unsigned long long* maxslots, double rtol,
+                        unsigned* stop, double* report) {
+  const double b = beta[jk];
+  const double coarse = __longlong_as_double((long long)maxslots[0]);
+  const double fine = __longlong_as_double((long long)maxslots[1]);
+  // what the host tests, in one block for one copy: b, coarse, fine
+  report[0] = b;
+  report[1] = coarse;
+  report[2] = fine;
+  if (!isfinite(b) || !isfinite(coarse) || !isfinite(fine)) {
+    *stop = 1u;
+    return;
+  }
+  const double bound = b * coarse > rtol ? b * coarse : b * fine;
+  if (bound <= rtol) *stop = 1u;
+}
+
 // Coefficients of V c for the poles [p0, p0 + P): per pole the UL sweep of
 // (T_k + s_p) (psi_{k-1} = a_{k-1} + s_p, psi_i = a_i + s_p - b_{i+1}^2 / psi_{i+1})
 // gives y = (T_k + s_p)^{-1} e_0 forward (y_0 = 1 / psi_0,
@@ -824,24 +913,25 @@ __global__ void lz_coeff_solve(int p0, int P, const double2* s, const double2* w
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= P) return;
   const double2 sp = s[p0 + q], wp = wgt[p0 + q];
-  double2 psi = make_double2(alpha[kk - 1] + sp.x, sp.y);
-  scratch[(size_t)(kk - 1) * P + q] = psi;
+  // the sweep keeps 1 / psi_i, so that the forward recurrence multiplies
+  double2 ip = crcp(make_double2(alpha[kk - 1] + sp.x, sp.y));
+  scratch[(size_t)(kk - 1) * P + q] = ip;
+#pragma unroll 4
   for (int i = kk - 2; i >= 0; --i) {
     const double b2 = beta[i + 1] * beta[i + 1];
-    const double2 r = cdivd(make_double2(b2, 0.0), psi);
-    psi = make_double2(alpha[i] + sp.x - r.x, sp.y - r.y);
-    scratch[(size_t)i * P + q] = psi;
+    ip = crcp(make_double2(fma(-b2, ip.x, alpha[i] + sp.x), fma(-b2, ip.y, sp.y)));
+    scratch[(size_t)i * P + q] = ip;
   }
-  // scale = -i ||f|| weight
+  // scale = -i ||f|| weight; y_0 = 1 / psi_0, y_i = -b_i y_{i-1} / psi_i
   const double fn = beta[0];
   const double2 sc = make_double2(fn * wp.y, -fn * wp.x);
-  double2 y = cdivd(make_double2(1.0, 0.0), scratch[q]);
-  scratch[q] = make_double2(sc.x * y.x - sc.y * y.y, sc.x * y.y + sc.y * y.x);
+  double2 y = ip;
+  scratch[q] = cmuld(sc, y);
+#pragma unroll 4
   for (int i = 1; i < kk; ++i) {
-    const double2 ps = scratch[(size_t)i * P + q];
-    const double2 t = cdivd(y, ps);
+    const double2 t = cmuld(y, scratch[(size_t)i * P + q]);
     y = make_double2(-beta[i] * t.x, -beta[i] * t.y);
-    scratch[(size_t)i * P + q] = make_double2(sc.x * y.x - sc.y * y.y, sc.x * y.y + sc.y * y.x);
+    scratch[(size_t)i * P + q] = cmuld(sc, y);
   }
 }
 
@@ -865,7 +955,10 @@ struct LLayout {
 // d = h |mu|, sample count 1 mod kCoarse (symmetric coarse subgrid); with
 // tau rho <= M h (pole-count rule) at most 8 M / |mu| + 2 + kCoarse samples.
 int nsamp_cap(int M) { return (int)std::ceil(8.0 * M / std::fabs(table_mu())) + 2 + kCoarse; }
-// poles per group of the partial sums (at most 128 groups)
+// poles per group of the partial sums (at most 128 groups).  The grouping
+// sets the rounding of phi, whose floor the bound reaches at tight
+// tolerances: groups of 16 instead of 64 raised that floor enough for a
+// 1e-13 bound to take four times the Lanczos steps.
 int bound_group(int np) { return std::max(64, (np + 127) / 128); }
 
 LLayout lz_layout(const KrylovSettings* k, int np_c, int M, size_t esize) {
@@ -1063,7 +1156,8 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   }
   e = cudaMemcpyAsync(d_sc, sc.data(), npc * sizeof(double2), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_wc, wc.data(), npc * sizeof(double2), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+  // the reduction counter and the stop flag of the first pass (lz_gate)
+  if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, 2 * sizeof(unsigned), s);
   mark(1);
   if (e == cudaSuccess) {
     if constexpr (DF)
@@ -1092,38 +1186,44 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   // of the order of Lh, so no chunk ending below Lh / 2 can meet the bound:
   // the bound is checked from there on (and at the step cap).
   const int first_check = (int)std::floor(0.5 * Lh);
+  // the device's copy of the convergence test (lz_gate), zeroed with the counter
+  unsigned* stop_w = counter + 1;
+  const unsigned* stop = stop_w;
+  // (b, coarse, fine) of a check for the host, beside the two maxima
+  double* report = reinterpret_cast<double*>(maxslots + 2);
   // par: pinned slot and event of a checked chunk (alternating over checked chunks)
   auto launch_chunk = [&](int par, int j0, int j1, bool check) -> cudaError_t {
     for (int j = j0; j < j1; ++j) {
       if constexpr (DF)
         launch_step_pdl(lz_dfstep<0>, grid, s, G_, k->Hdf, k->wdf, j, Wptr(j - 1), Wptr(j - 2), Wptr(j), alpha, beta,
                         invb, dfc, partials, counter, static_cast<float2*>(nullptr),
-                        static_cast<const float2*>(nullptr));
+                        static_cast<const float2*>(nullptr), stop);
       else if constexpr (REAL)
         lz_wstep<0><<<grid, THREADS, 0, s>>>(G_, j, Wptr(j - 1), Wptr(j - 2), Wptr(j), alpha, beta, invb, partials,
-                                             counter, nullptr, nullptr);
+                                             counter, nullptr, nullptr, stop);
       else
         lz_step<0, T><<<grid, THREADS, 0, s>>>(G_, j, wptr(j - 1), vptr(j - 1), vptr(j), wptr(j), alpha, beta,
-                                               invb, partials, counter, nullptr, nullptr);
+                                               invb, partials, counter, nullptr, nullptr, stop);
     }
-    lz_poles_advance<<<(npc + 127) / 128, 128, 0, s>>>(npc, d_sc, d_wc, alpha, beta, j0, j1, d_dg, d_wy);
+    lz_poles_advance<<<(npc + kPoleThreads - 1) / kPoleThreads, kPoleThreads, 0, s>>>(
+        npc, d_sc, d_wc, alpha, beta, j0, j1, d_dg, d_wy, stop, check ? maxslots : nullptr);
     if (!check) {
       launches += (j1 - j0) + 1;
       return cudaGetLastError();
     }
-    cudaError_t err = cudaMemsetAsync(maxslots, 0, 2 * sizeof(unsigned long long), s);
-    if (err != cudaSuccess) return err;
+    cudaError_t err;
     const int sym = REAL ? (((j1 - 1) & 1) ? -1 : 1) : 0;  // (-1)^(k-1), k = j1 steps
     const dim3 gc((nslot_c + BT - 1) / BT, groups), gf((nslot_f + BT - 1) / BT, groups);
     lz_bound_part<<<gc, BT, 0, s>>>(npc, G, d_sc, d_wy, Lh, dl, nslot_c, kCoarse, beta, j1, k->rtol, nullptr,
-                                    d_part);
-    lz_bound_max<<<gc.x, BT, 0, s>>>(groups, nslot_c, d_part, sym, beta, j1, k->rtol, nullptr, maxslots);
-    lz_bound_part<<<gf, BT, 0, s>>>(npc, G, d_sc, d_wy, Lh, dl, nslot_f, 1, beta, j1, k->rtol, maxslots, d_part);
-    lz_bound_max<<<gf.x, BT, 0, s>>>(groups, nslot_f, d_part, sym, beta, j1, k->rtol, maxslots, maxslots + 1);
-    launches += (j1 - j0) + 5;
-    err = cudaMemcpyAsync(pin + 3 * par, beta + j1, sizeof(double), cudaMemcpyDeviceToHost, s);
-    if (err == cudaSuccess)
-      err = cudaMemcpyAsync(pin + 3 * par + 1, maxslots, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+                                    d_part, stop);
+    lz_bound_max<<<gc.x, BT, 0, s>>>(groups, nslot_c, d_part, sym, beta, j1, k->rtol, nullptr, maxslots, stop);
+    lz_bound_part<<<gf, BT, 0, s>>>(npc, G, d_sc, d_wy, Lh, dl, nslot_f, 1, beta, j1, k->rtol, maxslots, d_part,
+                                    stop);
+    lz_bound_max<<<gf.x, BT, 0, s>>>(groups, nslot_f, d_part, sym, beta, j1, k->rtol, maxslots, maxslots + 1,
+                                     stop);
+    lz_gate<<<1, 1, 0, s>>>(beta, j1, maxslots, k->rtol, stop_w, report);
+    launches += (j1 - j0) + 6;
+    err = cudaMemcpyAsync(pin + 3 * par, report, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (err == cudaSuccess) err = cudaEventRecord(k->ev[par], s);
     if (err == cudaSuccess) err = cudaGetLastError();
     return err;
@@ -1167,8 +1267,9 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
     pending_j1 = j1;
   }
   if (e == cudaSuccess && !converged && !nonfinite && pending >= 0) e = evaluate(pending, pending_j1);
-  // the stream may still run one chunk past the converged step: harmless, the
-  // second pass uses steps < kk only
+  // the chunk enqueued behind the converged one finds the device's stop flag
+  // set by the same test and returns at once: the steps run are kk
+  if (converged) steps_run = kk;
   if (e != cudaSuccess) {
     set_last_error(cudaGetErrorString(e));
     return REXI_ECUDA;
@@ -1196,7 +1297,7 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
   const int P = (int)std::min<size_t>((size_t)npc, L.scratch_bytes / ((size_t)kk * sizeof(double2)));
   for (int p0 = 0; p0 < npc && e == cudaSuccess; p0 += P) {
     const int Pc = std::min(P, npc - p0);
-    lz_coeff_solve<<<(Pc + 127) / 128, 128, 0, s>>>(p0, Pc, d_sc, d_wc, alpha, beta, kk, scratch);
+    lz_coeff_solve<<<(Pc + kPoleThreads - 1) / kPoleThreads, kPoleThreads, 0, s>>>(p0, Pc, d_sc, d_wc, alpha, beta, kk, scratch);
     lz_coeff_sum<<<kk, THREADS, 0, s>>>(Pc, scratch, cvec, p0 == 0 ? 1 : 0);
     launches += 2;
     e = cudaGetLastError();
@@ -1222,13 +1323,13 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
     for (int j = nb; j < kk; ++j) {
       if constexpr (DF)
         launch_step_pdl(lz_dfstep<1>, grid, s, G_, k->Hdf, k->wdf, j, Wptr(j - 1), Wptr(j - 2), Wptr(j), alpha, beta,
-                        invb, dfc, partials, counter, acc, coef_df);
+                        invb, dfc, partials, counter, acc, coef_df, static_cast<const unsigned*>(nullptr));
       else if constexpr (REAL)
         lz_wstep<1><<<grid, THREADS, 0, s>>>(G_, j, Wptr(j - 1), Wptr(j - 2), Wptr(j), alpha, beta, invb, partials,
-                                             counter, acc, coef);
+                                             counter, acc, coef, nullptr);
       else
         lz_step<1, T><<<grid, THREADS, 0, s>>>(G_, j, wptr(j - 1), vptr(j - 1), vptr(j), wptr(j), alpha, beta,
-                                               invb, partials, counter, acc, cvec);
+                                               invb, partials, counter, acc, cvec, nullptr);
     }
     launches += kk - nb;
   }
@@ -1251,7 +1352,7 @@ rexi_status lanczos_impl(KrylovSettings* k, double h, int M, const void* in, voi
     info->krylov_iters = kk;
     info->krylov_unconverged = 0;
     info->krylov_max_rel_res = bound;
-    info->krylov_term_iters = steps_run;  // first-pass steps, with the chunk run past convergence
+    info->krylov_term_iters = steps_run;  // first-pass steps run
   }
   return REXI_OK;
 }
@@ -1278,17 +1379,19 @@ __global__ void lz_resolvent(int np, const double2* s, const double* alpha, cons
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
   const double2 sp = s[p];
-  double2 psi = make_double2(alpha[kk - 1] + sp.x, sp.y);
-  out[(size_t)(kk - 1) * np + p] = psi;
+  double2 ip = crcp(make_double2(alpha[kk - 1] + sp.x, sp.y));
+  out[(size_t)(kk - 1) * np + p] = ip;
+#pragma unroll 4
   for (int i = kk - 2; i >= 0; --i) {
-    const double2 r = cdivd(make_double2(beta[i + 1] * beta[i + 1], 0.0), psi);
-    psi = make_double2(alpha[i] + sp.x - r.x, sp.y - r.y);
-    out[(size_t)i * np + p] = psi;
+    const double b2 = beta[i + 1] * beta[i + 1];
+    ip = crcp(make_double2(fma(-b2, ip.x, alpha[i] + sp.x), fma(-b2, ip.y, sp.y)));
+    out[(size_t)i * np + p] = ip;
   }
-  double2 y = cdivd(make_double2(1.0, 0.0), out[p]);
+  double2 y = ip;
   out[p] = y;
+#pragma unroll 4
   for (int i = 1; i < kk; ++i) {
-    const double2 t = cdivd(y, out[(size_t)i * np + p]);
+    const double2 t = cmuld(y, out[(size_t)i * np + p]);
     y = make_double2(-beta[i] * t.x, -beta[i] * t.y);
     out[(size_t)i * np + p] = y;
   }
@@ -1584,6 +1687,12 @@ rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, int form, double h, int
     auto W = [&](int j) -> double* { return j < -1 ? nullptr : (j == -1 ? f0 : bas + (size_t)j * vstride); };
     auto Wf = [&](int j) -> float2* { return reinterpret_cast<float2*>(W(j)); };
     DfCoef* dfc = reinterpret_cast<DfCoef*>(base + L.dfc);
+    // this run's stop flag (lz_gate), cleared after the previous run's steps
+    unsigned* stop = counter + 1;
+    if (cudaMemsetAsync(stop, 0, sizeof(unsigned), s) != cudaSuccess) {
+      set_last_error("shared-Krylov depth gradient: clearing the stop flag failed");
+      return REXI_ECUDA;
+    }
     if (df)
       lz_init_df<<<grid, THREADS, 0, s>>>(G, src, adjoint, Wf(-1), beta, invb, dfc, partials, counter);
     else
@@ -1619,33 +1728,33 @@ rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, int form, double h, int
         if (df)
           launch_step_pdl(lz_dfstep<0>, grid, s, G, k->Hdf, k->wdf, j, Wf(j - 1), Wf(j - 2), Wf(j), alpha, beta,
                           invb, dfc, partials, counter, static_cast<float2*>(nullptr),
-                          static_cast<const float2*>(nullptr));
+                          static_cast<const float2*>(nullptr), static_cast<const unsigned*>(stop));
         else
           lz_wstep<0><<<grid, THREADS, 0, s>>>(G, j, W(j - 1), W(j - 2), W(j), alpha, beta, invb, partials, counter,
-                                               nullptr, nullptr);
+                                               nullptr, nullptr, stop);
       }
-      lz_poles_advance<<<(np + 127) / 128, 128, 0, s>>>(np, d_s, d_w, alpha, beta, j0, j1, D2(L.dg), D2(L.wy));
-      if (j1 < first_check && j1 < L.cap) {
+      const bool check = !(j1 < first_check && j1 < L.cap);
+      lz_poles_advance<<<(np + kPoleThreads - 1) / kPoleThreads, kPoleThreads, 0, s>>>(
+          np, d_s, d_w, alpha, beta, j0, j1, D2(L.dg), D2(L.wy), stop, check ? maxslots : nullptr);
+      if (!check) {
         launches += (j1 - j0) + 1;
         err = cudaGetLastError();
         continue;
       }
       const int par = nchecked++ & 1;
-      err = cudaMemsetAsync(maxslots, 0, 2 * sizeof(unsigned long long), s);
-      if (err != cudaSuccess) break;
       const int sym = ((j1 - 1) & 1) ? -1 : 1;
       const dim3 gc((nslot_c + BT - 1) / BT, groups), gf((nslot_f + BT - 1) / BT, groups);
       lz_bound_part<<<gc, BT, 0, s>>>(np, Gp, d_s, D2(L.wy), Lh, dl, nslot_c, kCoarse, beta, j1, k->rtol, nullptr,
-                                      D2(L.part));
-      lz_bound_max<<<gc.x, BT, 0, s>>>(groups, nslot_c, D2(L.part), sym, beta, j1, k->rtol, nullptr, maxslots);
+                                      D2(L.part), stop);
+      lz_bound_max<<<gc.x, BT, 0, s>>>(groups, nslot_c, D2(L.part), sym, beta, j1, k->rtol, nullptr, maxslots, stop);
       lz_bound_part<<<gf, BT, 0, s>>>(np, Gp, d_s, D2(L.wy), Lh, dl, nslot_f, 1, beta, j1, k->rtol, maxslots,
-                                      D2(L.part));
+                                      D2(L.part), stop);
       lz_bound_max<<<gf.x, BT, 0, s>>>(groups, nslot_f, D2(L.part), sym, beta, j1, k->rtol, maxslots,
-                                       maxslots + 1);
-      launches += (j1 - j0) + 5;
-      err = cudaMemcpyAsync(pin + 3 * par, beta + j1, sizeof(double), cudaMemcpyDeviceToHost, s);
-      if (err == cudaSuccess)
-        err = cudaMemcpyAsync(pin + 3 * par + 1, maxslots, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+                                       maxslots + 1, stop);
+      double* report = reinterpret_cast<double*>(maxslots + 2);  // (b, coarse, fine) for the host
+      lz_gate<<<1, 1, 0, s>>>(beta, j1, maxslots, k->rtol, stop, report);
+      launches += (j1 - j0) + 6;
+      err = cudaMemcpyAsync(pin + 3 * par, report, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
       if (err == cudaSuccess) err = cudaEventRecord(k->ev[par], s);
       if (err == cudaSuccess) err = cudaGetLastError();
       if (err != cudaSuccess) break;
@@ -1683,8 +1792,8 @@ rexi_status krylov_grad_depth_lanczos(KrylovSettings* k, int form, double h, int
                   D2(L.sB), D2(L.wB), &kB, &bB);
   mark(2);
   if (st == REXI_OK) {
-    lz_resolvent<<<(np + 127) / 128, 128, 0, s>>>(np, D2(L.sA), D(L.alA), D(L.beA), kA, D2(L.CA));
-    lz_resolvent<<<(np + 127) / 128, 128, 0, s>>>(np, D2(L.sB), D(L.alB), D(L.beB), kB, D2(L.DB));
+    lz_resolvent<<<(np + kPoleThreads - 1) / kPoleThreads, kPoleThreads, 0, s>>>(np, D2(L.sA), D(L.alA), D(L.beA), kA, D2(L.CA));
+    lz_resolvent<<<(np + kPoleThreads - 1) / kPoleThreads, kPoleThreads, 0, s>>>(np, D2(L.sB), D(L.alB), D(L.beB), kB, D2(L.DB));
     lz_bilinear<<<dim3((kA + 15) / 16, (kB + 15) / 16), 256, 0, s>>>(np, kA, kB, D2(L.CA), D2(L.DB), D2(L.wA),
                                                                      D(L.beA), D(L.ibA), D(L.beB), D(L.ibB), dt,
                                                                      D(L.R));

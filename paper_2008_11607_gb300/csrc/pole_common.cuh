@@ -454,9 +454,9 @@ __device__ __forceinline__ void df_term(const float4* ent, float X_hi, float X_l
   // y = x + h n with x = X_hi + X_lo + X_lo2: the grid-aligned high parts add
   // exactly, X_lo joins by an error-free FastTwoSum, the rest is far below it
   float y_h, y_l;
-  if (EXACT_HN) {
+  if (EXACT_HN) {  // hn_lo = hn_lo2 = 0 in such a table
     fast_two_sum(__fadd_rn(X_hi, e0.x), X_lo, y_h, y_l);
-    y_l = __fadd_rn(y_l, __fadd_rn(X_lo2, e2.y));
+    y_l = __fadd_rn(y_l, X_lo2);
   } else {
     float s_h, s_e;
     two_sum(X_lo, e2.y, s_h, s_e);  // |s_h| <= G <= |X_hi + hn_hi| unless that is 0
