@@ -63,7 +63,7 @@ PEAK_FP64_TFLOPS = 1.25
 # DRAM traffic per launch of the pole-sum kernel and of the combine pass from
 # ncu captures on the 2048^2 grid (the traffic does not depend on the term
 # count); None where no capture of the current kernel exists.
-NCU_POLE_TRAFFIC_BYTES = {"mixed": 284416 + 32000, "fp64": None}  # 2048^2, tau rho = 1000 (one-pass capture)
+NCU_POLE_TRAFFIC_BYTES = {"mixed": 283648 + 3840, "fp64": None}  # 2048^2, tau rho = 1000 (one-pass capture)
 NCU_COMBINE_TRAFFIC_BYTES = None
 # the forward double-float transform of real input at 2048^2 (fft_rows_r2c_kernel
 # + fft_cols_kernel, one launch each; --set full capture of the current
