@@ -304,9 +304,9 @@ rexi_status rexi_plan_create(rexi_plan_t* out, int32_t nx, int32_t ny, double Lx
     p->fx.tw = p->tw_x;
     p->fy.tw = p->tw_y;
     {  // double-float twiddles for the mixed form's transforms
-      std::vector<double2> fx4(nx), fy4(ny);
-      split_twiddles(twx.data(), nx, reinterpret_cast<float4*>(fx4.data()));
-      split_twiddles(twy.data(), ny, reinterpret_cast<float4*>(fy4.data()));
+      std::vector<double2> fx4(2 * nx), fy4(2 * ny);
+      df_twiddles(twx.data(), p->fx, reinterpret_cast<float4*>(fx4.data()));
+      df_twiddles(twy.data(), p->fy, reinterpret_cast<float4*>(fy4.data()));
       if (!upload_table(fx4, reinterpret_cast<double2**>(&p->twf_x), &st) ||
           !upload_table(fy4, reinterpret_cast<double2**>(&p->twf_y), &st)) {
         rexi_plan_destroy(p);
@@ -325,12 +325,12 @@ rexi_status rexi_plan_create(rexi_plan_t* out, int32_t nx, int32_t ny, double Lx
     }
     if (nx % 2 == 0 && fft_factor(nx / 2, &p->fxh)) {  // real-input transforms along x
       const int m = nx / 2;
-      std::vector<double2> twh(m), twh4(m);
+      std::vector<double2> twh(m), twh4(2 * m);
       for (int t = 0; t < m; ++t) {
         const double a = 2.0 * M_PI * (double)t / (double)m;
         twh[t] = make_double2(cos(a), -sin(a));
       }
-      split_twiddles(twh.data(), m, reinterpret_cast<float4*>(twh4.data()));
+      df_twiddles(twh.data(), p->fxh, reinterpret_cast<float4*>(twh4.data()));
       if (!upload_table(twh, &p->tw_xh, &st) || !upload_table(twh4, reinterpret_cast<double2**>(&p->twf_xh), &st)) {
         rexi_plan_destroy(p);
         return st;

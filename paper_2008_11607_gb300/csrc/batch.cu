@@ -446,15 +446,17 @@ rexi_status rexi_batch_create(rexi_batch_t* out, int32_t n, const int32_t* nx, c
       b->axis_tables[len] = {dtw, dhalf};
       cudaMemcpy(dtw, tw.data(), len * sizeof(double2), cudaMemcpyHostToDevice);
       cudaMemcpy(dhalf, half.data(), len * sizeof(double2), cudaMemcpyHostToDevice);
-      std::vector<float4> twf(len), hdf(len);
-      split_twiddles(tw.data(), len, twf.data());
+      FftPlan1D fl;
+      if (!fft_factor(len, &fl)) return false;
+      std::vector<float4> twf(2 * (size_t)len), hdf(len);
+      df_twiddles(tw.data(), fl, twf.data());
       split_twiddles(half.data(), len, hdf.data());
       float4 *dtwf = nullptr, *dhdf = nullptr;
-      if (cudaMalloc(&dtwf, len * sizeof(float4)) != cudaSuccess) return false;
+      if (cudaMalloc(&dtwf, 2 * (size_t)len * sizeof(float4)) != cudaSuccess) return false;
       b->axis_twf[len] = dtwf;
       if (cudaMalloc(&dhdf, len * sizeof(float4)) != cudaSuccess) return false;
       b->axis_halfdf[len] = dhdf;
-      cudaMemcpy(dtwf, twf.data(), len * sizeof(float4), cudaMemcpyHostToDevice);
+      cudaMemcpy(dtwf, twf.data(), 2 * (size_t)len * sizeof(float4), cudaMemcpyHostToDevice);
       cudaMemcpy(dhdf, hdf.data(), len * sizeof(float4), cudaMemcpyHostToDevice);
       return true;
     };

@@ -130,10 +130,13 @@ __device__ __forceinline__ void dft8(T* v) {
 }
 
 // One radix-R stage with register butterflies (R in {2, 4, 8}).
-// Element t of sequence b lives at b * sstride + t * estride.
+// Element t of sequence b lives at b * sstride + t * estride.  `tws`
+// (nullable): this stage's twiddles grouped by butterfly, tws[jm (R - 1) +
+// r - 1] = w^{r jm n / (Ns R)}, so that a butterfly's R - 1 twiddles are
+// adjacent (one or two cache lines instead of R - 1); else the full table tw.
 template <int SIGN, int R, typename T>
 __device__ __forceinline__ void stage_pow2(const T* src, T* dst, int n, int Ns, int nseq, int sstride, int estride,
-                                           bool seq_fastest, const T* tw) {
+                                           bool seq_fastest, const T* tw, const T* tws) {
   const int nb = n / R;
   const int total = nb * nseq;
   const int twstep = n / (Ns * R);
@@ -152,8 +155,13 @@ __device__ __forceinline__ void stage_pow2(const T* src, T* dst, int n, int Ns, 
     for (int r = 0; r < R; ++r) v[r] = s[(j + r * nb) * estride];
     const int jm = j % Ns;
     if (jm != 0) {
+      if (tws) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw_load<SIGN>(tw, r * jm * twstep));
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw_load<SIGN>(tws, jm * (R - 1) + r - 1));
+      } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw_load<SIGN>(tw, r * jm * twstep));
+      }
     }
     if (R == 2) dft2<SIGN>(v);
     if (R == 4) dft4<SIGN>(v);
@@ -199,24 +207,28 @@ __device__ __forceinline__ void stage_generic(const T* src, T* dst, int n, int R
   }
 }
 
-// Runs all stages; returns the buffer holding the result.
+// Runs all stages; returns the buffer holding the result.  Double-float
+// tables carry the per-stage grouping after the n entries of w (df_twiddles).
 template <int SIGN, typename T>
 __device__ T* run_stages(T* b0, T* b1, const StageList& st, int nseq, int sstride, int estride, bool seq_fastest,
                          const T* tw) {
+  constexpr bool STAGED = std::is_same<T, float4>::value;
   T* src = b0;
   T* dst = b1;
-  int Ns = 1;
+  int Ns = 1, off = st.n;
   for (int s = 0; s < st.nstages; ++s) {
     const int R = st.radix[s];
+    const T* tws = STAGED ? tw + off : nullptr;
     if (R == 8)
-      stage_pow2<SIGN, 8>(src, dst, st.n, Ns, nseq, sstride, estride, seq_fastest, tw);
+      stage_pow2<SIGN, 8>(src, dst, st.n, Ns, nseq, sstride, estride, seq_fastest, tw, tws);
     else if (R == 4)
-      stage_pow2<SIGN, 4>(src, dst, st.n, Ns, nseq, sstride, estride, seq_fastest, tw);
+      stage_pow2<SIGN, 4>(src, dst, st.n, Ns, nseq, sstride, estride, seq_fastest, tw, tws);
     else if (R == 2)
-      stage_pow2<SIGN, 2>(src, dst, st.n, Ns, nseq, sstride, estride, seq_fastest, tw);
+      stage_pow2<SIGN, 2>(src, dst, st.n, Ns, nseq, sstride, estride, seq_fastest, tw, tws);
     else
       stage_generic<SIGN>(src, dst, st.n, R, Ns, nseq, sstride, estride, seq_fastest, tw);
     __syncthreads();
+    off += Ns * (R - 1);
     Ns *= R;
     T* t = src;
     src = dst;
@@ -612,6 +624,25 @@ cudaError_t fft2d_df(const double2* in, double2* out, int nfields, const FftPlan
   if (!px.twf || !py.twf) return fft2d(in, out, nfields, px, py, sign, scale, zero_imag_in, real_out, s);
   if (sign < 0) return fft2d_impl<-1>(in, out, nfields, px, py, px.twf, py.twf, scale, zero_imag_in, real_out, s);
   return fft2d_impl<+1>(in, out, nfields, px, py, px.twf, py.twf, scale, zero_imag_in, real_out, s);
+}
+
+// Double-float FFT twiddles: out[0, n) = w[t] split into pairs, then for each
+// stage s (radix R, Ns the product of the earlier radices) the Ns (R - 1)
+// values w[r jm n / (Ns R)], jm < Ns, r = 1..R-1, in the order
+// [jm (R - 1) + r - 1] (run_stages); the stages' counts sum to n - 1, so out
+// holds 2n entries (the last one unused).
+void df_twiddles(const double2* tw, const FftPlan1D& p, float4* out) {
+  const int n = p.n;
+  split_twiddles(tw, n, out);
+  int off = n, Ns = 1;
+  for (int s = 0; s < p.nstages; ++s) {
+    const int R = p.radix[s], twstep = n / (Ns * R);
+    for (int jm = 0; jm < Ns; ++jm)
+      for (int r = 1; r < R; ++r) split_twiddles(tw + (size_t)r * jm * twstep, 1, out + off + jm * (R - 1) + r - 1);
+    off += Ns * (R - 1);
+    Ns *= R;
+  }
+  out[2 * n - 1] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 void split_twiddles(const double2* tw, int n, float4* out) {

@@ -59,7 +59,8 @@ struct FftPlan1D {
   int nstages = 0;
   int radix[kMaxStages] = {0};
   const double2* tw = nullptr;  // device table w[t] = exp(-2 pi i t / n), t < n
-  const float4* twf = nullptr;  // the same as double-float pairs (re_hi, re_lo, im_hi, im_lo), or null
+  const float4* twf = nullptr;  // the same as double-float pairs (re_hi, re_lo, im_hi, im_lo), then the
+                                // per-stage grouping of df_twiddles (2n entries), or null
 };
 bool fft_factor(int n, FftPlan1D* p);  // fills n, nstages, radix; false if unsupported
 // Forward (sign -1) or inverse (sign +1, scaled by `scale`) 2-D transform of
@@ -74,6 +75,8 @@ cudaError_t fft2d_df(const double2* in, double2* out, int nfields, const FftPlan
                      const FftPlan1D& py, int sign, double scale, int zero_imag_in, int real_out,
                      cudaStream_t s);
 void split_twiddles(const double2* tw, int n, float4* out);  // host: FP64 table -> double-float
+// host: the double-float twiddle table of a transform (2 p.n entries: w[t], then grouped per stage)
+void df_twiddles(const double2* tw, const FftPlan1D& p, float4* out);
 // Real input (nx = 2 m even): forward transform of the real parts of `in`
 // into the half spectrum, ny x (m + 1) complex128 per field (field stride
 // ny (m + 1)), through an m-point transform per row (pxh: plan of length m);
