@@ -66,9 +66,9 @@ PEAK_FP64_TFLOPS = 1.25
 NCU_POLE_TRAFFIC_BYTES = {"mixed": 283648 + 3840, "fp64": None}  # 2048^2, tau rho = 1000 (one-pass capture)
 NCU_COMBINE_TRAFFIC_BYTES = None
 # the forward double-float transform of real input at 2048^2 (fft_rows_r2c_kernel
-# + fft_cols_kernel, one launch each; --set full capture of the current
+# + fft_cols_kernel, one launch each; one-pass capture of the current
 # kernels): DRAM bytes read + written by the two launches
-NCU_FFT_FWD_TRAFFIC_BYTES = None  # no capture yet of the kernels with grouped twiddle tables
+NCU_FFT_FWD_TRAFFIC_BYTES = (201528832 + 66863616) + (100910080 + 42878720)
 
 
 def orbit_count(n):
