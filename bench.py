@@ -64,7 +64,9 @@ PEAK_FP64_TFLOPS = 1.25
 # ncu captures on the 2048^2 grid (the traffic does not depend on the term
 # count); None where no capture of the current kernel exists.
 NCU_POLE_TRAFFIC_BYTES = {"mixed": 283648 + 3840, "fp64": None}  # 2048^2, tau rho = 1000 (one-pass capture)
-NCU_COMBINE_TRAFFIC_BYTES = None
+# the combine pass of the mixed form at 2048^2 (pole_orbit_finalize_kernel +
+# pole_orbit_combine_df_kernel, one launch each, one-pass capture): DRAM bytes
+NCU_COMBINE_TRAFFIC_BYTES = (16884480 + 0) + (110867200 + 37490176)
 # the forward double-float transform of real input at 2048^2 (fft_rows_r2c_kernel
 # + fft_cols_kernel, one launch each; one-pass capture of the current
 # kernels): DRAM bytes read + written by the two launches
@@ -736,7 +738,8 @@ def run_ours(args):
     comb_kernel = "pole_orbit_combine_df_kernel" if args.form == "mixed" else "pole_orbit_combine_kernel"
     roofline_combine = {"kernel": "pole_orbit_finalize_kernel + " + comb_kernel, "bound": "hbm", "achieved": comb_gbs,
                         "peak": hbm_peak, "unit": "GB/s", "frac": comb_gbs / hbm_peak if comb_gbs else None,
-                        "traffic": NCU_COMBINE_TRAFFIC_BYTES, "algorithmic_bytes": comb_bytes}
+                        "traffic": NCU_COMBINE_TRAFFIC_BYTES if (D == 2048 and args.form == "mixed") else None,
+                        "algorithmic_bytes": comb_bytes}
 
     # end-to-end through the host-buffer C-ABI calls (pinned host memory):
     # every REXII step copies its input state in and its result out.  Headline:
