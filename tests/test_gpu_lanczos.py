@@ -149,6 +149,36 @@ def test_shared_kept_basis_is_bitwise_identical(form):
         assert torch.equal(o, outs[0])
 
 
+@pytest.mark.parametrize("form,real", [("fp64", True), ("mixed", True), ("fp64", False)])
+def test_shared_stop_flag_after_convergence(form, real):
+    """The host tests a chunk of Lanczos steps while the next chunk runs; the
+    device repeats the test and stops that next chunk at once.  A converged
+    step reports as run exactly the steps it converged at; its output agrees
+    to rounding with that of a plan whose step cap equals that count (there
+    the converged chunk is the last one and nothing is enqueued behind it;
+    the cap sizes the workspace, and with it how the coefficient sums group
+    the poles), and a second call on the same plan gives the same bits."""
+    torch = torch_cuda()
+    nx, ny = 40, 36
+    H = inputs.variable_depth(nx, ny, seed=6)
+    st = inputs.kminus3_field(nx, ny, seed=6) if real else inputs.complex_random_state(nx, ny, seed=6)
+    plan, _ = shared_plan(torch, nx, ny, H, rtol=1e-11, form=form)
+    dt = 120.0 / plan.rho
+    x = to_dev(torch, st)
+    out, info = plan.step(x, dt, real_input=real, want_info=True)
+    kk = int(info.krylov_iters)
+    assert int(info.krylov_term_iters) == kk
+    assert kk < 20000
+    capped, _ = shared_plan(torch, nx, ny, H, rtol=1e-11, max_iters=kk, form=form)
+    out2, info2 = capped.step(x, dt, real_input=real, want_info=True)
+    assert int(info2.krylov_iters) == kk
+    assert rel_l2(out.cpu().numpy(), out2.cpu().numpy()) < 1e-13
+    # a second call on the same plan starts with a cleared flag
+    out3, info3 = plan.step(x, dt, real_input=real, want_info=True)
+    assert int(info3.krylov_iters) == kk
+    assert torch.equal(out, out3)
+
+
 def test_shared_edges():
     torch = torch_cuda()
     from paper_2008_11607_gb300 import rexi
